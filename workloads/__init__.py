@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs for the AXB = C solvers.
+
+This module is shared by the CPU oracle tests, the GPU tests and the benchmark.
+It only draws random numbers and forms the problem data (C = A X* B plus
+optional noise); it holds none of the solver's arithmetic.
+
+Shapes follow the paper's workloads (Section 5 tables, Section 6 images) and
+the benchmark configurations:
+
+* ``gaussian``          -- i.i.d. N(0, s^2) A, B, X*, consistent C (Ex. 5.2 "randn" sets)
+* ``config_small``      -- A 200x100, B 80x150, X* 100x80, all N(0,1)
+* ``config_scale``      -- A = U diag(sigma) V^T (Haar U, V; sigma log-spaced 1 -> 1e-2),
+                           4000x1000 and 800x3000, optional rank-deficient variant
+* ``config_precision``  -- A 20000x2000, B 2000x20000 with N(0, 1/cols) entries
+* ``color_images`` / ``blur_systems`` -- piecewise-smooth synthetic RGB images, banded
+                           Toeplitz Gaussian blurs, C = A X B + noise per channel
+* ``duplicated``        -- [A;A] / [B,B] rank-deficient sets (Table 1 set 6, Table 7)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASE_SEED = 20240810
+
+
+def rng(tag: int) -> np.random.Generator:
+    return np.random.default_rng(BASE_SEED + int(tag))
+
+
+def gaussian(m, p, q, n, seed=0, a_scale=1.0, b_scale=1.0, x_scale=1.0, noise=0.0):
+    """A (m x p), B (q x n), X* (p x q) i.i.d. Gaussian; C = A X* B (+ noise)."""
+    g = rng(1000 + seed)
+    A = g.standard_normal((m, p)) * a_scale
+    B = g.standard_normal((q, n)) * b_scale
+    Xs = g.standard_normal((p, q)) * x_scale
+    C = A @ Xs @ B
+    if noise > 0:
+        C = C + g.standard_normal(C.shape) * noise
+    return A, B, C, Xs
+
+
+def config_small(seed=1):
+    """A 200x100, B 80x150 i.i.d. N(0,1), X* 100x80 N(0,1), C = A X* B."""
+    g = rng(seed)
+    A = g.standard_normal((200, 100))
+    B = g.standard_normal((80, 150))
+    Xs = g.standard_normal((100, 80))
+    return A, B, A @ Xs @ B, Xs
+
+
+def haar(g, rows, cols):
+    """rows x cols matrix with orthonormal columns, Haar distributed (QR of a
+    Gaussian with the signs of R's diagonal folded into Q)."""
+    Q, Rq = np.linalg.qr(g.standard_normal((rows, cols)))
+    return Q * np.sign(np.diag(Rq))[None, :]
+
+
+def lowrank_logspaced(g, rows, cols, rank, smax=1.0, smin=1e-2):
+    U = haar(g, rows, rank)
+    V = haar(g, cols, rank)
+    sig = np.logspace(np.log10(smax), np.log10(smin), rank)
+    return (U * sig[None, :]) @ V.T
+
+
+def config_scale(rank_deficient=False, seed=2, m=4000, p=1000, q=800, n=3000):
+    """A = U diag(sigma) V^T (m x p), B likewise (q x n), sigma log-spaced 1 -> 1e-2.
+    The rank-deficient variant uses rank 600 for A and 500 for B."""
+    g = rng(seed)
+    ra = 600 if rank_deficient else min(m, p)
+    rb = 500 if rank_deficient else min(q, n)
+    A = lowrank_logspaced(g, m, p, ra)
+    B = lowrank_logspaced(g, q, n, rb)
+    Xs = g.standard_normal((p, q))
+    return A, B, A @ Xs @ B, Xs
+
+
+def config_precision(m=20000, p=2000, q=2000, n=20000, noise=0.0, seed=3, dtype=np.float64):
+    """A m x p with N(0, 1/p) entries, B q x n with N(0, 1/n) entries, X* N(0,1),
+    C = A X* B (+ N(0, noise^2)).  The full size is 20000x2000 / 2000x20000; the
+    2000x200 / 200x2000 slice is the same recipe at smaller sizes."""
+    g = rng(seed)
+    A = (g.standard_normal((m, p), dtype=np.float64) / np.sqrt(p)).astype(dtype)
+    B = (g.standard_normal((q, n), dtype=np.float64) / np.sqrt(n)).astype(dtype)
+    Xs = g.standard_normal((p, q), dtype=np.float64).astype(dtype)
+    C = (A @ Xs) @ B
+    if noise > 0:
+        C = C + (g.standard_normal(C.shape) * noise).astype(dtype)
+    return A, B, C, Xs
+
+
+def duplicated(m, p, q, n, seed=4, how="rows"):
+    """Rank-deficient pairs by duplication: A = [A0; A0] (2m x p) and
+    B = [B0, B0] (q x 2n) (how='rows'), or A = [A0, A0], B = [B0; B0] (how='cols')."""
+    g = rng(5000 + seed)
+    A0 = g.standard_normal((m, p))
+    B0 = g.standard_normal((q, n))
+    if how == "rows":
+        A = np.vstack([A0, A0])
+        B = np.hstack([B0, B0])
+    else:
+        A = np.hstack([A0, A0])
+        B = np.vstack([B0, B0])
+    Xs = g.standard_normal((A.shape[1], B.shape[0]))
+    return A, B, A @ Xs @ B, Xs
+
+
+# ---------------------------------------------------------------------------
+# Colour images (Section 6 application) -- synthetic stand-ins
+# ---------------------------------------------------------------------------
+
+def _polygon_mask(h, w, cx, cy, radii, phase):
+    """Star-shaped polygon around (cx, cy): vertex k at angle phase + 2 pi k / K
+    and radius radii[k]; a pixel is inside when its radius is below the
+    piecewise-linear interpolation of the vertex radii at its angle."""
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    dx, dy = xx - cx, yy - cy
+    ang = (np.arctan2(dy, dx) - phase) % (2 * np.pi)
+    K = len(radii)
+    seg = ang / (2 * np.pi) * K
+    k0 = np.floor(seg).astype(np.int64) % K
+    k1 = (k0 + 1) % K
+    f = seg - np.floor(seg)
+    rad = radii[k0] * (1 - f) + radii[k1] * f
+    return np.hypot(dx, dy) <= rad
+
+
+def color_image(g, h, w):
+    """h x w x 3 image in [0,1]: a linear gradient background plus 3-8 random
+    star-shaped polygons of constant colour, each with its own gradient."""
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    img = np.empty((h, w, 3))
+    for c in range(3):
+        a, b, d = g.uniform(-0.5, 0.5, 3)
+        img[:, :, c] = 0.5 + a * (xx / w - 0.5) + b * (yy / h - 0.5) + 0.2 * d
+    for _ in range(int(g.integers(3, 9))):
+        K = int(g.integers(3, 9))
+        cx, cy = g.uniform(0, w), g.uniform(0, h)
+        base = g.uniform(0.08, 0.35) * min(h, w)
+        radii = base * g.uniform(0.5, 1.5, K)
+        mask = _polygon_mask(h, w, cx, cy, radii, g.uniform(0, 2 * np.pi))
+        col = g.uniform(0, 1, 3)
+        gx, gy = g.uniform(-0.3, 0.3, 2)
+        for c in range(3):
+            val = col[c] + gx * (xx - cx) / w + gy * (yy - cy) / h
+            img[:, :, c] = np.where(mask, val, img[:, :, c])
+    return np.clip(img, 0.0, 1.0)
+
+
+def gaussian_toeplitz(size, band, sigma):
+    """size x size symmetric banded Toeplitz blur: taps exp(-k^2 / (2 sigma^2))
+    for |k| <= band // 2, normalised to sum 1, zero boundary conditions."""
+    half = band // 2
+    k = np.arange(-half, half + 1)
+    taps = np.exp(-(k ** 2) / (2.0 * sigma ** 2))
+    taps /= taps.sum()
+    T = np.zeros((size, size))
+    for off, t in zip(k, taps):
+        idx = np.arange(max(0, -off), min(size, size - off))
+        T[idx, idx + off] = t
+    return T
+
+
+def blur_systems(n_images=64, seed=4, min_side=128, max_side=512, noise=1e-3,
+                 mild=False):
+    """Per image: sides h, w uniform in [min_side, max_side] (multiples of 16),
+    band b in {7, 9, ..., 15}, sigma_blur in [1.5, 3]; A (h x h) and B (w x w)
+    symmetric Toeplitz blurs; per channel C = A X B + N(0, noise^2).
+
+    Returns a list of dicts with keys A, B, C, X (clean channel), E (noise),
+    image index and channel.  ``mild`` replaces each blur T by (I + T) / 2
+    (a well-conditioned control system)."""
+    g = rng(seed)
+    systems = []
+    for im in range(n_images):
+        h = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
+        w = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
+        band = int(g.choice([7, 9, 11, 13, 15]))
+        sig = float(g.uniform(1.5, 3.0))
+        A = gaussian_toeplitz(h, band, sig)
+        B = gaussian_toeplitz(w, band, sig)
+        if mild:
+            A = 0.5 * (np.eye(h) + A)
+            B = 0.5 * (np.eye(w) + B)
+        img = color_image(g, h, w)
+        for c in range(3):
+            X = img[:, :, c]
+            E = g.standard_normal((h, w)) * noise
+            systems.append(dict(A=A, B=B, C=A @ X @ B + E, X=X, E=E, image=im, channel=c))
+    return systems
