@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark: ME-GRBK iterations per second on one GB300 (and N independent
+replicas under torchrun), with the HBM roofline of the persistent iteration
+kernel, the end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle as the baseline.
+
+Workload (default, "precision"): A 20000x2000 and B 2000x20000 with N(0, 1/cols)
+entries, X* N(0,1), C = A X* B; FP32 residual pass with the R refresh every 64
+iterations as split-BF16 tensor-core products ("chosen" form), next to the
+plain FP64 form (no refresh) on the same system.  One step = 64 iterations of
+the whole hot path (select, W/U, V, fused residual pass) plus one refresh of
+R = C - A X B and the stop check.  R (1.6 GB) is far larger than L2, so no
+flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the 2000x200 / 200x2000 slice of the same recipe, scaled to the full
+size by the ratio of per-iteration element work) and prints the same line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "ME-GRBK iters/s & time-to-RSE<=1e-6 (HBM GB/s vs peak), chosen vs plain form"
+UNIT = "iters/s"
+
+WORKLOADS = {
+    # name: (m, p, q, n, generator kwargs)
+    "precision": dict(m=20000, p=2000, q=2000, n=20000),
+    "precision_slice": dict(m=2000, p=200, q=200, n=2000),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
+    ap.add_argument("--iters-per-step", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gen_inputs(wl):
+    d = WORKLOADS[wl]
+    A, B, C, Xs = workloads.config_precision(d["m"], d["p"], d["q"], d["n"])
+    return A, B, C, Xs
+
+
+def iter_bytes(m, p, q, n, esz):
+    """Algorithmic bytes of one iteration: R read + written, B read twice
+    (w = R_i B^T and v = w B), A read once (u = A A_i^T), the vectors u, v, w
+    and the row norms (negligible but counted)."""
+    return 2 * m * n * esz + 2 * q * n * esz + m * p * esz + (m + n + q) * esz + 3 * m * 8
+
+
+def cpu_baseline_oracle(target_seconds=12.0):
+    """The FP64 oracle (single thread) on the 2000x200/200x2000 slice of the same
+    recipe: iterations per second, then scaled by the per-iteration element
+    work ratio to the full 20000x2000/2000x20000 size."""
+    import oracle
+    d = WORKLOADS["precision_slice"]
+    A, B, C, Xs = gen_inputs("precision_slice")
+    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
+    t0 = time.perf_counter()
+    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=0, mode=oracle.MODE_FACTORED, trace=False)
+    t_setup = time.perf_counter() - t0
+    n_it = 20
+    t0 = time.perf_counter()
+    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
+    per_it = max((time.perf_counter() - t0 - t_setup) / n_it, 1e-6)
+    n_it = max(20, int(target_seconds / per_it))
+    t0 = time.perf_counter()
+    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
+    el = time.perf_counter() - t0 - t_setup
+    slice_rate = n_it / el
+    full = WORKLOADS["precision"]
+    work = lambda w: w["m"] * w["n"] + w["m"] * w["p"] + 2 * w["q"] * w["n"] + w["p"] * w["q"]
+    scale = work(d) / work(full)
+    return {"value": slice_rate * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, single thread, {n_it} ME-GRBK iterations on the 2000x200/200x2000 slice "
+                      f"in {el:.1f} s ({slice_rate:.1f} iters/s), scaled by the per-iteration element work "
+                      f"ratio {scale:.4g} to 20000x2000/2000x20000"}
+
+
+def reference_arm(args):
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A, B, C, Xs = gen_inputs("precision_slice")
+    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
+    t0 = time.perf_counter()
+    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=0, mode=oracle.MODE_FACTORED, trace=False)
+    t_setup = time.perf_counter() - t0
+    n_it = 10
+    d, full = WORKLOADS["precision_slice"], WORKLOADS["precision"]
+    work = lambda w: w["m"] * w["n"] + w["m"] * w["p"] + 2 * w["q"] * w["n"] + w["p"] * w["q"]
+    scale = work(d) / work(full)
+    for _ in range(args.warmup):
+        oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, seed=s, mode=oracle.MODE_FACTORED, trace=False)
+        times.append(max(time.perf_counter() - t0 - t_setup, 1e-9))
+    tot = sum(times)
+    value = args.steps * n_it / tot * scale
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "precision: A 20000x2000, B 2000x20000 N(0,1/cols), "
+                                                        "C = A X* B", "sample": "2000x200/200x2000 slice"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_it} ME-GRBK iterations per step on the 2000x200/200x2000 slice, "
+                                       f"scaled by the per-iteration element work ratio {scale:.4g}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def native_arm(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2408_05444_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    T = args.iters_per_step
+    wl = args.workload
+    dm = WORKLOADS[wl]
+    m, p, q, n = dm["m"], dm["p"], dm["q"], dm["n"]
+
+    A, B, C, Xs = gen_inputs(wl)
+    Ah, Bh, Ch = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory() for x in (A, B, C))
+    Ad, Bd, Cd = (x.to(dev) for x in (Ah, Bh, Ch))
+    del A, B, C
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- chosen form: FP32 bulk + split-BF16 refresh every T ----
+    ctx = g.grbk_create(Ad, Bd, Cd, precision="f32", refresh_T=T, check_every=T, stream=stream)
+    Xd = torch.zeros(p, q, dtype=torch.float64, device=dev)
+    g.grbk_solve(ctx, "grbk", maxit=args.warmup * T, seed=1, X_out=Xd)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        st, res = g.grbk_solve(ctx, "grbk", maxit=args.steps * T, seed=2, X_out=Xd)
+        ev1.record(stream)
+        barrier()
+    el_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    iters = args.steps * T
+    value = world * iters / (el_ms / 1e3)
+    kern_ms = res["iter_kernel_ms"] / max(res["iter_kernel_launches"], 1)
+    bytes_per_launch = iter_bytes(m, p, q, n, 4) * T
+    hbm_peak, bf16_peak, peak_src = peaks()
+    achieved = bytes_per_launch / (kern_ms / 1e3) / 1e9
+
+    # ---------------- plain form: FP64, X0 = 0, no refresh ------------------
+    plain = None
+    if not args.no_plain:
+        ctx64 = g.grbk_create(Ad, Bd, Cd, precision="f64", check_every=T, stream=stream)
+        X64 = torch.zeros(p, q, dtype=torch.float64, device=dev)
+        g.grbk_solve(ctx64, "grbk", maxit=T, seed=1, X_out=X64)
+        barrier()
+        k64 = max(2, args.steps // 2)
+        ev0.record(stream)
+        st64, r64 = g.grbk_solve(ctx64, "grbk", maxit=k64 * T, seed=2, X_out=X64)
+        ev1.record(stream)
+        barrier()
+        ms64 = ev0.elapsed_time(ev1)
+        km64 = r64["iter_kernel_ms"] / max(r64["iter_kernel_launches"], 1)
+        plain = {"precision": "f64", "value": k64 * T / (ms64 / 1e3), "unit": UNIT,
+                 "kernel_GBs": iter_bytes(m, p, q, n, 8) * T / (km64 / 1e3) / 1e9,
+                 "note": "FP64 residual pass, X0 = 0, no refresh (R^0 = C)"}
+        g.grbk_destroy(ctx64)
+        del X64
+
+    # ---------------- end to end through the C ABI with host buffers --------
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.zeros(p, q, dtype=torch.float64).pin_memory()
+        k_e2e = min(args.steps, 3)
+        barrier()
+        t0 = time.perf_counter()
+        for s in range(k_e2e):
+            c2 = g.grbk_create(Ah, Bh, Ch, precision="f32", refresh_T=T, check_every=T, stream=stream)
+            g.grbk_solve(c2, "grbk", maxit=T, seed=s, X_out=Xh)
+            g.grbk_destroy(c2)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * k_e2e * T / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4 + Ch.numel() * 4),
+               "d2h_bytes_per_step": int(p * q * 8),
+               "note": "per step: grbk_create from pinned host A, B, C (FP32), 64 iterations with one "
+                       "refresh, X copied back to pinned host memory, grbk_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle()
+
+    # solution error reached by the timed run (context for the metric)
+    rse = float(torch.linalg.norm(Xd.cpu() - torch.from_numpy(Xs)) / np.linalg.norm(Xs))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"precision: A {m}x{p}, B {q}x{n} N(0,1/cols), X* N(0,1), C = A X* B; "
+                                   f"chosen form FP32 + split-BF16 refresh every {T}",
+                       "iters_per_step": T, "variant": "ME-GRBK", "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "iterate_kernel<float> (persistent, %d iterations per launch)" % T,
+                         "kernel_ms_per_launch": kern_ms, "peak_source": peak_src},
+            "plain": plain,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "rse_after_timed_run": rse,
+            "clocks": clk.summary(),
+            "gpu_launches": int(res["launches"]),
+        }
+        print(json.dumps(line), flush=True)
+    g.grbk_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        native_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * grbk.h -- C ABI of the GB300 (sm_103a) solver library for the matrix
+ * equation A X B = C by the greedy randomized block Kaczmarz family
+ * (Wang, Liu, Qu, arXiv 2408.05444).
+ *
+ *   A in R^{m x p}, B in R^{q x n}, C in R^{m x n}, X in R^{p x q}   (Eq. 1.1)
+ *
+ * Variants (one row index i_k per iteration, then one block update):
+ *   GRBK_GRBK   ME-GRBK,  Algorithm 3 (threshold zeta_k, theta fixed 1/2)
+ *   GRBK_RGRBK  ME-RGRBK, Algorithm 4 (threshold xi_k, relaxation theta in (0,1])
+ *   GRBK_MWRBK  ME-MWRBK, Algorithm 5 (largest ||R_i||^2 / ||A_i||^2; smallest index on ties)
+ *   GRBK_RBK    ME-RBK,   Algorithm 1 (row i with probability ||A_i||^2 / ||A||_F^2)
+ *   GRBK_BK     ME-BK,    Algorithm 2 (cyclic, i_k = k mod m)
+ * Every variant applies  X += (alpha/||A_i||^2) A_i^T (R_i B^T)  and keeps the
+ * residual R = C - A X B by the rank-1 update of Algorithm 3:
+ *   R -= (alpha/||A_i||^2) (A A_i^T) ((R_i B^T) B).
+ *
+ * Conventions for every entry point:
+ *   - All matrices are row-major; `ld` is the row stride in elements (>= cols).
+ *   - Rows are 0-based.  The random variants draw u_k in [0,1) from
+ *     Philox4x64-10 with key (seed, 0) and counter (k, system, 0, 0), first
+ *     output word, top 53 bits times 2^-53; i_k is the first admitted row (in
+ *     ascending order) whose running sum of ||R_i||^2 exceeds u_k times the
+ *     admitted total.
+ *   - Errors are reported by the returned grbk_status; no entry point aborts
+ *     the process.  A CUDA error leaves the context usable for destroy only.
+ *   - Work runs on opts.stream (a cudaStream_t; NULL = legacy default stream)
+ *     and every call returns after its work has finished.
+ *   - Not thread-safe per context; distinct contexts may be used concurrently.
+ */
+#ifndef GRBK_H
+#define GRBK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRBK_OK = 0,          /* success (converged, exact, or ran the requested iterations) */
+    GRBK_EINVAL = 1,      /* bad argument: shape mismatch, theta outside (0,1], alpha outside (0, 2/||B||_2^2), m == 0, ... */
+    GRBK_ENOMEM = 2,      /* device allocation failed */
+    GRBK_ECUDA = 3,       /* a CUDA runtime call or kernel failed */
+    GRBK_ENOTCONV = 4,    /* maxit reached before the tolerance; X_out still written */
+    GRBK_ETIMEOUT = 5,    /* a device-side barrier exceeded its spin budget; X_out not trusted */
+    GRBK_ENONFINITE = 6   /* NaN/Inf in the inputs or in the residual */
+} grbk_status;
+
+typedef enum { GRBK_GRBK = 0, GRBK_RGRBK = 1, GRBK_MWRBK = 2, GRBK_RBK = 3, GRBK_BK = 4 } grbk_variant;
+
+/* Arithmetic of the residual pass.  F64: everything FP64.  F32: A, B, C, R in
+ * FP32; row norms, their sums, the threshold, the pick and X kept in FP64;
+ * refresh of R as split-BF16 tensor-core products accumulated in FP32. */
+typedef enum { GRBK_F64 = 0, GRBK_F32 = 1 } grbk_precision;
+
+typedef enum { GRBK_DT_F64 = 0, GRBK_DT_F32 = 1 } grbk_dtype;
+
+/* Stopping rule, tested before each iteration.  RELRES: ||R||_F <= tol ||C||_F.
+ * RSE: ||X - X_ref||_F <= tol ||X_ref||_F, tested every `check_every`
+ * iterations (X is folded in at those points).  NONE: run maxit iterations. */
+typedef enum { GRBK_STOP_NONE = 0, GRBK_STOP_RELRES = 1, GRBK_STOP_RSE = 2 } grbk_stop;
+
+/* A matrix argument.  `ptr` is a host pointer (on_device = 0) or a device
+ * pointer (on_device = 1); the library never keeps it after the call returns. */
+typedef struct {
+    const void* ptr;
+    int64_t rows, cols, ld;
+    int32_t dtype;      /* grbk_dtype */
+    int32_t on_device;
+} grbk_mat;
+
+typedef struct {
+    int32_t precision;    /* grbk_precision */
+    int32_t refresh_T;    /* recompute R = C - A X B every refresh_T iterations; 0 = never */
+    double alpha;         /* step; <= 0 selects 1/||B||_2^2 (power iteration on B B^T) */
+    int32_t stop_kind;    /* grbk_stop */
+    int32_t split_terms;  /* F32 refresh: 2 (hi+lo) or 3 (hi+mid+lo) BF16 terms; 0 = 3 */
+    const grbk_mat* x_ref;/* reference solution for GRBK_STOP_RSE and result.rse; may be NULL */
+    int32_t* row_trace;   /* host buffer: selected row of iteration k, k < trace_len; may be NULL */
+    double* s_trace;      /* host buffer: ||R^k||_F^2 before iteration k, k < trace_len; may be NULL */
+    int64_t trace_len;
+    void* stream;         /* cudaStream_t */
+    int32_t grid_ctas;    /* persistent-kernel CTAs; 0 = chosen by the library */
+    int32_t check_every;  /* iterations per device chunk between host checks; 0 = refresh_T or 256 */
+} grbk_opts;
+
+typedef struct {
+    int64_t iters;        /* iterations performed */
+    double relres;        /* ||C - A X B||_F / ||C||_F of the kept residual at exit */
+    double rse;           /* ||X - X_ref||_F / ||X_ref||_F at exit (NaN without x_ref) */
+    double seconds;       /* wall time of the solve call */
+    double alpha;         /* step actually used */
+    double iter_kernel_ms;        /* device time of the persistent iteration kernel (CUDA events on the stream) */
+    int64_t iter_kernel_launches; /* its launches in this call */
+    int64_t launches;             /* all kernel launches made by this call */
+    int32_t status;       /* grbk_status of the call */
+} grbk_result;
+
+typedef struct grbk_ctx grbk_ctx;
+typedef struct grbk_batch grbk_batch;
+
+/* Fill `opts` with defaults (F64, no refresh, alpha = 1/||B||_2^2, STOP_NONE). */
+void grbk_default_opts(grbk_opts* opts);
+
+/*
+ * grbk_create -- set up one system A X B = C (Eq. 1.1).
+ * Copies A (m x p), B (q x n), C (m x n) into library-owned device memory in
+ * the precision of opts->precision; the caller may free its buffers at once.
+ * Computes ||A_i||^2, ||A||_F^2, ||C||_F^2 and alpha (Section 5 uses
+ * alpha = 1/||B||_2^2; Lemma 2.2 and Theorems 4.2-4.6 need 0 < alpha < 2/||B||_2^2).
+ * Errors: EINVAL (NULL pointers, shape mismatch, m == 0, explicit alpha not in
+ * (0, 2/||B||_2^2), non-finite input -> ENONFINITE), ENOMEM, ECUDA.
+ */
+grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk_mat* B, const grbk_mat* C,
+                        const grbk_opts* opts);
+
+/*
+ * grbk_solve -- run one of Algorithms 1-5 from X0 (NULL = zero matrix) for at
+ * most maxit iterations (Algorithm 3's loop "until convergence").
+ * theta: RGRBK relaxation in (0, 1] (Algorithm 4); ignored by other variants.
+ * tol: tolerance of opts->stop_kind.  seed: Philox key for RGRBK/GRBK/RBK.
+ * X_out: p x q, caller-owned, host or device, FP64 or FP32; written on OK and
+ * ENOTCONV.  res: may be NULL.
+ * The residual starts as R^0 = C - A X0 B; zero rows of A are never selected
+ * (an ME-BK step on such a row changes nothing).  ||R||_F = 0 stops with OK.
+ */
+grbk_status grbk_solve(grbk_ctx* ctx, int32_t variant, double theta, const grbk_mat* X0,
+                       double tol, int64_t maxit, uint64_t seed, grbk_mat* X_out,
+                       grbk_result* res);
+
+/*
+ * grbk_residual -- R_out = C - A X B for a caller X (p x q), with the same
+ * device path the solver uses to refresh its kept residual (FP64 SIMT GEMMs
+ * in F64 mode; split-BF16 tcgen05 GEMMs accumulated in FP32 in F32 mode).
+ * R_out is m x n, caller-owned, host or device, FP64 or FP32.
+ */
+grbk_status grbk_residual(grbk_ctx* ctx, const grbk_mat* X, grbk_mat* R_out);
+
+/* Copies of the kept state after a solve: residual R (m x n) and row norms
+ * ||R_i||^2 (m doubles, host or device per on_device). */
+grbk_status grbk_get_residual(grbk_ctx* ctx, grbk_mat* R_out);
+grbk_status grbk_get_rownorms(grbk_ctx* ctx, double* s_out, int32_t on_device);
+
+/* Problem sizes and the step in use. */
+grbk_status grbk_info(const grbk_ctx* ctx, int64_t dims[4], double* alpha);
+
+void grbk_destroy(grbk_ctx* ctx);
+
+/*
+ * Batched systems: nsys independent problems A_s X_s B_s = C_s of uneven sizes
+ * (the colour-image application of Section 6 solves one per channel), solved
+ * together in one persistent launch.  Arrays A, B, C have nsys entries.  The
+ * batch runs in FP32 (A, B, C, R) with FP64 row-norm sums, threshold and pick.
+ * System s draws its random numbers with counter (k, s, 0, 0).
+ * stop_kind: NONE, RELRES (per-system ||R_s||_F <= tol ||C_s||_F) or the
+ * discrepancy rule via grbk_batch_solve's `targets`.
+ */
+grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
+                              const grbk_mat* C, const grbk_opts* opts);
+
+/*
+ * grbk_batch_solve -- iterate every system until its own stop rule holds or
+ * maxit.  X0s: NULL (all zero) or nsys matrices.  targets: NULL, or nsys
+ * absolute residual targets ||R_s||_F <= targets[s] (discrepancy principle);
+ * when given they replace tol.  X_outs: nsys caller matrices (written).
+ * results: NULL or nsys entries.  Returns OK when every system stopped by its
+ * rule, ENOTCONV when some reached maxit.
+ */
+grbk_status grbk_batch_solve(grbk_batch* batch, int32_t variant, double theta, const grbk_mat* X0s,
+                             double tol, const double* targets, int64_t maxit, uint64_t seed,
+                             grbk_mat* X_outs, grbk_result* results);
+
+void grbk_batch_destroy(grbk_batch* batch);
+
+/* Human-readable name of a status code (static storage). */
+const char* grbk_strerror(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRBK_H */

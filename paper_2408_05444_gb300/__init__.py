@@ -1,0 +1,315 @@
+"""Python binding of the grbk C ABI (include/grbk.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Matrices may
+be numpy arrays (host), or torch tensors on the host or on a CUDA device; they
+must be row-major with unit column stride.  The library (``_build/libgrbk.so``)
+must have been built with ``paper_2408_05444_gb300.build.build()``; without it
+every call raises, there is no fallback path.
+
+Solver: greedy randomized block Kaczmarz for A X B = C (arXiv 2408.05444,
+Algorithms 1-5).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgrbk.so")
+
+GRBK_OK, GRBK_EINVAL, GRBK_ENOMEM, GRBK_ECUDA, GRBK_ENOTCONV, GRBK_ETIMEOUT, GRBK_ENONFINITE = range(7)
+GRBK_GRBK, GRBK_RGRBK, GRBK_MWRBK, GRBK_RBK, GRBK_BK = range(5)
+VARIANTS = {"grbk": GRBK_GRBK, "rgrbk": GRBK_RGRBK, "mwrbk": GRBK_MWRBK, "rbk": GRBK_RBK, "bk": GRBK_BK}
+GRBK_F64, GRBK_F32 = 0, 1
+GRBK_DT_F64, GRBK_DT_F32 = 0, 1
+GRBK_STOP_NONE, GRBK_STOP_RELRES, GRBK_STOP_RSE = 0, 1, 2
+
+
+class grbk_mat(ctypes.Structure):
+    _fields_ = [("ptr", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("dtype", ctypes.c_int32), ("on_device", ctypes.c_int32)]
+
+
+class grbk_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("refresh_T", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("stop_kind", ctypes.c_int32), ("split_terms", ctypes.c_int32),
+                ("x_ref", ctypes.POINTER(grbk_mat)), ("row_trace", ctypes.POINTER(ctypes.c_int32)),
+                ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
+                ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+class grbk_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("relres", ctypes.c_double), ("rse", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("alpha", ctypes.c_double), ("iter_kernel_ms", ctypes.c_double),
+                ("iter_kernel_launches", ctypes.c_int64), ("launches", ctypes.c_int64), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class GrbkError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"{where}: {grbk_strerror(status)} (status {status})")
+        self.status = status
+
+
+EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "grbk_get_residual",
+           "grbk_get_rownorms", "grbk_info", "grbk_destroy", "grbk_batch_create", "grbk_batch_solve",
+           "grbk_batch_destroy", "grbk_strerror"]
+
+_lib = None
+
+
+def lib():
+    """Load libgrbk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgrbk.so is not built ({LIB_PATH}); run paper_2408_05444_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        L.grbk_default_opts.argtypes = [P(grbk_opts)]
+        L.grbk_default_opts.restype = None
+        L.grbk_create.argtypes = [P(vp), P(grbk_mat), P(grbk_mat), P(grbk_mat), P(grbk_opts)]
+        L.grbk_create.restype = i32
+        L.grbk_solve.argtypes = [vp, i32, dbl, P(grbk_mat), dbl, i64, u64, P(grbk_mat), P(grbk_result)]
+        L.grbk_solve.restype = i32
+        L.grbk_residual.argtypes = [vp, P(grbk_mat), P(grbk_mat)]
+        L.grbk_residual.restype = i32
+        L.grbk_get_residual.argtypes = [vp, P(grbk_mat)]
+        L.grbk_get_residual.restype = i32
+        L.grbk_get_rownorms.argtypes = [vp, vp, i32]
+        L.grbk_get_rownorms.restype = i32
+        L.grbk_info.argtypes = [vp, P(i64), P(dbl)]
+        L.grbk_info.restype = i32
+        L.grbk_destroy.argtypes = [vp]
+        L.grbk_destroy.restype = None
+        L.grbk_batch_create.argtypes = [P(vp), i32, P(grbk_mat), P(grbk_mat), P(grbk_mat), P(grbk_opts)]
+        L.grbk_batch_create.restype = i32
+        L.grbk_batch_solve.argtypes = [vp, i32, dbl, P(grbk_mat), dbl, P(dbl), i64, u64, P(grbk_mat),
+                                       P(grbk_result)]
+        L.grbk_batch_solve.restype = i32
+        L.grbk_batch_destroy.argtypes = [vp]
+        L.grbk_batch_destroy.restype = None
+        L.grbk_strerror.argtypes = [i32]
+        L.grbk_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def mat(x) -> grbk_mat:
+    """Describe a 2-D numpy array or torch tensor (row-major, unit column stride)."""
+    if _is_torch(x):
+        import torch
+        assert x.dim() == 2 and (x.stride(1) == 1 or x.shape[1] <= 1), "need unit column stride"
+        assert x.dtype in (torch.float64, torch.float32)
+        return grbk_mat(x.data_ptr(), x.shape[0], x.shape[1], max(x.stride(0), x.shape[1]),
+                        GRBK_DT_F64 if x.dtype == torch.float64 else GRBK_DT_F32, 1 if x.is_cuda else 0)
+    a = x
+    assert isinstance(a, np.ndarray) and a.ndim == 2 and a.dtype in (np.float64, np.float32)
+    assert a.flags["C_CONTIGUOUS"] or a.strides[1] == a.itemsize, "need unit column stride"
+    return grbk_mat(a.ctypes.data, a.shape[0], a.shape[1], max(a.strides[0] // a.itemsize, a.shape[1]),
+                    GRBK_DT_F64 if a.dtype == np.float64 else GRBK_DT_F32, 0)
+
+
+def grbk_strerror(status: int) -> str:
+    return lib().grbk_strerror(int(status)).decode()
+
+
+def grbk_default_opts(**kw) -> grbk_opts:
+    o = grbk_opts()
+    lib().grbk_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class _Keep:
+    """Holds Python objects that back pointers inside an opts struct."""
+
+
+def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
+               x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None):
+    o = grbk_default_opts() if opts is None else opts
+    keep = _Keep()
+    if precision is not None:
+        o.precision = {"f64": GRBK_F64, "f32": GRBK_F32}.get(precision, precision)
+    if refresh_T is not None:
+        o.refresh_T = refresh_T
+    if alpha is not None:
+        o.alpha = alpha
+    if stop_kind is not None:
+        o.stop_kind = {"none": GRBK_STOP_NONE, "relres": GRBK_STOP_RELRES, "rse": GRBK_STOP_RSE}.get(stop_kind, stop_kind)
+    if split_terms is not None:
+        o.split_terms = split_terms
+    if grid_ctas is not None:
+        o.grid_ctas = grid_ctas
+    if check_every is not None:
+        o.check_every = check_every
+    if stream is not None:
+        o.stream = stream if isinstance(stream, int) else stream.cuda_stream
+    if x_ref is not None:
+        keep.xr_arr = x_ref
+        keep.xr = mat(x_ref)
+        o.x_ref = ctypes.pointer(keep.xr)
+    if trace_len > 0:
+        keep.rows = np.full(trace_len, -1, dtype=np.int32)
+        keep.S = np.zeros(trace_len, dtype=np.float64)
+        o.row_trace = keep.rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        o.s_trace = keep.S.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        o.trace_len = trace_len
+    return o, keep
+
+
+class Context:
+    """Owns a grbk_ctx* and the host buffers its opts point to."""
+
+    def __init__(self, handle, keep, opts):
+        self.handle = handle
+        self.keep = keep
+        self.opts = opts
+
+    @property
+    def row_trace(self):
+        return getattr(self.keep, "rows", None)
+
+    @property
+    def s_trace(self):
+        return getattr(self.keep, "S", None)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().grbk_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def grbk_create(A, B, C, opts=None, **kw) -> Context:
+    """grbk_create(A, B, C, opts) -- set up one system; keyword options fill
+    grbk_opts (precision='f64'|'f32', refresh_T, alpha, stop_kind, split_terms,
+    x_ref, trace_len, stream, grid_ctas, check_every)."""
+    o, keep = _make_opts(opts, **kw)
+    h = ctypes.c_void_p()
+    mA, mB, mC = mat(A), mat(B), mat(C)
+    st = lib().grbk_create(ctypes.byref(h), ctypes.byref(mA), ctypes.byref(mB), ctypes.byref(mC), ctypes.byref(o))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_create")
+    return Context(h.value, keep, o)
+
+
+def grbk_solve(ctx: Context, variant, theta=0.5, X0=None, tol=0.0, maxit=1000, seed=0, X_out=None):
+    """grbk_solve -> (status, result dict).  X_out (p x q) is written in place."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    res = grbk_result()
+    m0 = mat(X0) if X0 is not None else None
+    mo = mat(X_out) if X_out is not None else None
+    st = lib().grbk_solve(ctx.handle, v, float(theta), ctypes.byref(m0) if m0 is not None else None, float(tol),
+                          int(maxit), int(seed), ctypes.byref(mo) if mo is not None else None, ctypes.byref(res))
+    if st not in (GRBK_OK, GRBK_ENOTCONV):
+        raise GrbkError(st, "grbk_solve")
+    return st, res.as_dict()
+
+
+def grbk_residual(ctx: Context, X, R_out):
+    mx, mr = mat(X), mat(R_out)
+    st = lib().grbk_residual(ctx.handle, ctypes.byref(mx), ctypes.byref(mr))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_residual")
+
+
+def grbk_get_residual(ctx: Context, R_out):
+    mr = mat(R_out)
+    st = lib().grbk_get_residual(ctx.handle, ctypes.byref(mr))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_get_residual")
+
+
+def grbk_get_rownorms(ctx: Context, s_out):
+    if _is_torch(s_out):
+        st = lib().grbk_get_rownorms(ctx.handle, s_out.data_ptr(), 1 if s_out.is_cuda else 0)
+    else:
+        st = lib().grbk_get_rownorms(ctx.handle, s_out.ctypes.data, 0)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_get_rownorms")
+
+
+def grbk_info(ctx: Context):
+    dims = (ctypes.c_int64 * 4)()
+    al = ctypes.c_double()
+    st = lib().grbk_info(ctx.handle, dims, ctypes.byref(al))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_info")
+    return tuple(dims), al.value
+
+
+def grbk_destroy(ctx: Context):
+    if ctx.handle:
+        lib().grbk_destroy(ctx.handle)
+        ctx.handle = None
+
+
+class Batch:
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self.keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().grbk_batch_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _mat_array(xs):
+    arr = (grbk_mat * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = mat(x)
+    return arr
+
+
+def grbk_batch_create(As, Bs, Cs, opts=None, **kw) -> Batch:
+    o, keep = _make_opts(opts, **kw)
+    h = ctypes.c_void_p()
+    a, b, c = _mat_array(As), _mat_array(Bs), _mat_array(Cs)
+    st = lib().grbk_batch_create(ctypes.byref(h), len(As), a, b, c, ctypes.byref(o))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_batch_create")
+    return Batch(h.value, keep)
+
+
+def grbk_batch_solve(batch: Batch, variant, theta=0.5, X0s=None, tol=0.0, targets=None, maxit=1000, seed=0,
+                     X_outs=None):
+    """grbk_batch_solve -> (status, list of result dicts)."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    n = len(X_outs) if X_outs is not None else (len(X0s) if X0s is not None else None)
+    x0 = _mat_array(X0s) if X0s is not None else None
+    xo = _mat_array(X_outs) if X_outs is not None else None
+    tg = None
+    if targets is not None:
+        tgt = np.ascontiguousarray(targets, dtype=np.float64)
+        tg = tgt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        n = len(tgt)
+    if n is None:
+        raise ValueError("need X_outs, X0s or targets to size the results")
+    res = (grbk_result * n)()
+    st = lib().grbk_batch_solve(batch.handle, v, float(theta), x0, float(tol), tg, int(maxit), int(seed), xo, res)
+    if st not in (GRBK_OK, GRBK_ENOTCONV):
+        raise GrbkError(st, "grbk_batch_solve")
+    return st, [r.as_dict() for r in res]
+
+
+def grbk_batch_destroy(batch: Batch):
+    if batch.handle:
+        lib().grbk_batch_destroy(batch.handle)
+        batch.handle = None

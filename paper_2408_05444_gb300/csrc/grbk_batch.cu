@@ -1,0 +1,620 @@
+// grbk_batch.cu -- many independent systems A_s X_s B_s = C_s of uneven sizes
+// (one per colour channel of many images, Section 6) in ONE persistent launch.
+//
+// Each CTA takes systems from a queue ordered by decreasing work (longest
+// first) and runs the whole iteration of Algorithms 1-5 for its system with
+// CTA-local barriers only: no CTA ever waits on another.  R, A, B, C are FP32;
+// the row norms, their sums, the threshold and the pick are FP64; X (FP32) is
+// folded from the recorded rank-1 terms every `chunk` iterations.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "grbk_internal.cuh"
+
+namespace grbk {
+
+constexpr int kBB = 512;            // threads per CTA
+constexpr int kBW = kBB / 32;
+constexpr int kMaxSide = 1024;      // largest m, p, q, n of one system
+
+struct SysDesc {
+    int m, p, q, n;
+    int lda, ldb, ldr;              // row strides (elements)
+    int pad;
+    long long offA, offB, offR, offX, offRow, offHist, offHistW;
+    double F, alpha, stop_S;        // stop when S <= stop_S (< 0: never)
+};
+
+struct BatchParams {
+    int nsys;
+    const SysDesc* sys;
+    const int* order;               // queue order (system ids)
+    int* queue;                     // next queue slot
+    const float* A;
+    const float* B;
+    const float* C;
+    float* R;
+    float* X;
+    const double* a;                // ||A_i||^2 per row
+    const double* rbk_prefix;       // running sums of a_i per system
+    int* hist_rows;                 // [chunk] per system
+    float* hist_c;                  // [chunk] per system
+    float* hist_w;                  // [chunk x q] per system
+    long long* iters;               // out
+    double* S_out;                  // out
+    int* flag_out;                  // out: FLAG_*
+    int variant;
+    double theta;
+    uint64_t seed;
+    long long maxit;
+    int chunk;
+    int init_from_x;                // R = C - A X B before iterating (X holds X0)
+};
+
+__device__ __forceinline__ double block_sum_fixed(double v, double* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kBW; ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// X += sum_t c_t A_{i_t}^T w_t over the recorded terms (FP32)
+__device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh)
+{
+    if (nh <= 0) return;
+    const float* A = P.A + d.offA;
+    const int* hr = P.hist_rows + d.offHist;
+    const float* hc = P.hist_c + d.offHist;
+    const float* hw = P.hist_w + d.offHistW;
+    float* X = P.X + d.offX;
+    const int total = d.p * d.q;
+    __syncthreads();
+    for (int e = threadIdx.x; e < total; e += kBB) {
+        const int rr = e / d.q, j = e % d.q;
+        float acc = 0.f;
+        for (int t = 0; t < nh; ++t)
+            acc = fmaf(hc[t] * A[(long long)hr[t] * d.lda + rr], hw[(long long)t * d.q + j], acc);
+        X[(long long)rr * d.q + j] += acc;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
+{
+    __shared__ double s_s[kMaxSide];          // ||R_i||^2
+    __shared__ double s_r[kMaxSide];          // s_i / a_i
+    __shared__ float s_vec[kMaxSide];         // R_{i_k} row, then v
+    __shared__ float s_arow[kMaxSide];        // A_{i_k}
+    __shared__ float s_w[kMaxSide];           // w
+    __shared__ float s_u[kMaxSide];           // u
+    __shared__ double red[2 * kBW];
+    __shared__ long long redi[kBW];
+    __shared__ int s_sys, s_first, s_last, s_stop;
+    __shared__ double s_S, s_rmax;
+    __shared__ long long s_imax;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int slot = atomicAdd(P.queue, 1);
+            s_sys = (slot < P.nsys) ? P.order[slot] : -1;
+        }
+        __syncthreads();
+        const int sid = s_sys;
+        if (sid < 0) return;
+        const SysDesc d = P.sys[sid];
+        const float* A = P.A + d.offA;
+        const float* B = P.B + d.offB;
+        const float* C = P.C + d.offR;
+        float* R = P.R + d.offR;
+        const double* a = P.a + d.offRow;
+        const double* pref = P.rbk_prefix + d.offRow;
+        int* hrow = P.hist_rows + d.offHist;
+        float* hcf = P.hist_c + d.offHist;
+        float* hw = P.hist_w + d.offHistW;
+
+        // R^0 = C - A X^0 B (row by row) or R^0 = C
+        if (P.init_from_x) {
+            const float* X = P.X + d.offX;
+            for (int i = 0; i < d.m; ++i) {
+                for (int j = threadIdx.x; j < d.q; j += kBB) {  // t = A_i X
+                    float acc = 0.f;
+                    for (int c2 = 0; c2 < d.p; ++c2)
+                        acc = fmaf(A[(long long)i * d.lda + c2], X[(long long)c2 * d.q + j], acc);
+                    s_w[j] = acc;
+                }
+                __syncthreads();
+                for (int l = threadIdx.x; l < d.n; l += kBB) {  // R_i = C_i - t B
+                    float acc = 0.f;
+                    for (int j = 0; j < d.q; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
+                    R[(long long)i * d.ldr + l] = C[(long long)i * d.ldr + l] - acc;
+                }
+                __syncthreads();
+            }
+        } else {
+            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += kBB) R[e] = C[e];
+        }
+        __syncthreads();
+
+        // row norms of R^0: warp per row (Kahan FP32 lanes, FP64 across lanes)
+        for (int i = warp; i < d.m; i += kBW) {
+            float acc = 0.f, comp = 0.f;
+            for (int l = lane; l < d.n; l += 32) {
+                const float x = R[(long long)i * d.ldr + l];
+                const float y = fmaf(x, x, -comp);
+                const float t = acc + y;
+                comp = (t - acc) - y;
+                acc = t;
+            }
+            const double tot = warp_sum((double)acc - (double)comp);
+            if (lane == 0) {
+                s_s[i] = tot;
+                s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
+            }
+        }
+        __syncthreads();
+
+        long long k = 0;
+        int nh = 0, flag = FLAG_RUNNING;
+        for (;;) {
+            // ---- totals and stop test
+            {
+                double Sv = 0.0, br = -INFINITY;
+                long long bi = 0x7fffffffffffffffLL;
+                for (int i = threadIdx.x; i < d.m; i += kBB) {
+                    Sv += s_s[i];
+                    if (s_r[i] > br) { br = s_r[i]; bi = i; }
+                }
+                Sv = warp_sum(Sv);
+                warp_argmax(br, bi);
+                if (lane == 0) { red[warp] = Sv; red[kBW + warp] = br; redi[warp] = bi; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double S = 0.0, bb = -INFINITY;
+                    long long bbi = 0x7fffffffffffffffLL;
+                    for (int w2 = 0; w2 < kBW; ++w2) {
+                        S += red[w2];
+                        if (red[kBW + w2] > bb || (red[kBW + w2] == bb && redi[w2] < bbi)) {
+                            bb = red[kBW + w2];
+                            bbi = redi[w2];
+                        }
+                    }
+                    s_S = S; s_rmax = bb; s_imax = bbi;
+                    int stop = 0;
+                    if (!(S > 0.0)) stop = 2;
+                    else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
+                    else if (k >= P.maxit) stop = 4;
+                    s_stop = stop;
+                }
+                __syncthreads();
+            }
+            if (s_stop) {
+                if (s_stop == 1) flag = FLAG_TOL_MET;
+                if (s_stop == 2) flag = FLAG_EXACT;
+                break;
+            }
+            // ---- select i_k
+            int ik;
+            const int var = P.variant;
+            if (var == GRBK_GRBK || var == GRBK_RGRBK) {
+                const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
+                double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, d.F)));
+                if (t > s_rmax) t = s_rmax;
+                double SJ = 0.0;
+                for (int i = threadIdx.x; i < d.m; i += kBB) SJ += (s_r[i] >= t) ? s_s[i] : 0.0;
+                SJ = block_sum_fixed(SJ, red);
+                const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), SJ);
+                if (threadIdx.x == 0) { s_first = 0x7fffffff; s_last = -1; }
+                __syncthreads();
+                double base = 0.0;
+                for (int i0 = 0; i0 < d.m; i0 += kBB) {
+                    const int i = i0 + threadIdx.x;
+                    const bool adm = (i < d.m) && (s_r[i] >= t);
+                    const double val = adm ? s_s[i] : 0.0;
+                    const double incw = warp_inclusive_scan(val);
+                    if (lane == 31) red[warp] = incw;
+                    __syncthreads();
+                    double wbase = base;
+                    for (int w2 = 0; w2 < warp; ++w2) wbase += red[w2];
+                    if (adm && wbase + incw > target) atomicMin(&s_first, i);
+                    if (adm) atomicMax(&s_last, i);
+                    double tot = base;
+                    for (int w2 = 0; w2 < kBW; ++w2) tot += red[w2];
+                    __syncthreads();
+                    base = tot;
+                    if (s_first != 0x7fffffff) break;
+                }
+                ik = (s_first != 0x7fffffff) ? s_first : s_last;
+            } else if (var == GRBK_MWRBK) {
+                ik = (int)s_imax;
+            } else if (var == GRBK_RBK) {
+                if (threadIdx.x == 0) {
+                    const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), d.F);
+                    int lo = 0, hi = d.m;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pref[mid] > target) hi = mid; else lo = mid + 1;
+                    }
+                    if (lo >= d.m) {
+                        lo = d.m - 1;
+                        while (lo > 0 && !(a[lo] > 0.0)) --lo;
+                    }
+                    s_first = lo;
+                }
+                __syncthreads();
+                ik = s_first;
+            } else {
+                ik = (int)(k % d.m);
+            }
+            __syncthreads();
+            const double aik = a[ik];
+            const double ck = aik > 0.0 ? __ddiv_rn(d.alpha, aik) : 0.0;
+
+            // ---- w = R_ik B^T, u = A A_ik^T
+            for (int l = threadIdx.x; l < d.n; l += kBB) s_vec[l] = R[(long long)ik * d.ldr + l];
+            for (int c2 = threadIdx.x; c2 < d.p; c2 += kBB) s_arow[c2] = A[(long long)ik * d.lda + c2];
+            __syncthreads();
+            for (int task = warp; task < d.q + d.m; task += kBW) {
+                const bool isw = task < d.q;
+                const int row = isw ? task : task - d.q;
+                const float* x = isw ? (B + (long long)row * d.ldb) : (A + (long long)row * d.lda);
+                const float* y = isw ? s_vec : s_arow;
+                const int len = isw ? d.n : d.p;
+                float acc = 0.f;
+                for (int e = lane; e < len; e += 32) acc = fmaf(x[e], y[e], acc);
+                acc = warp_sum_f(acc);
+                if (lane == 0) {
+                    if (isw) s_w[row] = acc; else s_u[row] = acc;
+                }
+            }
+            __syncthreads();
+            // ---- record the term, v = w B
+            if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
+            for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
+            for (int l = threadIdx.x; l < d.n; l += kBB) {
+                float acc = 0.f;
+                for (int j = 0; j < d.q; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
+                s_vec[l] = acc;
+            }
+            __syncthreads();
+            // ---- R -= c u v fused with the new row norms
+            for (int i = warp; i < d.m; i += kBW) {
+                const float coef = (float)(ck * (double)s_u[i]);
+                float acc = 0.f, comp = 0.f;
+                float* Ri = R + (long long)i * d.ldr;
+                for (int l = lane; l < d.n; l += 32) {
+                    const float x = fmaf(-coef, s_vec[l], Ri[l]);
+                    Ri[l] = x;
+                    const float y = fmaf(x, x, -comp);
+                    const float tt = acc + y;
+                    comp = (tt - acc) - y;
+                    acc = tt;
+                }
+                const double tot = warp_sum((double)acc - (double)comp);
+                if (lane == 0) {
+                    s_s[i] = tot;
+                    s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
+                }
+            }
+            ++k;
+            ++nh;
+            if (nh == P.chunk) {
+                batch_fold(P, d, nh);
+                nh = 0;
+            }
+            __syncthreads();
+        }
+        batch_fold(P, d, nh);
+        if (threadIdx.x == 0) {
+            P.iters[sid] = k;
+            P.S_out[sid] = s_S;
+            P.flag_out[sid] = flag;
+        }
+    }
+}
+
+}  // namespace grbk
+
+// ============================================================================
+// host side
+// ============================================================================
+using namespace grbk;
+
+struct grbk_batch {
+    int nsys;
+    grbk_opts opts;
+    cudaStream_t stream;
+    std::vector<SysDesc> hsys;
+    std::vector<int> order;
+    std::vector<double> normC2;
+    SysDesc* dsys;
+    int* dorder;
+    int* dqueue;
+    float *A, *B, *C, *R, *X;
+    double *a, *pref;
+    int* hist_rows;
+    float *hist_c, *hist_w;
+    long long* iters;
+    double* S;
+    int* flags;
+    int chunk;
+    long long totA, totB, totR, totX, totRow, totHist, totHistW;
+};
+
+static void* dmalloc(size_t bytes)
+{
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes > 0 ? bytes : 16) != cudaSuccess) return nullptr;
+    return p;
+}
+
+extern "C" void grbk_batch_destroy(grbk_batch* b)
+{
+    if (!b) return;
+    void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->A, b->B, b->C, b->R, b->X, b->a, b->pref,
+                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+static grbk_status batch_load(const grbk_mat* M, float* dst, int64_t ldd, cudaStream_t st)
+{
+    const int64_t rows = M->rows, cols = M->cols;
+    const int es = M->dtype == GRBK_DT_F64 ? 8 : 4;
+    if (M->on_device) {
+        GRBK_CK(convert_matrix(dst, GRBK_DT_F32, ldd, M->ptr, M->dtype, M->ld, rows, cols, st));
+        return GRBK_OK;
+    }
+    void* tmp = dmalloc((size_t)rows * cols * es);
+    if (!tmp) return GRBK_ENOMEM;
+    cudaError_t e = cudaMemcpy2DAsync(tmp, cols * es, M->ptr, M->ld * es, cols * es, rows, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = convert_matrix(dst, GRBK_DT_F32, ldd, tmp, M->dtype, cols, rows, cols, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return GRBK_ECUDA;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
+                                         const grbk_mat* C, const grbk_opts* opts)
+{
+    if (!out || nsys <= 0 || !A || !B || !C) return GRBK_EINVAL;
+    *out = nullptr;
+    grbk_opts o;
+    if (opts) o = *opts; else grbk_default_opts(&o);
+    for (int s = 0; s < nsys; ++s) {
+        const int64_t m = A[s].rows, p = A[s].cols, q = B[s].rows, n = B[s].cols;
+        if (!A[s].ptr || !B[s].ptr || !C[s].ptr) return GRBK_EINVAL;
+        if (m <= 0 || p <= 0 || q <= 0 || n <= 0 || C[s].rows != m || C[s].cols != n) return GRBK_EINVAL;
+        if (m > kMaxSide || p > kMaxSide || q > kMaxSide || n > kMaxSide) return GRBK_EINVAL;
+        if (A[s].ld < p || B[s].ld < n || C[s].ld < n) return GRBK_EINVAL;
+    }
+    grbk_batch* b = new grbk_batch();
+    b->nsys = nsys;
+    b->opts = o;
+    b->stream = (cudaStream_t)o.stream;
+    b->chunk = o.check_every > 0 ? o.check_every : 64;
+    b->hsys.resize(nsys);
+    long long oA = 0, oB = 0, oR = 0, oX = 0, oRow = 0, oH = 0, oHW = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SysDesc& d = b->hsys[s];
+        memset(&d, 0, sizeof(d));
+        d.m = (int)A[s].rows; d.p = (int)A[s].cols; d.q = (int)B[s].rows; d.n = (int)B[s].cols;
+        d.lda = (int)round_up(d.p, 4); d.ldb = (int)round_up(d.n, 4); d.ldr = d.ldb;
+        d.offA = oA; d.offB = oB; d.offR = oR; d.offX = oX; d.offRow = oRow; d.offHist = oH; d.offHistW = oHW;
+        oA += (long long)d.m * d.lda; oB += (long long)d.q * d.ldb; oR += (long long)d.m * d.ldr;
+        oX += (long long)d.p * d.q; oRow += d.m; oH += b->chunk; oHW += (long long)b->chunk * d.q;
+    }
+    b->totA = oA; b->totB = oB; b->totR = oR; b->totX = oX; b->totRow = oRow; b->totHist = oH; b->totHistW = oHW;
+    b->A = (float*)dmalloc(oA * 4); b->B = (float*)dmalloc(oB * 4); b->C = (float*)dmalloc(oR * 4);
+    b->R = (float*)dmalloc(oR * 4); b->X = (float*)dmalloc(oX * 4);
+    b->a = (double*)dmalloc(oRow * 8); b->pref = (double*)dmalloc(oRow * 8);
+    b->hist_rows = (int*)dmalloc(oH * 4); b->hist_c = (float*)dmalloc(oH * 4); b->hist_w = (float*)dmalloc(oHW * 4);
+    b->dsys = (SysDesc*)dmalloc(sizeof(SysDesc) * nsys); b->dorder = (int*)dmalloc(4 * nsys);
+    b->dqueue = (int*)dmalloc(4); b->iters = (long long*)dmalloc(8 * nsys); b->S = (double*)dmalloc(8 * nsys);
+    b->flags = (int*)dmalloc(4 * nsys);
+    if (!b->A || !b->B || !b->C || !b->R || !b->X || !b->a || !b->pref || !b->hist_rows || !b->hist_c ||
+        !b->hist_w || !b->dsys || !b->dorder || !b->dqueue || !b->iters || !b->S || !b->flags) {
+        grbk_batch_destroy(b);
+        return GRBK_ENOMEM;
+    }
+    cudaStream_t st = b->stream;
+    cudaMemsetAsync(b->A, 0, oA * 4, st);
+    cudaMemsetAsync(b->B, 0, oB * 4, st);
+    cudaMemsetAsync(b->C, 0, oR * 4, st);
+    b->normC2.resize(nsys);
+    std::vector<double> ha, hp;
+    for (int s = 0; s < nsys; ++s) {
+        SysDesc& d = b->hsys[s];
+        grbk_status e;
+        if ((e = batch_load(&A[s], b->A + d.offA, d.lda, st)) != GRBK_OK ||
+            (e = batch_load(&B[s], b->B + d.offB, d.ldb, st)) != GRBK_OK ||
+            (e = batch_load(&C[s], b->C + d.offR, d.ldr, st)) != GRBK_OK) {
+            grbk_batch_destroy(b);
+            return e;
+        }
+    }
+    // host-side set-up scalars from the FP32 copies
+    std::vector<float> hA(oA), hB(oB), hC(oR);
+    if (cudaMemcpyAsync(hA.data(), b->A, oA * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hB.data(), b->B, oB * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hC.data(), b->C, oR * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        grbk_batch_destroy(b);
+        return GRBK_ECUDA;
+    }
+    ha.resize(oRow);
+    hp.resize(oRow);
+    for (int s = 0; s < nsys; ++s) {
+        SysDesc& d = b->hsys[s];
+        double F = 0.0;
+        for (int i = 0; i < d.m; ++i) {
+            double acc = 0.0;
+            for (int c2 = 0; c2 < d.p; ++c2) {
+                const double x = hA[d.offA + (long long)i * d.lda + c2];
+                acc += x * x;
+            }
+            ha[d.offRow + i] = acc;
+            F += acc;
+            hp[d.offRow + i] = F;
+        }
+        if (!(F > 0.0) || !std::isfinite(F)) { grbk_batch_destroy(b); return F > 0.0 ? GRBK_ENONFINITE : GRBK_EINVAL; }
+        d.F = F;
+        double c2s = 0.0;
+        for (int i = 0; i < d.m; ++i)
+            for (int l = 0; l < d.n; ++l) {
+                const double x = hC[d.offR + (long long)i * d.ldr + l];
+                c2s += x * x;
+            }
+        if (!std::isfinite(c2s)) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
+        b->normC2[s] = c2s;
+        // ||B||_2^2 by power iteration on B B^T (host, FP64)
+        std::vector<double> x(d.q, 1.0 / sqrt((double)d.q)), t(d.n), y(d.q);
+        double lam = 0.0;
+        for (int it = 0; it < 200; ++it) {
+            for (int l = 0; l < d.n; ++l) t[l] = 0.0;
+            for (int j = 0; j < d.q; ++j)
+                for (int l = 0; l < d.n; ++l) t[l] += (double)hB[d.offB + (long long)j * d.ldb + l] * x[j];
+            double yy = 0.0, xy = 0.0;
+            for (int j = 0; j < d.q; ++j) {
+                double acc = 0.0;
+                for (int l = 0; l < d.n; ++l) acc += (double)hB[d.offB + (long long)j * d.ldb + l] * t[l];
+                y[j] = acc;
+                yy += acc * acc;
+                xy += x[j] * acc;
+            }
+            lam = xy;
+            const double nrm = sqrt(yy);
+            if (!(nrm > 0.0)) break;
+            for (int j = 0; j < d.q; ++j) x[j] = y[j] / nrm;
+        }
+        if (!(lam > 0.0)) { grbk_batch_destroy(b); return GRBK_EINVAL; }
+        if (o.alpha > 0.0) {
+            if (!(o.alpha * lam < 2.0 * (1.0 + 1e-9))) { grbk_batch_destroy(b); return GRBK_EINVAL; }
+            d.alpha = o.alpha;
+        } else {
+            d.alpha = 1.0 / lam;
+        }
+        d.stop_S = -1.0;
+    }
+    // longest-processing-time order: largest R first
+    b->order.resize(nsys);
+    for (int s = 0; s < nsys; ++s) b->order[s] = s;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        return (long long)b->hsys[x].m * b->hsys[x].n > (long long)b->hsys[y].m * b->hsys[y].n;
+    });
+    if (cudaMemcpyAsync(b->a, ha.data(), oRow * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->pref, hp.data(), oRow * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->dorder, b->order.data(), 4 * nsys, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        grbk_batch_destroy(b);
+        return GRBK_ECUDA;
+    }
+    *out = b;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double theta, const grbk_mat* X0s,
+                                        double tol, const double* targets, int64_t maxit, uint64_t seed,
+                                        grbk_mat* X_outs, grbk_result* results)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!b) return GRBK_EINVAL;
+    if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
+    if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
+    if (maxit < 0) return GRBK_EINVAL;
+    cudaStream_t st = b->stream;
+    for (int s = 0; s < b->nsys; ++s) {
+        SysDesc& d = b->hsys[s];
+        if (X0s && (X0s[s].rows != d.p || X0s[s].cols != d.q || !X0s[s].ptr)) return GRBK_EINVAL;
+        if (X_outs && (X_outs[s].rows != d.p || X_outs[s].cols != d.q || !X_outs[s].ptr)) return GRBK_EINVAL;
+        if (targets) d.stop_S = targets[s] * targets[s];
+        else if (b->opts.stop_kind == GRBK_STOP_RELRES) d.stop_S = tol * tol * b->normC2[s];
+        else d.stop_S = -1.0;
+    }
+    GRBK_CK(cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st));
+    if (X0s) {
+        for (int s = 0; s < b->nsys; ++s) {
+            const SysDesc& d = b->hsys[s];
+            grbk_status e = batch_load(&X0s[s], b->X + d.offX, d.q, st);
+            if (e != GRBK_OK) return e;
+        }
+    } else {
+        GRBK_CK(cudaMemsetAsync(b->X, 0, b->totX * 4, st));
+    }
+    GRBK_CK(cudaMemsetAsync(b->dqueue, 0, 4, st));
+    BatchParams P;
+    memset(&P, 0, sizeof(P));
+    P.nsys = b->nsys; P.sys = b->dsys; P.order = b->dorder; P.queue = b->dqueue;
+    P.A = b->A; P.B = b->B; P.C = b->C; P.R = b->R; P.X = b->X; P.a = b->a; P.rbk_prefix = b->pref;
+    P.hist_rows = b->hist_rows; P.hist_c = b->hist_c; P.hist_w = b->hist_w;
+    P.iters = b->iters; P.S_out = b->S; P.flag_out = b->flags;
+    P.variant = variant; P.theta = theta; P.seed = seed; P.maxit = maxit; P.chunk = b->chunk;
+    P.init_from_x = X0s != nullptr;
+    int dev = 0, nsm = 0, per_sm = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBB, 0));
+    int grid = nsm * (per_sm > 0 ? per_sm : 1);
+    if (b->opts.grid_ctas > 0) grid = b->opts.grid_ctas;
+    if (grid > b->nsys) grid = b->nsys;
+    batch_kernel<<<grid, kBB, 0, st>>>(P);
+    GRBK_CK(cudaGetLastError());
+    std::vector<long long> it(b->nsys);
+    std::vector<double> S(b->nsys);
+    std::vector<int> fl(b->nsys);
+    GRBK_CK(cudaMemcpyAsync(it.data(), b->iters, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(S.data(), b->S, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(fl.data(), b->flags, 4 * b->nsys, cudaMemcpyDeviceToHost, st));
+    if (X_outs) {
+        for (int s = 0; s < b->nsys; ++s) {
+            const SysDesc& d = b->hsys[s];
+            grbk_mat& M = X_outs[s];
+            const int es = M.dtype == GRBK_DT_F64 ? 8 : 4;
+            if (M.on_device) {
+                GRBK_CK(convert_matrix((void*)M.ptr, M.dtype, M.ld, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st));
+            } else {
+                void* tmp = dmalloc((size_t)d.p * d.q * es);
+                if (!tmp) return GRBK_ENOMEM;
+                cudaError_t e = convert_matrix(tmp, M.dtype, d.q, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st);
+                if (e == cudaSuccess)
+                    e = cudaMemcpy2DAsync((void*)M.ptr, M.ld * es, tmp, d.q * es, d.q * es, d.p, cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                cudaFree(tmp);
+                if (e != cudaSuccess) return GRBK_ECUDA;
+            }
+        }
+    }
+    GRBK_CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    grbk_status overall = GRBK_OK;
+    for (int s = 0; s < b->nsys; ++s) {
+        const bool stopped_by_rule = fl[s] != FLAG_RUNNING;
+        grbk_status ss = GRBK_OK;
+        if (b->hsys[s].stop_S >= 0.0 && !stopped_by_rule) ss = GRBK_ENOTCONV;
+        if (!std::isfinite(S[s])) ss = GRBK_ENONFINITE;
+        if (ss != GRBK_OK && overall == GRBK_OK) overall = ss;
+        if (results) {
+            results[s].iters = it[s];
+            results[s].relres = b->normC2[s] > 0 ? sqrt(S[s] / b->normC2[s]) : 0.0;
+            results[s].rse = NAN;
+            results[s].seconds = secs;
+            results[s].alpha = b->hsys[s].alpha;
+            results[s].status = ss;
+        }
+    }
+    return overall;
+}

@@ -1,0 +1,196 @@
+// grbk_internal.cuh -- internal declarations shared by the library's translation
+// units: device helpers (bounded grid barrier, Philox4x64-10, warp reductions),
+// the context layout and the internal launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "grbk.h"
+
+namespace grbk {
+
+// ----------------------------------------------------------------------------
+// error plumbing
+// ----------------------------------------------------------------------------
+#define GRBK_CK(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) {                                   \
+            grbk::set_last_cuda_error(e_, #call, __FILE__, __LINE__); \
+            return GRBK_ECUDA;                                     \
+        }                                                          \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// ----------------------------------------------------------------------------
+// device-side status (one per context / batch)
+// ----------------------------------------------------------------------------
+enum : int { FLAG_RUNNING = 0, FLAG_TOL_MET = 1, FLAG_EXACT = 2 };
+
+struct DevState {
+    int status;          // grbk_status raised on the device (0 = none)
+    int flag;            // FLAG_*
+    long long k;         // iteration index reached by the last chunk
+    double S;            // ||R||_F^2 at iteration k
+    int timeout_site;    // which barrier gave up (diagnostics)
+    int pad;
+};
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Spin budget of one barrier wait, in SM clock cycles (about 2 s at 2 GHz).
+// A legitimate wait lasts at most one phase of one iteration.
+constexpr long long kBarrierBudget = 4000000000LL;
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+
+// Grid-wide barrier for a co-resident (cooperative) grid.  Every wait is
+// bounded: on expiry the CTA records GRBK_ETIMEOUT and the barrier returns
+// false, as it also does when any CTA has recorded an error; callers then
+// leave the kernel.  s_ok must be a __shared__ int.
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int site, int& s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int nb = gridDim.x;
+        const unsigned int g = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == nb - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, g + 1u);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&bar->gen) == g) {
+                if (clock64() - t0 > kBarrierBudget) {
+                    if (atomicCAS(&st->status, 0, (int)GRBK_ETIMEOUT) == 0) st->timeout_site = site;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (ld_volatile_int(&st->status) == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ----------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): key (seed, 0), counter
+// (k, sys, 0, 0); u = top 53 bits of the first output word times 2^-53.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t k, uint64_t sys)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = k, x1 = sys, x2 = 0, x3 = 0, k0 = seed, k1 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;
+        const uint64_t hi1 = __umul64hi(M1, x2), lo1 = M1 * x2;
+        const uint64_t y0 = hi1 ^ x1 ^ k0;
+        const uint64_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    return (double)(x0 >> 11) * 0x1.0p-53;
+}
+
+// ----------------------------------------------------------------------------
+// warp helpers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// argmax of (val, idx) pairs; ties go to the smaller index.
+__device__ __forceinline__ void warp_argmax(double& v, long long& i)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ov > v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+}
+
+// inclusive scan across the warp (fixed order)
+__device__ __forceinline__ double warp_inclusive_scan(double v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// ----------------------------------------------------------------------------
+// internal launchers implemented in other translation units
+// ----------------------------------------------------------------------------
+
+// Cout = beta * Cin + alpha * A * B (row-major; M x K times K x N), SIMT.
+template <typename T>
+cudaError_t gemm_simt(int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda,
+                      const T* B, int64_t ldb, double beta, const T* Cin, int64_t ldcin, T* Cout,
+                      int64_t ldc, cudaStream_t st);
+
+// dst(rows x cols, ldd) of type Td <- src(rows x cols, lds) of type Ts, device to device.
+cudaError_t convert_matrix(void* dst, int dtd, int64_t ldd, const void* src, int dts, int64_t lds,
+                           int64_t rows, int64_t cols, cudaStream_t st);
+
+// Split-BF16 tensor-core refresh engine (tcgen05 + TMA), FP32 mode.
+struct SplitGemm;
+grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, int64_t n,
+                             const float* A, int64_t lda, const float* B, int64_t ldb, int terms,
+                             cudaStream_t st);
+// R = C - A X B with X (p x q FP64 row-major, ldx); C and R are m x n (ld ldr).
+grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const float* C,
+                               float* R, int64_t ldr, cudaStream_t st);
+void splitgemm_destroy(SplitGemm* g);
+// kernel launches made by one splitgemm_residual call
+int splitgemm_launches(const SplitGemm* g);
+
+}  // namespace grbk

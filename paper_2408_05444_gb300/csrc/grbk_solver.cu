@@ -1,0 +1,1294 @@
+// grbk_solver.cu -- single-system solver: set-up kernels, the persistent
+// grid-synchronised iteration kernel and the host driver behind grbk_create /
+// grbk_solve / grbk_residual / grbk_destroy.
+//
+// One iteration k (Algorithms 1-5 with the residual recursion of Algorithm 3):
+//   select   S = sum_i s_i, r_max, threshold, admitted set, Philox pick i_k
+//   W/U      w = R_{i_k} B^T (q values), u = A A_{i_k}^T (m values)
+//   V        v = w B (n values)
+//   F        R -= (alpha/a_{i_k}) u v  fused with the new s_i = ||R_i||^2,
+//            r_i = s_i / a_i and per-CTA partial sums / maxima
+// separated by bounded grid barriers.  X is not touched inside the loop: the
+// pairs (i_k, c_k, w_k) are recorded and folded into X once per chunk as a
+// small GEMM (the sum of the same rank-1 terms, re-associated).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "grbk_internal.cuh"
+
+namespace grbk {
+
+static thread_local char g_err[512];
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line)
+{
+    snprintf(g_err, sizeof(g_err), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    if (getenv("GRBK_VERBOSE")) fprintf(stderr, "grbk: %s\n", g_err);
+}
+
+constexpr int kBlock = 512;        // threads per CTA of the persistent kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kUnroll = 8;         // independent vector loads in flight per lane
+constexpr int kPartsCap = 2048;    // per-CTA (row, chunk) partial slots in shared memory
+
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; static constexpr int N = 4; };
+template <> struct VecOf<double> { using V = double2; static constexpr int N = 2; };
+
+__device__ __forceinline__ float4 ldcg_v(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg_v(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg_v(float4* p, float4 v) { __stcg(p, v); }
+__device__ __forceinline__ void stcg_v(double2* p, double2 v) { __stcg(p, v); }
+
+// ----------------------------------------------------------------------------
+// kernel parameters
+// ----------------------------------------------------------------------------
+template <typename T>
+struct IterParams {
+    int64_t m, p, q, n;
+    int64_t lda, ldb, ldr;      // row strides (elements) of A, B and R/C (padded)
+    const T* A;
+    const T* B;
+    T* R;
+    const double* a;            // ||A_i||^2
+    const double* rbk_prefix;   // running sums of a_i (ME-RBK inverse CDF)
+    double* s;                  // ||R_i||^2
+    double* r;                  // s_i / a_i  (-inf for zero rows of A)
+    T* u;                       // A A_{i_k}^T
+    T* v;                       // w B, ldr entries (padding stays 0)
+    T* w;                       // R_{i_k} B^T
+    double* part_S;             // per-CTA partial sums of s_i
+    double* part_best_r;        // per-CTA max of r_i
+    long long* part_best_i;     //   and its row
+    double* part_SJ;            // per-CTA admitted sums
+    int* hist_rows;             // per chunk: i_k
+    double* hist_c;             //            alpha / a_{i_k}
+    double* hist_w;             //            w (q doubles per iteration)
+    int* trace_rows;            // whole solve: i_k (device copy of the host trace)
+    double* trace_S;
+    long long trace_len;
+    GridBarrier* bar;
+    DevState* st;
+    double F, alpha, theta, stop_S;   // stop when S <= stop_S (RELRES), < 0 disables
+    int variant;
+    uint64_t seed, sys;
+    long long k0;
+    int nit;
+    int smem_v;                 // v / R_{i_k} staged in shared memory
+    int smem_arow;              // A_{i_k} staged in shared memory
+};
+
+// balanced contiguous row range of CTA c among G
+__device__ __forceinline__ void cta_rows(int64_t m, int c, int G, int64_t& r0, int64_t& r1)
+{
+    r0 = (m * (int64_t)c) / G;
+    r1 = (m * (int64_t)(c + 1)) / G;
+}
+
+// ----------------------------------------------------------------------------
+// Fused residual pass over rows [r0, r1): R_i -= coef_i v (if UPDATE), then
+// s_i = ||R_i||^2 (FP64 sum of per-lane partials; FP32 lanes use Kahan
+// compensation), r_i = s_i / a_i, and the CTA's partial sum / argmax.
+// ----------------------------------------------------------------------------
+template <typename T, bool UPDATE>
+__device__ void fused_pass(const IterParams<T>& P, double ck, const T* vsrc, int64_t r0, int64_t r1,
+                           double* sm_parts, double* sm_red, long long* sm_redi)
+{
+    using V = typename VecOf<T>::V;
+    constexpr int VN = VecOf<T>::N;
+    constexpr int CHV = 32 * kUnroll * 2;       // vectors per (row, chunk) unit
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nvec_row = P.ldr / VN;
+    const int nch = (int)((nvec_row + CHV - 1) / CHV);
+    int64_t rows_per_batch = kPartsCap / nch;
+    if (rows_per_batch < 1) rows_per_batch = 1;
+    if (rows_per_batch > kBlock) rows_per_batch = kBlock;
+
+    double cta_S = 0.0, cta_best = -INFINITY;
+    long long cta_bi = 0x7fffffffffffffffLL;
+
+    for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
+        const int64_t b1 = min(r1, b0 + rows_per_batch);
+        const int64_t units = (b1 - b0) * nch;
+        for (int64_t unit = warp; unit < units; unit += kWarps) {
+            const int64_t row = b0 + unit / nch;
+            const int ch = (int)(unit % nch);
+            const int64_t e0 = (int64_t)ch * CHV;
+            const int64_t e1 = min(nvec_row, e0 + CHV);
+            V* Rrow = reinterpret_cast<V*>(P.R + row * P.ldr);
+            const V* vrow = reinterpret_cast<const V*>(vsrc);
+            T coef = (T)0;
+            if (UPDATE) coef = (T)(ck * (double)__ldcg(P.u + row));
+            double acc_d = 0.0;
+            float acc_f = 0.f, comp_f = 0.f;
+            for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
+                V rv[kUnroll], vv[kUnroll];
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t e = base + uu * 32 + lane;
+                    if (e < e1) {
+                        rv[uu] = ldcg_v(Rrow + e);
+                        if (UPDATE) vv[uu] = P.smem_v ? vrow[e] : ldcg_v(vrow + e);
+                    }
+                }
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t e = base + uu * 32 + lane;
+                    if (e < e1) {
+                        T* x = reinterpret_cast<T*>(&rv[uu]);
+                        const T* y = reinterpret_cast<const T*>(&vv[uu]);
+#pragma unroll
+                        for (int c = 0; c < VN; ++c) {
+                            if (UPDATE) x[c] = fma(-coef, y[c], x[c]);
+                            if constexpr (sizeof(T) == 8) {
+                                acc_d = fma((double)x[c], (double)x[c], acc_d);
+                            } else {
+                                const float yk = fmaf((float)x[c], (float)x[c], -comp_f);
+                                const float tk = acc_f + yk;
+                                comp_f = (tk - acc_f) - yk;
+                                acc_f = tk;
+                            }
+                        }
+                        if (UPDATE) stcg_v(Rrow + e, rv[uu]);
+                    }
+                }
+            }
+            double tot = (sizeof(T) == 8) ? acc_d : ((double)acc_f - (double)comp_f);
+            tot = warp_sum(tot);
+            if (lane == 0) sm_parts[unit] = tot;
+        }
+        __syncthreads();
+        // finalise the rows of this batch: one thread per row
+        double my_S = 0.0, my_best = -INFINITY;
+        long long my_bi = 0x7fffffffffffffffLL;
+        for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
+            double sv = 0.0;
+            for (int c = 0; c < nch; ++c) sv += sm_parts[rr * nch + c];
+            const int64_t row = b0 + rr;
+            const double ai = __ldg(P.a + row);
+            const double ri = (ai > 0.0) ? __ddiv_rn(sv, ai) : -INFINITY;
+            __stcg(P.s + row, sv);
+            __stcg(P.r + row, ri);
+            my_S += sv;
+            if (ri > my_best) { my_best = ri; my_bi = row; }
+        }
+        // block reduction, fixed order
+        my_S = warp_sum(my_S);
+        warp_argmax(my_best, my_bi);
+        if (lane == 0) { sm_red[warp] = my_S; sm_red[kWarps + warp] = my_best; sm_redi[warp] = my_bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double bs = 0.0, bb = -INFINITY;
+            long long bi = 0x7fffffffffffffffLL;
+            for (int w2 = 0; w2 < kWarps; ++w2) {
+                bs += sm_red[w2];
+                const double cand = sm_red[kWarps + w2];
+                if (cand > bb || (cand == bb && sm_redi[w2] < bi)) { bb = cand; bi = sm_redi[w2]; }
+            }
+            cta_S += bs;
+            if (bb > cta_best || (bb == cta_best && bi < cta_bi)) { cta_best = bb; cta_bi = bi; }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __stcg(P.part_S + blockIdx.x, cta_S);
+        __stcg(P.part_best_r + blockIdx.x, cta_best);
+        __stcg(P.part_best_i + blockIdx.x, cta_bi);
+    }
+}
+
+// Row norms of the current R (no update), same partition and partials as the
+// persistent kernel.  Launched with the solve's grid size.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) rownorms_kernel(IterParams<T> P)
+{
+    __shared__ double sm_parts[kPartsCap];
+    __shared__ double sm_red[2 * kWarps];
+    __shared__ long long sm_redi[kWarps];
+    int64_t r0, r1;
+    cta_rows(P.m, blockIdx.x, gridDim.x, r0, r1);
+    IterParams<T> Q = P;
+    Q.smem_v = 0;
+    fused_pass<T, false>(Q, 0.0, nullptr, r0, r1, sm_parts, sm_red, sm_redi);
+}
+
+// ----------------------------------------------------------------------------
+// the persistent iteration kernel
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ double sm_parts[kPartsCap];
+    __shared__ double sm_red[2 * kWarps];
+    __shared__ long long sm_redi[kWarps];
+    __shared__ int s_ok;
+    __shared__ double s_S, s_rmax, s_t, s_ck;
+    __shared__ long long s_imax, s_ik;
+    __shared__ int s_stop;
+
+    T* sv = reinterpret_cast<T*>(dsm);                               // ldr: R_{i_k}, then v
+    T* sa = sv + (P.smem_v ? P.ldr : 0);                              // lda: A_{i_k}
+    T* sw = sa + (P.smem_arow ? P.lda : 0);                           // q: w
+
+    const int G = gridDim.x, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t r0, r1;
+    cta_rows(P.m, c, G, r0, r1);
+    using V = typename VecOf<T>::V;
+    constexpr int VN = VecOf<T>::N;
+
+    for (int it = 0; it <= P.nit; ++it) {
+        const long long k = P.k0 + it;
+        // ---------------- select: totals from the per-CTA partials ----------
+        if (warp == 0) {
+            double S = 0.0, br = -INFINITY;
+            long long bi = 0x7fffffffffffffffLL;
+            for (int cc = lane; cc < G; cc += 32) {
+                S += __ldcg(P.part_S + cc);
+                const double rr = __ldcg(P.part_best_r + cc);
+                const long long ii = __ldcg(P.part_best_i + cc);
+                if (rr > br || (rr == br && ii < bi)) { br = rr; bi = ii; }
+            }
+            S = warp_sum(S);
+            warp_argmax(br, bi);
+            if (lane == 0) {
+                s_S = S; s_rmax = br; s_imax = bi;
+                int stop = 0;
+                if (!(S > 0.0)) stop = (S == 0.0) ? 2 : 3;      // 3: NaN
+                else if (P.stop_S >= 0.0 && S <= P.stop_S) stop = 1;
+                else if (it == P.nit) stop = 4;
+                s_stop = stop;
+                if (c == 0) {
+                    if (stop == 0 && k < P.trace_len) P.trace_S[k] = S;
+                    if (stop != 0) {
+                        P.st->k = k;
+                        P.st->S = S;
+                        if (stop == 1) P.st->flag = FLAG_TOL_MET;
+                        if (stop == 2) P.st->flag = FLAG_EXACT;
+                        if (stop == 3) atomicCAS(&P.st->status, 0, (int)GRBK_ENONFINITE);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+
+        // ---------------- select: the row -----------------------------------
+        long long ik = -1;
+        const int var = P.variant;
+        if (var == GRBK_GRBK || var == GRBK_RGRBK) {
+            const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
+            double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, P.F)));
+            if (t > s_rmax) t = s_rmax;
+            // admitted sum of this CTA's rows
+            if (warp == 0) {
+                double sj = 0.0;
+                for (int64_t i = r0 + lane; i < r1; i += 32) {
+                    const double ri = __ldcg(P.r + i);
+                    if (ri >= t) sj += __ldcg(P.s + i);
+                }
+                sj = warp_sum(sj);
+                if (lane == 0) __stcg(P.part_SJ + c, sj);
+            }
+            if (!grid_sync(P.bar, P.st, 1, s_ok)) return;
+            if (warp == 0) {
+                double SJ = 0.0;
+                for (int cc = lane; cc < G; cc += 32) SJ += __ldcg(P.part_SJ + cc);
+                SJ = warp_sum(SJ);
+                const double u = philox_uniform(P.seed, (uint64_t)k, P.sys);
+                const double target = __dmul_rn(u, SJ);
+                // owning CTA: first with inclusive prefix > target
+                double base = 0.0;
+                int cstar = -1;
+                double excl = 0.0;
+                for (int cb = 0; cb < G && cstar < 0; cb += 32) {
+                    const int cc = cb + lane;
+                    const double val = (cc < G) ? __ldcg(P.part_SJ + cc) : 0.0;
+                    const double inc = base + warp_inclusive_scan(val);
+                    const unsigned hit = __ballot_sync(0xffffffffu, (cc < G) && (inc > target) && val > 0.0);
+                    if (hit) {
+                        const int l = __ffs(hit) - 1;
+                        cstar = cb + l;
+                        excl = __shfl_sync(0xffffffffu, inc - val, l);
+                    }
+                    base = __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (cstar < 0) {  // rounding left the target uncovered: last CTA with admitted rows
+                    for (int cc = G - 1; cc >= 0; --cc)
+                        if (__ldcg(P.part_SJ + cc) > 0.0) { cstar = cc; break; }
+                    excl = -INFINITY;  // forces the last admitted row of cstar
+                }
+                int64_t q0 = 0, q1 = 0;
+                if (cstar >= 0) cta_rows(P.m, cstar, G, q0, q1);
+                long long pick = -1, last = -1;
+                double run = excl;
+                for (int64_t ib = q0; ib < q1 && pick < 0; ib += 32) {
+                    const int64_t i = ib + lane;
+                    double val = 0.0;
+                    bool adm = false;
+                    if (i < q1) {
+                        const double ri = __ldcg(P.r + i);
+                        adm = (ri >= t);
+                        if (adm) val = __ldcg(P.s + i);
+                    }
+                    const double inc = run + warp_inclusive_scan(val);
+                    const unsigned am = __ballot_sync(0xffffffffu, adm);
+                    if (am) last = ib + (31 - __clz(am));
+                    const unsigned hit = __ballot_sync(0xffffffffu, adm && (inc > target));
+                    if (hit) pick = ib + (__ffs(hit) - 1);
+                    run = __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (pick < 0) pick = last;
+                if (pick < 0) pick = s_imax;  // admitted sum vanished (cannot happen with S > 0)
+                if (lane == 0) { s_ik = pick; s_t = t; }
+            }
+            __syncthreads();
+            ik = s_ik;
+        } else if (var == GRBK_MWRBK) {
+            ik = s_imax;
+        } else if (var == GRBK_RBK) {
+            if (threadIdx.x == 0) {
+                const double u = philox_uniform(P.seed, (uint64_t)k, P.sys);
+                const double target = __dmul_rn(u, P.F);
+                // first i with prefix[i] > target (prefix is non-decreasing)
+                int64_t lo = 0, hi = P.m;  // answer in [lo, hi]
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (__ldg(P.rbk_prefix + mid) > target) hi = mid; else lo = mid + 1;
+                }
+                if (lo >= P.m) {  // none exceeded: last row with a_i > 0
+                    lo = P.m - 1;
+                    while (lo > 0 && !(__ldg(P.a + lo) > 0.0)) --lo;
+                }
+                s_ik = lo;
+            }
+            __syncthreads();
+            ik = s_ik;
+        } else {  // GRBK_BK
+            ik = k % P.m;
+        }
+        const double aik = __ldg(P.a + ik);
+        const double ck = (aik > 0.0) ? __ddiv_rn(P.alpha, aik) : 0.0;
+        if (c == 0 && threadIdx.x == 0) {
+            P.hist_rows[it] = (int)ik;
+            P.hist_c[it] = ck;
+            if (k < P.trace_len) P.trace_rows[k] = (int)ik;
+        }
+
+        // ---------------- W/U: w = R_ik B^T, u = A A_ik^T ---------------------
+        const T* Rik = P.R + ik * P.ldr;
+        const T* Aik = P.A + ik * P.lda;
+        if (P.smem_v) {
+            for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
+                reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(Rik) + e);
+        }
+        if (P.smem_arow) {
+            for (int64_t e = threadIdx.x; e < P.lda / VN; e += kBlock)
+                reinterpret_cast<V*>(sa)[e] = __ldg(reinterpret_cast<const V*>(Aik) + e);
+        }
+        __syncthreads();
+        {
+            const T* rsrc = P.smem_v ? sv : Rik;
+            const T* asrc = P.smem_arow ? sa : Aik;
+            const int64_t gw = (int64_t)c * kWarps + warp, nw = (int64_t)G * kWarps;
+            const int64_t ntask = P.q + P.m;
+            for (int64_t task = gw; task < ntask; task += nw) {
+                const bool isw = task < P.q;
+                const int64_t row = isw ? task : task - P.q;
+                const T* x = isw ? (P.B + row * P.ldb) : (P.A + row * P.lda);
+                const T* y = isw ? rsrc : asrc;
+                const bool ysh = isw ? (P.smem_v != 0) : (P.smem_arow != 0);
+                const int64_t nv = (isw ? P.ldb : P.lda) / VN;
+                T acc0 = 0, acc1 = 0;
+                for (int64_t e = lane; e < nv; e += 32) {
+                    const V xv = __ldg(reinterpret_cast<const V*>(x) + e);
+                    const V yv = ysh ? reinterpret_cast<const V*>(y)[e]
+                                     : (isw ? ldcg_v(reinterpret_cast<const V*>(y) + e)
+                                            : __ldg(reinterpret_cast<const V*>(y) + e));
+                    const T* xs = reinterpret_cast<const T*>(&xv);
+                    const T* ys = reinterpret_cast<const T*>(&yv);
+#pragma unroll
+                    for (int cc = 0; cc < VN; cc += 2) {
+                        acc0 = fma(xs[cc], ys[cc], acc0);
+                        acc1 = fma(xs[cc + 1], ys[cc + 1], acc1);
+                    }
+                }
+                double tot = warp_sum((double)acc0 + (double)acc1);
+                if (lane == 0) {
+                    if (isw) {
+                        __stcg(P.w + row, (T)tot);
+                        P.hist_w[(int64_t)it * P.q + row] = tot;
+                    } else {
+                        __stcg(P.u + row, (T)tot);
+                    }
+                }
+            }
+        }
+        if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
+
+        // ---------------- V: v = w B (column slab of this CTA) ---------------
+        for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
+        __syncthreads();
+        {
+            const int64_t slab = (P.ldr + G - 1) / G;
+            const int64_t l0 = (int64_t)c * slab, l1 = min(P.ldr, l0 + slab);
+            const int64_t width = l1 > l0 ? l1 - l0 : 0;
+            const int64_t ngrp = (width + 31) / 32;  // 32-column groups
+            if (ngrp > 0) {
+                if (ngrp >= kWarps) {
+                    for (int64_t gI = warp; gI < ngrp; gI += kWarps) {
+                        const int64_t l = l0 + gI * 32 + lane;
+                        if (l < l1) {
+                            T acc = 0;
+                            for (int64_t j = 0; j < P.q; ++j) acc = fma(sw[j], __ldg(P.B + j * P.ldb + l), acc);
+                            __stcg(P.v + l, acc);
+                        }
+                    }
+                } else {
+                    const int rs = kWarps / (int)ngrp;  // row phases per column group
+                    const int gI = warp % (int)ngrp, ph = warp / (int)ngrp;
+                    T acc = 0;
+                    const int64_t l = l0 + (int64_t)gI * 32 + lane;
+                    if (ph < rs && l < l1)
+                        for (int64_t j = ph; j < P.q; j += rs) acc = fma(sw[j], __ldg(P.B + j * P.ldb + l), acc);
+                    double* red = sm_parts;  // reuse: [rs][ngrp*32]
+                    if (ph < rs) red[(int64_t)ph * ngrp * 32 + gI * 32 + lane] = (double)acc;
+                    __syncthreads();
+                    for (int64_t e = threadIdx.x; e < ngrp * 32; e += kBlock) {
+                        const int64_t ll = l0 + e;
+                        if (ll < l1) {
+                            double tot = 0.0;
+                            for (int ph2 = 0; ph2 < rs; ++ph2) tot += red[(int64_t)ph2 * ngrp * 32 + e];
+                            __stcg(P.v + ll, (T)tot);
+                        }
+                    }
+                }
+            }
+        }
+        if (!grid_sync(P.bar, P.st, 3, s_ok)) return;
+
+        // ---------------- F: fused rank-1 update + row norms -----------------
+        if (P.smem_v) {
+            for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
+                reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(P.v) + e);
+            __syncthreads();
+        }
+        fused_pass<T, true>(P, ck, P.smem_v ? sv : P.v, r0, r1, sm_parts, sm_red, sm_redi);
+        if (!grid_sync(P.bar, P.st, 4, s_ok)) return;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// small kernels
+// ----------------------------------------------------------------------------
+
+// a_i = ||A_i||^2 (FP64), one warp per row
+template <typename T>
+__global__ void row_sqnorm_kernel(const T* A, int64_t m, int64_t p, int64_t lda, double* a)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    double acc = 0.0;
+    for (int64_t c = lane; c < p; c += 32) {
+        const double x = (double)A[row * lda + c];
+        acc = fma(x, x, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) a[row] = acc;
+}
+
+// sum of squares (and non-finite count) of a matrix, per-block partials
+template <typename T>
+__global__ void sumsq_kernel(const T* M, int64_t rows, int64_t cols, int64_t ld, double* part,
+                             int* nonfinite)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    int bad = 0;
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e % cols;
+        const double x = (double)M[i * ld + j];
+        if (!isfinite(x)) bad = 1;
+        acc = fma(x, x, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if (bad) atomicOr(nonfinite, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// ||X - Xref||^2 and ||Xref||^2 partials (FP64 X, Xref with ldr)
+__global__ void rse_kernel(const double* X, int64_t p, int64_t q, const double* Xr, double* part)
+{
+    __shared__ double red[2][32];
+    double e2 = 0.0, r2 = 0.0;
+    const int64_t total = p * q;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double d = X[e] - Xr[e];
+        e2 = fma(d, d, e2);
+        r2 = fma(Xr[e], Xr[e], r2);
+    }
+    e2 = warp_sum(e2);
+    r2 = warp_sum(r2);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = e2; red[1][threadIdx.x >> 5] = r2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// X += sum_t c_t A_{i_t}^T w_t   (fold the chunk's rank-1 terms into X)
+template <typename T>
+__global__ void x_fold_kernel(double* X, int64_t p, int64_t q, const T* A, int64_t lda,
+                              const int* rows, const double* cs, const double* W, int nit)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p * q) return;
+    const int64_t rr = idx / q, j = idx % q;
+    double acc = 0.0;
+    for (int t = 0; t < nit; ++t) {
+        const double ca = cs[t] * (double)__ldg(A + (int64_t)rows[t] * lda + rr);
+        acc = fma(ca, W[(int64_t)t * q + j], acc);
+    }
+    X[idx] += acc;
+}
+
+// power iteration pieces for ||B||_2^2: t = B^T x ; y = B t
+template <typename T>
+__global__ void bt_x_kernel(const T* B, int64_t q, int64_t n, int64_t ldb, const double* x, double* t)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    double acc = 0.0;
+    for (int64_t j = 0; j < q; ++j) acc = fma((double)B[j * ldb + l], x[j], acc);
+    t[l] = acc;
+}
+
+template <typename T>
+__global__ void b_t_kernel(const T* B, int64_t q, int64_t n, int64_t ldb, const double* t, double* y)
+{
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= q) return;
+    double acc = 0.0;
+    for (int64_t l = lane; l < n; l += 32) acc = fma((double)B[row * ldb + l], t[l], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[row] = acc;
+}
+
+// x <- y / ||y||, lambda = x.y (one block)
+__global__ void power_normalize_kernel(double* x, const double* y, int64_t q, double* lambda)
+{
+    __shared__ double red[2][32];
+    double xy = 0.0, yy = 0.0;
+    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) {
+        xy = fma(x[j], y[j], xy);
+        yy = fma(y[j], y[j], yy);
+    }
+    xy = warp_sum(xy);
+    yy = warp_sum(yy);
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = xy; red[1][threadIdx.x >> 5] = yy; }
+    __syncthreads();
+    __shared__ double s_n;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+        *lambda = a;
+        s_n = sqrt(b);
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) x[j] = y[j] / s_n;
+}
+
+__global__ void fill_kernel(double* x, int64_t n, double v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+// dtype conversion / re-pitch, device to device
+template <typename Td, typename Ts>
+__global__ void convert_kernel(Td* dst, int64_t ldd, const Ts* src, int64_t lds, int64_t rows, int64_t cols)
+{
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / cols, j = e % cols;
+        dst[i * ldd + j] = (Td)src[i * lds + j];
+    }
+}
+
+cudaError_t convert_matrix(void* dst, int dtd, int64_t ldd, const void* src, int dts, int64_t lds,
+                           int64_t rows, int64_t cols, cudaStream_t st)
+{
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const int64_t total = rows * cols;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    if (dtd == GRBK_DT_F64 && dts == GRBK_DT_F64)
+        convert_kernel<double, double><<<grid, 256, 0, st>>>((double*)dst, ldd, (const double*)src, lds, rows, cols);
+    else if (dtd == GRBK_DT_F64 && dts == GRBK_DT_F32)
+        convert_kernel<double, float><<<grid, 256, 0, st>>>((double*)dst, ldd, (const float*)src, lds, rows, cols);
+    else if (dtd == GRBK_DT_F32 && dts == GRBK_DT_F64)
+        convert_kernel<float, double><<<grid, 256, 0, st>>>((float*)dst, ldd, (const double*)src, lds, rows, cols);
+    else
+        convert_kernel<float, float><<<grid, 256, 0, st>>>((float*)dst, ldd, (const float*)src, lds, rows, cols);
+    return cudaGetLastError();
+}
+
+}  // namespace grbk
+
+// ============================================================================
+// host side
+// ============================================================================
+using namespace grbk;
+
+struct grbk_ctx {
+    int64_t m, p, q, n, lda, ldb, ldr;
+    int prec;        // grbk_precision
+    int esz;         // element size of the bulk arrays
+    grbk_opts opts;
+    cudaStream_t stream;
+    int G;           // persistent grid
+    int smem_v, smem_arow;
+    size_t dyn_smem;
+    // device buffers
+    void *A, *B, *C, *R, *u, *v, *w;
+    double *a, *rbk_prefix, *s, *r, *X;
+    double *part_S, *part_best_r, *part_SJ;
+    long long* part_best_i;
+    int* hist_rows;
+    double *hist_c, *hist_w;
+    int chunk_cap;
+    GridBarrier* bar;
+    DevState* st;
+    DevState* st_host;      // pinned
+    double* scratch;        // reductions
+    double* scratch_host;   // pinned
+    // scalars
+    double F, alpha, normC2, lambda;
+    SplitGemm* sg;
+    void* tmp;              // staging for host <-> device conversions
+    size_t tmp_bytes;
+    cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
+    long long launches;     // kernel launches issued (reset per solve)
+};
+
+static grbk_status ensure_tmp(grbk_ctx* c, size_t bytes)
+{
+    if (c->tmp_bytes >= bytes) return GRBK_OK;
+    if (c->tmp) cudaFree(c->tmp);
+    c->tmp = nullptr;
+    c->tmp_bytes = 0;
+    if (cudaMalloc(&c->tmp, bytes) != cudaSuccess) return GRBK_ENOMEM;
+    c->tmp_bytes = bytes;
+    return GRBK_OK;
+}
+
+static int dsize(int dt) { return dt == GRBK_DT_F64 ? 8 : 4; }
+
+// Copy a caller matrix (host or device, any dtype, any ld) into a device
+// buffer dst (dtype dtd, row stride ldd); padding columns are left untouched.
+static grbk_status load_matrix(grbk_ctx* c, const grbk_mat* M, void* dst, int dtd, int64_t ldd)
+{
+    const int64_t rows = M->rows, cols = M->cols;
+    if (rows == 0 || cols == 0) return GRBK_OK;
+    const int es = dsize(M->dtype);
+    if (M->on_device) {
+        GRBK_CK(convert_matrix(dst, dtd, ldd, M->ptr, M->dtype, M->ld, rows, cols, c->stream));
+        return GRBK_OK;
+    }
+    grbk_status s = ensure_tmp(c, (size_t)rows * cols * es);
+    if (s != GRBK_OK) return s;
+    GRBK_CK(cudaMemcpy2DAsync(c->tmp, cols * es, M->ptr, M->ld * es, cols * es, rows,
+                              cudaMemcpyHostToDevice, c->stream));
+    GRBK_CK(convert_matrix(dst, dtd, ldd, c->tmp, M->dtype, cols, rows, cols, c->stream));
+    return GRBK_OK;
+}
+
+// Write a device matrix (dtype dts, ld lds) into a caller matrix.
+static grbk_status store_matrix(grbk_ctx* c, grbk_mat* M, const void* src, int dts, int64_t lds)
+{
+    const int64_t rows = M->rows, cols = M->cols;
+    if (rows == 0 || cols == 0) return GRBK_OK;
+    const int es = dsize(M->dtype);
+    if (M->on_device) {
+        GRBK_CK(convert_matrix((void*)M->ptr, M->dtype, M->ld, src, dts, lds, rows, cols, c->stream));
+        return GRBK_OK;
+    }
+    grbk_status s = ensure_tmp(c, (size_t)rows * cols * es);
+    if (s != GRBK_OK) return s;
+    GRBK_CK(convert_matrix(c->tmp, M->dtype, cols, src, dts, lds, rows, cols, c->stream));
+    GRBK_CK(cudaMemcpy2DAsync((void*)M->ptr, M->ld * es, c->tmp, cols * es, cols * es, rows,
+                              cudaMemcpyDeviceToHost, c->stream));
+    return GRBK_OK;
+}
+
+static bool mat_ok(const grbk_mat* M)
+{
+    return M && M->ptr && M->rows >= 0 && M->cols >= 0 && M->ld >= M->cols &&
+           (M->dtype == GRBK_DT_F64 || M->dtype == GRBK_DT_F32);
+}
+
+template <typename T>
+static IterParams<T> make_params(grbk_ctx* c)
+{
+    IterParams<T> P;
+    memset(&P, 0, sizeof(P));
+    P.m = c->m; P.p = c->p; P.q = c->q; P.n = c->n;
+    P.lda = c->lda; P.ldb = c->ldb; P.ldr = c->ldr;
+    P.A = (const T*)c->A; P.B = (const T*)c->B; P.R = (T*)c->R;
+    P.a = c->a; P.rbk_prefix = c->rbk_prefix; P.s = c->s; P.r = c->r;
+    P.u = (T*)c->u; P.v = (T*)c->v; P.w = (T*)c->w;
+    P.part_S = c->part_S; P.part_best_r = c->part_best_r; P.part_best_i = c->part_best_i;
+    P.part_SJ = c->part_SJ;
+    P.hist_rows = c->hist_rows; P.hist_c = c->hist_c; P.hist_w = c->hist_w;
+    P.bar = c->bar; P.st = c->st;
+    P.F = c->F; P.alpha = c->alpha;
+    P.smem_v = c->smem_v; P.smem_arow = c->smem_arow;
+    P.stop_S = -1.0;
+    return P;
+}
+
+static grbk_status run_rownorms(grbk_ctx* c)
+{
+    c->launches += 1;
+    if (c->prec == GRBK_F64) {
+        IterParams<double> P = make_params<double>(c);
+        rownorms_kernel<double><<<c->G, kBlock, 0, c->stream>>>(P);
+    } else {
+        IterParams<float> P = make_params<float>(c);
+        rownorms_kernel<float><<<c->G, kBlock, 0, c->stream>>>(P);
+    }
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
+
+// R = C - A X B with the context's device X (FP64 master), into dst (ld ldr, bulk precision)
+static grbk_status compute_residual(grbk_ctx* c, const double* Xd, void* dst)
+{
+    const int64_t m = c->m, p = c->p, q = c->q, n = c->n;
+    c->launches += (c->prec == GRBK_F64) ? 2 : splitgemm_launches(c->sg);
+    if (c->prec == GRBK_F64) {
+        // T1 = A X (m x q), then dst = C - T1 B, evaluated in whichever order has fewer flops
+        const bool ax_first = (m * p * q + m * q * n) <= (p * q * n + m * p * n);
+        if (ax_first) {
+            grbk_status s = ensure_tmp(c, (size_t)m * q * 8);
+            if (s != GRBK_OK) return s;
+            GRBK_CK(gemm_simt<double>(m, q, p, 1.0, (const double*)c->A, c->lda, Xd, q, 0.0, nullptr, 0,
+                                      (double*)c->tmp, q, c->stream));
+            GRBK_CK(gemm_simt<double>(m, n, q, -1.0, (const double*)c->tmp, q, (const double*)c->B, c->ldb,
+                                      1.0, (const double*)c->C, c->ldr, (double*)dst, c->ldr, c->stream));
+        } else {
+            grbk_status s = ensure_tmp(c, (size_t)p * n * 8);
+            if (s != GRBK_OK) return s;
+            GRBK_CK(gemm_simt<double>(p, n, q, 1.0, Xd, q, (const double*)c->B, c->ldb, 0.0, nullptr, 0,
+                                      (double*)c->tmp, n, c->stream));
+            GRBK_CK(gemm_simt<double>(m, n, p, -1.0, (const double*)c->A, c->lda, (const double*)c->tmp, n,
+                                      1.0, (const double*)c->C, c->ldr, (double*)dst, c->ldr, c->stream));
+        }
+        return GRBK_OK;
+    }
+    return splitgemm_residual(c->sg, Xd, q, (const float*)c->C, (float*)dst, c->ldr, c->stream);
+}
+
+extern "C" void grbk_default_opts(grbk_opts* o)
+{
+    memset(o, 0, sizeof(*o));
+    o->precision = GRBK_F64;
+    o->refresh_T = 0;
+    o->alpha = 0.0;
+    o->stop_kind = GRBK_STOP_NONE;
+    o->split_terms = 3;
+}
+
+extern "C" const char* grbk_strerror(int32_t s)
+{
+    switch (s) {
+    case GRBK_OK: return "ok";
+    case GRBK_EINVAL: return "invalid argument";
+    case GRBK_ENOMEM: return "out of device memory";
+    case GRBK_ECUDA: return "CUDA error";
+    case GRBK_ENOTCONV: return "not converged within maxit";
+    case GRBK_ETIMEOUT: return "device barrier timed out";
+    case GRBK_ENONFINITE: return "non-finite value";
+    default: return "unknown status";
+    }
+}
+
+extern "C" void grbk_destroy(grbk_ctx* c)
+{
+    if (!c) return;
+    void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->s, c->r, c->X,
+                    c->part_S, c->part_best_r, c->part_SJ, c->part_best_i, c->hist_rows, c->hist_c,
+                    c->hist_w, c->bar, c->st, c->scratch, c->tmp};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->scratch_host) cudaFreeHost(c->scratch_host);
+    if (c->sg) splitgemm_destroy(c->sg);
+    delete c;
+}
+
+#define ALLOC(ptr, bytes)                                                     \
+    do {                                                                      \
+        if (cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16) != cudaSuccess) { \
+            grbk_destroy(c);                                                  \
+            return GRBK_ENOMEM;                                               \
+        }                                                                     \
+    } while (0)
+
+#define TRY(expr)                          \
+    do {                                   \
+        grbk_status s_ = (expr);           \
+        if (s_ != GRBK_OK) {               \
+            grbk_destroy(c);               \
+            return s_;                     \
+        }                                  \
+    } while (0)
+
+static grbk_status reduce_scratch(grbk_ctx* c, int nparts, int stride, double* out)
+{
+    GRBK_CK(cudaMemcpyAsync(c->scratch_host, c->scratch, sizeof(double) * nparts * stride,
+                            cudaMemcpyDeviceToHost, c->stream));
+    GRBK_CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < stride; ++k) out[k] = 0.0;
+    for (int i = 0; i < nparts; ++i)
+        for (int k = 0; k < stride; ++k) out[k] += c->scratch_host[i * stride + k];
+    return GRBK_OK;
+}
+
+static grbk_status sumsq_nonfinite(grbk_ctx* c, const void* M, int64_t rows, int64_t cols, int64_t ld,
+                                   double* ss, int* bad)
+{
+    int* d_bad = (int*)(c->scratch + 1024);
+    GRBK_CK(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    if (c->prec == GRBK_F64)
+        sumsq_kernel<double><<<256, 256, 0, c->stream>>>((const double*)M, rows, cols, ld, c->scratch, d_bad);
+    else
+        sumsq_kernel<float><<<256, 256, 0, c->stream>>>((const float*)M, rows, cols, ld, c->scratch, d_bad);
+    GRBK_CK(cudaGetLastError());
+    int hb = 0;
+    GRBK_CK(cudaMemcpyAsync(&hb, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    grbk_status s = reduce_scratch(c, 256, 1, ss);
+    if (s != GRBK_OK) return s;
+    *bad = hb;
+    return GRBK_OK;
+}
+
+template <typename T>
+static grbk_status setup_launch_shape(grbk_ctx* c)
+{
+    int dev = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    GRBK_CK(cudaGetDeviceProperties(&prop, dev));
+    const size_t esz = sizeof(T);
+    const size_t static_est = sizeof(double) * (kPartsCap + 2 * kWarps) + 8 * kWarps + 256;
+    const size_t budget = (size_t)prop.sharedMemPerBlockOptin - static_est - 1024;
+    size_t need = (size_t)c->q * esz;
+    c->smem_arow = 0;
+    c->smem_v = 0;
+    if (need + (size_t)c->ldr * esz <= budget) { c->smem_v = 1; need += (size_t)c->ldr * esz; }
+    if (need + (size_t)c->lda * esz <= budget) { c->smem_arow = 1; need += (size_t)c->lda * esz; }
+    if (need > budget) return GRBK_EINVAL;  // q too large for the w buffer
+    // (row, chunk) partial slots: one row's chunks must fit in shared memory
+    const int64_t chv = 32 * kUnroll * 2, vn = 16 / (int64_t)esz;
+    if ((c->ldr / vn + chv - 1) / chv > kPartsCap) return GRBK_EINVAL;
+    c->dyn_smem = need;
+    GRBK_CK(cudaFuncSetAttribute(iterate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    int per_sm = 0;
+    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_kernel<T>, kBlock, need));
+    if (per_sm < 1) return GRBK_EINVAL;
+    int G = prop.multiProcessorCount * min(per_sm, 1);
+    // small systems: fewer CTAs keep the barriers cheap (about 4K elements of R per CTA)
+    const int64_t want = std::max<int64_t>(1, (c->m * c->ldr) / 4096);
+    if (want < G) G = (int)want;
+    if (c->opts.grid_ctas > 0) G = min(c->opts.grid_ctas, prop.multiProcessorCount * per_sm);
+    if (G > c->m) G = (int)std::max<int64_t>(1, c->m);
+    c->G = G;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk_mat* B,
+                                   const grbk_mat* C, const grbk_opts* opts)
+{
+    if (!out) return GRBK_EINVAL;
+    *out = nullptr;
+    if (!mat_ok(A) || !mat_ok(B) || !mat_ok(C)) return GRBK_EINVAL;
+    const int64_t m = A->rows, p = A->cols, q = B->rows, n = B->cols;
+    if (m <= 0 || p <= 0 || q <= 0 || n <= 0) return GRBK_EINVAL;
+    if (C->rows != m || C->cols != n) return GRBK_EINVAL;
+    if (m > 0x7fffffffLL) return GRBK_EINVAL;
+    grbk_opts o;
+    if (opts) o = *opts; else grbk_default_opts(&o);
+    if (o.precision != GRBK_F64 && o.precision != GRBK_F32) return GRBK_EINVAL;
+    if (o.split_terms == 0) o.split_terms = 3;
+    if (o.split_terms != 2 && o.split_terms != 3) return GRBK_EINVAL;
+    if (o.refresh_T < 0) return GRBK_EINVAL;
+
+    grbk_ctx* c = new grbk_ctx;
+    memset(c, 0, sizeof(*c));
+    c->m = m; c->p = p; c->q = q; c->n = n;
+    c->opts = o;
+    c->prec = o.precision;
+    c->esz = (c->prec == GRBK_F64) ? 8 : 4;
+    c->stream = (cudaStream_t)o.stream;
+    c->lda = round_up(p, 32);
+    c->ldb = round_up(n, 32);
+    c->ldr = c->ldb;
+    const int dt = (c->prec == GRBK_F64) ? GRBK_DT_F64 : GRBK_DT_F32;
+    const size_t es = c->esz;
+
+    ALLOC(c->A, (size_t)m * c->lda * es);
+    ALLOC(c->B, (size_t)q * c->ldb * es);
+    ALLOC(c->C, (size_t)m * c->ldr * es);
+    ALLOC(c->R, (size_t)m * c->ldr * es);
+    ALLOC(c->u, (size_t)m * es);
+    ALLOC(c->v, (size_t)c->ldr * es);
+    ALLOC(c->w, (size_t)q * es);
+    ALLOC(c->a, (size_t)m * 8);
+    ALLOC(c->rbk_prefix, (size_t)m * 8);
+    ALLOC(c->s, (size_t)m * 8);
+    ALLOC(c->r, (size_t)m * 8);
+    ALLOC(c->X, (size_t)p * q * 8);
+    ALLOC(c->bar, sizeof(GridBarrier));
+    ALLOC(c->st, sizeof(DevState));
+    ALLOC(c->scratch, sizeof(double) * 2048);
+    if (cudaMallocHost((void**)&c->st_host, sizeof(DevState)) != cudaSuccess) { grbk_destroy(c); return GRBK_ENOMEM; }
+    if (cudaMallocHost((void**)&c->scratch_host, sizeof(double) * 2048) != cudaSuccess) { grbk_destroy(c); return GRBK_ENOMEM; }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+
+    cudaStream_t st = c->stream;
+    if (cudaMemsetAsync(c->A, 0, (size_t)m * c->lda * es, st) != cudaSuccess ||
+        cudaMemsetAsync(c->B, 0, (size_t)q * c->ldb * es, st) != cudaSuccess ||
+        cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, st) != cudaSuccess ||
+        cudaMemsetAsync(c->R, 0, (size_t)m * c->ldr * es, st) != cudaSuccess ||
+        cudaMemsetAsync(c->v, 0, (size_t)c->ldr * es, st) != cudaSuccess ||
+        cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), st) != cudaSuccess ||
+        cudaMemsetAsync(c->st, 0, sizeof(DevState), st) != cudaSuccess) {
+        grbk_destroy(c);
+        return GRBK_ECUDA;
+    }
+    TRY(load_matrix(c, A, c->A, dt, c->lda));
+    TRY(load_matrix(c, B, c->B, dt, c->ldb));
+    TRY(load_matrix(c, C, c->C, dt, c->ldr));
+
+    // non-finite check and norms
+    double ssA, ssB, ssC;
+    int badA, badB, badC;
+    TRY(sumsq_nonfinite(c, c->A, m, p, c->lda, &ssA, &badA));
+    TRY(sumsq_nonfinite(c, c->B, q, n, c->ldb, &ssB, &badB));
+    TRY(sumsq_nonfinite(c, c->C, m, n, c->ldr, &ssC, &badC));
+    if (badA || badB || badC) { grbk_destroy(c); return GRBK_ENONFINITE; }
+    c->normC2 = ssC;
+
+    // a_i, F and the RBK prefix (sequential, ascending rows)
+    {
+        const int threads = 256;
+        const int64_t blocks = (m * 32 + threads - 1) / threads;
+        if (c->prec == GRBK_F64)
+            row_sqnorm_kernel<double><<<(unsigned)blocks, threads, 0, st>>>((const double*)c->A, m, p, c->lda, c->a);
+        else
+            row_sqnorm_kernel<float><<<(unsigned)blocks, threads, 0, st>>>((const float*)c->A, m, p, c->lda, c->a);
+        if (cudaGetLastError() != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+        std::vector<double> ha(m), pref(m);
+        if (cudaMemcpyAsync(ha.data(), c->a, m * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+        double run = 0.0;
+        for (int64_t i = 0; i < m; ++i) { run += ha[i]; pref[i] = run; }
+        c->F = run;
+        if (!(c->F > 0.0)) { grbk_destroy(c); return GRBK_EINVAL; }
+        if (cudaMemcpyAsync(c->rbk_prefix, pref.data(), m * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+    }
+
+    // ||B||_2^2 by power iteration on B B^T with a Rayleigh quotient
+    {
+        double *x = nullptr, *t = nullptr, *y = nullptr, *lam = nullptr;
+        if (cudaMalloc(&x, q * 8) != cudaSuccess || cudaMalloc(&t, n * 8) != cudaSuccess ||
+            cudaMalloc(&y, q * 8) != cudaSuccess || cudaMalloc(&lam, 8) != cudaSuccess) {
+            cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+            grbk_destroy(c);
+            return GRBK_ENOMEM;
+        }
+        fill_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(x, q, 1.0 / sqrt((double)q));
+        const int iters = 300;
+        for (int itp = 0; itp < iters; ++itp) {
+            if (c->prec == GRBK_F64) {
+                bt_x_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double*)c->B, q, n, c->ldb, x, t);
+                b_t_kernel<double><<<(unsigned)((q * 32 + 255) / 256), 256, 0, st>>>((const double*)c->B, q, n, c->ldb, t, y);
+            } else {
+                bt_x_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)c->B, q, n, c->ldb, x, t);
+                b_t_kernel<float><<<(unsigned)((q * 32 + 255) / 256), 256, 0, st>>>((const float*)c->B, q, n, c->ldb, t, y);
+            }
+            power_normalize_kernel<<<1, 1024, 0, st>>>(x, y, q, lam);
+        }
+        double hl = 0.0;
+        cudaError_t e1 = cudaGetLastError();
+        cudaError_t e2 = cudaMemcpyAsync(&hl, lam, 8, cudaMemcpyDeviceToHost, st);
+        cudaError_t e3 = cudaStreamSynchronize(st);
+        cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+        c->lambda = hl;
+        if (!(hl > 0.0)) { grbk_destroy(c); return GRBK_EINVAL; }
+        if (o.alpha > 0.0) {
+            // Lemma 2.2 / Theorems 4.2-4.6 need 0 < alpha < 2/||B||_2^2 (small slack for the estimate)
+            if (!(o.alpha * hl < 2.0 * (1.0 + 1e-9))) { grbk_destroy(c); return GRBK_EINVAL; }
+            c->alpha = o.alpha;
+        } else {
+            c->alpha = 1.0 / hl;
+        }
+    }
+
+    TRY(c->prec == GRBK_F64 ? setup_launch_shape<double>(c) : setup_launch_shape<float>(c));
+    ALLOC(c->part_S, (size_t)c->G * 8);
+    ALLOC(c->part_best_r, (size_t)c->G * 8);
+    ALLOC(c->part_best_i, (size_t)c->G * 8);
+    ALLOC(c->part_SJ, (size_t)c->G * 8);
+    c->chunk_cap = o.check_every > 0 ? o.check_every : (o.refresh_T > 0 ? o.refresh_T : 256);
+    if (o.refresh_T > 0 && c->chunk_cap > o.refresh_T) c->chunk_cap = o.refresh_T;
+    ALLOC(c->hist_rows, (size_t)c->chunk_cap * 4);
+    ALLOC(c->hist_c, (size_t)c->chunk_cap * 8);
+    ALLOC(c->hist_w, (size_t)c->chunk_cap * q * 8);
+
+    if (c->prec == GRBK_F32)
+        TRY(splitgemm_create(&c->sg, m, p, q, n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
+                             o.split_terms, st));
+    if (cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+    *out = c;
+    return GRBK_OK;
+}
+
+static grbk_status launch_chunk(grbk_ctx* c, int variant, double theta, uint64_t seed, long long k0,
+                                int nit, double stop_S, int* d_trace_rows, double* d_trace_S,
+                                long long trace_len)
+{
+    void* args[1];
+    if (c->prec == GRBK_F64) {
+        IterParams<double> P = make_params<double>(c);
+        P.variant = variant; P.theta = theta; P.seed = seed; P.sys = 0; P.k0 = k0; P.nit = nit;
+        P.stop_S = stop_S; P.trace_rows = d_trace_rows; P.trace_S = d_trace_S; P.trace_len = trace_len;
+        args[0] = &P;
+        GRBK_CK(cudaLaunchCooperativeKernel((const void*)iterate_kernel<double>, dim3(c->G), dim3(kBlock),
+                                            args, c->dyn_smem, c->stream));
+    } else {
+        IterParams<float> P = make_params<float>(c);
+        P.variant = variant; P.theta = theta; P.seed = seed; P.sys = 0; P.k0 = k0; P.nit = nit;
+        P.stop_S = stop_S; P.trace_rows = d_trace_rows; P.trace_S = d_trace_S; P.trace_len = trace_len;
+        args[0] = &P;
+        GRBK_CK(cudaLaunchCooperativeKernel((const void*)iterate_kernel<float>, dim3(c->G), dim3(kBlock),
+                                            args, c->dyn_smem, c->stream));
+    }
+    return GRBK_OK;
+}
+
+static grbk_status fold_x(grbk_ctx* c, int nit)
+{
+    if (nit <= 0) return GRBK_OK;
+    c->launches += 1;
+    const int64_t tot = c->p * c->q;
+    const unsigned blocks = (unsigned)((tot + 255) / 256);
+    if (c->prec == GRBK_F64)
+        x_fold_kernel<double><<<blocks, 256, 0, c->stream>>>(c->X, c->p, c->q, (const double*)c->A, c->lda,
+                                                            c->hist_rows, c->hist_c, c->hist_w, nit);
+    else
+        x_fold_kernel<float><<<blocks, 256, 0, c->stream>>>(c->X, c->p, c->q, (const float*)c->A, c->lda,
+                                                           c->hist_rows, c->hist_c, c->hist_w, nit);
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
+
+static grbk_status compute_rse(grbk_ctx* c, const double* Xref_d, double* rse)
+{
+    c->launches += 1;
+    rse_kernel<<<256, 256, 0, c->stream>>>(c->X, c->p, c->q, Xref_d, c->scratch);
+    GRBK_CK(cudaGetLastError());
+    double out[2];
+    grbk_status s = reduce_scratch(c, 256, 2, out);
+    if (s != GRBK_OK) return s;
+    *rse = out[1] > 0.0 ? sqrt(out[0] / out[1]) : sqrt(out[0]);
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, const grbk_mat* X0,
+                                  double tol, int64_t maxit, uint64_t seed, grbk_mat* X_out,
+                                  grbk_result* res)
+{
+    const auto t_start = std::chrono::steady_clock::now();
+    if (!c) return GRBK_EINVAL;
+    if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
+    if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
+    if (maxit < 0) return GRBK_EINVAL;
+    if (X0 && (!mat_ok(X0) || X0->rows != c->p || X0->cols != c->q)) return GRBK_EINVAL;
+    if (X_out && (!X_out->ptr || X_out->rows != c->p || X_out->cols != c->q || X_out->ld < c->q)) return GRBK_EINVAL;
+    const grbk_opts& o = c->opts;
+    const grbk_mat* xr = o.x_ref;
+    if (xr && (!mat_ok(xr) || xr->rows != c->p || xr->cols != c->q)) return GRBK_EINVAL;
+    if (o.stop_kind == GRBK_STOP_RSE && !xr) return GRBK_EINVAL;
+    cudaStream_t st = c->stream;
+
+    // X^0 and R^0 = C - A X^0 B
+    if (X0) {
+        c->launches += 1;
+        grbk_status s = load_matrix(c, X0, c->X, GRBK_DT_F64, c->q);
+        if (s != GRBK_OK) return s;
+        s = compute_residual(c, c->X, c->R);
+        if (s != GRBK_OK) return s;
+    } else {
+        GRBK_CK(cudaMemsetAsync(c->X, 0, (size_t)c->p * c->q * 8, st));
+        GRBK_CK(cudaMemcpyAsync(c->R, c->C, (size_t)c->m * c->ldr * c->esz, cudaMemcpyDeviceToDevice, st));
+    }
+    double* Xref_d = nullptr;
+    if (xr) {
+        GRBK_CK(cudaMalloc(&Xref_d, (size_t)c->p * c->q * 8));
+        grbk_status s = load_matrix(c, xr, Xref_d, GRBK_DT_F64, c->q);
+        if (s != GRBK_OK) { cudaFree(Xref_d); return s; }
+    }
+    const long long trace_len = (o.row_trace || o.s_trace) ? o.trace_len : 0;
+    int* d_trace_rows = nullptr;
+    double* d_trace_S = nullptr;
+    if (trace_len > 0) {
+        if (cudaMalloc(&d_trace_rows, trace_len * 4) != cudaSuccess ||
+            cudaMalloc(&d_trace_S, trace_len * 8) != cudaSuccess) {
+            cudaFree(d_trace_rows); cudaFree(Xref_d);
+            return GRBK_ENOMEM;
+        }
+        cudaMemsetAsync(d_trace_rows, 0xff, trace_len * 4, st);
+        cudaMemsetAsync(d_trace_S, 0, trace_len * 8, st);
+    }
+    grbk_status result = GRBK_OK;
+    double stop_S = -1.0;
+    if (o.stop_kind == GRBK_STOP_RELRES) stop_S = tol * tol * c->normC2;
+
+    GRBK_CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), st));
+    GRBK_CK(cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), st));
+    c->launches = 0;
+    double iter_ms = 0.0;
+    long long iter_launches = 0;
+    result = run_rownorms(c);
+
+    long long k = 0;
+    int flag = FLAG_RUNNING;
+    double S = NAN, rse = NAN;
+    while (result == GRBK_OK) {
+        const long long left = maxit - k;
+        const int nit = (int)std::min<long long>(left, (long long)c->chunk_cap);
+        if (cudaEventRecord(c->ev0, st) != cudaSuccess) { result = GRBK_ECUDA; break; }
+        result = launch_chunk(c, variant, theta, seed, k, nit, stop_S, d_trace_rows, d_trace_S, trace_len);
+        if (result != GRBK_OK) break;
+        c->launches += 1;
+        iter_launches += 1;
+        if (cudaEventRecord(c->ev1, st) != cudaSuccess) { result = GRBK_ECUDA; break; }
+        if (cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { result = GRBK_ECUDA; break; }
+        {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) iter_ms += ms;
+        }
+        const DevState ds = *c->st_host;
+        if (ds.status != 0) { result = (grbk_status)ds.status; break; }
+        const int done = (int)(ds.k - k);
+        result = fold_x(c, done);
+        if (result != GRBK_OK) break;
+        k = ds.k;
+        S = ds.S;
+        flag = ds.flag;
+        if (flag != FLAG_RUNNING) break;
+        if (o.stop_kind == GRBK_STOP_RSE) {
+            result = compute_rse(c, Xref_d, &rse);
+            if (result != GRBK_OK) break;
+            if (rse <= tol) { flag = FLAG_TOL_MET; break; }
+        }
+        if (k >= maxit) break;
+        if (o.refresh_T > 0 && k % o.refresh_T == 0) {
+            result = compute_residual(c, c->X, c->R);
+            if (result == GRBK_OK) result = run_rownorms(c);
+        }
+    }
+    if (result == GRBK_OK && xr) result = compute_rse(c, Xref_d, &rse);
+    if (result == GRBK_OK && X_out) result = store_matrix(c, X_out, c->X, GRBK_DT_F64, c->q);
+    if (trace_len > 0 && result == GRBK_OK) {
+        if (o.row_trace) cudaMemcpyAsync(o.row_trace, d_trace_rows, trace_len * 4, cudaMemcpyDeviceToHost, st);
+        if (o.s_trace) cudaMemcpyAsync(o.s_trace, d_trace_S, trace_len * 8, cudaMemcpyDeviceToHost, st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && result == GRBK_OK) result = GRBK_ECUDA;
+    cudaFree(d_trace_rows);
+    cudaFree(d_trace_S);
+    cudaFree(Xref_d);
+    if (result == GRBK_OK && o.stop_kind != GRBK_STOP_NONE && flag == FLAG_RUNNING) result = GRBK_ENOTCONV;
+    if (res) {
+        res->iters = k;
+        res->relres = sqrt(S / c->normC2);
+        res->rse = rse;
+        res->alpha = c->alpha;
+        res->iter_kernel_ms = iter_ms;
+        res->iter_kernel_launches = iter_launches;
+        res->launches = c->launches;
+        res->status = result;
+        res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return result;
+}
+
+extern "C" grbk_status grbk_residual(grbk_ctx* c, const grbk_mat* X, grbk_mat* R_out)
+{
+    if (!c || !mat_ok(X) || X->rows != c->p || X->cols != c->q) return GRBK_EINVAL;
+    if (!R_out || !R_out->ptr || R_out->rows != c->m || R_out->cols != c->n || R_out->ld < c->n) return GRBK_EINVAL;
+    double* Xd = nullptr;
+    void* Rd = nullptr;
+    GRBK_CK(cudaMalloc(&Xd, (size_t)c->p * c->q * 8));
+    if (cudaMalloc(&Rd, (size_t)c->m * c->ldr * c->esz) != cudaSuccess) { cudaFree(Xd); return GRBK_ENOMEM; }
+    grbk_status s = load_matrix(c, X, Xd, GRBK_DT_F64, c->q);
+    if (s == GRBK_OK) s = compute_residual(c, Xd, Rd);
+    if (s == GRBK_OK) s = store_matrix(c, R_out, Rd, c->prec == GRBK_F64 ? GRBK_DT_F64 : GRBK_DT_F32, c->ldr);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && s == GRBK_OK) s = GRBK_ECUDA;
+    cudaFree(Xd);
+    cudaFree(Rd);
+    return s;
+}
+
+extern "C" grbk_status grbk_get_residual(grbk_ctx* c, grbk_mat* R_out)
+{
+    if (!c || !R_out || !R_out->ptr || R_out->rows != c->m || R_out->cols != c->n || R_out->ld < c->n) return GRBK_EINVAL;
+    grbk_status s = store_matrix(c, R_out, c->R, c->prec == GRBK_F64 ? GRBK_DT_F64 : GRBK_DT_F32, c->ldr);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && s == GRBK_OK) s = GRBK_ECUDA;
+    return s;
+}
+
+extern "C" grbk_status grbk_get_rownorms(grbk_ctx* c, double* s_out, int32_t on_device)
+{
+    if (!c || !s_out) return GRBK_EINVAL;
+    GRBK_CK(cudaMemcpyAsync(s_out, c->s, c->m * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    GRBK_CK(cudaStreamSynchronize(c->stream));
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_info(const grbk_ctx* c, int64_t dims[4], double* alpha)
+{
+    if (!c) return GRBK_EINVAL;
+    if (dims) { dims[0] = c->m; dims[1] = c->p; dims[2] = c->q; dims[3] = c->n; }
+    if (alpha) *alpha = c->alpha;
+    return GRBK_OK;
+}

@@ -1,0 +1,70 @@
+"""The C-ABI library loads, exports every function include/grbk.h declares, and
+the Python binding's ctypes structs have the C layout (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2408_05444_gb300 as g
+from paper_2408_05444_gb300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "grbk.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(grbk_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    return gbuild.build()
+
+
+def test_every_declared_symbol_is_exported(built):
+    names = declared_functions()
+    assert len(names) >= 12
+    L = ctypes.CDLL(built)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(names) == set(g.EXPORTS)
+
+
+def test_strerror_without_gpu(built):
+    assert g.grbk_strerror(g.GRBK_EINVAL) == "invalid argument"
+    assert g.grbk_strerror(99) == "unknown status"
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "grbk.h"
+int main(void) {
+  printf("%zu %zu %zu\\n", sizeof(grbk_mat), sizeof(grbk_opts), sizeof(grbk_result));
+  printf("%zu %zu %zu %zu %zu %zu\\n", offsetof(grbk_opts, alpha), offsetof(grbk_opts, x_ref),
+         offsetof(grbk_opts, trace_len), offsetof(grbk_opts, stream), offsetof(grbk_opts, check_every),
+         offsetof(grbk_result, status));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = list(map(int, out[:3]))
+    offs = list(map(int, out[3:]))
+    assert sizes == [ctypes.sizeof(g.grbk_mat), ctypes.sizeof(g.grbk_opts), ctypes.sizeof(g.grbk_result)]
+    assert offs == [g.grbk_opts.alpha.offset, g.grbk_opts.x_ref.offset, g.grbk_opts.trace_len.offset,
+                    g.grbk_opts.stream.offset, g.grbk_opts.check_every.offset, g.grbk_result.status.offset]
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(g, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(g, "_lib", None)
+    with pytest.raises(RuntimeError):
+        g.lib()
