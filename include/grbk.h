@@ -154,7 +154,9 @@ void grbk_destroy(grbk_ctx* ctx);
  * batch runs in FP32 (A, B, C, R) with FP64 row-norm sums, threshold and pick.
  * System s draws its random numbers with counter (k, s, 0, 0).
  * stop_kind: NONE, RELRES (per-system ||R_s||_F <= tol ||C_s||_F) or the
- * discrepancy rule via grbk_batch_solve's `targets`.
+ * discrepancy rule via grbk_batch_solve's `targets`.  opts->row_trace, when
+ * set, must hold nsys * trace_len entries: system s writes its first
+ * trace_len selected rows at row_trace[s * trace_len + k] (s_trace unused).
  */
 grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
                               const grbk_mat* C, const grbk_opts* opts);

@@ -262,6 +262,10 @@ class Batch:
         self.handle = handle
         self.keep = keep
 
+    @property
+    def row_trace(self):
+        return getattr(self.keep, "rows_view", None)
+
     def __del__(self):
         if getattr(self, "handle", None):
             try:
@@ -278,8 +282,13 @@ def _mat_array(xs):
     return arr
 
 
-def grbk_batch_create(As, Bs, Cs, opts=None, **kw) -> Batch:
-    o, keep = _make_opts(opts, **kw)
+def grbk_batch_create(As, Bs, Cs, opts=None, trace_len=0, **kw) -> Batch:
+    """Batched systems; trace_len > 0 records each system's first trace_len rows
+    (available as batch.row_trace, shape nsys x trace_len)."""
+    o, keep = _make_opts(opts, trace_len=trace_len * len(As), **kw)
+    if trace_len > 0:
+        o.trace_len = trace_len
+        keep.rows_view = keep.rows.reshape(len(As), trace_len)
     h = ctypes.c_void_p()
     a, b, c = _mat_array(As), _mat_array(Bs), _mat_array(Cs)
     st = lib().grbk_batch_create(ctypes.byref(h), len(As), a, b, c, ctypes.byref(o))

@@ -48,6 +48,8 @@ struct BatchParams {
     long long* iters;               // out
     double* S_out;                  // out
     int* flag_out;                  // out: FLAG_*
+    int* trace_rows;                // [nsys x trace_len] selected rows, or null
+    long long trace_len;
     int variant;
     double theta;
     uint64_t seed;
@@ -261,6 +263,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             __syncthreads();
             const double aik = a[ik];
             const double ck = aik > 0.0 ? __ddiv_rn(d.alpha, aik) : 0.0;
+            if (threadIdx.x == 0 && k < P.trace_len) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
 
             // ---- w = R_ik B^T, u = A A_ik^T
             for (int l = threadIdx.x; l < d.n; l += kBB) s_vec[l] = R[(long long)ik * d.ldr + l];
@@ -349,6 +352,7 @@ struct grbk_batch {
     long long* iters;
     double* S;
     int* flags;
+    int* trace;
     int chunk;
     long long totA, totB, totR, totX, totRow, totHist, totHistW;
 };
@@ -364,7 +368,7 @@ extern "C" void grbk_batch_destroy(grbk_batch* b)
 {
     if (!b) return;
     void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->A, b->B, b->C, b->R, b->X, b->a, b->pref,
-                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags};
+                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags, b->trace};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -563,6 +567,15 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     P.hist_rows = b->hist_rows; P.hist_c = b->hist_c; P.hist_w = b->hist_w;
     P.iters = b->iters; P.S_out = b->S; P.flag_out = b->flags;
     P.variant = variant; P.theta = theta; P.seed = seed; P.maxit = maxit; P.chunk = b->chunk;
+    const long long tlen = b->opts.row_trace ? b->opts.trace_len : 0;
+    if (tlen > 0) {
+        if (b->trace) cudaFree(b->trace);
+        b->trace = (int*)dmalloc((size_t)tlen * b->nsys * 4);
+        if (!b->trace) return GRBK_ENOMEM;
+        GRBK_CK(cudaMemsetAsync(b->trace, 0xff, (size_t)tlen * b->nsys * 4, st));
+        P.trace_rows = b->trace;
+        P.trace_len = tlen;
+    }
     P.init_from_x = X0s != nullptr;
     int dev = 0, nsm = 0, per_sm = 0;
     GRBK_CK(cudaGetDevice(&dev));
@@ -579,6 +592,8 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     GRBK_CK(cudaMemcpyAsync(it.data(), b->iters, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
     GRBK_CK(cudaMemcpyAsync(S.data(), b->S, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
     GRBK_CK(cudaMemcpyAsync(fl.data(), b->flags, 4 * b->nsys, cudaMemcpyDeviceToHost, st));
+    if (tlen > 0)
+        GRBK_CK(cudaMemcpyAsync(b->opts.row_trace, b->trace, (size_t)tlen * b->nsys * 4, cudaMemcpyDeviceToHost, st));
     if (X_outs) {
         for (int s = 0; s < b->nsys; ++s) {
             const SysDesc& d = b->hsys[s];

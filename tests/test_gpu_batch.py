@@ -37,22 +37,26 @@ def test_batch_converges_to_clean_images():
 
 @pytest.mark.parametrize("variant", ["mwrbk", "grbk", "rgrbk", "rbk", "bk"])
 def test_batch_matches_oracle_per_system(variant):
-    """Fixed 120 iterations per system: rows agree with the FP64 oracle's up to
-    the first decision the oracle itself marks as closer than FP32 can resolve,
-    and X agrees to FP32 accuracy when no such decision occurred."""
+    """Fixed 120 iterations per system: the selected rows agree with the FP64
+    oracle's up to the first decision the oracle marks as closer than FP32
+    resolves (relative margin 1e-5); with no such decision X agrees to 1e-4."""
     sy = _systems()
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120)
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, variant, theta=0.7, maxit=120, seed=11, X_outs=Xo)
     assert st == g.GRBK_OK
+    checked = 0
     for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
         assert r["iters"] == 120
         orc = oracle.solve(s["A"], s["B"], s["C"], variant, theta=0.7, alpha=r["alpha"], seed=11, sys=sid,
                            maxit=120, mode=oracle.MODE_FACTORED)
-        margins = np.minimum(orc["margin_pick"], orc["margin_adm"])
-        near = np.nonzero(margins < 1e-4)[0]
+        margins = np.minimum(orc["margin_pick"], np.where(np.isnan(orc["margin_adm"]), np.inf, orc["margin_adm"]))
+        near = np.nonzero(margins < 1e-5)[0]
         kk = int(near[0]) if len(near) else 120
-        assert kk > 0
+        rows = b.row_trace[sid]
+        assert np.array_equal(rows[:kk], orc["rows"][:kk]), (sid, kk, rows[:kk], orc["rows"][:kk])
         if kk == 120:
             assert _rel(X, orc["X"]) < 1e-4
+            checked += 1
+    assert checked >= 1
