@@ -41,6 +41,9 @@ WORKLOADS = {
     # name: (m, p, q, n, generator kwargs)
     "precision": dict(m=20000, p=2000, q=2000, n=20000),
     "precision_slice": dict(m=2000, p=200, q=200, n=2000),
+    # same recipe at 8000x800 / 800x8000: R is 256 MB (larger than L2), about
+    # 2 GB on the device in all; used for ncu captures
+    "precision_8k": dict(m=8000, p=800, q=800, n=8000),
 }
 
 
@@ -306,7 +309,7 @@ def native_arm(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"precision: A {m}x{p}, B {q}x{n} N(0,1/cols), X* N(0,1), C = A X* B; "
+            "config": {"workload": f"{wl}: A {m}x{p}, B {q}x{n} N(0,1/cols), X* N(0,1), C = A X* B; "
                                    f"chosen form FP32 + split-BF16 refresh every {T}",
                        "iters_per_step": T, "variant": "ME-GRBK", "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
