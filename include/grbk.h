@@ -175,6 +175,47 @@ grbk_status grbk_batch_solve(grbk_batch* batch, int32_t variant, double theta, c
 
 void grbk_batch_destroy(grbk_batch* batch);
 
+/*
+ * grbk_solve_small_noalloc -- one small system A X B = C in FP32 solved with no
+ * device or host allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate, e.g. code that runs while a CUDA
+ * graph is being captured, processes whose device memory comes from a fixed
+ * pool they do not own, or loops where the cost and device-wide
+ * synchronisation of cudaMalloc/cudaFree are not acceptable.
+ *
+ * It runs the batched kernel on a single system (system index 0 for the
+ * Philox counter), so its arithmetic is that of grbk_batch_solve.  All working
+ * memory (residual, row norms, recorded update terms, counters) lives in one
+ * static device array of GRBK_NOALLOC_SCRATCH_BYTES bytes that every GPU which
+ * loads this library holds until the process exits.  Limits: m, p, q, n each
+ * at most GRBK_NOALLOC_MAX_SIDE; larger sizes return GRBK_EINVAL.
+ *
+ * A (m x p), B (q x n), C (m x n): device pointers, FP32, row-major and
+ * contiguous (row stride = number of columns), owned by the caller.
+ * X_out (p x q): device pointer, FP32, contiguous; zeroed, then overwritten
+ * (X^0 = 0).  alpha <= 0 selects 1/||B||_2^2 (200 power iterations on the
+ * device); an explicit alpha must lie in (0, 2/||B||_2^2).  tol > 0 stops
+ * when ||R||_F <= tol ||C||_F (GRBK_ENOTCONV if maxit comes first); tol <= 0
+ * runs exactly maxit iterations.  iters_out and relres_out are host pointers
+ * (either may be NULL).  stream is a cudaStream_t; the call returns after the
+ * work has finished.
+ *
+ * The first call on a device looks up the device address of the static array
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream
+ * capture.  Every call uses the same array and leaves the previous call's
+ * contents in it: the call clears what must start at zero itself.  Calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on the
+ * array and must be serialised by the caller.
+ * Errors: EINVAL (NULL pointer, size outside [1, GRBK_NOALLOC_MAX_SIDE],
+ * variant, theta, alpha), ENONFINITE (NaN/Inf input or residual), ECUDA.
+ */
+#define GRBK_NOALLOC_MAX_SIDE 512
+#define GRBK_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+grbk_status grbk_solve_small_noalloc(const float* A, const float* B, const float* C, int32_t m, int32_t p,
+                                     int32_t q, int32_t n, int32_t variant, double theta, double alpha,
+                                     double tol, int64_t maxit, uint64_t seed, float* X_out,
+                                     int64_t* iters_out, double* relres_out, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* grbk_strerror(int32_t status);
 

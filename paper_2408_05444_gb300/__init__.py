@@ -57,7 +57,8 @@ class GrbkError(RuntimeError):
 
 EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "grbk_get_residual",
            "grbk_get_rownorms", "grbk_info", "grbk_destroy", "grbk_batch_create", "grbk_batch_solve",
-           "grbk_batch_destroy", "grbk_strerror"]
+           "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc"]
+GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
 
@@ -94,6 +95,9 @@ def lib():
         L.grbk_batch_solve.restype = i32
         L.grbk_batch_destroy.argtypes = [vp]
         L.grbk_batch_destroy.restype = None
+        L.grbk_solve_small_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, dbl, dbl, dbl, i64, u64, vp,
+                                               P(i64), P(dbl), vp]
+        L.grbk_solve_small_noalloc.restype = i32
         L.grbk_strerror.argtypes = [i32]
         L.grbk_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -322,3 +326,21 @@ def grbk_batch_destroy(batch: Batch):
     if batch.handle:
         lib().grbk_batch_destroy(batch.handle)
         batch.handle = None
+
+
+def grbk_solve_small_noalloc(A, B, C, X_out, variant="grbk", theta=0.5, alpha=0.0, tol=0.0, maxit=1000, seed=0,
+                             stream=None):
+    """grbk_solve_small_noalloc -> (status, iters, relres).  A, B, C, X_out are
+    contiguous FP32 CUDA tensors; nothing is allocated by the library."""
+    for t in (A, B, C, X_out):
+        assert _is_torch(t) and t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    m, p = A.shape
+    q, n = B.shape
+    it = ctypes.c_int64(0)
+    rr = ctypes.c_double(0.0)
+    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    st = lib().grbk_solve_small_noalloc(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, p, q, n, v, float(theta),
+                                        float(alpha), float(tol), int(maxit), int(seed), X_out.data_ptr(),
+                                        ctypes.byref(it), ctypes.byref(rr), sp)
+    return st, it.value, rr.value

@@ -12,6 +12,9 @@
 #include <string.h>
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <cstddef>
+#include <mutex>
 #include <vector>
 
 #include "grbk_internal.cuh"
@@ -632,4 +635,222 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
         }
     }
     return overall;
+}
+
+// ============================================================================
+// grbk_solve_small_noalloc: one small FP32 system, no allocation at all.
+//
+// Some callers cannot allocate device memory: code running while a CUDA graph
+// is being captured, processes whose device memory is handed out by a fixed
+// pool they do not own, or latency-critical loops where a cudaMalloc /
+// cudaFree (and the device-wide synchronisation cudaFree implies) is not
+// acceptable.  For them this entry point runs the batch kernel above on one
+// system with every working buffer (residual, row norms, recorded terms,
+// queue, outputs) taken from the file-scope array below.  The array lives as
+// long as the library is loaded on a device; every call shares it.
+// ============================================================================
+namespace grbk {
+
+constexpr int kNoAllocSide = GRBK_NOALLOC_MAX_SIDE;
+constexpr int kNoAllocChunk = 64;
+
+struct NoAllocScratch {
+    SysDesc desc;
+    int order;
+    int queue;
+    long long iters;
+    double S;
+    int flag;
+    int status;
+    double normC2;
+    double lambda;
+    int hist_rows[kNoAllocChunk];
+    float hist_c[kNoAllocChunk];
+    double a[kNoAllocSide];
+    double pref[kNoAllocSide];
+    double px[kNoAllocSide];
+    double pt[kNoAllocSide];
+    double py[kNoAllocSide];
+    float hist_w[kNoAllocChunk * kNoAllocSide];
+    float R[kNoAllocSide * kNoAllocSide];
+};
+static_assert(sizeof(NoAllocScratch) <= GRBK_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
+
+// The working memory of grbk_solve_small_noalloc.  In host code this name is a
+// host-side stand-in, not a device address: host code only ever passes the
+// address obtained from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GRBK_NOALLOC_SCRATCH_BYTES];
+
+// Set-up for one system in one CTA: ||A_i||^2 and their running sums, ||A||_F^2,
+// ||C||_F^2, ||B||_2^2 by 200 power iterations on B B^T, the step, the stop
+// level, a non-finite scan.  On an error the queue is filled so that the batch
+// kernel finds no work.
+__global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, const float* A, const float* B,
+                                                            const float* C, int m, int p, int q, int n,
+                                                            double alpha_in, double tol)
+{
+    __shared__ double red[2 * kBW];
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    int mybad = 0;
+    for (int i = threadIdx.x; i < m; i += kBB) {
+        double acc = 0.0;
+        for (int c = 0; c < p; ++c) {
+            const double x = (double)A[(long long)i * p + c];
+            if (!isfinite(x)) mybad = 1;
+            acc = __dadd_rn(acc, __dmul_rn(x, x));
+        }
+        S->a[i] = acc;
+    }
+    double c2 = 0.0;
+    for (long long e = threadIdx.x; e < (long long)m * n; e += kBB) {
+        const double x = (double)C[e];
+        if (!isfinite(x)) mybad = 1;
+        c2 = fma(x, x, c2);
+    }
+    for (long long e = threadIdx.x; e < (long long)q * n; e += kBB)
+        if (!isfinite(B[e])) mybad = 1;
+    if (mybad) atomicOr(&bad, 1);
+    c2 = block_sum_fixed(c2, red);
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int i = 0; i < m; ++i) { run += S->a[i]; S->pref[i] = run; }
+        S->desc.F = run;
+        S->normC2 = c2;
+    }
+    // power iteration: x <- B B^T x / ||B B^T x||, lambda = x . B B^T x
+    for (int j = threadIdx.x; j < q; j += kBB) S->px[j] = 1.0 / sqrt((double)q);
+    __syncthreads();
+    double lam = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        for (int l = threadIdx.x; l < n; l += kBB) {
+            double acc = 0.0;
+            for (int j = 0; j < q; ++j) acc = fma((double)B[(long long)j * n + l], S->px[j], acc);
+            S->pt[l] = acc;
+        }
+        __syncthreads();
+        double xy = 0.0, yy = 0.0;
+        for (int j = threadIdx.x; j < q; j += kBB) {
+            double acc = 0.0;
+            for (int l = 0; l < n; ++l) acc = fma((double)B[(long long)j * n + l], S->pt[l], acc);
+            S->py[j] = acc;
+            xy = fma(S->px[j], acc, xy);
+            yy = fma(acc, acc, yy);
+        }
+        xy = block_sum_fixed(xy, red);
+        yy = block_sum_fixed(yy, red);
+        lam = xy;
+        const double nrm = sqrt(yy);
+        for (int j = threadIdx.x; j < q; j += kBB) S->px[j] = nrm > 0.0 ? S->py[j] / nrm : 0.0;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int status = 0;
+        if (bad) status = GRBK_ENONFINITE;
+        else if (!(S->desc.F > 0.0) || !(lam > 0.0)) status = GRBK_EINVAL;
+        else if (alpha_in > 0.0 && !(alpha_in * lam < 2.0 * (1.0 + 1e-9))) status = GRBK_EINVAL;
+        SysDesc& d = S->desc;
+        d.m = m; d.p = p; d.q = q; d.n = n;
+        d.lda = p; d.ldb = n; d.ldr = n;
+        d.pad = 0;
+        d.offA = 0; d.offB = 0; d.offR = 0; d.offX = 0; d.offRow = 0; d.offHist = 0; d.offHistW = 0;
+        d.alpha = alpha_in > 0.0 ? alpha_in : 1.0 / lam;
+        d.stop_S = tol > 0.0 ? tol * tol * c2 : -1.0;
+        S->lambda = lam;
+        S->status = status;
+        S->order = 0;
+        S->iters = 0;
+        S->S = 0.0;
+        S->flag = FLAG_RUNNING;
+        S->queue = status ? 1 : 0;   // an error leaves the batch kernel without work
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+static void* g_noalloc_ptr[64];
+static std::mutex g_noalloc_mu;
+
+static grbk_status noalloc_scratch_address(void** out)
+{
+    int dev = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return GRBK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        GRBK_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return GRBK_OK;
+}
+
+}  // namespace grbk
+
+extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, const float* C, int32_t m, int32_t p,
+                                                int32_t q, int32_t n, int32_t variant, double theta, double alpha,
+                                                double tol, int64_t maxit, uint64_t seed, float* X_out,
+                                                int64_t* iters_out, double* relres_out, void* stream)
+{
+    if (!A || !B || !C || !X_out) return GRBK_EINVAL;
+    if (m <= 0 || p <= 0 || q <= 0 || n <= 0) return GRBK_EINVAL;
+    if (m > GRBK_NOALLOC_MAX_SIDE || p > GRBK_NOALLOC_MAX_SIDE || q > GRBK_NOALLOC_MAX_SIDE ||
+        n > GRBK_NOALLOC_MAX_SIDE)
+        return GRBK_EINVAL;
+    if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
+    if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
+    if (maxit < 0) return GRBK_EINVAL;
+    void* base = nullptr;
+    grbk_status s = noalloc_scratch_address(&base);
+    if (s != GRBK_OK) return s;
+    NoAllocScratch* S = reinterpret_cast<NoAllocScratch*>(base);
+    cudaStream_t st = (cudaStream_t)stream;
+    GRBK_CK(cudaMemsetAsync(X_out, 0, sizeof(float) * (size_t)p * q, st));
+    noalloc_setup_kernel<<<1, kBB, 0, st>>>(S, A, B, C, m, p, q, n, alpha, tol);
+    GRBK_CK(cudaGetLastError());
+    BatchParams P;
+    memset(&P, 0, sizeof(P));
+    P.nsys = 1;
+    P.sys = &S->desc;
+    P.order = &S->order;
+    P.queue = &S->queue;
+    P.A = A; P.B = B; P.C = C;
+    P.R = S->R;
+    P.X = X_out;
+    P.a = S->a;
+    P.rbk_prefix = S->pref;
+    P.hist_rows = S->hist_rows;
+    P.hist_c = S->hist_c;
+    P.hist_w = S->hist_w;
+    P.iters = &S->iters;
+    P.S_out = &S->S;
+    P.flag_out = &S->flag;
+    P.variant = variant;
+    P.theta = theta;
+    P.seed = seed;
+    P.maxit = maxit;
+    P.chunk = kNoAllocChunk;
+    P.init_from_x = 0;
+    batch_kernel<<<1, kBB, 0, st>>>(P);
+    GRBK_CK(cudaGetLastError());
+    struct {
+        long long iters;
+        double S;
+        int flag;
+        int status;
+        double normC2;
+    } h;
+    GRBK_CK(cudaMemcpyAsync(&h.iters, &S->iters, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(&h.S, &S->S, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(&h.flag, &S->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(&h.status, &S->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(&h.normC2, &S->normC2, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaStreamSynchronize(st));
+    if (h.status != 0) return (grbk_status)h.status;
+    if (iters_out) *iters_out = h.iters;
+    if (relres_out) *relres_out = h.normC2 > 0.0 ? sqrt(h.S / h.normC2) : 0.0;
+    if (!std::isfinite(h.S)) return GRBK_ENONFINITE;
+    if (tol > 0.0 && h.flag == FLAG_RUNNING) return GRBK_ENOTCONV;
+    return GRBK_OK;
 }
