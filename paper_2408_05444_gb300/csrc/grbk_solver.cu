@@ -97,7 +97,7 @@ __device__ __forceinline__ void cta_rows(int64_t m, int c, int G, int64_t& r0, i
 // compensation), r_i = s_i / a_i, and the CTA's partial sum / argmax.
 // ----------------------------------------------------------------------------
 template <typename T, bool UPDATE>
-__device__ void fused_pass(const IterParams<T>& P, double ck, const T* vsrc, int64_t r0, int64_t r1,
+__device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const T* vsrc, int64_t r0, int64_t r1,
                            double* sm_parts, double* sm_red, long long* sm_redi)
 {
     using V = typename VecOf<T>::V;
@@ -128,21 +128,20 @@ __device__ void fused_pass(const IterParams<T>& P, double ck, const T* vsrc, int
             double acc_d = 0.0;
             float acc_f = 0.f, comp_f = 0.f;
             for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
-                V rv[kUnroll], vv[kUnroll];
+                V rv[kUnroll];
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
                     const int64_t e = base + uu * 32 + lane;
-                    if (e < e1) {
-                        rv[uu] = ldcg_v(Rrow + e);
-                        if (UPDATE) vv[uu] = P.smem_v ? vrow[e] : ldcg_v(vrow + e);
-                    }
+                    if (e < e1) rv[uu] = ldcg_v(Rrow + e);
                 }
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
                     const int64_t e = base + uu * 32 + lane;
                     if (e < e1) {
+                        V vv;
+                        if (UPDATE) vv = P.smem_v ? vrow[e] : ldcg_v(vrow + e);
                         T* x = reinterpret_cast<T*>(&rv[uu]);
-                        const T* y = reinterpret_cast<const T*>(&vv[uu]);
+                        const T* y = reinterpret_cast<const T*>(&vv);
 #pragma unroll
                         for (int c = 0; c < VN; ++c) {
                             if (UPDATE) x[c] = fma(-coef, y[c], x[c]);
@@ -216,6 +215,129 @@ __global__ void __launch_bounds__(kBlock) rownorms_kernel(IterParams<T> P)
     IterParams<T> Q = P;
     Q.smem_v = 0;
     fused_pass<T, false>(Q, 0.0, nullptr, r0, r1, sm_parts, sm_red, sm_redi);
+}
+
+// ----------------------------------------------------------------------------
+// dst[row] = X_row . y for rows [r0, r1) of X (row stride ld elements), as
+// (row, chunk) units per warp with kUnroll independent vector loads in flight;
+// per-unit partial sums are combined in a fixed order.  ymode: 0 = y in shared
+// memory, 1 = y written earlier in this kernel (L2 loads), 2 = y read-only.
+// dst_hist (optional) receives the FP64 sums.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void rows_dot(const T* X, int64_t ld, int64_t r0, int64_t r1, const T* y, int ymode, T* dst,
+                         double* dst_hist, double* sm_parts)
+{
+    using V = typename VecOf<T>::V;
+    constexpr int VN = VecOf<T>::N;
+    constexpr int CHV = 32 * kUnroll * 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nvec = ld / VN;
+    const int nch = (int)((nvec + CHV - 1) / CHV);
+    int64_t rows_per_batch = kPartsCap / nch;
+    if (rows_per_batch < 1) rows_per_batch = 1;
+    if (rows_per_batch > kBlock) rows_per_batch = kBlock;
+    const V* yv = reinterpret_cast<const V*>(y);
+    for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
+        const int64_t b1 = min(r1, b0 + rows_per_batch);
+        const int64_t units = (b1 - b0) * nch;
+        for (int64_t unit = warp; unit < units; unit += kWarps) {
+            const int64_t row = b0 + unit / nch;
+            const int ch = (int)(unit % nch);
+            const int64_t e0 = (int64_t)ch * CHV, e1 = min(nvec, e0 + CHV);
+            const V* xrow = reinterpret_cast<const V*>(X + row * ld);
+            T acc0 = 0, acc1 = 0;
+            for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
+                V xs[kUnroll];
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t e = base + uu * 32 + lane;
+                    if (e < e1) xs[uu] = __ldg(xrow + e);
+                }
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t e = base + uu * 32 + lane;
+                    if (e < e1) {
+                        const V ys = (ymode == 0) ? yv[e] : (ymode == 1 ? ldcg_v(yv + e) : __ldg(yv + e));
+                        const T* a = reinterpret_cast<const T*>(&xs[uu]);
+                        const T* b = reinterpret_cast<const T*>(&ys);
+#pragma unroll
+                        for (int cc = 0; cc < VN; cc += 2) {
+                            acc0 = fma(a[cc], b[cc], acc0);
+                            acc1 = fma(a[cc + 1], b[cc + 1], acc1);
+                        }
+                    }
+                }
+            }
+            const double tot = warp_sum((double)acc0 + (double)acc1);
+            if (lane == 0) sm_parts[unit] = tot;
+        }
+        __syncthreads();
+        for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
+            double sum = 0.0;
+            for (int c2 = 0; c2 < nch; ++c2) sum += sm_parts[rr * nch + c2];
+            __stcg(dst + b0 + rr, (T)sum);
+            if (dst_hist) dst_hist[b0 + rr] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// v = w B for this CTA's slab of vector columns: each thread owns one vector
+// column and a residue class of rows, kUnroll rows in flight; the row classes
+// are combined in a fixed order in shared memory.  w is in shared memory.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void cols_gemv(const T* B, int64_t ldb, int64_t q, const T* w, T* v, int c, int G, double* sm_parts)
+{
+    using V = typename VecOf<T>::V;
+    constexpr int VN = VecOf<T>::N;
+    const int64_t nvt = ldb / VN;
+    const int64_t slab = (nvt + G - 1) / G;
+    const int64_t e0 = (int64_t)c * slab, e1 = min(nvt, e0 + slab);
+    for (int64_t cb = e0; cb < e1; cb += kBlock) {
+        const int ncols = (int)min((int64_t)kBlock, e1 - cb);
+        const int RG = kBlock / ncols;
+        const int e = threadIdx.x % ncols, rg = threadIdx.x / ncols;
+        T acc[VN];
+#pragma unroll
+        for (int cc = 0; cc < VN; ++cc) acc[cc] = 0;
+        if (rg < RG) {
+            const V* col = reinterpret_cast<const V*>(B) + cb + e;
+            const int64_t ldv = ldb / VN;
+            for (int64_t jb = rg; jb < q; jb += (int64_t)RG * kUnroll) {
+                V bv[kUnroll];
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t j = jb + (int64_t)uu * RG;
+                    if (j < q) bv[uu] = __ldg(col + j * ldv);
+                }
+#pragma unroll
+                for (int uu = 0; uu < kUnroll; ++uu) {
+                    const int64_t j = jb + (int64_t)uu * RG;
+                    if (j < q) {
+                        const T wj = w[j];
+                        const T* b = reinterpret_cast<const T*>(&bv[uu]);
+#pragma unroll
+                        for (int cc = 0; cc < VN; ++cc) acc[cc] = fma(wj, b[cc], acc[cc]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (rg < RG) {
+#pragma unroll
+            for (int cc = 0; cc < VN; ++cc) sm_parts[((int64_t)rg * ncols + e) * VN + cc] = (double)acc[cc];
+        }
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < (int64_t)ncols * VN; t += kBlock) {
+            double sum = 0.0;
+            for (int r2 = 0; r2 < RG; ++r2) sum += sm_parts[(int64_t)r2 * ncols * VN + t];
+            __stcg(v + cb * VN + t, (T)sum);
+        }
+        __syncthreads();
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -395,83 +517,20 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         }
         __syncthreads();
         {
-            const T* rsrc = P.smem_v ? sv : Rik;
-            const T* asrc = P.smem_arow ? sa : Aik;
-            const int64_t gw = (int64_t)c * kWarps + warp, nw = (int64_t)G * kWarps;
-            const int64_t ntask = P.q + P.m;
-            for (int64_t task = gw; task < ntask; task += nw) {
-                const bool isw = task < P.q;
-                const int64_t row = isw ? task : task - P.q;
-                const T* x = isw ? (P.B + row * P.ldb) : (P.A + row * P.lda);
-                const T* y = isw ? rsrc : asrc;
-                const bool ysh = isw ? (P.smem_v != 0) : (P.smem_arow != 0);
-                const int64_t nv = (isw ? P.ldb : P.lda) / VN;
-                T acc0 = 0, acc1 = 0;
-                for (int64_t e = lane; e < nv; e += 32) {
-                    const V xv = __ldg(reinterpret_cast<const V*>(x) + e);
-                    const V yv = ysh ? reinterpret_cast<const V*>(y)[e]
-                                     : (isw ? ldcg_v(reinterpret_cast<const V*>(y) + e)
-                                            : __ldg(reinterpret_cast<const V*>(y) + e));
-                    const T* xs = reinterpret_cast<const T*>(&xv);
-                    const T* ys = reinterpret_cast<const T*>(&yv);
-#pragma unroll
-                    for (int cc = 0; cc < VN; cc += 2) {
-                        acc0 = fma(xs[cc], ys[cc], acc0);
-                        acc1 = fma(xs[cc + 1], ys[cc + 1], acc1);
-                    }
-                }
-                double tot = warp_sum((double)acc0 + (double)acc1);
-                if (lane == 0) {
-                    if (isw) {
-                        __stcg(P.w + row, (T)tot);
-                        P.hist_w[(int64_t)it * P.q + row] = tot;
-                    } else {
-                        __stcg(P.u + row, (T)tot);
-                    }
-                }
-            }
+            // each CTA streams a contiguous block of rows of B (for w) and its own
+            // rows of A (for u, consumed by the same CTA in the fused pass)
+            int64_t j0, j1;
+            cta_rows(P.q, c, G, j0, j1);
+            rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w,
+                        P.hist_w + (int64_t)it * P.q, sm_parts);
+            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts);
         }
         if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
 
         // ---------------- V: v = w B (column slab of this CTA) ---------------
         for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
         __syncthreads();
-        {
-            const int64_t slab = (P.ldr + G - 1) / G;
-            const int64_t l0 = (int64_t)c * slab, l1 = min(P.ldr, l0 + slab);
-            const int64_t width = l1 > l0 ? l1 - l0 : 0;
-            const int64_t ngrp = (width + 31) / 32;  // 32-column groups
-            if (ngrp > 0) {
-                if (ngrp >= kWarps) {
-                    for (int64_t gI = warp; gI < ngrp; gI += kWarps) {
-                        const int64_t l = l0 + gI * 32 + lane;
-                        if (l < l1) {
-                            T acc = 0;
-                            for (int64_t j = 0; j < P.q; ++j) acc = fma(sw[j], __ldg(P.B + j * P.ldb + l), acc);
-                            __stcg(P.v + l, acc);
-                        }
-                    }
-                } else {
-                    const int rs = kWarps / (int)ngrp;  // row phases per column group
-                    const int gI = warp % (int)ngrp, ph = warp / (int)ngrp;
-                    T acc = 0;
-                    const int64_t l = l0 + (int64_t)gI * 32 + lane;
-                    if (ph < rs && l < l1)
-                        for (int64_t j = ph; j < P.q; j += rs) acc = fma(sw[j], __ldg(P.B + j * P.ldb + l), acc);
-                    double* red = sm_parts;  // reuse: [rs][ngrp*32]
-                    if (ph < rs) red[(int64_t)ph * ngrp * 32 + gI * 32 + lane] = (double)acc;
-                    __syncthreads();
-                    for (int64_t e = threadIdx.x; e < ngrp * 32; e += kBlock) {
-                        const int64_t ll = l0 + e;
-                        if (ll < l1) {
-                            double tot = 0.0;
-                            for (int ph2 = 0; ph2 < rs; ++ph2) tot += red[(int64_t)ph2 * ngrp * 32 + e];
-                            __stcg(P.v + ll, (T)tot);
-                        }
-                    }
-                }
-            }
-        }
+        cols_gemv<T>(P.B, P.ldb, P.q, sw, P.v, c, G, sm_parts);
         if (!grid_sync(P.bar, P.st, 3, s_ok)) return;
 
         // ---------------- F: fused rank-1 update + row norms -----------------
