@@ -1,8 +1,12 @@
 // grbk_gemm.cu -- dense products for the residual refresh R = C - A X B
 // (Algorithm 3 initialisation, repeated every refresh period): a tiled SIMT
 // GEMM used in FP64 mode, and the FP32-mode refresh engine.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "grbk_internal.cuh"
 
@@ -86,49 +90,437 @@ template cudaError_t gemm_simt<float>(int64_t, int64_t, int64_t, double, const f
                                       int64_t, cudaStream_t);
 
 // ----------------------------------------------------------------------------
-// FP32-mode refresh engine
+// FP32-mode refresh engine: R = C - (A X) B with split-BF16 operands on the
+// 5th-generation tensor cores (tcgen05.mma, accumulators in TMEM, operands
+// staged by TMA with 128-byte swizzle).
+//
+// Each FP32 (or FP64) operand x is split into BF16 terms x = x0 + x1 (+ x2)
+// with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); a product is
+// the sum of the cross terms whose orders add up to at most terms-1
+// (2 terms: x0 y0 + x0 y1 + x1 y0; 3 terms adds x0 y2 + x2 y0 + x1 y1),
+// accumulated in FP32.  The terms are stored as [term][rows][Kpad] planes
+// (K contiguous, zero padded to a multiple of 64) so that one 3-D tensor map
+// serves every term; the kernel walks (term pair, K block) in one
+// accumulation chain.
 // ----------------------------------------------------------------------------
-struct SplitGemm {
-    int64_t m, p, q, n, lda, ldb;
-    const float* A;
-    const float* B;
-    int terms;
-    float* Xf;   // p x q
-    float* T1;   // m x q
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;            // 16 KB
+constexpr int B_TILE = BN * BK * 2;            // 32 KB
+constexpr int STAGE_BYTES = A_TILE + B_TILE;   // 48 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 256;
+constexpr long long kWaitBudget = 2000000000LL;  // cycles (about 1 s)
+
+enum { EPI_SPLIT = 0, EPI_RESID = 1 };
+
+struct Args {
+    int M, N, K;                 // K: padded inner size (multiple of BK)
+    int npairs;
+    int ta[6], tb[6];            // term of A / of B for each pair
+    int mode;
+    int out_terms;               // EPI_SPLIT: terms written
+    int out_rows;                // EPI_SPLIT: rows per output plane (>= M)
+    __nv_bfloat16* out_split;    // [out_terms][out_rows][out_ld]
+    int64_t out_ld;
+    const float* cin;            // EPI_RESID: out = cin - D
+    float* out;
+    int64_t ld;
+    int* err;
 };
 
-__global__ void x_to_f32_kernel(const double* X, int64_t total, float* Xf)
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < total) Xf[i] = (float)X[i];
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M x N
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_f(float x, int terms, __nv_bfloat16* t)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    t[0] = h;
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+    t[1] = l;
+    if (terms > 2) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+}
+
+// D[M x N] = sum over pairs of A_ta[M x K] * B_tb[N x K]^T; 256 threads:
+// warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM owner, warps 4-7 = epilogue.
+__global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, Args g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_TILE;
+    uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+    __shared__ int s_abort;
+
+    // a CTA that finds the error flag already set (an earlier CTA's wait
+    // expired) leaves at once, before touching barriers or TMEM
+    if (*(volatile int*)g.err != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nkb = g.K / BK;
+    const int total = g.npairs * nkb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int it = 0; it < total; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; break; }
+            if (*(volatile int*)&s_abort) break;
+            const int pair = it / nkb, kb = it % nkb;
+            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+            tma_load_3d(smem_u32(sA + s * A_TILE), &tmA, kb * BK, m0, g.ta[pair], full0 + 8 * s);
+            tma_load_3d(smem_u32(sB + s * B_TILE), &tmB, kb * BK, n0, g.tb[pair], full0 + 8 * s);
+            ++issued;
+        }
+        // wait (bounded) for this CTA's copies still in flight before anyone leaves
+        for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+            mbar_wait(full0 + 8 * (it % STAGES), (uint32_t)((it / STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        for (int it = 0; it < total; ++it) {
+            const int s = it % STAGES;
+            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+            if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; break; }
+            if (*(volatile int*)&s_abort) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * A_TILE), b0 = smem_u32(sB + s * B_TILE);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_bf16(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);  // arrives once every MMA issued above has completed
+    } else if (warp >= 4) {
+        const int e = warp - 4;
+        const bool ok = mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = m0 + e * 32 + lane;
+        const bool write = ok && !*(volatile int*)&s_abort;
+        for (int cb = 0; cb < BN; cb += 32) {
+            uint32_t r[32];
+            tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)cb, r);
+            if (!write || row >= g.M || n0 + cb >= g.N) continue;
+            const int col0 = n0 + cb;
+            const bool full = col0 + 32 <= g.N;
+            if (g.mode == EPI_RESID) {
+                const float* ci = g.cin + (int64_t)row * g.ld + col0;
+                float* oi = g.out + (int64_t)row * g.ld + col0;
+                if (full) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 cv = __ldg(reinterpret_cast<const float4*>(ci + j));
+                        float4 ov;
+                        ov.x = cv.x - __uint_as_float(r[j]);
+                        ov.y = cv.y - __uint_as_float(r[j + 1]);
+                        ov.z = cv.z - __uint_as_float(r[j + 2]);
+                        ov.w = cv.w - __uint_as_float(r[j + 3]);
+                        *reinterpret_cast<float4*>(oi + j) = ov;
+                    }
+                } else {
+                    for (int j = 0; j < 32 && col0 + j < g.N; ++j) oi[j] = ci[j] - __uint_as_float(r[j]);
+                }
+            } else {
+                for (int j = 0; j < 32 && col0 + j < g.N; ++j) {
+                    __nv_bfloat16 t[3];
+                    split_f(__uint_as_float(r[j]), g.out_terms, t);
+                    for (int tt = 0; tt < g.out_terms; ++tt)
+                        g.out_split[((int64_t)tt * g.out_rows + row) * g.out_ld + col0 + j] = t[tt];
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 || (warp >= 4 && lane == 0)) {
+        if (*(volatile int*)&s_abort) atomicExch(g.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 2) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// planes [terms][rows][Kpad] of the split of src rows (src[r][k], k < K); K..Kpad-1 left as zeros
+template <typename S>
+__global__ void split_rows_kernel(const S* src, int64_t ld, int64_t rows, int64_t K, int64_t Kpad, int terms,
+                                  int64_t plane_rows, __nv_bfloat16* dst)
+{
+    const int64_t total = rows * K;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / K, k = e % K;
+        const double x = (double)src[r * ld + k];
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const double r1 = x - (double)__bfloat162float(h);
+        const __nv_bfloat16 l = __double2bfloat16(r1);
+        dst[r * Kpad + k] = h;
+        dst[(plane_rows + r) * Kpad + k] = l;
+        if (terms > 2) dst[(2 * plane_rows + r) * Kpad + k] = __double2bfloat16(r1 - (double)__bfloat162float(l));
+    }
+}
+
+// planes [terms][N][Kpad] of the split of src^T (src is K x N, row stride ld)
+template <typename S>
+__global__ void split_transpose_kernel(const S* src, int64_t ld, int64_t K, int64_t N, int64_t Kpad, int terms,
+                                       int64_t plane_rows, __nv_bfloat16* dst)
+{
+    __shared__ double tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t k = k0 + dy, j = j0 + threadIdx.x;
+        tile[dy][threadIdx.x] = (k < K && j < N) ? (double)src[k * ld + j] : 0.0;
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t j = j0 + dy, k = k0 + threadIdx.x;
+        if (j < N && k < K) {
+            const double x = tile[threadIdx.x][dy];
+            const __nv_bfloat16 h = __double2bfloat16(x);
+            const double r1 = x - (double)__bfloat162float(h);
+            const __nv_bfloat16 l = __double2bfloat16(r1);
+            dst[j * Kpad + k] = h;
+            dst[(plane_rows + j) * Kpad + k] = l;
+            if (terms > 2) dst[(2 * plane_rows + j) * Kpad + k] = __double2bfloat16(r1 - (double)__bfloat162float(l));
+        }
+    }
+}
+
+}  // namespace tc
+
+struct SplitGemm {
+    int64_t m, p, q, n, lda, ldb;
+    int terms;
+    int64_t Kp, Kq;                 // p and q padded to multiples of 64
+    int64_t mr, nr, qr;             // m padded to BM, n and q padded to BN (plane rows)
+    __nv_bfloat16* As;              // [terms][mr][Kp]
+    __nv_bfloat16* BTs;             // [terms][nr][Kq]
+    __nv_bfloat16* XTs;             // [terms][qr][Kp]
+    __nv_bfloat16* T1s;             // [terms][mr][Kq]
+    CUtensorMap tmA, tmXT, tmT1, tmBT;
+    int* err;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 3-D map over [terms][rows][Kpad] BF16 planes, box 64 x box_rows x 1, 128-byte swizzle
+static bool make_map(CUtensorMap* map, void* base, int64_t Kpad, int64_t rows, int terms, int box_rows)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)Kpad, (cuuint64_t)rows, (cuuint64_t)terms};
+    cuuint64_t strides[2] = {(cuuint64_t)(Kpad * 2), (cuuint64_t)(rows * Kpad * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static void pairs_for(int terms, tc::Args& a)
+{
+    // smallest cross terms first, so the FP32 accumulator adds them before the large ones
+    static const int t2a[3] = {0, 1, 0}, t2b[3] = {1, 0, 0};
+    static const int t3a[6] = {1, 2, 0, 1, 0, 0}, t3b[6] = {1, 0, 2, 0, 1, 0};
+    a.npairs = terms == 2 ? 3 : 6;
+    for (int i = 0; i < a.npairs; ++i) {
+        a.ta[i] = terms == 2 ? t2a[i] : t3a[i];
+        a.tb[i] = terms == 2 ? t2b[i] : t3b[i];
+    }
 }
 
 grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, int64_t n, const float* A,
                              int64_t lda, const float* B, int64_t ldb, int terms, cudaStream_t st)
 {
-    (void)st;
     SplitGemm* g = new SplitGemm();
-    g->m = m; g->p = p; g->q = q; g->n = n; g->lda = lda; g->ldb = ldb;
-    g->A = A; g->B = B; g->terms = terms;
-    g->Xf = nullptr; g->T1 = nullptr;
-    if (cudaMalloc(&g->Xf, (size_t)p * q * 4) != cudaSuccess || cudaMalloc(&g->T1, (size_t)m * q * 4) != cudaSuccess) {
+    memset(g, 0, sizeof(*g));
+    g->m = m; g->p = p; g->q = q; g->n = n; g->lda = lda; g->ldb = ldb; g->terms = terms;
+    g->Kp = round_up(p, tc::BK);
+    g->Kq = round_up(q, tc::BK);
+    g->mr = round_up(m, tc::BM);
+    g->nr = round_up(n, tc::BN);
+    g->qr = round_up(q, tc::BN);
+    const size_t szA = (size_t)terms * g->mr * g->Kp * 2, szB = (size_t)terms * g->nr * g->Kq * 2;
+    const size_t szX = (size_t)terms * g->qr * g->Kp * 2, szT = (size_t)terms * g->mr * g->Kq * 2;
+    if (cudaMalloc(&g->As, szA) != cudaSuccess || cudaMalloc(&g->BTs, szB) != cudaSuccess ||
+        cudaMalloc(&g->XTs, szX) != cudaSuccess || cudaMalloc(&g->T1s, szT) != cudaSuccess ||
+        cudaMalloc(&g->err, sizeof(int)) != cudaSuccess) {
         splitgemm_destroy(g);
         return GRBK_ENOMEM;
+    }
+    if (cudaMemsetAsync(g->As, 0, szA, st) != cudaSuccess || cudaMemsetAsync(g->BTs, 0, szB, st) != cudaSuccess ||
+        cudaMemsetAsync(g->XTs, 0, szX, st) != cudaSuccess || cudaMemsetAsync(g->T1s, 0, szT, st) != cudaSuccess ||
+        cudaMemsetAsync(g->err, 0, sizeof(int), st) != cudaSuccess) {
+        splitgemm_destroy(g);
+        return GRBK_ECUDA;
+    }
+    tc::split_rows_kernel<float><<<2048, 256, 0, st>>>(A, lda, m, p, g->Kp, terms, g->mr, g->As);
+    dim3 tb(32, 8), grd((unsigned)((n + 31) / 32), (unsigned)((q + 31) / 32));
+    tc::split_transpose_kernel<float><<<grd, tb, 0, st>>>(B, ldb, q, n, g->Kq, terms, g->nr, g->BTs);
+    if (cudaGetLastError() != cudaSuccess) { splitgemm_destroy(g); return GRBK_ECUDA; }
+    if (!make_map(&g->tmA, g->As, g->Kp, g->mr, terms, tc::BM) ||
+        !make_map(&g->tmXT, g->XTs, g->Kp, g->qr, terms, tc::BN) ||
+        !make_map(&g->tmT1, g->T1s, g->Kq, g->mr, terms, tc::BM) ||
+        !make_map(&g->tmBT, g->BTs, g->Kq, g->nr, terms, tc::BN)) {
+        splitgemm_destroy(g);
+        return GRBK_ECUDA;
+    }
+    if (cudaFuncSetAttribute(tc::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
+        cudaSuccess) {
+        splitgemm_destroy(g);
+        return GRBK_ECUDA;
     }
     *out = g;
     return GRBK_OK;
 }
 
-grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const float* C, float* R,
-                               int64_t ldr, cudaStream_t st)
+grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const float* C, float* R, int64_t ldr,
+                               cudaStream_t st)
 {
-    (void)ldx;
-    const int64_t tot = g->p * g->q;
-    x_to_f32_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, tot, g->Xf);
+    // X^T terms: [terms][q][Kp] from X (p x q, FP64)
+    dim3 tb(32, 8), grd((unsigned)((g->q + 31) / 32), (unsigned)((g->p + 31) / 32));
+    tc::split_transpose_kernel<double><<<grd, tb, 0, st>>>(X, ldx, g->p, g->q, g->Kp, g->terms, g->qr, g->XTs);
     GRBK_CK(cudaGetLastError());
-    GRBK_CK(gemm_simt<float>(g->m, g->q, g->p, 1.0, g->A, g->lda, g->Xf, g->q, 0.0, nullptr, 0, g->T1, g->q, st));
-    GRBK_CK(gemm_simt<float>(g->m, g->n, g->q, -1.0, g->T1, g->q, g->B, g->ldb, 1.0, C, ldr, R, ldr, st));
+    // T1 = A X  (M = m, N = q, K = p); epilogue writes the split terms of T1
+    tc::Args a1;
+    memset(&a1, 0, sizeof(a1));
+    a1.M = (int)g->m; a1.N = (int)g->q; a1.K = (int)g->Kp;
+    pairs_for(g->terms, a1);
+    a1.mode = tc::EPI_SPLIT; a1.out_terms = g->terms; a1.out_rows = (int)g->mr; a1.out_split = g->T1s;
+    a1.out_ld = g->Kq; a1.err = g->err;
+    dim3 g1((unsigned)((g->q + tc::BN - 1) / tc::BN), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    tc::gemm_kernel<<<g1, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmXT, a1);
+    GRBK_CK(cudaGetLastError());
+    // R = C - T1 B  (M = m, N = n, K = q)
+    tc::Args a2;
+    memset(&a2, 0, sizeof(a2));
+    a2.M = (int)g->m; a2.N = (int)g->n; a2.K = (int)g->Kq;
+    pairs_for(g->terms, a2);
+    a2.mode = tc::EPI_RESID; a2.cin = C; a2.out = R; a2.ld = ldr; a2.err = g->err;
+    dim3 g2((unsigned)((g->n + tc::BN - 1) / tc::BN), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    tc::gemm_kernel<<<g2, 256, tc::SMEM_BYTES, st>>>(g->tmT1, g->tmBT, a2);
+    GRBK_CK(cudaGetLastError());
     return GRBK_OK;
+}
+
+grbk_status splitgemm_check(SplitGemm* g, cudaStream_t st)
+{
+    int h = 0;
+    GRBK_CK(cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaStreamSynchronize(st));
+    return h ? GRBK_ETIMEOUT : GRBK_OK;
 }
 
 int splitgemm_launches(const SplitGemm*) { return 3; }
@@ -136,8 +528,9 @@ int splitgemm_launches(const SplitGemm*) { return 3; }
 void splitgemm_destroy(SplitGemm* g)
 {
     if (!g) return;
-    if (g->Xf) cudaFree(g->Xf);
-    if (g->T1) cudaFree(g->T1);
+    void* bufs[] = {g->As, g->BTs, g->XTs, g->T1s, g->err};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
     delete g;
 }
 

@@ -190,6 +190,8 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
 grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const float* C,
                                float* R, int64_t ldr, cudaStream_t st);
 void splitgemm_destroy(SplitGemm* g);
+// reads the device error flag of the tensor-core kernels (GRBK_ETIMEOUT if a wait expired)
+grbk_status splitgemm_check(SplitGemm* g, cudaStream_t st);
 // kernel launches made by one splitgemm_residual call
 int splitgemm_launches(const SplitGemm* g);
 

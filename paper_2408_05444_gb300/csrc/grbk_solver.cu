@@ -866,7 +866,9 @@ static grbk_status compute_residual(grbk_ctx* c, const double* Xd, void* dst)
         }
         return GRBK_OK;
     }
-    return splitgemm_residual(c->sg, Xd, q, (const float*)c->C, (float*)dst, c->ldr, c->stream);
+    grbk_status s = splitgemm_residual(c->sg, Xd, q, (const float*)c->C, (float*)dst, c->ldr, c->stream);
+    if (s != GRBK_OK) return s;
+    return splitgemm_check(c->sg, c->stream);
 }
 
 extern "C" void grbk_default_opts(grbk_opts* o)

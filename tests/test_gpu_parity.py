@@ -179,6 +179,24 @@ def test_nonzero_x0_and_limit():
     assert _rel(X, lim) < 1e-9
 
 
+@pytest.mark.parametrize("terms,bound", [(3, 2e-6), (2, 6e-5)])
+@pytest.mark.parametrize("m,p,q,n", [(700, 130, 300, 517), (129, 64, 256, 256)])
+def test_fp32_split_bf16_refresh(terms, bound, m, p, q, n):
+    """The tensor-core refresh R = C - (A X) B with split-BF16 operands: every
+    entry within `bound` of |A||X||B| + |C| (3 terms ~ FP32 rounding of the
+    inputs, 2 terms ~ 2^-16 per product), on shapes with several M, N and K
+    tiles and ragged tails."""
+    A, B, C, _ = workloads.gaussian(m, p, q, n, seed=m + q)
+    X = np.random.default_rng(2).standard_normal((p, q))
+    ref = oracle.residual(A, X, B, C)
+    ctx = g.grbk_create(A, B, C, precision="f32", split_terms=terms)
+    R32 = np.zeros(C.shape, dtype=np.float32)
+    g.grbk_residual(ctx, X, R32)
+    scale = np.abs(A) @ np.abs(X) @ np.abs(B) + np.abs(C)
+    err = np.abs(R32 - ref) / scale
+    assert np.max(err) < bound, np.max(err)
+
+
 def test_residual_entry_point():
     A, B, C, _ = workloads.gaussian(257, 33, 19, 131, seed=6)
     X = np.random.default_rng(1).standard_normal((33, 19))
