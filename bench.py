@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--mode", default="rate", choices=["rate", "ttt"],
+                    help="rate: iterations per second (the bench line); ttt: time to a solution error target")
+    ap.add_argument("--split-terms", type=int, default=3)
     return ap.parse_args()
 
 
@@ -232,15 +235,17 @@ def native_arm(args):
         torch.cuda.synchronize(dev)
 
     # ---------------- chosen form: FP32 bulk + split-BF16 refresh every T ----
+    # each step: T iterations and one refresh R = C - A X B; the solve starts
+    # from the current iterate, so its initial residual is the first refresh
     ctx = g.grbk_create(Ad, Bd, Cd, precision="f32", refresh_T=T, check_every=T, stream=stream)
     Xd = torch.zeros(p, q, dtype=torch.float64, device=dev)
-    g.grbk_solve(ctx, "grbk", maxit=args.warmup * T, seed=1, X_out=Xd)
+    g.grbk_solve(ctx, "grbk", X0=Xd, maxit=args.warmup * T, seed=1, X_out=Xd)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()
         ev0.record(stream)
-        st, res = g.grbk_solve(ctx, "grbk", maxit=args.steps * T, seed=2, X_out=Xd)
+        st, res = g.grbk_solve(ctx, "grbk", X0=Xd, maxit=args.steps * T, seed=2, X_out=Xd)
         ev1.record(stream)
         barrier()
     el_ms = ev0.elapsed_time(ev1)
@@ -284,7 +289,7 @@ def native_arm(args):
         t0 = time.perf_counter()
         for s in range(k_e2e):
             c2 = g.grbk_create(Ah, Bh, Ch, precision="f32", refresh_T=T, check_every=T, stream=stream)
-            g.grbk_solve(c2, "grbk", maxit=T, seed=s, X_out=Xh)
+            g.grbk_solve(c2, "grbk", X0=Xh, maxit=T, seed=s, X_out=Xh)
             g.grbk_destroy(c2)
         barrier()
         e2e_s = time.perf_counter() - t0
@@ -295,8 +300,8 @@ def native_arm(args):
         e2e = {"value": world * k_e2e * T / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4 + Ch.numel() * 4),
                "d2h_bytes_per_step": int(p * q * 8),
-               "note": "per step: grbk_create from pinned host A, B, C (FP32), 64 iterations with one "
-                       "refresh, X copied back to pinned host memory, grbk_destroy"}
+               "note": "per step: grbk_create from pinned host A, B, C (FP32), X0 from pinned host memory, "
+                       "one refresh and 64 iterations, X copied back to pinned host memory, grbk_destroy"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,8 +335,50 @@ def native_arm(args):
         dist.destroy_process_group()
 
 
+def time_to_target(args):
+    """Wall time (device events around one grbk_solve) until ||X - X*|| <= tol ||X*||
+    for the chosen form (FP32 + split-BF16 refresh every 64, tol 1e-4), the plain
+    FP64 form (tol 1e-4 and 1e-6) on the selected workload, and for the
+    200x100 / 80x150 system in FP64 (tol 1e-6)."""
+    import torch
+    import paper_2408_05444_gb300 as g
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"mode": "time_to_target", "workload": args.workload, "variant": "ME-GRBK"}
+
+    def run(A, B, C, Xs, precision, tol, maxit, refresh_T, check):
+        ctx = g.grbk_create(A, B, C, precision=precision, refresh_T=refresh_T, check_every=check,
+                            stop_kind="rse", x_ref=Xs, stream=stream, split_terms=args.split_terms)
+        X = torch.zeros(Xs.shape, dtype=torch.float64, device=dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        st, res = g.grbk_solve(ctx, "grbk", tol=tol, maxit=maxit, seed=1, X_out=X)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        g.grbk_destroy(ctx)
+        return {"precision": precision, "tol": tol, "status": g.grbk_strerror(st), "iters": res["iters"],
+                "seconds": ev0.elapsed_time(ev1) / 1e3, "rse": res["rse"], "refresh_T": refresh_T}
+
+    A1, B1, C1, X1 = workloads.config_small()
+    out["small_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0, 4096)
+    A, B, C, Xs = gen_inputs(args.workload)
+    Ad, Bd, Cd = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev) for x in (A, B, C))
+    Xsd = torch.from_numpy(Xs).to(dev)
+    del A, B, C
+    out["chosen_f32_rse1e-4"] = run(Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, 64, 64)
+    Ad64, Bd64, Cd64 = Ad.double(), Bd.double(), Cd.double()
+    out["plain_f64_rse1e-4"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0, 256)
+    if args.steps >= 2:
+        out["plain_f64_rse1e-6"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-6, 4_000_000, 0, 256)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "ttt":
+        time_to_target(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

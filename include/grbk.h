@@ -94,6 +94,7 @@ typedef struct {
     double iter_kernel_ms;        /* device time of the persistent iteration kernel (CUDA events on the stream) */
     int64_t iter_kernel_launches; /* its launches in this call */
     int64_t launches;             /* all kernel launches made by this call */
+    int32_t x0_rejected;  /* batched solves: 1 when the given X0 had ||C - A X0 B|| >= ||C|| and 0 was used */
     int32_t status;       /* grbk_status of the call */
 } grbk_result;
 
@@ -163,7 +164,9 @@ grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A,
 
 /*
  * grbk_batch_solve -- iterate every system until its own stop rule holds or
- * maxit.  X0s: NULL (all zero) or nsys matrices.  targets: NULL, or nsys
+ * maxit.  X0s: NULL (all zero) or nsys matrices; a given X0 whose residual
+ * ||C - A X0 B||_F is not below ||C||_F (or is not finite) is replaced by the
+ * zero matrix on the device and reported in results[s].x0_rejected.  targets: NULL, or nsys
  * absolute residual targets ||R_s||_F <= targets[s] (discrepancy principle);
  * when given they replace tol.  X_outs: nsys caller matrices (written).
  * results: NULL or nsys entries.  Returns OK when every system stopped by its
@@ -215,6 +218,42 @@ grbk_status grbk_solve_small_noalloc(const float* A, const float* B, const float
                                      int32_t q, int32_t n, int32_t variant, double theta, double alpha,
                                      double tol, int64_t maxit, uint64_t seed, float* X_out,
                                      int64_t* iters_out, double* relres_out, void* stream);
+
+/*
+ * Learned warm start for the colour-image application (Section 6 solves one
+ * deblurring system per channel): a 3-level convolutional U-Net maps a blurred
+ * channel C (h x w, h and w multiples of 4) to an initial iterate
+ * X0 = C + f(C).  The solver's own iteration decides the answer (A, B square
+ * and full rank: X0 changes the iteration count, not the limit); a caller
+ * falls back to X0 = 0 when X0 is non-finite or its residual is larger.
+ *
+ * Architecture for width w: enc 1->w->w | 2x2 avg pool | w->2w->2w | pool |
+ * 2w->4w->4w | nearest 2x up, concat | 6w->2w->2w | up, concat | 3w->w->w |
+ * w->1; 3x3 convolutions with zero padding, ReLU except the last.  Parameters
+ * form one FP32 array, layer by layer in that order, each W[out][in][3][3]
+ * followed by b[out] (grbk_unet_num_params entries); the convolutions use a
+ * BF16 copy of the weights and accumulate in FP32.  Training minimises
+ * mean((X0 - T)^2) with Adam (beta 0.9 / 0.999, eps 1e-8) on the FP32 copy.
+ *
+ * Images are NCHW with one channel: n images of h x w FP32, contiguous, device
+ * pointers.  All calls run on the stream given at creation and return when the
+ * work is done.  Errors: EINVAL (shape, NULL), ENOMEM, ECUDA.
+ */
+typedef struct grbk_unet grbk_unet;
+grbk_status grbk_unet_create(grbk_unet** out, int32_t width, void* stream);
+int64_t grbk_unet_num_params(const grbk_unet* net);
+/* params: FP32 array of grbk_unet_num_params entries, host (on_device = 0) or device; resets Adam */
+grbk_status grbk_unet_set_params(grbk_unet* net, const float* params, int32_t on_device);
+grbk_status grbk_unet_get_params(grbk_unet* net, float* params, int32_t on_device);
+/* X0 = C + f(C) for n images */
+grbk_status grbk_unet_forward(grbk_unet* net, const float* C, int32_t n, int32_t h, int32_t w, float* X0);
+/* loss = mean((X0 - T)^2) and its gradient w.r.t. the parameters (grad may be NULL) */
+grbk_status grbk_unet_loss_grad(grbk_unet* net, const float* C, const float* T, int32_t n, int32_t h, int32_t w,
+                                double* loss, float* grad, int32_t grad_on_device);
+/* one Adam step on mean((X0 - T)^2); loss (host, may be NULL) is the loss before the step */
+grbk_status grbk_unet_train_step(grbk_unet* net, const float* C, const float* T, int32_t n, int32_t h, int32_t w,
+                                 float lr, double* loss);
+void grbk_unet_destroy(grbk_unet* net);
 
 /* Human-readable name of a status code (static storage). */
 const char* grbk_strerror(int32_t status);

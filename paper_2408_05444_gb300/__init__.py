@@ -43,7 +43,8 @@ class grbk_opts(ctypes.Structure):
 class grbk_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("relres", ctypes.c_double), ("rse", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("alpha", ctypes.c_double), ("iter_kernel_ms", ctypes.c_double),
-                ("iter_kernel_launches", ctypes.c_int64), ("launches", ctypes.c_int64), ("status", ctypes.c_int32)]
+                ("iter_kernel_launches", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("x0_rejected", ctypes.c_int32), ("status", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,7 +58,9 @@ class GrbkError(RuntimeError):
 
 EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "grbk_get_residual",
            "grbk_get_rownorms", "grbk_info", "grbk_destroy", "grbk_batch_create", "grbk_batch_solve",
-           "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc"]
+           "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
+           "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
+           "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -98,6 +101,22 @@ def lib():
         L.grbk_solve_small_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, dbl, dbl, dbl, i64, u64, vp,
                                                P(i64), P(dbl), vp]
         L.grbk_solve_small_noalloc.restype = i32
+        L.grbk_unet_create.argtypes = [P(vp), i32, vp]
+        L.grbk_unet_create.restype = i32
+        L.grbk_unet_num_params.argtypes = [vp]
+        L.grbk_unet_num_params.restype = i64
+        L.grbk_unet_set_params.argtypes = [vp, vp, i32]
+        L.grbk_unet_set_params.restype = i32
+        L.grbk_unet_get_params.argtypes = [vp, vp, i32]
+        L.grbk_unet_get_params.restype = i32
+        L.grbk_unet_forward.argtypes = [vp, vp, i32, i32, i32, vp]
+        L.grbk_unet_forward.restype = i32
+        L.grbk_unet_loss_grad.argtypes = [vp, vp, vp, i32, i32, i32, P(dbl), vp, i32]
+        L.grbk_unet_loss_grad.restype = i32
+        L.grbk_unet_train_step.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, P(dbl)]
+        L.grbk_unet_train_step.restype = i32
+        L.grbk_unet_destroy.argtypes = [vp]
+        L.grbk_unet_destroy.restype = None
         L.grbk_strerror.argtypes = [i32]
         L.grbk_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -344,3 +363,90 @@ def grbk_solve_small_noalloc(A, B, C, X_out, variant="grbk", theta=0.5, alpha=0.
                                         float(alpha), float(tol), int(maxit), int(seed), X_out.data_ptr(),
                                         ctypes.byref(it), ctypes.byref(rr), sp)
     return st, it.value, rr.value
+
+
+# ---------------------------------------------------------------------------
+# learned warm start (U-Net)
+# ---------------------------------------------------------------------------
+class UNetHandle:
+    def __init__(self, handle, width):
+        self.handle = handle
+        self.width = width
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().grbk_unet_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _cuda_f32(t):
+    assert _is_torch(t) and t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4 and t.dim() == 3
+    return t.data_ptr()
+
+
+def grbk_unet_create(width=20, stream=None) -> UNetHandle:
+    h = ctypes.c_void_p()
+    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    st = lib().grbk_unet_create(ctypes.byref(h), int(width), sp)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_create")
+    return UNetHandle(h.value, width)
+
+
+def grbk_unet_num_params(net: UNetHandle) -> int:
+    return int(lib().grbk_unet_num_params(net.handle))
+
+
+def grbk_unet_set_params(net: UNetHandle, params):
+    if _is_torch(params):
+        st = lib().grbk_unet_set_params(net.handle, params.data_ptr(), 1 if params.is_cuda else 0)
+    else:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        st = lib().grbk_unet_set_params(net.handle, a.ctypes.data, 0)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_set_params")
+
+
+def grbk_unet_get_params(net: UNetHandle) -> np.ndarray:
+    out = np.zeros(grbk_unet_num_params(net), dtype=np.float32)
+    st = lib().grbk_unet_get_params(net.handle, out.ctypes.data, 0)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_get_params")
+    return out
+
+
+def grbk_unet_forward(net: UNetHandle, C, X0):
+    """C, X0: contiguous FP32 CUDA tensors [n, h, w]."""
+    n, h, w = C.shape
+    st = lib().grbk_unet_forward(net.handle, _cuda_f32(C), n, h, w, _cuda_f32(X0))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_forward")
+
+
+def grbk_unet_loss_grad(net: UNetHandle, C, T, want_grad=True):
+    n, h, w = C.shape
+    loss = ctypes.c_double(0.0)
+    g = np.zeros(grbk_unet_num_params(net), dtype=np.float32) if want_grad else None
+    st = lib().grbk_unet_loss_grad(net.handle, _cuda_f32(C), _cuda_f32(T), n, h, w, ctypes.byref(loss),
+                                   g.ctypes.data if g is not None else None, 0)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_loss_grad")
+    return loss.value, g
+
+
+def grbk_unet_train_step(net: UNetHandle, C, T, lr) -> float:
+    n, h, w = C.shape
+    loss = ctypes.c_double(0.0)
+    st = lib().grbk_unet_train_step(net.handle, _cuda_f32(C), _cuda_f32(T), n, h, w, float(lr), ctypes.byref(loss))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_train_step")
+    return loss.value
+
+
+def grbk_unet_destroy(net: UNetHandle):
+    if net.handle:
+        lib().grbk_unet_destroy(net.handle)
+        net.handle = None

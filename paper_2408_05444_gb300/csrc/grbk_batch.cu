@@ -31,6 +31,7 @@ struct SysDesc {
     int pad;
     long long offA, offB, offR, offX, offRow, offHist, offHistW;
     double F, alpha, stop_S;        // stop when S <= stop_S (< 0: never)
+    double normC2;                  // ||C||_F^2 (judge of a caller's X0)
 };
 
 struct BatchParams {
@@ -53,6 +54,7 @@ struct BatchParams {
     int* flag_out;                  // out: FLAG_*
     int* trace_rows;                // [nsys x trace_len] selected rows, or null
     long long trace_len;
+    int* x0_rejected;               // per system: 1 when the caller's X0 was replaced by 0, or null
     int variant;
     double theta;
     uint64_t seed;
@@ -154,22 +156,38 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
         __syncthreads();
 
         // row norms of R^0: warp per row (Kahan FP32 lanes, FP64 across lanes)
-        for (int i = warp; i < d.m; i += kBW) {
-            float acc = 0.f, comp = 0.f;
-            for (int l = lane; l < d.n; l += 32) {
-                const float x = R[(long long)i * d.ldr + l];
-                const float y = fmaf(x, x, -comp);
-                const float t = acc + y;
-                comp = (t - acc) - y;
-                acc = t;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = warp; i < d.m; i += kBW) {
+                float acc = 0.f, comp = 0.f;
+                for (int l = lane; l < d.n; l += 32) {
+                    const float x = R[(long long)i * d.ldr + l];
+                    const float y = fmaf(x, x, -comp);
+                    const float t = acc + y;
+                    comp = (t - acc) - y;
+                    acc = t;
+                }
+                float hi = acc, lo = -comp;
+                warp_sum_df(hi, lo);
+                if (lane == 0) {
+                    const double tot = (double)hi + (double)lo;
+                    s_s[i] = tot;
+                    s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
+                }
             }
-            const double tot = warp_sum((double)acc - (double)comp);
-            if (lane == 0) {
-                s_s[i] = tot;
-                s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
-            }
+            __syncthreads();
+            if (!P.init_from_x || pass == 1) break;
+            // judge the caller's X0 against X0 = 0: keep it only if ||C - A X0 B|| < ||C||
+            double S0 = 0.0;
+            for (int i = threadIdx.x; i < d.m; i += kBB) S0 += s_s[i];
+            S0 = block_sum_fixed(S0, red);
+            const bool reject = !(S0 < d.normC2);
+            if (threadIdx.x == 0 && P.x0_rejected) P.x0_rejected[sid] = reject ? 1 : 0;
+            if (!reject) break;
+            float* X = P.X + d.offX;
+            for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += kBB) X[e] = 0.f;
+            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += kBB) R[e] = C[e];
+            __syncthreads();
         }
-        __syncthreads();
 
         long long k = 0;
         int nh = 0, flag = FLAG_RUNNING;
@@ -308,8 +326,10 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     comp = (tt - acc) - y;
                     acc = tt;
                 }
-                const double tot = warp_sum((double)acc - (double)comp);
+                float hi = acc, lo = -comp;
+                warp_sum_df(hi, lo);
                 if (lane == 0) {
+                    const double tot = (double)hi + (double)lo;
                     s_s[i] = tot;
                     s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
                 }
@@ -356,6 +376,7 @@ struct grbk_batch {
     double* S;
     int* flags;
     int* trace;
+    int* rejected;
     int chunk;
     long long totA, totB, totR, totX, totRow, totHist, totHistW;
 };
@@ -371,7 +392,7 @@ extern "C" void grbk_batch_destroy(grbk_batch* b)
 {
     if (!b) return;
     void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->A, b->B, b->C, b->R, b->X, b->a, b->pref,
-                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags, b->trace};
+                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags, b->trace, b->rejected};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -433,7 +454,8 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     b->dsys = (SysDesc*)dmalloc(sizeof(SysDesc) * nsys); b->dorder = (int*)dmalloc(4 * nsys);
     b->dqueue = (int*)dmalloc(4); b->iters = (long long*)dmalloc(8 * nsys); b->S = (double*)dmalloc(8 * nsys);
     b->flags = (int*)dmalloc(4 * nsys);
-    if (!b->A || !b->B || !b->C || !b->R || !b->X || !b->a || !b->pref || !b->hist_rows || !b->hist_c ||
+    b->rejected = (int*)dmalloc(4 * nsys);
+    if (!b->rejected || !b->A || !b->B || !b->C || !b->R || !b->X || !b->a || !b->pref || !b->hist_rows || !b->hist_c ||
         !b->hist_w || !b->dsys || !b->dorder || !b->dqueue || !b->iters || !b->S || !b->flags) {
         grbk_batch_destroy(b);
         return GRBK_ENOMEM;
@@ -488,6 +510,7 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
             }
         if (!std::isfinite(c2s)) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
         b->normC2[s] = c2s;
+        d.normC2 = c2s;
         // ||B||_2^2 by power iteration on B B^T (host, FP64)
         std::vector<double> x(d.q, 1.0 / sqrt((double)d.q)), t(d.n), y(d.q);
         double lam = 0.0;
@@ -563,6 +586,7 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
         GRBK_CK(cudaMemsetAsync(b->X, 0, b->totX * 4, st));
     }
     GRBK_CK(cudaMemsetAsync(b->dqueue, 0, 4, st));
+    GRBK_CK(cudaMemsetAsync(b->rejected, 0, 4 * b->nsys, st));
     BatchParams P;
     memset(&P, 0, sizeof(P));
     P.nsys = b->nsys; P.sys = b->dsys; P.order = b->dorder; P.queue = b->dqueue;
@@ -580,6 +604,7 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
         P.trace_len = tlen;
     }
     P.init_from_x = X0s != nullptr;
+    P.x0_rejected = b->rejected;
     int dev = 0, nsm = 0, per_sm = 0;
     GRBK_CK(cudaGetDevice(&dev));
     GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -591,10 +616,11 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     GRBK_CK(cudaGetLastError());
     std::vector<long long> it(b->nsys);
     std::vector<double> S(b->nsys);
-    std::vector<int> fl(b->nsys);
+    std::vector<int> fl(b->nsys), rej(b->nsys);
     GRBK_CK(cudaMemcpyAsync(it.data(), b->iters, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
     GRBK_CK(cudaMemcpyAsync(S.data(), b->S, 8 * b->nsys, cudaMemcpyDeviceToHost, st));
     GRBK_CK(cudaMemcpyAsync(fl.data(), b->flags, 4 * b->nsys, cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(rej.data(), b->rejected, 4 * b->nsys, cudaMemcpyDeviceToHost, st));
     if (tlen > 0)
         GRBK_CK(cudaMemcpyAsync(b->opts.row_trace, b->trace, (size_t)tlen * b->nsys * 4, cudaMemcpyDeviceToHost, st));
     if (X_outs) {
@@ -631,6 +657,7 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
             results[s].rse = NAN;
             results[s].seconds = secs;
             results[s].alpha = b->hsys[s].alpha;
+            results[s].x0_rejected = rej[s];
             results[s].status = ss;
         }
     }
@@ -757,6 +784,7 @@ __global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, c
         d.offA = 0; d.offB = 0; d.offR = 0; d.offX = 0; d.offRow = 0; d.offHist = 0; d.offHistW = 0;
         d.alpha = alpha_in > 0.0 ? alpha_in : 1.0 / lam;
         d.stop_S = tol > 0.0 ? tol * tol * c2 : -1.0;
+        d.normC2 = c2;
         S->lambda = lam;
         S->status = status;
         S->order = 0;

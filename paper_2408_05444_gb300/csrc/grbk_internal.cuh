@@ -141,6 +141,24 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
+// Double-float (hi + lo) sum across the warp, in FP32 arithmetic only: each
+// step adds two (hi, lo) pairs with Knuth's two-sum and renormalises.  Keeps
+// about 44 bits without touching the FP64 pipe (1/64 of the FP32 rate here).
+__device__ __forceinline__ void warp_sum_df(float& hi, float& lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, bh);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+        const float l = __fadd_rn(__fadd_rn(err, lo), bl);
+        hi = __fadd_rn(s, l);
+        lo = __fsub_rn(l, __fsub_rn(hi, s));
+    }
+}
+
 // argmax of (val, idx) pairs; ties go to the smaller index.
 __device__ __forceinline__ void warp_argmax(double& v, long long& i)
 {

@@ -158,9 +158,14 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
                     }
                 }
             }
-            double tot = (sizeof(T) == 8) ? acc_d : ((double)acc_f - (double)comp_f);
-            tot = warp_sum(tot);
-            if (lane == 0) sm_parts[unit] = tot;
+            if constexpr (sizeof(T) == 8) {
+                const double tot = warp_sum(acc_d);
+                if (lane == 0) sm_parts[unit] = tot;
+            } else {
+                float hi = acc_f, lo = -comp_f;  // Kahan state as a double-float
+                warp_sum_df(hi, lo);
+                if (lane == 0) sm_parts[unit] = (double)hi + (double)lo;
+            }
         }
         __syncthreads();
         // finalise the rows of this batch: one thread per row
@@ -269,8 +274,13 @@ __device__ __noinline__ void rows_dot(const T* X, int64_t ld, int64_t r0, int64_
                     }
                 }
             }
-            const double tot = warp_sum((double)acc0 + (double)acc1);
-            if (lane == 0) sm_parts[unit] = tot;
+            if constexpr (sizeof(T) == 8) {
+                const double tot = warp_sum(acc0 + acc1);
+                if (lane == 0) sm_parts[unit] = tot;
+            } else {
+                const float tot = warp_sum_f(acc0 + acc1);
+                if (lane == 0) sm_parts[unit] = (double)tot;
+            }
         }
         __syncthreads();
         for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
@@ -326,15 +336,16 @@ __device__ __noinline__ void cols_gemv(const T* B, int64_t ldb, int64_t q, const
             }
         }
         __syncthreads();
+        T* red = reinterpret_cast<T*>(sm_parts);
         if (rg < RG) {
 #pragma unroll
-            for (int cc = 0; cc < VN; ++cc) sm_parts[((int64_t)rg * ncols + e) * VN + cc] = (double)acc[cc];
+            for (int cc = 0; cc < VN; ++cc) red[((int64_t)rg * ncols + e) * VN + cc] = acc[cc];
         }
         __syncthreads();
         for (int64_t t = threadIdx.x; t < (int64_t)ncols * VN; t += kBlock) {
-            double sum = 0.0;
-            for (int r2 = 0; r2 < RG; ++r2) sum += sm_parts[(int64_t)r2 * ncols * VN + t];
-            __stcg(v + cb * VN + t, (T)sum);
+            T sum = 0;
+            for (int r2 = 0; r2 < RG; ++r2) sum += red[(int64_t)r2 * ncols * VN + t];
+            __stcg(v + cb * VN + t, sum);
         }
         __syncthreads();
     }
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     __shared__ double sm_red[2 * kWarps];
     __shared__ long long sm_redi[kWarps];
     __shared__ int s_ok;
-    __shared__ double s_S, s_rmax, s_t, s_ck;
+    __shared__ double s_S, s_rmax, s_t;
     __shared__ long long s_imax, s_ik;
     __shared__ int s_stop;
 
@@ -631,37 +642,37 @@ __global__ void x_fold_kernel(double* X, int64_t p, int64_t q, const T* A, int64
     X[idx] += acc;
 }
 
-// power iteration pieces for ||B||_2^2: t = B^T x ; y = B t
+// power iteration pieces for ||B||_2^2 on the streaming helpers:
+// t = B^T x (column slabs, x staged in shared memory) ; y = B t (row blocks)
 template <typename T>
-__global__ void bt_x_kernel(const T* B, int64_t q, int64_t n, int64_t ldb, const double* x, double* t)
+__global__ void __launch_bounds__(kBlock) bt_x_kernel(const T* B, int64_t q, int64_t ldb, const T* x, T* t)
 {
-    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n) return;
-    double acc = 0.0;
-    for (int64_t j = 0; j < q; ++j) acc = fma((double)B[j * ldb + l], x[j], acc);
-    t[l] = acc;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ double sm_parts[kPartsCap];
+    T* sx = reinterpret_cast<T*>(dsm);
+    for (int64_t j = threadIdx.x; j < q; j += kBlock) sx[j] = x[j];
+    __syncthreads();
+    cols_gemv<T>(B, ldb, q, sx, t, blockIdx.x, gridDim.x, sm_parts);
 }
 
 template <typename T>
-__global__ void b_t_kernel(const T* B, int64_t q, int64_t n, int64_t ldb, const double* t, double* y)
+__global__ void __launch_bounds__(kBlock) b_t_kernel(const T* B, int64_t q, int64_t ldb, const T* t, T* y)
 {
-    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (row >= q) return;
-    double acc = 0.0;
-    for (int64_t l = lane; l < n; l += 32) acc = fma((double)B[row * ldb + l], t[l], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) y[row] = acc;
+    __shared__ double sm_parts[kPartsCap];
+    int64_t j0, j1;
+    cta_rows(q, blockIdx.x, gridDim.x, j0, j1);
+    rows_dot<T>(B, ldb, j0, j1, t, 2, y, nullptr, sm_parts);
 }
 
-// x <- y / ||y||, lambda = x.y (one block)
-__global__ void power_normalize_kernel(double* x, const double* y, int64_t q, double* lambda)
+// x <- y / ||y||, lambda = x.y (one block, FP64 sums)
+template <typename T>
+__global__ void power_normalize_kernel(T* x, const T* y, int64_t q, double* lambda)
 {
     __shared__ double red[2][32];
     double xy = 0.0, yy = 0.0;
     for (int64_t j = threadIdx.x; j < q; j += blockDim.x) {
-        xy = fma(x[j], y[j], xy);
-        yy = fma(y[j], y[j], yy);
+        xy = fma((double)x[j], (double)y[j], xy);
+        yy = fma((double)y[j], (double)y[j], yy);
     }
     xy = warp_sum(xy);
     yy = warp_sum(yy);
@@ -675,13 +686,14 @@ __global__ void power_normalize_kernel(double* x, const double* y, int64_t q, do
         s_n = sqrt(b);
     }
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) x[j] = y[j] / s_n;
+    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) x[j] = (T)((double)y[j] / s_n);
 }
 
-__global__ void fill_kernel(double* x, int64_t n, double v)
+template <typename T>
+__global__ void fill_kernel(T* x, int64_t n, double v)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = v;
+    if (i < n) x[i] = (T)v;
 }
 
 // dtype conversion / re-pitch, device to device
@@ -991,6 +1003,49 @@ static grbk_status setup_launch_shape(grbk_ctx* c)
     return GRBK_OK;
 }
 
+// lambda = ||B||_2^2 estimated by kPowerIters power iterations x <- B B^T x / ||.||
+// (Rayleigh quotient; a lower bound that converges to ||B||_2^2 from below)
+constexpr int kPowerIters = 100;
+
+template <typename T>
+static grbk_status power_iteration(grbk_ctx* c, double* lambda_out)
+{
+    const int64_t q = c->q, ldb = c->ldb;
+    cudaStream_t st = c->stream;
+    T *x = nullptr, *t = nullptr, *y = nullptr;
+    double* lam = nullptr;
+    if (cudaMalloc(&x, q * sizeof(T)) != cudaSuccess || cudaMalloc(&t, ldb * sizeof(T)) != cudaSuccess ||
+        cudaMalloc(&y, q * sizeof(T)) != cudaSuccess || cudaMalloc(&lam, 8) != cudaSuccess) {
+        cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+        return GRBK_ENOMEM;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t xs = (size_t)q * sizeof(T);
+    grbk_status s = GRBK_OK;
+    if (xs > 48 * 1024 &&
+        cudaFuncSetAttribute(bt_x_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
+        s = GRBK_EINVAL;
+    const int gcols = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, (ldb / (16 / (int64_t)sizeof(T)) + 31) / 32));
+    const int grows = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, q));
+    if (s == GRBK_OK) {
+        fill_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(x, q, 1.0 / sqrt((double)q));
+        for (int it = 0; it < kPowerIters; ++it) {
+            bt_x_kernel<T><<<gcols, kBlock, xs, st>>>((const T*)c->B, q, ldb, x, t);
+            b_t_kernel<T><<<grows, kBlock, 0, st>>>((const T*)c->B, q, ldb, t, y);
+            power_normalize_kernel<T><<<1, 1024, 0, st>>>(x, y, q, lam);
+        }
+        double hl = 0.0;
+        if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&hl, lam, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            s = GRBK_ECUDA;
+        *lambda_out = hl;
+    }
+    cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+    return s;
+}
+
 extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk_mat* B,
                                    const grbk_mat* C, const grbk_opts* opts)
 {
@@ -1086,31 +1141,9 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
 
     // ||B||_2^2 by power iteration on B B^T with a Rayleigh quotient
     {
-        double *x = nullptr, *t = nullptr, *y = nullptr, *lam = nullptr;
-        if (cudaMalloc(&x, q * 8) != cudaSuccess || cudaMalloc(&t, n * 8) != cudaSuccess ||
-            cudaMalloc(&y, q * 8) != cudaSuccess || cudaMalloc(&lam, 8) != cudaSuccess) {
-            cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
-            grbk_destroy(c);
-            return GRBK_ENOMEM;
-        }
-        fill_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(x, q, 1.0 / sqrt((double)q));
-        const int iters = 300;
-        for (int itp = 0; itp < iters; ++itp) {
-            if (c->prec == GRBK_F64) {
-                bt_x_kernel<double><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const double*)c->B, q, n, c->ldb, x, t);
-                b_t_kernel<double><<<(unsigned)((q * 32 + 255) / 256), 256, 0, st>>>((const double*)c->B, q, n, c->ldb, t, y);
-            } else {
-                bt_x_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const float*)c->B, q, n, c->ldb, x, t);
-                b_t_kernel<float><<<(unsigned)((q * 32 + 255) / 256), 256, 0, st>>>((const float*)c->B, q, n, c->ldb, t, y);
-            }
-            power_normalize_kernel<<<1, 1024, 0, st>>>(x, y, q, lam);
-        }
         double hl = 0.0;
-        cudaError_t e1 = cudaGetLastError();
-        cudaError_t e2 = cudaMemcpyAsync(&hl, lam, 8, cudaMemcpyDeviceToHost, st);
-        cudaError_t e3 = cudaStreamSynchronize(st);
-        cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+        grbk_status ps = (c->prec == GRBK_F64) ? power_iteration<double>(c, &hl) : power_iteration<float>(c, &hl);
+        if (ps != GRBK_OK) { grbk_destroy(c); return ps; }
         c->lambda = hl;
         if (!(hl > 0.0)) { grbk_destroy(c); return GRBK_EINVAL; }
         if (o.alpha > 0.0) {
