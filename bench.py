@@ -58,9 +58,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--mode", default="rate", choices=["rate", "ttt"],
+    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=3)
+    ap.add_argument("--train-images", type=int, default=20000)
+    ap.add_argument("--train-side", type=int, default=128)
+    ap.add_argument("--eval-images", type=int, default=64)
+    ap.add_argument("--eval-side", type=int, default=512)
+    ap.add_argument("--epochs", type=int, default=2)
     return ap.parse_args()
 
 
@@ -374,8 +379,96 @@ def time_to_target(args):
     print(json.dumps(out), flush=True)
 
 
+def warmstart_bench(args):
+    """Learned warm start on batched colour-image restoration: generate
+    train-images seeded images (train-side^2, 3 channels each), restore every
+    channel with ME-GRBK (theta 0.8) to the discrepancy stop, train the U-Net
+    (width 20) on (blurred channel, restoration) pairs, then restore
+    eval-images held-out eval-side^2 RGB images (seeds disjoint from training)
+    from X0 = 0 and from X0 = U-Net(C): iterations, device time, PSNR."""
+    import torch
+    import paper_2408_05444_gb300 as g
+    from paper_2408_05444_gb300 import warmstart as ws
+    dev = torch.device("cuda", 0)
+    t_all = time.perf_counter()
+    import os as _os
+    procs = max(1, min(16, (_os.cpu_count() or 2) - 1))
+    Cs_t, Ts_t = [], []
+    chunk = 1024
+    gen_s = solve_s = 0.0
+    n_iters_train = 0
+    for c0 in range(0, args.train_images, chunk):
+        nimg = min(chunk, args.train_images - c0)
+        t0 = time.perf_counter()
+        sy = workloads.blur_systems(n_images=nimg, min_side=args.train_side, max_side=args.train_side, seed=11,
+                                    first=c0, processes=procs)
+        gen_s += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        Xr, res = ws.restore([q["A"] for q in sy], [q["B"] for q in sy], [q["C"] for q in sy],
+                             [np.linalg.norm(q["E"]) for q in sy], theta=0.8, seed=c0)
+        solve_s += time.perf_counter() - t0
+        n_iters_train += sum(r["iters"] for r in res)
+        Cs_t.append(torch.tensor(np.stack([q["C"] for q in sy]), dtype=torch.float32, device=dev))
+        Ts_t.append(torch.tensor(np.stack(Xr), dtype=torch.float32, device=dev))
+    C_t, T_t = torch.cat(Cs_t), torch.cat(Ts_t)
+    del Cs_t, Ts_t
+    net = ws.make_net(20, seed=0)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    losses = ws.train(net, C_t, T_t, epochs=args.epochs, batch=64, lr=2e-3)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    del C_t, T_t
+
+    ev = workloads.blur_systems(n_images=args.eval_images, min_side=args.eval_side, max_side=args.eval_side,
+                                seed=12, processes=procs)
+    As, Bs, Cs = [q["A"] for q in ev], [q["B"] for q in ev], [q["C"] for q in ev]
+    nn_ = [np.linalg.norm(q["E"]) for q in ev]
+    clean = [q["X"] for q in ev]
+
+    def psnr(X, ref):
+        return 10 * np.log10(1.0 / np.mean((np.clip(X, 0, 1) - ref) ** 2))
+
+    def timed_restore(X0s):
+        b = g.grbk_batch_create(As, Bs, Cs)
+        X = [np.zeros((A.shape[1], B.shape[0])) for A, B in zip(As, Bs)]
+        targets = ws.DISCREPANCY_TAU * np.asarray(nn_)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        st, res = g.grbk_batch_solve(b, "grbk", theta=0.8, X0s=X0s, targets=targets, maxit=5_000_000, seed=7,
+                                     X_outs=X)
+        el = time.perf_counter() - t0
+        return X, res, el
+
+    X0z, r0, t0s = timed_restore(None)
+    torch.cuda.synchronize(dev)
+    tw = time.perf_counter()
+    X0n = ws.warm_starts(net, Cs)
+    torch.cuda.synchronize(dev)
+    t_net = time.perf_counter() - tw
+    Xw, rw, tws = timed_restore([x.astype(np.float64) for x in X0n])
+    it0 = np.array([r["iters"] for r in r0])
+    itw = np.array([r["iters"] for r in rw])
+    out = {"mode": "warmstart", "train_images": args.train_images, "train_side": args.train_side,
+           "train_systems": 3 * args.train_images, "train_target_iters": int(n_iters_train),
+           "data_gen_s": gen_s, "target_solve_s": solve_s, "train_s": train_s, "epochs": args.epochs,
+           "final_loss": float(np.mean(losses[-20:])) if losses else None,
+           "eval_images": args.eval_images, "eval_side": args.eval_side, "eval_systems": len(ev),
+           "x0_zero": {"iters_mean": float(it0.mean()), "iters_max": int(it0.max()), "solve_s": t0s,
+                       "psnr_db": float(np.mean([psnr(x, c) for x, c in zip(X0z, clean)]))},
+           "x0_unet": {"iters_mean": float(itw.mean()), "iters_max": int(itw.max()), "solve_s": tws,
+                       "unet_forward_s": t_net, "rejected": int(sum(r["x0_rejected"] for r in rw)),
+                       "psnr_db": float(np.mean([psnr(x, c) for x, c in zip(Xw, clean)]))},
+           "blurred_psnr_db": float(np.mean([psnr(C, c) for C, c in zip(Cs, clean)])),
+           "total_s": time.perf_counter() - t_all}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "warmstart":
+        warmstart_bench(args)
+        return
     if args.mode == "ttt":
         time_to_target(args)
         return

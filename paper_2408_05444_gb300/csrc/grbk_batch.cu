@@ -97,6 +97,97 @@ __device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh)
     __syncthreads();
 }
 
+// Set-up of one system by one CTA: a_i = ||A_i||^2 (FP64, ascending columns) and
+// their running sums, F = ||A||_F^2, ||C||_F^2, lambda ~ ||B||_2^2 from 200 power
+// iterations x <- B B^T x / ||.|| (Rayleigh quotient), and a non-finite flag.
+// x, t, y: FP64 work vectors of q, n, q entries.  Results valid in thread 0.
+struct SetupOut {
+    double F, normC2, lambda;
+    int bad;
+};
+
+__device__ SetupOut system_setup(const float* A, int lda, const float* B, int ldb, const float* C, int ldr, int m,
+                                 int p, int q, int n, double* a, double* pref, double* x, double* t, double* y,
+                                 double* red, int* s_bad)
+{
+    if (threadIdx.x == 0) *s_bad = 0;
+    __syncthreads();
+    int mybad = 0;
+    for (int i = threadIdx.x; i < m; i += kBB) {
+        double acc = 0.0;
+        for (int c = 0; c < p; ++c) {
+            const double v = (double)A[(long long)i * lda + c];
+            if (!isfinite(v)) mybad = 1;
+            acc = __dadd_rn(acc, __dmul_rn(v, v));
+        }
+        a[i] = acc;
+    }
+    double c2 = 0.0;
+    for (long long e = threadIdx.x; e < (long long)m * n; e += kBB) {
+        const double v = (double)C[(e / n) * ldr + e % n];
+        if (!isfinite(v)) mybad = 1;
+        c2 = fma(v, v, c2);
+    }
+    for (long long e = threadIdx.x; e < (long long)q * n; e += kBB)
+        if (!isfinite(B[(e / n) * ldb + e % n])) mybad = 1;
+    if (mybad) atomicOr(s_bad, 1);
+    c2 = block_sum_fixed(c2, red);
+    SetupOut o;
+    o.normC2 = c2;
+    o.F = 0.0;
+    if (threadIdx.x == 0) {
+        double run = 0.0;
+        for (int i = 0; i < m; ++i) { run += a[i]; pref[i] = run; }
+        o.F = run;
+    }
+    for (int j = threadIdx.x; j < q; j += kBB) x[j] = 1.0 / sqrt((double)q);
+    __syncthreads();
+    double lam = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        for (int l = threadIdx.x; l < n; l += kBB) {
+            double acc = 0.0;
+            for (int j = 0; j < q; ++j) acc = fma((double)B[(long long)j * ldb + l], x[j], acc);
+            t[l] = acc;
+        }
+        __syncthreads();
+        double xy = 0.0, yy = 0.0;
+        for (int j = threadIdx.x; j < q; j += kBB) {
+            double acc = 0.0;
+            for (int l = 0; l < n; ++l) acc = fma((double)B[(long long)j * ldb + l], t[l], acc);
+            y[j] = acc;
+            xy = fma(x[j], acc, xy);
+            yy = fma(acc, acc, yy);
+        }
+        xy = block_sum_fixed(xy, red);
+        yy = block_sum_fixed(yy, red);
+        lam = xy;
+        const double nrm = sqrt(yy);
+        for (int j = threadIdx.x; j < q; j += kBB) x[j] = nrm > 0.0 ? y[j] / nrm : 0.0;
+        __syncthreads();
+    }
+    o.lambda = lam;
+    o.bad = *s_bad;
+    return o;
+}
+
+// one CTA per system: scalars[s] = {F, ||C||^2, lambda, bad}
+__global__ void __launch_bounds__(kBB) batch_setup_kernel(const SysDesc* sys, const float* A, const float* B,
+                                                          const float* C, double* a, double* pref, double* scalars)
+{
+    __shared__ double x[kMaxSide], t[kMaxSide], y[kMaxSide];
+    __shared__ double red[2 * kBW];
+    __shared__ int bad;
+    const SysDesc d = sys[blockIdx.x];
+    const SetupOut o = system_setup(A + d.offA, d.lda, B + d.offB, d.ldb, C + d.offR, d.ldr, d.m, d.p, d.q, d.n,
+                                    a + d.offRow, pref + d.offRow, x, t, y, red, &bad);
+    if (threadIdx.x == 0) {
+        scalars[4 * blockIdx.x + 0] = o.F;
+        scalars[4 * blockIdx.x + 1] = o.normC2;
+        scalars[4 * blockIdx.x + 2] = o.lambda;
+        scalars[4 * blockIdx.x + 3] = (double)o.bad;
+    }
+}
+
 __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
 {
     __shared__ double s_s[kMaxSide];          // ||R_i||^2
@@ -465,7 +556,6 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     cudaMemsetAsync(b->B, 0, oB * 4, st);
     cudaMemsetAsync(b->C, 0, oR * 4, st);
     b->normC2.resize(nsys);
-    std::vector<double> ha, hp;
     for (int s = 0; s < nsys; ++s) {
         SysDesc& d = b->hsys[s];
         grbk_status e;
@@ -476,69 +566,36 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
             return e;
         }
     }
-    // host-side set-up scalars from the FP32 copies
-    std::vector<float> hA(oA), hB(oB), hC(oR);
-    if (cudaMemcpyAsync(hA.data(), b->A, oA * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(hB.data(), b->B, oB * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(hC.data(), b->C, oR * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        grbk_batch_destroy(b);
-        return GRBK_ECUDA;
-    }
-    ha.resize(oRow);
-    hp.resize(oRow);
-    for (int s = 0; s < nsys; ++s) {
-        SysDesc& d = b->hsys[s];
-        double F = 0.0;
-        for (int i = 0; i < d.m; ++i) {
-            double acc = 0.0;
-            for (int c2 = 0; c2 < d.p; ++c2) {
-                const double x = hA[d.offA + (long long)i * d.lda + c2];
-                acc += x * x;
-            }
-            ha[d.offRow + i] = acc;
-            F += acc;
-            hp[d.offRow + i] = F;
+    // per-system set-up on the device (one CTA per system)
+    {
+        std::vector<double> sc(4 * (size_t)nsys);
+        double* dsc = (double*)dmalloc(sizeof(double) * 4 * nsys);
+        if (!dsc) { grbk_batch_destroy(b); return GRBK_ENOMEM; }
+        cudaError_t e = cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) {
+            batch_setup_kernel<<<nsys, kBB, 0, st>>>(b->dsys, b->A, b->B, b->C, b->a, b->pref, dsc);
+            e = cudaGetLastError();
         }
-        if (!(F > 0.0) || !std::isfinite(F)) { grbk_batch_destroy(b); return F > 0.0 ? GRBK_ENONFINITE : GRBK_EINVAL; }
-        d.F = F;
-        double c2s = 0.0;
-        for (int i = 0; i < d.m; ++i)
-            for (int l = 0; l < d.n; ++l) {
-                const double x = hC[d.offR + (long long)i * d.ldr + l];
-                c2s += x * x;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc.data(), dsc, sizeof(double) * 4 * nsys, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dsc);
+        if (e != cudaSuccess) { grbk_batch_destroy(b); return GRBK_ECUDA; }
+        for (int s = 0; s < nsys; ++s) {
+            SysDesc& d = b->hsys[s];
+            const double F = sc[4 * s], c2s = sc[4 * s + 1], lam = sc[4 * s + 2];
+            if (sc[4 * s + 3] != 0.0) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
+            if (!(F > 0.0) || !(lam > 0.0)) { grbk_batch_destroy(b); return GRBK_EINVAL; }
+            d.F = F;
+            b->normC2[s] = c2s;
+            d.normC2 = c2s;
+            if (o.alpha > 0.0) {
+                if (!(o.alpha * lam < 2.0 * (1.0 + 1e-9))) { grbk_batch_destroy(b); return GRBK_EINVAL; }
+                d.alpha = o.alpha;
+            } else {
+                d.alpha = 1.0 / lam;
             }
-        if (!std::isfinite(c2s)) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
-        b->normC2[s] = c2s;
-        d.normC2 = c2s;
-        // ||B||_2^2 by power iteration on B B^T (host, FP64)
-        std::vector<double> x(d.q, 1.0 / sqrt((double)d.q)), t(d.n), y(d.q);
-        double lam = 0.0;
-        for (int it = 0; it < 200; ++it) {
-            for (int l = 0; l < d.n; ++l) t[l] = 0.0;
-            for (int j = 0; j < d.q; ++j)
-                for (int l = 0; l < d.n; ++l) t[l] += (double)hB[d.offB + (long long)j * d.ldb + l] * x[j];
-            double yy = 0.0, xy = 0.0;
-            for (int j = 0; j < d.q; ++j) {
-                double acc = 0.0;
-                for (int l = 0; l < d.n; ++l) acc += (double)hB[d.offB + (long long)j * d.ldb + l] * t[l];
-                y[j] = acc;
-                yy += acc * acc;
-                xy += x[j] * acc;
-            }
-            lam = xy;
-            const double nrm = sqrt(yy);
-            if (!(nrm > 0.0)) break;
-            for (int j = 0; j < d.q; ++j) x[j] = y[j] / nrm;
+            d.stop_S = -1.0;
         }
-        if (!(lam > 0.0)) { grbk_batch_destroy(b); return GRBK_EINVAL; }
-        if (o.alpha > 0.0) {
-            if (!(o.alpha * lam < 2.0 * (1.0 + 1e-9))) { grbk_batch_destroy(b); return GRBK_EINVAL; }
-            d.alpha = o.alpha;
-        } else {
-            d.alpha = 1.0 / lam;
-        }
-        d.stop_S = -1.0;
     }
     // longest-processing-time order: largest R first
     b->order.resize(nsys);
@@ -546,9 +603,7 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
         return (long long)b->hsys[x].m * b->hsys[x].n > (long long)b->hsys[y].m * b->hsys[y].n;
     });
-    if (cudaMemcpyAsync(b->a, ha.data(), oRow * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(b->pref, hp.data(), oRow * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(b->dorder, b->order.data(), 4 * nsys, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(b->dorder, b->order.data(), 4 * nsys, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         grbk_batch_destroy(b);
         return GRBK_ECUDA;
@@ -718,73 +773,23 @@ __global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, c
 {
     __shared__ double red[2 * kBW];
     __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    int mybad = 0;
-    for (int i = threadIdx.x; i < m; i += kBB) {
-        double acc = 0.0;
-        for (int c = 0; c < p; ++c) {
-            const double x = (double)A[(long long)i * p + c];
-            if (!isfinite(x)) mybad = 1;
-            acc = __dadd_rn(acc, __dmul_rn(x, x));
-        }
-        S->a[i] = acc;
-    }
-    double c2 = 0.0;
-    for (long long e = threadIdx.x; e < (long long)m * n; e += kBB) {
-        const double x = (double)C[e];
-        if (!isfinite(x)) mybad = 1;
-        c2 = fma(x, x, c2);
-    }
-    for (long long e = threadIdx.x; e < (long long)q * n; e += kBB)
-        if (!isfinite(B[e])) mybad = 1;
-    if (mybad) atomicOr(&bad, 1);
-    c2 = block_sum_fixed(c2, red);
-    if (threadIdx.x == 0) {
-        double run = 0.0;
-        for (int i = 0; i < m; ++i) { run += S->a[i]; S->pref[i] = run; }
-        S->desc.F = run;
-        S->normC2 = c2;
-    }
-    // power iteration: x <- B B^T x / ||B B^T x||, lambda = x . B B^T x
-    for (int j = threadIdx.x; j < q; j += kBB) S->px[j] = 1.0 / sqrt((double)q);
-    __syncthreads();
-    double lam = 0.0;
-    for (int it = 0; it < 200; ++it) {
-        for (int l = threadIdx.x; l < n; l += kBB) {
-            double acc = 0.0;
-            for (int j = 0; j < q; ++j) acc = fma((double)B[(long long)j * n + l], S->px[j], acc);
-            S->pt[l] = acc;
-        }
-        __syncthreads();
-        double xy = 0.0, yy = 0.0;
-        for (int j = threadIdx.x; j < q; j += kBB) {
-            double acc = 0.0;
-            for (int l = 0; l < n; ++l) acc = fma((double)B[(long long)j * n + l], S->pt[l], acc);
-            S->py[j] = acc;
-            xy = fma(S->px[j], acc, xy);
-            yy = fma(acc, acc, yy);
-        }
-        xy = block_sum_fixed(xy, red);
-        yy = block_sum_fixed(yy, red);
-        lam = xy;
-        const double nrm = sqrt(yy);
-        for (int j = threadIdx.x; j < q; j += kBB) S->px[j] = nrm > 0.0 ? S->py[j] / nrm : 0.0;
-        __syncthreads();
-    }
+    const SetupOut o = system_setup(A, p, B, n, C, n, m, p, q, n, S->a, S->pref, S->px, S->pt, S->py, red, &bad);
     if (threadIdx.x == 0) {
         int status = 0;
-        if (bad) status = GRBK_ENONFINITE;
-        else if (!(S->desc.F > 0.0) || !(lam > 0.0)) status = GRBK_EINVAL;
+        const double lam = o.lambda;
+        if (o.bad) status = GRBK_ENONFINITE;
+        else if (!(o.F > 0.0) || !(lam > 0.0)) status = GRBK_EINVAL;
         else if (alpha_in > 0.0 && !(alpha_in * lam < 2.0 * (1.0 + 1e-9))) status = GRBK_EINVAL;
         SysDesc& d = S->desc;
         d.m = m; d.p = p; d.q = q; d.n = n;
         d.lda = p; d.ldb = n; d.ldr = n;
         d.pad = 0;
         d.offA = 0; d.offB = 0; d.offR = 0; d.offX = 0; d.offRow = 0; d.offHist = 0; d.offHistW = 0;
+        d.F = o.F;
         d.alpha = alpha_in > 0.0 ? alpha_in : 1.0 / lam;
-        d.stop_S = tol > 0.0 ? tol * tol * c2 : -1.0;
-        d.normC2 = c2;
+        d.stop_S = tol > 0.0 ? tol * tol * o.normC2 : -1.0;
+        d.normC2 = o.normC2;
+        S->normC2 = o.normC2;
         S->lambda = lam;
         S->status = status;
         S->order = 0;

@@ -108,11 +108,11 @@ def duplicated(m, p, q, n, seed=4, how="rows"):
 # Colour images (Section 6 application) -- synthetic stand-ins
 # ---------------------------------------------------------------------------
 
-def _polygon_mask(h, w, cx, cy, radii, phase):
+def _polygon_mask(yy, xx, cx, cy, radii, phase):
     """Star-shaped polygon around (cx, cy): vertex k at angle phase + 2 pi k / K
     and radius radii[k]; a pixel is inside when its radius is below the
-    piecewise-linear interpolation of the vertex radii at its angle."""
-    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    piecewise-linear interpolation of the vertex radii at its angle.
+    yy, xx: pixel coordinates of the region to test."""
     dx, dy = xx - cx, yy - cy
     ang = (np.arctan2(dy, dx) - phase) % (2 * np.pi)
     K = len(radii)
@@ -137,12 +137,20 @@ def color_image(g, h, w):
         cx, cy = g.uniform(0, w), g.uniform(0, h)
         base = g.uniform(0.08, 0.35) * min(h, w)
         radii = base * g.uniform(0.5, 1.5, K)
-        mask = _polygon_mask(h, w, cx, cy, radii, g.uniform(0, 2 * np.pi))
+        phase = g.uniform(0, 2 * np.pi)
         col = g.uniform(0, 1, 3)
         gx, gy = g.uniform(-0.3, 0.3, 2)
+        # only the polygon's bounding box can be inside it
+        rmax = float(np.max(radii))
+        y0, y1 = max(0, int(np.floor(cy - rmax))), min(h, int(np.ceil(cy + rmax)) + 1)
+        x0, x1 = max(0, int(np.floor(cx - rmax))), min(w, int(np.ceil(cx + rmax)) + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        sy, sx = yy[y0:y1, x0:x1], xx[y0:y1, x0:x1]
+        mask = _polygon_mask(sy, sx, cx, cy, radii, phase)
         for c in range(3):
-            val = col[c] + gx * (xx - cx) / w + gy * (yy - cy) / h
-            img[:, :, c] = np.where(mask, val, img[:, :, c])
+            region = img[y0:y1, x0:x1, c]
+            region[mask] = (col[c] + gx * (sx - cx) / w + gy * (sy - cy) / h)[mask]
     return np.clip(img, 0.0, 1.0)
 
 
@@ -160,30 +168,62 @@ def gaussian_toeplitz(size, band, sigma):
     return T
 
 
-def blur_systems(n_images=64, seed=4, min_side=128, max_side=512, noise=1e-3,
-                 mild=False):
-    """Per image: sides h, w uniform in [min_side, max_side] (multiples of 16),
-    band b in {7, 9, ..., 15}, sigma_blur in [1.5, 3]; A (h x h) and B (w x w)
-    symmetric Toeplitz blurs; per channel C = A X B + N(0, noise^2).
+def _image_params(index, seed, min_side, max_side):
+    """Sizes, blur and image of image `index` from its own stream
+    (seed sequence [base, seed, index, 0]); the image is rounded to FP32."""
+    g = np.random.default_rng([BASE_SEED, int(seed), int(index), 0])
+    h = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
+    w = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
+    band = int(g.choice([7, 9, 11, 13, 15]))
+    sig = float(g.uniform(1.5, 3.0))
+    img = color_image(g, h, w).astype(np.float32)
+    return h, w, band, sig, img
 
-    Returns a list of dicts with keys A, B, C, X (clean channel), E (noise),
-    image index and channel.  ``mild`` replaces each blur T by (I + T) / 2
-    (a well-conditioned control system)."""
-    g = rng(seed)
-    systems = []
-    for im in range(n_images):
-        h = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
-        w = int(g.integers(min_side // 16, max_side // 16 + 1)) * 16
-        band = int(g.choice([7, 9, 11, 13, 15]))
-        sig = float(g.uniform(1.5, 3.0))
-        A = gaussian_toeplitz(h, band, sig)
-        B = gaussian_toeplitz(w, band, sig)
-        if mild:
-            A = 0.5 * (np.eye(h) + A)
-            B = 0.5 * (np.eye(w) + B)
-        img = color_image(g, h, w)
-        for c in range(3):
-            X = img[:, :, c]
-            E = g.standard_normal((h, w)) * noise
-            systems.append(dict(A=A, B=B, C=A @ X @ B + E, X=X, E=E, image=im, channel=c))
-    return systems
+
+def _image_job(args):
+    return _image_params(*args)
+
+
+def _systems_from(index, seed, noise, mild, params):
+    h, w, band, sig, img = params
+    A = gaussian_toeplitz(h, band, sig)
+    B = gaussian_toeplitz(w, band, sig)
+    if mild:
+        A = 0.5 * (np.eye(h) + A)
+        B = 0.5 * (np.eye(w) + B)
+    gn = np.random.default_rng([BASE_SEED, int(seed), int(index), 1])
+    out = []
+    for c in range(3):
+        X = img[:, :, c].astype(np.float64)
+        E = gn.standard_normal((h, w)) * noise
+        out.append(dict(A=A, B=B, C=A @ X @ B + E, X=X, E=E, image=int(index), channel=c))
+    return out
+
+
+def blur_image_systems(index, seed=4, min_side=128, max_side=512, noise=1e-3, mild=False):
+    """The three channel systems of image `index`: sides h, w uniform in
+    [min_side, max_side] (multiples of 16), band b in {7, 9, ..., 15},
+    sigma_blur in [1.5, 3]; A (h x h) and B (w x w) symmetric Toeplitz blurs;
+    per channel C = A X B + N(0, noise^2).  Each image has its own random
+    streams, so images can be generated in any order or in parallel.
+    ``mild`` replaces each blur T by (I + T) / 2 (a well-conditioned control)."""
+    return _systems_from(index, seed, noise, mild, _image_params(index, seed, min_side, max_side))
+
+
+def blur_systems(n_images=64, seed=4, min_side=128, max_side=512, noise=1e-3, mild=False, first=0,
+                 processes=1):
+    """Systems of images first .. first + n_images - 1 (3 per image, see
+    blur_image_systems), as a list of dicts with keys A, B, C, X (clean
+    channel), E (noise), image, channel.  processes > 1 draws the images in a
+    spawn-started process pool (identical result)."""
+    jobs = [(first + i, seed, min_side, max_side) for i in range(n_images)]
+    if processes > 1 and n_images > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            params = pool.map(_image_job, jobs, chunksize=max(1, n_images // (4 * processes)))
+    else:
+        params = [_image_job(j) for j in jobs]
+    out = []
+    for (idx, *_), pr in zip(jobs, params):
+        out += _systems_from(idx, seed, noise, mild, pr)
+    return out
