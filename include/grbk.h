@@ -75,7 +75,7 @@ typedef struct {
     int32_t refresh_T;    /* recompute R = C - A X B every refresh_T iterations; 0 = never */
     double alpha;         /* step; <= 0 selects 1/||B||_2^2 (power iteration on B B^T) */
     int32_t stop_kind;    /* grbk_stop */
-    int32_t split_terms;  /* F32 refresh: 2 (hi+lo) or 3 (hi+mid+lo) BF16 terms; 0 = 3 */
+    int32_t split_terms;  /* F32 refresh: 2 (hi+lo, default) or 3 (hi+mid+lo) BF16 terms; 0 = 2 */
     const grbk_mat* x_ref;/* reference solution for GRBK_STOP_RSE and result.rse; may be NULL */
     int32_t* row_trace;   /* host buffer: selected row of iteration k, k < trace_len; may be NULL */
     double* s_trace;      /* host buffer: ||R^k||_F^2 before iteration k, k < trace_len; may be NULL */
@@ -188,7 +188,8 @@ void grbk_batch_destroy(grbk_batch* batch);
  *
  * It runs the batched kernel on a single system (system index 0 for the
  * Philox counter), so its arithmetic is that of grbk_batch_solve.  All working
- * memory (residual, row norms, recorded update terms, counters) lives in one
+ * memory (residual, padded copies of A and B, row norms, recorded update
+ * terms, counters) lives in one
  * static device array of GRBK_NOALLOC_SCRATCH_BYTES bytes that every GPU which
  * loads this library holds until the process exits.  Limits: m, p, q, n each
  * at most GRBK_NOALLOC_MAX_SIDE; larger sizes return GRBK_EINVAL.
@@ -213,7 +214,7 @@ void grbk_batch_destroy(grbk_batch* batch);
  * variant, theta, alpha), ENONFINITE (NaN/Inf input or residual), ECUDA.
  */
 #define GRBK_NOALLOC_MAX_SIDE 512
-#define GRBK_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+#define GRBK_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
 grbk_status grbk_solve_small_noalloc(const float* A, const float* B, const float* C, int32_t m, int32_t p,
                                      int32_t q, int32_t n, int32_t variant, double theta, double alpha,
                                      double tol, int64_t maxit, uint64_t seed, float* X_out,
@@ -254,6 +255,17 @@ grbk_status grbk_unet_loss_grad(grbk_unet* net, const float* C, const float* T, 
 grbk_status grbk_unet_train_step(grbk_unet* net, const float* C, const float* T, int32_t n, int32_t h, int32_t w,
                                  float lr, double* loss);
 void grbk_unet_destroy(grbk_unet* net);
+
+/*
+ * grbk_barrier_selftest -- no counterpart in the paper: exercises the bounded
+ * grid barrier the iteration kernel uses between its phases.  A small
+ * cooperative grid (at most 8 CTAs) meets at one barrier with a spin budget of
+ * about 0.1 s.  absent_cta < 0: every CTA arrives, returns GRBK_OK.
+ * absent_cta = c >= 0: CTA c leaves without arriving, the others give up when
+ * the budget runs out and the call returns GRBK_ETIMEOUT; the CUDA context
+ * stays usable.  Nothing faults or hangs in either case.
+ */
+grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* grbk_strerror(int32_t status);

@@ -60,7 +60,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_get_rownorms", "grbk_info", "grbk_destroy", "grbk_batch_create", "grbk_batch_solve",
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
-           "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy"]
+           "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -117,6 +117,8 @@ def lib():
         L.grbk_unet_train_step.restype = i32
         L.grbk_unet_destroy.argtypes = [vp]
         L.grbk_unet_destroy.restype = None
+        L.grbk_barrier_selftest.argtypes = [i32, vp]
+        L.grbk_barrier_selftest.restype = i32
         L.grbk_strerror.argtypes = [i32]
         L.grbk_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -450,3 +452,9 @@ def grbk_unet_destroy(net: UNetHandle):
     if net.handle:
         lib().grbk_unet_destroy(net.handle)
         net.handle = None
+
+
+def grbk_barrier_selftest(absent_cta=-1, stream=None) -> int:
+    """Status of one bounded grid barrier; absent_cta >= 0 leaves that CTA out."""
+    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    return int(lib().grbk_barrier_selftest(int(absent_cta), sp))

@@ -76,8 +76,13 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red)
     return t;
 }
 
-// X += sum_t c_t A_{i_t}^T w_t over the recorded terms (FP32)
-__device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh)
+// X += sum_t c_t A_{i_t}^T w_t over the recorded terms (FP32), as a small GEMM
+// over tiles of 64 rows x 128 columns of X with the chunk's terms staged in
+// shared memory: sa[t][r] = c_t A[i_t][r0 + r], sw[t][j] = w_t[j0 + j].
+constexpr int kFoldRows = 64, kFoldCols = 128, kMaxChunk = 64;
+constexpr int kFoldSmemBytes = kMaxChunk * (kFoldRows + kFoldCols) * 4;
+
+__device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh, float* fsm)
 {
     if (nh <= 0) return;
     const float* A = P.A + d.offA;
@@ -85,16 +90,80 @@ __device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh)
     const float* hc = P.hist_c + d.offHist;
     const float* hw = P.hist_w + d.offHistW;
     float* X = P.X + d.offX;
-    const int total = d.p * d.q;
+    float* sa = fsm;                          // [nh][kFoldRows]
+    float* sw = fsm + kMaxChunk * kFoldRows;  // [nh][kFoldCols]
+    const int tr = threadIdx.x / 16, tcol = threadIdx.x % 16;  // rows 2tr, 2tr+1; cols tcol + 16k
     __syncthreads();
-    for (int e = threadIdx.x; e < total; e += kBB) {
-        const int rr = e / d.q, j = e % d.q;
-        float acc = 0.f;
-        for (int t = 0; t < nh; ++t)
-            acc = fmaf(hc[t] * A[(long long)hr[t] * d.lda + rr], hw[(long long)t * d.q + j], acc);
-        X[(long long)rr * d.q + j] += acc;
+    for (int r0 = 0; r0 < d.p; r0 += kFoldRows) {
+        for (int e = threadIdx.x; e < nh * kFoldRows; e += kBB) {
+            const int t = e / kFoldRows, r = e % kFoldRows;
+            sa[e] = (r0 + r < d.p) ? hc[t] * A[(long long)hr[t] * d.lda + r0 + r] : 0.f;
+        }
+        for (int j0 = 0; j0 < d.q; j0 += kFoldCols) {
+            for (int e = threadIdx.x; e < nh * kFoldCols; e += kBB) {
+                const int t = e / kFoldCols, j = e % kFoldCols;
+                sw[e] = (j0 + j < d.q) ? hw[(long long)t * d.q + j0 + j] : 0.f;
+            }
+            __syncthreads();
+            float acc[2][8];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+            for (int t = 0; t < nh; ++t) {
+                const float a0 = sa[t * kFoldRows + 2 * tr], a1 = sa[t * kFoldRows + 2 * tr + 1];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const float wv = sw[t * kFoldCols + tcol + 16 * b];
+                    acc[0][b] = fmaf(a0, wv, acc[0][b]);
+                    acc[1][b] = fmaf(a1, wv, acc[1][b]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int rr = r0 + 2 * tr + a;
+                if (rr >= d.p) continue;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int j = j0 + tcol + 16 * b;
+                    if (j < d.q) X[(long long)rr * d.q + j] += acc[a][b];
+                }
+            }
+            __syncthreads();
+        }
     }
-    __syncthreads();
+}
+
+// dst[r] = X_r . y for rows r < rows (rows of nv float4 vectors, stride ldx
+// floats); y in shared memory.  Each warp takes RP rows at a time, so a lane
+// has RP independent vector loads in flight per step.
+template <int RP>
+__device__ __forceinline__ void batch_rows_dot(const float* X, int ldx, int rows, int nv, const float* y, float* dst)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* y4 = reinterpret_cast<const float4*>(y);
+    for (int r0 = warp * RP; r0 < rows; r0 += kBW * RP) {
+        float acc[RP];
+#pragma unroll
+        for (int k = 0; k < RP; ++k) acc[k] = 0.f;
+#pragma unroll 2
+        for (int e = lane; e < nv; e += 32) {
+            float4 xv[RP];
+#pragma unroll
+            for (int k = 0; k < RP; ++k)
+                if (r0 + k < rows) xv[k] = __ldg(reinterpret_cast<const float4*>(X + (long long)(r0 + k) * ldx) + e);
+            const float4 yv = y4[e];
+#pragma unroll
+            for (int k = 0; k < RP; ++k)
+                if (r0 + k < rows)
+                    acc[k] = fmaf(xv[k].x, yv.x, fmaf(xv[k].y, yv.y, fmaf(xv[k].z, yv.z, fmaf(xv[k].w, yv.w, acc[k]))));
+        }
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            const float t = warp_sum_f(acc[k]);
+            if (lane == 0 && r0 + k < rows) dst[r0 + k] = t;
+        }
+    }
 }
 
 // Set-up of one system by one CTA: a_i = ||A_i||^2 (FP64, ascending columns) and
@@ -190,12 +259,13 @@ __global__ void __launch_bounds__(kBB) batch_setup_kernel(const SysDesc* sys, co
 
 __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
 {
-    __shared__ double s_s[kMaxSide];          // ||R_i||^2
-    __shared__ double s_r[kMaxSide];          // s_i / a_i
-    __shared__ float s_vec[kMaxSide];         // R_{i_k} row, then v
-    __shared__ float s_arow[kMaxSide];        // A_{i_k}
-    __shared__ float s_w[kMaxSide];           // w
-    __shared__ float s_u[kMaxSide];           // u
+    __shared__ double s_s[kMaxSide];                      // ||R_i||^2
+    __shared__ double s_r[kMaxSide];                      // s_i / a_i
+    __shared__ __align__(16) float s_vec[kMaxSide];       // R_{i_k} row, then v
+    __shared__ __align__(16) float s_arow[kMaxSide];      // A_{i_k}
+    __shared__ __align__(16) float s_w[kMaxSide];         // w
+    __shared__ __align__(16) float s_u[kMaxSide];         // u
+    extern __shared__ __align__(16) float fold_smem[];    // kFoldSmemBytes
     __shared__ double red[2 * kBW];
     __shared__ long long redi[kBW];
     __shared__ int s_sys, s_first, s_last, s_stop;
@@ -242,7 +312,9 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 __syncthreads();
             }
         } else {
-            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += kBB) R[e] = C[e];
+            const float4* C4 = reinterpret_cast<const float4*>(C);
+            float4* R4 = reinterpret_cast<float4*>(R);
+            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr / 4; e += kBB) R4[e] = __ldg(C4 + e);
         }
         __syncthreads();
 
@@ -377,63 +449,106 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             const double ck = aik > 0.0 ? __ddiv_rn(d.alpha, aik) : 0.0;
             if (threadIdx.x == 0 && k < P.trace_len) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
 
-            // ---- w = R_ik B^T, u = A A_ik^T
-            for (int l = threadIdx.x; l < d.n; l += kBB) s_vec[l] = R[(long long)ik * d.ldr + l];
-            for (int c2 = threadIdx.x; c2 < d.p; c2 += kBB) s_arow[c2] = A[(long long)ik * d.lda + c2];
-            __syncthreads();
-            for (int task = warp; task < d.q + d.m; task += kBW) {
-                const bool isw = task < d.q;
-                const int row = isw ? task : task - d.q;
-                const float* x = isw ? (B + (long long)row * d.ldb) : (A + (long long)row * d.lda);
-                const float* y = isw ? s_vec : s_arow;
-                const int len = isw ? d.n : d.p;
-                float acc = 0.f;
-                for (int e = lane; e < len; e += 32) acc = fmaf(x[e], y[e], acc);
-                acc = warp_sum_f(acc);
-                if (lane == 0) {
-                    if (isw) s_w[row] = acc; else s_u[row] = acc;
-                }
+            // ---- w = R_ik B^T, u = A A_ik^T (rows of B and A streamed as float4, 4 rows per warp)
+            {
+                const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
+                const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
+                for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
+                for (int e = threadIdx.x; e < d.lda / 4; e += kBB) reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
             }
             __syncthreads();
-            // ---- record the term, v = w B
+            batch_rows_dot<4>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
+            batch_rows_dot<4>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
+            __syncthreads();
+            // ---- record the term, v = w B (vector columns, row classes reduced in shared memory)
             if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
             for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
-            for (int l = threadIdx.x; l < d.n; l += kBB) {
-                float acc = 0.f;
-                for (int j = 0; j < d.q; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
-                s_vec[l] = acc;
-            }
-            __syncthreads();
-            // ---- R -= c u v fused with the new row norms
-            for (int i = warp; i < d.m; i += kBW) {
-                const float coef = (float)(ck * (double)s_u[i]);
-                float acc = 0.f, comp = 0.f;
-                float* Ri = R + (long long)i * d.ldr;
-                for (int l = lane; l < d.n; l += 32) {
-                    const float x = fmaf(-coef, s_vec[l], Ri[l]);
-                    Ri[l] = x;
-                    const float y = fmaf(x, x, -comp);
-                    const float tt = acc + y;
-                    comp = (tt - acc) - y;
-                    acc = tt;
+            {
+                const int nv4 = d.ldb / 4;
+                float4* red4 = reinterpret_cast<float4*>(fold_smem);  // [RG][cols] float4
+                for (int cb = 0; cb < nv4; cb += kBB) {
+                    const int ncols = min(kBB, nv4 - cb);
+                    const int RG = kBB / ncols;
+                    const int e = threadIdx.x % ncols, rg = threadIdx.x / ncols;
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (rg < RG) {
+                        const float4* col = reinterpret_cast<const float4*>(B) + cb + e;
+                        const int ldv = d.ldb / 4;
+#pragma unroll 8
+                        for (int j = rg; j < d.q; j += RG) {
+                            const float4 bv = __ldg(col + (long long)j * ldv);
+                            const float wj = s_w[j];
+                            acc.x = fmaf(wj, bv.x, acc.x);
+                            acc.y = fmaf(wj, bv.y, acc.y);
+                            acc.z = fmaf(wj, bv.z, acc.z);
+                            acc.w = fmaf(wj, bv.w, acc.w);
+                        }
+                        red4[rg * ncols + e] = acc;
+                    }
+                    __syncthreads();
+                    for (int t = threadIdx.x; t < ncols; t += kBB) {
+                        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                        for (int r2 = 0; r2 < RG; ++r2) {
+                            const float4 v = red4[r2 * ncols + t];
+                            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+                        }
+                        reinterpret_cast<float4*>(s_vec)[cb + t] = sum;
+                    }
+                    __syncthreads();
                 }
-                float hi = acc, lo = -comp;
-                warp_sum_df(hi, lo);
-                if (lane == 0) {
-                    const double tot = (double)hi + (double)lo;
-                    s_s[i] = tot;
-                    s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
+            }
+            // ---- R -= c u v fused with the new row norms (float4, two rows per warp)
+            {
+                const float4* v4 = reinterpret_cast<const float4*>(s_vec);
+                const int nv = d.ldr / 4;
+                for (int i0 = 2 * warp; i0 < d.m; i0 += 2 * kBW) {
+                    float acc[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
+                    float coef[2];
+#pragma unroll
+                    for (int k2 = 0; k2 < 2; ++k2) coef[k2] = (i0 + k2 < d.m) ? (float)(ck * (double)s_u[i0 + k2]) : 0.f;
+                    for (int e = lane; e < nv; e += 32) {
+                        float4 rv[2];
+#pragma unroll
+                        for (int k2 = 0; k2 < 2; ++k2)
+                            if (i0 + k2 < d.m) rv[k2] = reinterpret_cast<float4*>(R + (long long)(i0 + k2) * d.ldr)[e];
+                        const float4 vv = v4[e];
+#pragma unroll
+                        for (int k2 = 0; k2 < 2; ++k2) {
+                            if (i0 + k2 >= d.m) continue;
+                            float* x = reinterpret_cast<float*>(&rv[k2]);
+                            const float* y = reinterpret_cast<const float*>(&vv);
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                x[c] = fmaf(-coef[k2], y[c], x[c]);
+                                const float yk = fmaf(x[c], x[c], -comp[k2]);
+                                const float tk = acc[k2] + yk;
+                                comp[k2] = (tk - acc[k2]) - yk;
+                                acc[k2] = tk;
+                            }
+                            reinterpret_cast<float4*>(R + (long long)(i0 + k2) * d.ldr)[e] = rv[k2];
+                        }
+                    }
+#pragma unroll
+                    for (int k2 = 0; k2 < 2; ++k2) {
+                        float hi = acc[k2], lo = -comp[k2];
+                        warp_sum_df(hi, lo);
+                        if (lane == 0 && i0 + k2 < d.m) {
+                            const double tot = (double)hi + (double)lo;
+                            s_s[i0 + k2] = tot;
+                            s_r[i0 + k2] = a[i0 + k2] > 0.0 ? __ddiv_rn(tot, a[i0 + k2]) : -INFINITY;
+                        }
+                    }
                 }
             }
             ++k;
             ++nh;
             if (nh == P.chunk) {
-                batch_fold(P, d, nh);
+                batch_fold(P, d, nh, fold_smem);
                 nh = 0;
             }
             __syncthreads();
         }
-        batch_fold(P, d, nh);
+        batch_fold(P, d, nh, fold_smem);
         if (threadIdx.x == 0) {
             P.iters[sid] = k;
             P.S_out[sid] = s_S;
@@ -525,7 +640,7 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     b->nsys = nsys;
     b->opts = o;
     b->stream = (cudaStream_t)o.stream;
-    b->chunk = o.check_every > 0 ? o.check_every : 64;
+    b->chunk = o.check_every > 0 ? std::min(o.check_every, kMaxChunk) : kMaxChunk;
     b->hsys.resize(nsys);
     long long oA = 0, oB = 0, oR = 0, oX = 0, oRow = 0, oH = 0, oHW = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -663,11 +778,12 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     int dev = 0, nsm = 0, per_sm = 0;
     GRBK_CK(cudaGetDevice(&dev));
     GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBB, 0));
+    GRBK_CK(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemBytes));
+    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBB, kFoldSmemBytes));
     int grid = nsm * (per_sm > 0 ? per_sm : 1);
     if (b->opts.grid_ctas > 0) grid = b->opts.grid_ctas;
     if (grid > b->nsys) grid = b->nsys;
-    batch_kernel<<<grid, kBB, 0, st>>>(P);
+    batch_kernel<<<grid, kBB, kFoldSmemBytes, st>>>(P);
     GRBK_CK(cudaGetLastError());
     std::vector<long long> it(b->nsys);
     std::vector<double> S(b->nsys);
@@ -754,9 +870,15 @@ struct NoAllocScratch {
     double pt[kNoAllocSide];
     double py[kNoAllocSide];
     float hist_w[kNoAllocChunk * kNoAllocSide];
-    float R[kNoAllocSide * kNoAllocSide];
+    // the batched kernel reads these with 16-byte vector loads: keep them 16-byte aligned
+    __align__(16) float R[kNoAllocSide * kNoAllocSide];   // rows padded to a multiple of 4
+    __align__(16) float A[kNoAllocSide * kNoAllocSide];   // padded copy of the caller's A
+    __align__(16) float B[kNoAllocSide * kNoAllocSide];   // padded copy of the caller's B
 };
 static_assert(sizeof(NoAllocScratch) <= GRBK_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
+static_assert(offsetof(NoAllocScratch, R) % 16 == 0 && offsetof(NoAllocScratch, A) % 16 == 0 &&
+                  offsetof(NoAllocScratch, B) % 16 == 0,
+              "vector-loaded arrays must be 16-byte aligned");
 
 // The working memory of grbk_solve_small_noalloc.  In host code this name is a
 // host-side stand-in, not a device address: host code only ever passes the
@@ -767,6 +889,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[GRBK_NOALLOC_SC
 // ||C||_F^2, ||B||_2^2 by 200 power iterations on B B^T, the step, the stop
 // level, a non-finite scan.  On an error the queue is filled so that the batch
 // kernel finds no work.
+// caller's contiguous A, B, C -> the array's rows padded to a multiple of 4 (zeros in the padding)
+__global__ void noalloc_copy_kernel(NoAllocScratch* S, const float* A, const float* B, const float* C, int m, int p,
+                                    int q, int n)
+{
+    const int lda = (p + 3) & ~3, ldb = (n + 3) & ~3;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * lda;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / lda), c = (int)(e % lda);
+        S->A[e] = c < p ? A[(long long)i * p + c] : 0.f;
+    }
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)q * ldb;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldb), c = (int)(e % ldb);
+        S->B[e] = c < n ? B[(long long)i * n + c] : 0.f;
+    }
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * ldb;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldb), c = (int)(e % ldb);
+        S->R[e] = c < n ? C[(long long)i * n + c] : 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, const float* A, const float* B,
                                                             const float* C, int m, int p, int q, int n,
                                                             double alpha_in, double tol)
@@ -782,7 +926,7 @@ __global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, c
         else if (alpha_in > 0.0 && !(alpha_in * lam < 2.0 * (1.0 + 1e-9))) status = GRBK_EINVAL;
         SysDesc& d = S->desc;
         d.m = m; d.p = p; d.q = q; d.n = n;
-        d.lda = p; d.ldb = n; d.ldr = n;
+        d.lda = (p + 3) & ~3; d.ldb = (n + 3) & ~3; d.ldr = d.ldb;
         d.pad = 0;
         d.offA = 0; d.offB = 0; d.offR = 0; d.offX = 0; d.offRow = 0; d.offHist = 0; d.offHistW = 0;
         d.F = o.F;
@@ -813,6 +957,7 @@ static grbk_status noalloc_scratch_address(void** out)
     if (!g_noalloc_ptr[dev]) {
         void* ptr = nullptr;
         GRBK_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        GRBK_CK(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemBytes));
         g_noalloc_ptr[dev] = ptr;
     }
     *out = g_noalloc_ptr[dev];
@@ -840,6 +985,7 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
     NoAllocScratch* S = reinterpret_cast<NoAllocScratch*>(base);
     cudaStream_t st = (cudaStream_t)stream;
     GRBK_CK(cudaMemsetAsync(X_out, 0, sizeof(float) * (size_t)p * q, st));
+    noalloc_copy_kernel<<<64, 256, 0, st>>>(S, A, B, C, m, p, q, n);
     noalloc_setup_kernel<<<1, kBB, 0, st>>>(S, A, B, C, m, p, q, n, alpha, tol);
     GRBK_CK(cudaGetLastError());
     BatchParams P;
@@ -848,7 +994,7 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
     P.sys = &S->desc;
     P.order = &S->order;
     P.queue = &S->queue;
-    P.A = A; P.B = B; P.C = C;
+    P.A = S->A; P.B = S->B; P.C = S->R;   // R starts as the padded copy of C
     P.R = S->R;
     P.X = X_out;
     P.a = S->a;
@@ -865,7 +1011,7 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
     P.maxit = maxit;
     P.chunk = kNoAllocChunk;
     P.init_from_x = 0;
-    batch_kernel<<<1, kBB, 0, st>>>(P);
+    batch_kernel<<<1, kBB, kFoldSmemBytes, st>>>(P);
     GRBK_CK(cudaGetLastError());
     struct {
         long long iters;

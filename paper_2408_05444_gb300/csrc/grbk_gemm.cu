@@ -105,20 +105,28 @@ template cudaError_t gemm_simt<float>(int64_t, int64_t, int64_t, double, const f
 // ----------------------------------------------------------------------------
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int A_TILE = BM * BK * 2;            // 16 KB
-constexpr int B_TILE = BN * BK * 2;            // 32 KB
-constexpr int STAGE_BYTES = A_TILE + B_TILE;   // 48 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 256;
+// Tile: BM x BN(TERMS) outputs, K blocks of BK.  A pipeline stage holds every
+// split term of one K block of both operands, and the MMA issuer runs all term
+// pairs from that stage, so each operand tile crosses L2 once per K block.
+// 2 terms: BN = 256, stage = 2 x (16 + 32) KB; 3 terms: BN = 128, stage =
+// 3 x (16 + 16) KB.  Two stages (192 KB).
+constexpr int BM = 128, BK = 64, STAGES = 2;
+constexpr int A_TILE = BM * BK * 2;            // 16 KB per term
+template <int TERMS> struct Cfg {
+    static constexpr int BN = TERMS == 2 ? 256 : 128;
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE_BYTES = TERMS * (A_TILE + B_TILE);
+    static constexpr int NPAIRS = TERMS == 2 ? 3 : 6;
+};
+constexpr int SMEM_BYTES = STAGES * 98304 + 1024 + 256;
+static_assert(Cfg<2>::STAGE_BYTES == 98304 && Cfg<3>::STAGE_BYTES == 98304, "stage size");
+constexpr int BN_MAX = 256;                    // plane rows are padded to this
 constexpr long long kWaitBudget = 2000000000LL;  // cycles (about 1 s)
 
 enum { EPI_SPLIT = 0, EPI_RESID = 1 };
 
 struct Args {
     int M, N, K;                 // K: padded inner size (multiple of BK)
-    int npairs;
-    int ta[6], tb[6];            // term of A / of B for each pair
     int mode;
     int out_terms;               // EPI_SPLIT: terms written
     int out_rows;                // EPI_SPLIT: rows per output plane (>= M)
@@ -181,15 +189,28 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     return d;
 }
 
-// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, M x N
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major, BM x N
+__host__ __device__ constexpr uint32_t idesc_for(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
+}
+
+// term pairs, smallest cross terms first so the FP32 accumulator adds them before the large ones:
+// 2 terms: x0 y1, x1 y0, x0 y0;  3 terms: x1 y1, x2 y0, x0 y2, x1 y0, x0 y1, x0 y0
+__device__ __forceinline__ void pair_terms(int terms, int p, int& ta, int& tb)
+{
+    const int a2[3] = {0, 1, 0}, b2[3] = {1, 0, 0};
+    const int a3[6] = {1, 2, 0, 1, 0, 0}, b3[6] = {1, 0, 2, 0, 1, 0};
+    ta = terms == 2 ? a2[p] : a3[p];
+    tb = terms == 2 ? b2[p] : b3[p];
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -220,15 +241,20 @@ __device__ __forceinline__ void split_f(float x, int terms, __nv_bfloat16* t)
     if (terms > 2) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(l));
 }
 
-// D[M x N] = sum over pairs of A_ta[M x K] * B_tb[N x K]^T; 256 threads:
+// D[M x N] = sum over term pairs of A_ta[M x K] * B_tb[N x K]^T; 256 threads:
 // warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM owner, warps 4-7 = epilogue.
+template <int TERMS>
 __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, Args g)
 {
+    constexpr int BN = Cfg<TERMS>::BN, B_TILE = Cfg<TERMS>::B_TILE, STAGE_BYTES = Cfg<TERMS>::STAGE_BYTES;
+    constexpr int TMEM_COLS = BN;
+    constexpr uint32_t IDESC = idesc_for(BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + STAGES * A_TILE;
+    // stage s: [A term 0 .. TERMS-1][B term 0 .. TERMS-1]
+    auto sA = [&](int s, int t) { return smem + s * STAGE_BYTES + t * A_TILE; };
+    auto sB = [&](int s, int t) { return smem + s * STAGE_BYTES + TERMS * A_TILE + t * B_TILE; };
     uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
     uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
@@ -240,7 +266,7 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nkb = g.K / BK;
-    const int total = g.npairs * nkb;
+    const int total = nkb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -269,10 +295,13 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
             const uint32_t ph = (uint32_t)((it / STAGES) & 1);
             if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; break; }
             if (*(volatile int*)&s_abort) break;
-            const int pair = it / nkb, kb = it % nkb;
+            const int kb = it;
             mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-            tma_load_3d(smem_u32(sA + s * A_TILE), &tmA, kb * BK, m0, g.ta[pair], full0 + 8 * s);
-            tma_load_3d(smem_u32(sB + s * B_TILE), &tmB, kb * BK, n0, g.tb[pair], full0 + 8 * s);
+#pragma unroll
+            for (int t = 0; t < TERMS; ++t) {
+                tma_load_3d(smem_u32(sA(s, t)), &tmA, kb * BK, m0, t, full0 + 8 * s);
+                tma_load_3d(smem_u32(sB(s, t)), &tmB, kb * BK, n0, t, full0 + 8 * s);
+            }
             ++issued;
         }
         // wait (bounded) for this CTA's copies still in flight before anyone leaves
@@ -285,10 +314,16 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
             if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; break; }
             if (*(volatile int*)&s_abort) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * A_TILE), b0 = smem_u32(sB + s * B_TILE);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), (it > 0 || kk > 0) ? 1u : 0u);
+            for (int p = 0; p < Cfg<TERMS>::NPAIRS; ++p) {
+                int ta, tb;
+                pair_terms(TERMS, p, ta, tb);
+                const uint32_t a0 = smem_u32(sA(s, ta)), b0 = smem_u32(sB(s, tb));
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    mma_bf16(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
+                             (it > 0 || p > 0 || kk > 0) ? 1u : 0u);
+            }
             mma_commit(empty0 + 8 * s);
         }
         mma_commit(done);  // arrives once every MMA issued above has completed
@@ -429,18 +464,6 @@ static bool make_map(CUtensorMap* map, void* base, int64_t Kpad, int64_t rows, i
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static void pairs_for(int terms, tc::Args& a)
-{
-    // smallest cross terms first, so the FP32 accumulator adds them before the large ones
-    static const int t2a[3] = {0, 1, 0}, t2b[3] = {1, 0, 0};
-    static const int t3a[6] = {1, 2, 0, 1, 0, 0}, t3b[6] = {1, 0, 2, 0, 1, 0};
-    a.npairs = terms == 2 ? 3 : 6;
-    for (int i = 0; i < a.npairs; ++i) {
-        a.ta[i] = terms == 2 ? t2a[i] : t3a[i];
-        a.tb[i] = terms == 2 ? t2b[i] : t3b[i];
-    }
-}
-
 grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, int64_t n, const float* A,
                              int64_t lda, const float* B, int64_t ldb, int terms, cudaStream_t st)
 {
@@ -450,8 +473,8 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     g->Kp = round_up(p, tc::BK);
     g->Kq = round_up(q, tc::BK);
     g->mr = round_up(m, tc::BM);
-    g->nr = round_up(n, tc::BN);
-    g->qr = round_up(q, tc::BN);
+    g->nr = round_up(n, tc::BN_MAX);
+    g->qr = round_up(q, tc::BN_MAX);
     const size_t szA = (size_t)terms * g->mr * g->Kp * 2, szB = (size_t)terms * g->nr * g->Kq * 2;
     const size_t szX = (size_t)terms * g->qr * g->Kp * 2, szT = (size_t)terms * g->mr * g->Kq * 2;
     if (cudaMalloc(&g->As, szA) != cudaSuccess || cudaMalloc(&g->BTs, szB) != cudaSuccess ||
@@ -470,15 +493,18 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     dim3 tb(32, 8), grd((unsigned)((n + 31) / 32), (unsigned)((q + 31) / 32));
     tc::split_transpose_kernel<float><<<grd, tb, 0, st>>>(B, ldb, q, n, g->Kq, terms, g->nr, g->BTs);
     if (cudaGetLastError() != cudaSuccess) { splitgemm_destroy(g); return GRBK_ECUDA; }
+    const int bn = terms == 2 ? tc::Cfg<2>::BN : tc::Cfg<3>::BN;
     if (!make_map(&g->tmA, g->As, g->Kp, g->mr, terms, tc::BM) ||
-        !make_map(&g->tmXT, g->XTs, g->Kp, g->qr, terms, tc::BN) ||
+        !make_map(&g->tmXT, g->XTs, g->Kp, g->qr, terms, bn) ||
         !make_map(&g->tmT1, g->T1s, g->Kq, g->mr, terms, tc::BM) ||
-        !make_map(&g->tmBT, g->BTs, g->Kq, g->nr, terms, tc::BN)) {
+        !make_map(&g->tmBT, g->BTs, g->Kq, g->nr, terms, bn)) {
         splitgemm_destroy(g);
         return GRBK_ECUDA;
     }
-    if (cudaFuncSetAttribute(tc::gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(tc::gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(tc::gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) !=
+            cudaSuccess) {
         splitgemm_destroy(g);
         return GRBK_ECUDA;
     }
@@ -497,20 +523,25 @@ grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const
     tc::Args a1;
     memset(&a1, 0, sizeof(a1));
     a1.M = (int)g->m; a1.N = (int)g->q; a1.K = (int)g->Kp;
-    pairs_for(g->terms, a1);
     a1.mode = tc::EPI_SPLIT; a1.out_terms = g->terms; a1.out_rows = (int)g->mr; a1.out_split = g->T1s;
     a1.out_ld = g->Kq; a1.err = g->err;
-    dim3 g1((unsigned)((g->q + tc::BN - 1) / tc::BN), (unsigned)((g->m + tc::BM - 1) / tc::BM));
-    tc::gemm_kernel<<<g1, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmXT, a1);
-    GRBK_CK(cudaGetLastError());
     // R = C - T1 B  (M = m, N = n, K = q)
     tc::Args a2;
     memset(&a2, 0, sizeof(a2));
     a2.M = (int)g->m; a2.N = (int)g->n; a2.K = (int)g->Kq;
-    pairs_for(g->terms, a2);
     a2.mode = tc::EPI_RESID; a2.cin = C; a2.out = R; a2.ld = ldr; a2.err = g->err;
-    dim3 g2((unsigned)((g->n + tc::BN - 1) / tc::BN), (unsigned)((g->m + tc::BM - 1) / tc::BM));
-    tc::gemm_kernel<<<g2, 256, tc::SMEM_BYTES, st>>>(g->tmT1, g->tmBT, a2);
+    const int bn = g->terms == 2 ? tc::Cfg<2>::BN : tc::Cfg<3>::BN;
+    dim3 g1((unsigned)((g->q + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    dim3 g2((unsigned)((g->n + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    if (g->terms == 2) {
+        tc::gemm_kernel<2><<<g1, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmXT, a1);
+        GRBK_CK(cudaGetLastError());
+        tc::gemm_kernel<2><<<g2, 256, tc::SMEM_BYTES, st>>>(g->tmT1, g->tmBT, a2);
+    } else {
+        tc::gemm_kernel<3><<<g1, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmXT, a1);
+        GRBK_CK(cudaGetLastError());
+        tc::gemm_kernel<3><<<g2, 256, tc::SMEM_BYTES, st>>>(g->tmT1, g->tmBT, a2);
+    }
     GRBK_CK(cudaGetLastError());
     return GRBK_OK;
 }

@@ -68,9 +68,15 @@ __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile
 // bounded: on expiry the CTA records GRBK_ETIMEOUT and the barrier returns
 // false, as it also does when any CTA has recorded an error; callers then
 // leave the kernel.  s_ok must be a __shared__ int.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int site, int& s_ok)
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int site, int& s_ok,
+                                          long long budget = kBarrierBudget)
 {
     __syncthreads();
+    if (gridDim.x == 1) {  // a single CTA: the block barrier is the grid barrier
+        if (threadIdx.x == 0) s_ok = (ld_volatile_int(&st->status) == 0);
+        __syncthreads();
+        return s_ok != 0;
+    }
     if (threadIdx.x == 0) {
         const unsigned int nb = gridDim.x;
         const unsigned int g = ld_acquire_u32(&bar->gen);
@@ -84,7 +90,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
         } else {
             const long long t0 = clock64();
             while (ld_acquire_u32(&bar->gen) == g) {
-                if (clock64() - t0 > kBarrierBudget) {
+                if (clock64() - t0 > budget) {
                     if (atomicCAS(&st->status, 0, (int)GRBK_ETIMEOUT) == 0) st->timeout_site = site;
                     ok = 0;
                     break;

@@ -890,7 +890,7 @@ extern "C" void grbk_default_opts(grbk_opts* o)
     o->refresh_T = 0;
     o->alpha = 0.0;
     o->stop_kind = GRBK_STOP_NONE;
-    o->split_terms = 3;
+    o->split_terms = 2;
 }
 
 extern "C" const char* grbk_strerror(int32_t s)
@@ -1059,7 +1059,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     grbk_opts o;
     if (opts) o = *opts; else grbk_default_opts(&o);
     if (o.precision != GRBK_F64 && o.precision != GRBK_F32) return GRBK_EINVAL;
-    if (o.split_terms == 0) o.split_terms = 3;
+    if (o.split_terms == 0) o.split_terms = 2;
     if (o.split_terms != 2 && o.split_terms != 3) return GRBK_EINVAL;
     if (o.refresh_T < 0) return GRBK_EINVAL;
 
@@ -1377,6 +1377,45 @@ extern "C" grbk_status grbk_get_rownorms(grbk_ctx* c, double* s_out, int32_t on_
                             c->stream));
     GRBK_CK(cudaStreamSynchronize(c->stream));
     return GRBK_OK;
+}
+
+// One grid barrier of the iteration kernel with a short spin budget; CTA
+// `absent` (if >= 0) leaves without arriving, so the others must give up.
+__global__ void barrier_selftest_kernel(GridBarrier* bar, DevState* st, int absent, long long budget)
+{
+    __shared__ int s_ok;
+    if ((int)blockIdx.x == absent) return;
+    grid_sync(bar, st, 9, s_ok, budget);
+}
+
+extern "C" grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int G = std::max(2, std::min(nsm, 8));
+    if (absent_cta >= G) return GRBK_EINVAL;
+    GridBarrier* bar = nullptr;
+    DevState* ds = nullptr;
+    if (cudaMalloc(&bar, sizeof(GridBarrier)) != cudaSuccess) return GRBK_ENOMEM;
+    if (cudaMalloc(&ds, sizeof(DevState)) != cudaSuccess) { cudaFree(bar); return GRBK_ENOMEM; }
+    grbk_status r = GRBK_OK;
+    DevState h;
+    memset(&h, 0, sizeof(h));
+    int absent = absent_cta;
+    long long budget = 200000000LL;  // about 0.1 s at 2 GHz
+    void* args[] = {&bar, &ds, &absent, &budget};
+    if (cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st) != cudaSuccess ||
+        cudaMemsetAsync(ds, 0, sizeof(DevState), st) != cudaSuccess ||
+        cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(G), dim3(32), args, 0, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h, ds, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        r = GRBK_ECUDA;
+    cudaFree(bar);
+    cudaFree(ds);
+    if (r != GRBK_OK) return r;
+    return (grbk_status)h.status;
 }
 
 extern "C" grbk_status grbk_info(const grbk_ctx* c, int64_t dims[4], double* alpha)

@@ -205,10 +205,10 @@ def test_residual_entry_point():
     R = np.zeros_like(C)
     g.grbk_residual(ctx, X, R)
     assert np.max(np.abs(R - ref)) < 1e-12 * np.max(np.abs(C))
-    ctx32 = g.grbk_create(A, B, C, precision="f32")
+    ctx32 = g.grbk_create(A, B, C, precision="f32", split_terms=3)
     R32 = np.zeros(C.shape, dtype=np.float32)
     g.grbk_residual(ctx32, X, R32)
-    # FP32 inputs: entries of A, B, C and X rounded to 2^-24; products of depth p and q
+    # 3 split terms and FP32 inputs: entries of A, B, C and X rounded to 2^-24; products of depth p and q
     scale = np.abs(A) @ np.abs(X) @ np.abs(B) + np.abs(C)
     assert np.max(np.abs(R32 - ref) / scale) < 2e-6
 
