@@ -142,6 +142,22 @@ def gen_inputs(wl):
     return A, B, C, Xs
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None when the
+    kernel's sources changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+    except Exception:
+        return None
+
+
 def iter_bytes(m, p, q, n, esz):
     """Algorithmic bytes of one iteration: R read + written, B read twice
     (w = R_i B^T and v = w B), A read once (u = A A_i^T), the vectors u, v, w
@@ -329,7 +345,10 @@ def native_arm(args):
                        "split_terms": args.split_terms,
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak,
+                         "traffic": (recorded_traffic("iterate_kernel<float>")
+                                     if (wl == "precision" and T == 64) else None),
+                         "algorithmic_bytes_per_launch": bytes_per_launch,
                          "kernel": "iterate_kernel<float> (persistent, %d iterations per launch)" % T,
                          "kernel_ms_per_launch": kern_ms, "peak_source": peak_src},
             "plain": plain,

@@ -63,6 +63,8 @@ struct BatchParams {
     int init_from_x;                // R = C - A X B before iterating (X holds X0)
 };
 
+// block-wide sum in a fixed order; one thread adds the warp partials (FP64 is
+// 1/64 of the FP32 rate here, so it is kept off the other 511 threads)
 __device__ __forceinline__ double block_sum_fixed(double v, double* red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -70,8 +72,13 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red)
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < kBW; ++w) t += red[w];
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kBW; ++w) t += red[w];
+        red[kBW] = t;
+    }
+    __syncthreads();
+    const double t = red[kBW];
     __syncthreads();
     return t;
 }
@@ -269,7 +276,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
     __shared__ double red[2 * kBW];
     __shared__ long long redi[kBW];
     __shared__ int s_sys, s_first, s_last, s_stop;
-    __shared__ double s_S, s_rmax;
+    __shared__ double s_S, s_rmax, s_base_next;
     __shared__ long long s_imax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -412,14 +419,19 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     const double incw = warp_inclusive_scan(val);
                     if (lane == 31) red[warp] = incw;
                     __syncthreads();
-                    double wbase = base;
-                    for (int w2 = 0; w2 < warp; ++w2) wbase += red[w2];
+                    if (warp == 0) {  // exclusive bases of the warps, and the chunk total
+                        const double wt = lane < kBW ? red[lane] : 0.0;
+                        const double inc = warp_inclusive_scan(wt);
+                        if (lane < kBW) red[kBW + lane] = base + inc - wt;
+                        const double tot = __shfl_sync(0xffffffffu, inc, kBW - 1);
+                        if (lane == 0) s_base_next = base + tot;
+                    }
+                    __syncthreads();
+                    const double wbase = red[kBW + warp];
                     if (adm && wbase + incw > target) atomicMin(&s_first, i);
                     if (adm) atomicMax(&s_last, i);
-                    double tot = base;
-                    for (int w2 = 0; w2 < kBW; ++w2) tot += red[w2];
                     __syncthreads();
-                    base = tot;
+                    base = s_base_next;
                     if (s_first != 0x7fffffff) break;
                 }
                 ik = (s_first != 0x7fffffff) ? s_first : s_last;
@@ -460,6 +472,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             batch_rows_dot<4>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
             batch_rows_dot<4>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
             __syncthreads();
+            for (int i = threadIdx.x; i < d.m; i += kBB) s_u[i] = (float)(ck * (double)s_u[i]);  // coefficient c_k u_i
             // ---- record the term, v = w B (vector columns, row classes reduced in shared memory)
             if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
             for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     float acc[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
                     float coef[2];
 #pragma unroll
-                    for (int k2 = 0; k2 < 2; ++k2) coef[k2] = (i0 + k2 < d.m) ? (float)(ck * (double)s_u[i0 + k2]) : 0.f;
+                    for (int k2 = 0; k2 < 2; ++k2) coef[k2] = (i0 + k2 < d.m) ? s_u[i0 + k2] : 0.f;
                     for (int e = lane; e < nv; e += 32) {
                         float4 rv[2];
 #pragma unroll

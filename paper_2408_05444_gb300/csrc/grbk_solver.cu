@@ -124,7 +124,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             V* Rrow = reinterpret_cast<V*>(P.R + row * P.ldr);
             const V* vrow = reinterpret_cast<const V*>(vsrc);
             T coef = (T)0;
-            if (UPDATE) coef = (T)(ck * (double)__ldcg(P.u + row));
+            if (UPDATE) coef = __ldcg(P.u + row);  // c_k u_row, formed once per row
             double acc_d = 0.0;
             float acc_f = 0.f, comp_f = 0.f;
             for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kBlock) rownorms_kernel(IterParams<T> P)
 // ----------------------------------------------------------------------------
 template <typename T>
 __device__ __noinline__ void rows_dot(const T* X, int64_t ld, int64_t r0, int64_t r1, const T* y, int ymode, T* dst,
-                         double* dst_hist, double* sm_parts)
+                         double* dst_hist, double* sm_parts, double scale = 1.0)
 {
     using V = typename VecOf<T>::V;
     constexpr int VN = VecOf<T>::N;
@@ -286,7 +286,7 @@ __device__ __noinline__ void rows_dot(const T* X, int64_t ld, int64_t r0, int64_
         for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
             double sum = 0.0;
             for (int c2 = 0; c2 < nch; ++c2) sum += sm_parts[rr * nch + c2];
-            __stcg(dst + b0 + rr, (T)sum);
+            __stcg(dst + b0 + rr, (T)(scale * sum));
             if (dst_hist) dst_hist[b0 + rr] = sum;
         }
         __syncthreads();
@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             cta_rows(P.q, c, G, j0, j1);
             rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w,
                         P.hist_w + (int64_t)it * P.q, sm_parts);
-            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts);
+            // u holds the row coefficients c_k (A A_ik^T)_i of the rank-1 update
+            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
         }
         if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
 
