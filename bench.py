@@ -158,11 +158,12 @@ def recorded_traffic(kernel):
         return None
 
 
-def iter_bytes(m, p, q, n, esz):
+def iter_bytes(m, p, q, n, esz, gram=False):
     """Algorithmic bytes of one iteration: R read + written, B read twice
-    (w = R_i B^T and v = w B), A read once (u = A A_i^T), the vectors u, v, w
-    and the row norms (negligible but counted)."""
-    return 2 * m * n * esz + 2 * q * n * esz + m * p * esz + (m + n + q) * esz + 3 * m * 8
+    (w = R_i B^T and v = w B), A read once for u = A A_i^T (or one row of the
+    precomputed A A^T), the vectors u, v, w and the row norms."""
+    u_bytes = m * esz if gram else m * p * esz
+    return 2 * m * n * esz + 2 * q * n * esz + u_bytes + (m + n + q) * esz + 3 * m * 8
 
 
 def cpu_baseline_oracle(target_seconds=12.0):
@@ -280,7 +281,7 @@ def native_arm(args):
     iters = args.steps * T
     value = world * iters / (el_ms / 1e3)
     kern_ms = res["iter_kernel_ms"] / max(res["iter_kernel_launches"], 1)
-    bytes_per_launch = iter_bytes(m, p, q, n, 4) * T
+    bytes_per_launch = iter_bytes(m, p, q, n, 4, gram=bool(res["gram"])) * T
     hbm_peak, bf16_peak, peak_src = peaks()
     achieved = bytes_per_launch / (kern_ms / 1e3) / 1e9
 
@@ -299,7 +300,7 @@ def native_arm(args):
         ms64 = ev0.elapsed_time(ev1)
         km64 = r64["iter_kernel_ms"] / max(r64["iter_kernel_launches"], 1)
         plain = {"precision": "f64", "value": k64 * T / (ms64 / 1e3), "unit": UNIT,
-                 "kernel_GBs": iter_bytes(m, p, q, n, 8) * T / (km64 / 1e3) / 1e9,
+                 "kernel_GBs": iter_bytes(m, p, q, n, 8, gram=bool(r64["gram"])) * T / (km64 / 1e3) / 1e9,
                  "note": "FP64 residual pass, X0 = 0, no refresh (R^0 = C)"}
         g.grbk_destroy(ctx64)
         del X64
@@ -342,7 +343,7 @@ def native_arm(args):
             "config": {"workload": f"{wl}: A {m}x{p}, B {q}x{n} N(0,1/cols), X* N(0,1), C = A X* B; "
                                    f"chosen form FP32 + split-BF16 refresh every {T}",
                        "iters_per_step": T, "variant": "ME-GRBK", "parallelism": f"replicas{world}",
-                       "split_terms": args.split_terms,
+                       "split_terms": args.split_terms, "gram": bool(res["gram"]),
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,

@@ -83,6 +83,9 @@ typedef struct {
     void* stream;         /* cudaStream_t */
     int32_t grid_ctas;    /* persistent-kernel CTAs; 0 = chosen by the library */
     int32_t check_every;  /* iterations per device chunk between host checks; 0 = refresh_T or 256 */
+    int32_t use_gram;     /* form A A^T once and read u = (A A^T)_{:,i_k} from it (the practice note after
+                             Algorithm 3): 1 on, -1 off (u = A A_{i_k}^T every iteration), 0 on when the
+                             m x m matrix takes at most 4 GB */
 } grbk_opts;
 
 typedef struct {
@@ -94,6 +97,7 @@ typedef struct {
     double iter_kernel_ms;        /* device time of the persistent iteration kernel (CUDA events on the stream) */
     int64_t iter_kernel_launches; /* its launches in this call */
     int64_t launches;             /* all kernel launches made by this call */
+    int32_t gram;         /* 1 when u came from the precomputed A A^T */
     int32_t x0_rejected;  /* batched solves: 1 when the given X0 had ||C - A X0 B|| >= ||C|| and 0 was used */
     int32_t status;       /* grbk_status of the call */
 } grbk_result;

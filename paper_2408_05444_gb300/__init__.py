@@ -37,14 +37,15 @@ class grbk_opts(ctypes.Structure):
                 ("stop_kind", ctypes.c_int32), ("split_terms", ctypes.c_int32),
                 ("x_ref", ctypes.POINTER(grbk_mat)), ("row_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
-                ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("use_gram", ctypes.c_int32)]
 
 
 class grbk_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("relres", ctypes.c_double), ("rse", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("alpha", ctypes.c_double), ("iter_kernel_ms", ctypes.c_double),
                 ("iter_kernel_launches", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("x0_rejected", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("gram", ctypes.c_int32), ("x0_rejected", ctypes.c_int32), ("status", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -161,7 +162,7 @@ class _Keep:
 
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
-               x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None):
+               x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -178,6 +179,8 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.grid_ctas = grid_ctas
     if check_every is not None:
         o.check_every = check_every
+    if use_gram is not None:
+        o.use_gram = {True: 1, False: -1}.get(use_gram, use_gram)
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     if x_ref is not None:

@@ -13,7 +13,8 @@
 namespace grbk {
 
 // Cout = beta * Cin + alpha * A(MxK) * B(KxN); 64x64 tiles, 16x16 threads, 4x4 per thread.
-template <typename T>
+// BT: B is given as its transpose (N x K, row stride ldb), e.g. A A^T with B = A.
+template <typename T, bool BT>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(int64_t M, int64_t N, int64_t K, double alpha,
                                                         const T* __restrict__ A, int64_t lda,
                                                         const T* __restrict__ B, int64_t ldb, double beta,
@@ -39,7 +40,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int64_t M, int64_t N, in
         for (int e = threadIdx.x; e < BK * BN; e += 256) {
             const int kk = e / BN, cc = e % BN;
             const int64_t gk = k0 + kk, gc = col0 + cc;
-            Bs[kk][cc] = (gk < K && gc < N) ? B[gk * ldb + gc] : (T)0;
+            Bs[kk][cc] = (gk < K && gc < N) ? (BT ? B[gc * ldb + gk] : B[gk * ldb + gc]) : (T)0;
         }
         __syncthreads();
 #pragma unroll
@@ -78,9 +79,20 @@ cudaError_t gemm_simt(int64_t M, int64_t N, int64_t K, double alpha, const T* A,
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
-    gemm_simt_kernel<T><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, Cout, ldc);
+    gemm_simt_kernel<T, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, Cout, ldc);
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t gram_simt(int64_t M, int64_t K, const T* A, int64_t lda, T* G, int64_t ldg, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((M + 63) / 64));
+    gemm_simt_kernel<T, true><<<grid, 256, 0, st>>>(M, M, K, 1.0, A, lda, A, lda, 0.0, nullptr, 0, G, ldg);
+    return cudaGetLastError();
+}
+template cudaError_t gram_simt<double>(int64_t, int64_t, const double*, int64_t, double*, int64_t, cudaStream_t);
+template cudaError_t gram_simt<float>(int64_t, int64_t, const float*, int64_t, float*, int64_t, cudaStream_t);
 
 template cudaError_t gemm_simt<double>(int64_t, int64_t, int64_t, double, const double*, int64_t,
                                        const double*, int64_t, double, const double*, int64_t, double*,
@@ -123,7 +135,7 @@ static_assert(Cfg<2>::STAGE_BYTES == 98304 && Cfg<3>::STAGE_BYTES == 98304, "sta
 constexpr int BN_MAX = 256;                    // plane rows are padded to this
 constexpr long long kWaitBudget = 2000000000LL;  // cycles (about 1 s)
 
-enum { EPI_SPLIT = 0, EPI_RESID = 1 };
+enum { EPI_SPLIT = 0, EPI_RESID = 1, EPI_STORE = 2 };
 
 struct Args {
     int M, N, K;                 // K: padded inner size (multiple of BK)
@@ -339,22 +351,29 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
             if (!write || row >= g.M || n0 + cb >= g.N) continue;
             const int col0 = n0 + cb;
             const bool full = col0 + 32 <= g.N;
-            if (g.mode == EPI_RESID) {
-                const float* ci = g.cin + (int64_t)row * g.ld + col0;
+            if (g.mode == EPI_RESID || g.mode == EPI_STORE) {
+                const bool resid = g.mode == EPI_RESID;
+                const float* ci = resid ? g.cin + (int64_t)row * g.ld + col0 : nullptr;
                 float* oi = g.out + (int64_t)row * g.ld + col0;
                 if (full) {
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
-                        const float4 cv = __ldg(reinterpret_cast<const float4*>(ci + j));
                         float4 ov;
-                        ov.x = cv.x - __uint_as_float(r[j]);
-                        ov.y = cv.y - __uint_as_float(r[j + 1]);
-                        ov.z = cv.z - __uint_as_float(r[j + 2]);
-                        ov.w = cv.w - __uint_as_float(r[j + 3]);
+                        if (resid) {
+                            const float4 cv = __ldg(reinterpret_cast<const float4*>(ci + j));
+                            ov.x = cv.x - __uint_as_float(r[j]);
+                            ov.y = cv.y - __uint_as_float(r[j + 1]);
+                            ov.z = cv.z - __uint_as_float(r[j + 2]);
+                            ov.w = cv.w - __uint_as_float(r[j + 3]);
+                        } else {
+                            ov = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        }
                         *reinterpret_cast<float4*>(oi + j) = ov;
                     }
                 } else {
-                    for (int j = 0; j < 32 && col0 + j < g.N; ++j) oi[j] = ci[j] - __uint_as_float(r[j]);
+                    for (int j = 0; j < 32 && col0 + j < g.N; ++j)
+                        oi[j] = resid ? ci[j] - __uint_as_float(r[j]) : __uint_as_float(r[j]);
                 }
             } else {
                 for (int j = 0; j < 32 && col0 + j < g.N; ++j) {
@@ -433,6 +452,7 @@ struct SplitGemm {
     __nv_bfloat16* XTs;             // [terms][qr][Kp]
     __nv_bfloat16* T1s;             // [terms][mr][Kq]
     CUtensorMap tmA, tmXT, tmT1, tmBT;
+    CUtensorMap tmAn;               // A's planes as the N-side operand (for A A^T)
     int* err;
 };
 
@@ -472,7 +492,7 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     g->m = m; g->p = p; g->q = q; g->n = n; g->lda = lda; g->ldb = ldb; g->terms = terms;
     g->Kp = round_up(p, tc::BK);
     g->Kq = round_up(q, tc::BK);
-    g->mr = round_up(m, tc::BM);
+    g->mr = round_up(m, tc::BN_MAX);   // A's planes also serve as the N-side operand of A A^T
     g->nr = round_up(n, tc::BN_MAX);
     g->qr = round_up(q, tc::BN_MAX);
     const size_t szA = (size_t)terms * g->mr * g->Kp * 2, szB = (size_t)terms * g->nr * g->Kq * 2;
@@ -497,7 +517,8 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     if (!make_map(&g->tmA, g->As, g->Kp, g->mr, terms, tc::BM) ||
         !make_map(&g->tmXT, g->XTs, g->Kp, g->qr, terms, bn) ||
         !make_map(&g->tmT1, g->T1s, g->Kq, g->mr, terms, tc::BM) ||
-        !make_map(&g->tmBT, g->BTs, g->Kq, g->nr, terms, bn)) {
+        !make_map(&g->tmBT, g->BTs, g->Kq, g->nr, terms, bn) ||
+        !make_map(&g->tmAn, g->As, g->Kp, g->mr, terms, bn)) {
         splitgemm_destroy(g);
         return GRBK_ECUDA;
     }
@@ -542,6 +563,20 @@ grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const
         GRBK_CK(cudaGetLastError());
         tc::gemm_kernel<3><<<g2, 256, tc::SMEM_BYTES, st>>>(g->tmT1, g->tmBT, a2);
     }
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
+
+grbk_status splitgemm_gram(SplitGemm* g, float* G, int64_t ldg, cudaStream_t st)
+{
+    tc::Args a;
+    memset(&a, 0, sizeof(a));
+    a.M = (int)g->m; a.N = (int)g->m; a.K = (int)g->Kp;
+    a.mode = tc::EPI_STORE; a.out = G; a.ld = ldg; a.err = g->err;
+    const int bn = g->terms == 2 ? tc::Cfg<2>::BN : tc::Cfg<3>::BN;
+    dim3 grid((unsigned)((g->m + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    if (g->terms == 2) tc::gemm_kernel<2><<<grid, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmAn, a);
+    else tc::gemm_kernel<3><<<grid, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmAn, a);
     GRBK_CK(cudaGetLastError());
     return GRBK_OK;
 }

@@ -78,14 +78,15 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
         return s_ok != 0;
     }
     if (threadIdx.x == 0) {
+        // The block barrier orders the CTA's writes before thread 0's release
+        // fence; the arrival is a relaxed atomic after it, the waiters acquire.
         const unsigned int nb = gridDim.x;
         const unsigned int g = ld_acquire_u32(&bar->gen);
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         const unsigned int arrived = atomicAdd(&bar->count, 1u);
         int ok = 1;
         if (arrived == nb - 1) {
             atomicExch(&bar->count, 0u);
-            __threadfence();
             st_release_u32(&bar->gen, g + 1u);
         } else {
             const long long t0 = clock64();
@@ -95,10 +96,10 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(32);  // polling without a pause slows the CTAs still working
             }
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         s_ok = ok && (ld_volatile_int(&st->status) == 0);
     }
     __syncthreads();
@@ -201,6 +202,10 @@ cudaError_t gemm_simt(int64_t M, int64_t N, int64_t K, double alpha, const T* A,
                       const T* B, int64_t ldb, double beta, const T* Cin, int64_t ldcin, T* Cout,
                       int64_t ldc, cudaStream_t st);
 
+// G = A A^T (M x M, row stride ldg) for A (M x K, row stride lda), SIMT.
+template <typename T>
+cudaError_t gram_simt(int64_t M, int64_t K, const T* A, int64_t lda, T* G, int64_t ldg, cudaStream_t st);
+
 // dst(rows x cols, ldd) of type Td <- src(rows x cols, lds) of type Ts, device to device.
 cudaError_t convert_matrix(void* dst, int dtd, int64_t ldd, const void* src, int dts, int64_t lds,
                            int64_t rows, int64_t cols, cudaStream_t st);
@@ -214,6 +219,8 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
 grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const float* C,
                                float* R, int64_t ldr, cudaStream_t st);
 void splitgemm_destroy(SplitGemm* g);
+// G = A A^T (m x m, row stride ldg) with the split-BF16 tensor-core GEMM
+grbk_status splitgemm_gram(SplitGemm* g, float* G, int64_t ldg, cudaStream_t st);
 // reads the device error flag of the tensor-core kernels (GRBK_ETIMEOUT if a wait expired)
 grbk_status splitgemm_check(SplitGemm* g, cudaStream_t st);
 // kernel launches made by one splitgemm_residual call

@@ -58,14 +58,11 @@ struct IterParams {
     T* R;
     const double* a;            // ||A_i||^2
     const double* rbk_prefix;   // running sums of a_i (ME-RBK inverse CDF)
-    double* s;                  // ||R_i||^2
-    double* r;                  // s_i / a_i  (-inf for zero rows of A)
+    double2* sr;                // (||R_i||^2, s_i / a_i); r = -inf for zero rows of A
     T* u;                       // A A_{i_k}^T
     T* v;                       // w B, ldr entries (padding stays 0)
     T* w;                       // R_{i_k} B^T
-    double* part_S;             // per-CTA partial sums of s_i
-    double* part_best_r;        // per-CTA max of r_i
-    long long* part_best_i;     //   and its row
+    double4* part;              // per CTA: (sum of s_i, max r_i, its row as bits, unused)
     double* part_SJ;            // per-CTA admitted sums
     int* hist_rows;             // per chunk: i_k
     double* hist_c;             //            alpha / a_{i_k}
@@ -82,6 +79,8 @@ struct IterParams {
     int nit;
     int smem_v;                 // v / R_{i_k} staged in shared memory
     int smem_arow;              // A_{i_k} staged in shared memory
+    const T* G;                 // A A^T (m x ldg) or null
+    int64_t ldg;
 };
 
 // balanced contiguous row range of CTA c among G
@@ -96,9 +95,12 @@ __device__ __forceinline__ void cta_rows(int64_t m, int c, int G, int64_t& r0, i
 // s_i = ||R_i||^2 (FP64 sum of per-lane partials; FP32 lanes use Kahan
 // compensation), r_i = s_i / a_i, and the CTA's partial sum / argmax.
 // ----------------------------------------------------------------------------
+// sm_sr (optional): this CTA's (s_i, r_i), rows r0.. in order, kept in shared memory
+constexpr int kSrCap = 512;
+
 template <typename T, bool UPDATE>
 __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const T* vsrc, int64_t r0, int64_t r1,
-                           double* sm_parts, double* sm_red, long long* sm_redi)
+                           double* sm_parts, double* sm_red, long long* sm_redi, double2* sm_sr = nullptr)
 {
     using V = typename VecOf<T>::V;
     constexpr int VN = VecOf<T>::N;
@@ -177,8 +179,8 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             const int64_t row = b0 + rr;
             const double ai = __ldg(P.a + row);
             const double ri = (ai > 0.0) ? __ddiv_rn(sv, ai) : -INFINITY;
-            __stcg(P.s + row, sv);
-            __stcg(P.r + row, ri);
+            __stcg(P.sr + row, make_double2(sv, ri));
+            if (sm_sr) sm_sr[row - r0] = make_double2(sv, ri);
             my_S += sv;
             if (ri > my_best) { my_best = ri; my_bi = row; }
         }
@@ -201,9 +203,9 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        __stcg(P.part_S + blockIdx.x, cta_S);
-        __stcg(P.part_best_r + blockIdx.x, cta_best);
-        __stcg(P.part_best_i + blockIdx.x, cta_bi);
+        double2* pp = reinterpret_cast<double2*>(P.part + blockIdx.x);
+        __stcg(pp, make_double2(cta_S, cta_best));
+        __stcg(pp + 1, make_double2(__longlong_as_double(cta_bi), 0.0));
     }
 }
 
@@ -365,6 +367,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     __shared__ double s_S, s_rmax, s_t;
     __shared__ long long s_imax, s_ik;
     __shared__ int s_stop;
+    __shared__ double2 sm_sr[kSrCap];          // this CTA's (s_i, r_i) when it owns <= kSrCap rows
 
     T* sv = reinterpret_cast<T*>(dsm);                               // ldr: R_{i_k}, then v
     T* sa = sv + (P.smem_v ? P.ldr : 0);                              // lda: A_{i_k}
@@ -376,6 +379,10 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     cta_rows(P.m, c, G, r0, r1);
     using V = typename VecOf<T>::V;
     constexpr int VN = VecOf<T>::N;
+    const bool own_sm = (r1 - r0) <= kSrCap;
+    if (own_sm)
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) sm_sr[i - r0] = __ldcg(P.sr + i);
+    __syncthreads();
 
     for (int it = 0; it <= P.nit; ++it) {
         const long long k = P.k0 + it;
@@ -384,9 +391,11 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             double S = 0.0, br = -INFINITY;
             long long bi = 0x7fffffffffffffffLL;
             for (int cc = lane; cc < G; cc += 32) {
-                S += __ldcg(P.part_S + cc);
-                const double rr = __ldcg(P.part_best_r + cc);
-                const long long ii = __ldcg(P.part_best_i + cc);
+                const double2* pp = reinterpret_cast<const double2*>(P.part + cc);
+                const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
+                S += p0.x;
+                const double rr = p0.y;
+                const long long ii = __double_as_longlong(p1.x);
                 if (rr > br || (rr == br && ii < bi)) { br = rr; bi = ii; }
             }
             S = warp_sum(S);
@@ -424,16 +433,25 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             if (warp == 0) {
                 double sj = 0.0;
                 for (int64_t i = r0 + lane; i < r1; i += 32) {
-                    const double ri = __ldcg(P.r + i);
-                    if (ri >= t) sj += __ldcg(P.s + i);
+                    const double2 v = own_sm ? sm_sr[i - r0] : __ldcg(P.sr + i);
+                    if (v.y >= t) sj += v.x;
                 }
                 sj = warp_sum(sj);
                 if (lane == 0) __stcg(P.part_SJ + c, sj);
             }
             if (!grid_sync(P.bar, P.st, 1, s_ok)) return;
             if (warp == 0) {
+                // every partial this lane will scan, loaded at once (G <= 32 * kPartRegs)
+                constexpr int kPartRegs = 10;
+                double pv[kPartRegs];
+#pragma unroll
+                for (int j = 0; j < kPartRegs; ++j) {
+                    const int cc = j * 32 + lane;
+                    pv[j] = (cc < G) ? __ldcg(P.part_SJ + cc) : 0.0;
+                }
                 double SJ = 0.0;
-                for (int cc = lane; cc < G; cc += 32) SJ += __ldcg(P.part_SJ + cc);
+#pragma unroll
+                for (int j = 0; j < kPartRegs; ++j) SJ += pv[j];
                 SJ = warp_sum(SJ);
                 const double u = philox_uniform(P.seed, (uint64_t)k, P.sys);
                 const double target = __dmul_rn(u, SJ);
@@ -443,7 +461,10 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
                 double excl = 0.0;
                 for (int cb = 0; cb < G && cstar < 0; cb += 32) {
                     const int cc = cb + lane;
-                    const double val = (cc < G) ? __ldcg(P.part_SJ + cc) : 0.0;
+                    double val = 0.0;
+#pragma unroll
+                    for (int j = 0; j < kPartRegs; ++j)
+                        if (j == cb / 32) val = pv[j];
                     const double inc = base + warp_inclusive_scan(val);
                     const unsigned hit = __ballot_sync(0xffffffffu, (cc < G) && (inc > target) && val > 0.0);
                     if (hit) {
@@ -462,14 +483,30 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
                 if (cstar >= 0) cta_rows(P.m, cstar, G, q0, q1);
                 long long pick = -1, last = -1;
                 double run = excl;
+                // the owning CTA's rows, loaded at once (up to 32 * kRowRegs rows, then in further rounds)
+                constexpr int kRowRegs = 8;
+                double2 rv[kRowRegs];
+#pragma unroll
+                for (int j = 0; j < kRowRegs; ++j) {
+                    const int64_t i = q0 + j * 32 + lane;
+                    rv[j] = (i < q1) ? __ldcg(P.sr + i) : make_double2(0.0, -INFINITY);
+                }
                 for (int64_t ib = q0; ib < q1 && pick < 0; ib += 32) {
                     const int64_t i = ib + lane;
                     double val = 0.0;
                     bool adm = false;
                     if (i < q1) {
-                        const double ri = __ldcg(P.r + i);
-                        adm = (ri >= t);
-                        if (adm) val = __ldcg(P.s + i);
+                        const int64_t jr = (ib - q0) / 32;
+                        double2 v = make_double2(0.0, -INFINITY);
+                        if (jr < kRowRegs) {
+#pragma unroll
+                            for (int j = 0; j < kRowRegs; ++j)
+                                if (j == jr) v = rv[j];
+                        } else {
+                            v = __ldcg(P.sr + i);
+                        }
+                        adm = (v.y >= t);
+                        if (adm) val = v.x;
                     }
                     const double inc = run + warp_inclusive_scan(val);
                     const unsigned am = __ballot_sync(0xffffffffu, adm);
@@ -522,7 +559,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
                 reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(Rik) + e);
         }
-        if (P.smem_arow) {
+        if (P.smem_arow && !P.G) {
             for (int64_t e = threadIdx.x; e < P.lda / VN; e += kBlock)
                 reinterpret_cast<V*>(sa)[e] = __ldg(reinterpret_cast<const V*>(Aik) + e);
         }
@@ -532,10 +569,17 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             // rows of A (for u, consumed by the same CTA in the fused pass)
             int64_t j0, j1;
             cta_rows(P.q, c, G, j0, j1);
-            rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w,
-                        P.hist_w + (int64_t)it * P.q, sm_parts);
-            // u holds the row coefficients c_k (A A_ik^T)_i of the rank-1 update
-            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
+            // u first, then w: B is read last here, so the part of it still in L2 serves
+            // the v = w B phase that follows; u holds the row coefficients c_k (A A_ik^T)_i,
+            // read from row i_k of the precomputed A A^T when there is one
+            if (P.G) {
+                const T* Gi = P.G + ik * P.ldg;
+                for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
+            } else {
+                rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
+            }
+            rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w, P.hist_w + (int64_t)it * P.q,
+                        sm_parts);
         }
         if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
 
@@ -551,7 +595,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
                 reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(P.v) + e);
             __syncthreads();
         }
-        fused_pass<T, true>(P, ck, P.smem_v ? sv : P.v, r0, r1, sm_parts, sm_red, sm_redi);
+        fused_pass<T, true>(P, ck, P.smem_v ? sv : P.v, r0, r1, sm_parts, sm_red, sm_redi, own_sm ? sm_sr : nullptr);
         if (!grid_sync(P.bar, P.st, 4, s_ok)) return;
     }
 }
@@ -744,9 +788,10 @@ struct grbk_ctx {
     size_t dyn_smem;
     // device buffers
     void *A, *B, *C, *R, *u, *v, *w;
-    double *a, *rbk_prefix, *s, *r, *X;
-    double *part_S, *part_best_r, *part_SJ;
-    long long* part_best_i;
+    double *a, *rbk_prefix, *X;
+    double2* sr;
+    double4* part;
+    double* part_SJ;
     int* hist_rows;
     double *hist_c, *hist_w;
     int chunk_cap;
@@ -760,6 +805,8 @@ struct grbk_ctx {
     SplitGemm* sg;
     void* tmp;              // staging for host <-> device conversions
     size_t tmp_bytes;
+    void* gram;             // A A^T (m x ldg) when used
+    int64_t ldg;
     cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
     long long launches;     // kernel launches issued (reset per solve)
 };
@@ -828,14 +875,15 @@ static IterParams<T> make_params(grbk_ctx* c)
     P.m = c->m; P.p = c->p; P.q = c->q; P.n = c->n;
     P.lda = c->lda; P.ldb = c->ldb; P.ldr = c->ldr;
     P.A = (const T*)c->A; P.B = (const T*)c->B; P.R = (T*)c->R;
-    P.a = c->a; P.rbk_prefix = c->rbk_prefix; P.s = c->s; P.r = c->r;
+    P.a = c->a; P.rbk_prefix = c->rbk_prefix; P.sr = c->sr;
     P.u = (T*)c->u; P.v = (T*)c->v; P.w = (T*)c->w;
-    P.part_S = c->part_S; P.part_best_r = c->part_best_r; P.part_best_i = c->part_best_i;
+    P.part = c->part;
     P.part_SJ = c->part_SJ;
     P.hist_rows = c->hist_rows; P.hist_c = c->hist_c; P.hist_w = c->hist_w;
     P.bar = c->bar; P.st = c->st;
     P.F = c->F; P.alpha = c->alpha;
     P.smem_v = c->smem_v; P.smem_arow = c->smem_arow;
+    P.G = (const T*)c->gram; P.ldg = c->ldg;
     P.stop_S = -1.0;
     return P;
 }
@@ -911,9 +959,9 @@ extern "C" const char* grbk_strerror(int32_t s)
 extern "C" void grbk_destroy(grbk_ctx* c)
 {
     if (!c) return;
-    void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->s, c->r, c->X,
-                    c->part_S, c->part_best_r, c->part_SJ, c->part_best_i, c->hist_rows, c->hist_c,
-                    c->hist_w, c->bar, c->st, c->scratch, c->tmp};
+    void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->sr, c->X,
+                    c->part, c->part_SJ, c->hist_rows, c->hist_c,
+                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -1086,8 +1134,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     ALLOC(c->w, (size_t)q * es);
     ALLOC(c->a, (size_t)m * 8);
     ALLOC(c->rbk_prefix, (size_t)m * 8);
-    ALLOC(c->s, (size_t)m * 8);
-    ALLOC(c->r, (size_t)m * 8);
+    ALLOC(c->sr, (size_t)m * 16);
     ALLOC(c->X, (size_t)p * q * 8);
     ALLOC(c->bar, sizeof(GridBarrier));
     ALLOC(c->st, sizeof(DevState));
@@ -1157,9 +1204,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     }
 
     TRY(c->prec == GRBK_F64 ? setup_launch_shape<double>(c) : setup_launch_shape<float>(c));
-    ALLOC(c->part_S, (size_t)c->G * 8);
-    ALLOC(c->part_best_r, (size_t)c->G * 8);
-    ALLOC(c->part_best_i, (size_t)c->G * 8);
+    ALLOC(c->part, (size_t)c->G * sizeof(double4));
     ALLOC(c->part_SJ, (size_t)c->G * 8);
     c->chunk_cap = o.check_every > 0 ? o.check_every : (o.refresh_T > 0 ? o.refresh_T : 256);
     if (o.refresh_T > 0 && c->chunk_cap > o.refresh_T) c->chunk_cap = o.refresh_T;
@@ -1170,6 +1215,21 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     if (c->prec == GRBK_F32)
         TRY(splitgemm_create(&c->sg, m, p, q, n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
                              o.split_terms, st));
+    // A A^T, formed once (the practice note after Algorithm 3)
+    c->ldg = round_up(m, 32);
+    const bool want_gram = o.use_gram > 0 || (o.use_gram == 0 && (double)m * c->ldg * es <= 4.0e9);
+    if (want_gram) {
+        ALLOC(c->gram, (size_t)m * c->ldg * es);
+        if (c->prec == GRBK_F64) {
+            if (gram_simt<double>(m, p, (const double*)c->A, c->lda, (double*)c->gram, c->ldg, st) != cudaSuccess) {
+                grbk_destroy(c);
+                return GRBK_ECUDA;
+            }
+        } else {
+            TRY(splitgemm_gram(c->sg, (float*)c->gram, c->ldg, st));
+            TRY(splitgemm_check(c->sg, st));
+        }
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
     *out = c;
     return GRBK_OK;
@@ -1339,6 +1399,7 @@ extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, co
         res->alpha = c->alpha;
         res->iter_kernel_ms = iter_ms;
         res->iter_kernel_launches = iter_launches;
+        res->gram = c->gram != nullptr;
         res->launches = c->launches;
         res->status = result;
         res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
@@ -1374,8 +1435,9 @@ extern "C" grbk_status grbk_get_residual(grbk_ctx* c, grbk_mat* R_out)
 extern "C" grbk_status grbk_get_rownorms(grbk_ctx* c, double* s_out, int32_t on_device)
 {
     if (!c || !s_out) return GRBK_EINVAL;
-    GRBK_CK(cudaMemcpyAsync(s_out, c->s, c->m * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                            c->stream));
+    // the row norms are the first members of the (s_i, r_i) pairs
+    GRBK_CK(cudaMemcpy2DAsync(s_out, 8, c->sr, 16, 8, c->m,
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     GRBK_CK(cudaStreamSynchronize(c->stream));
     return GRBK_OK;
 }

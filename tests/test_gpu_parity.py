@@ -118,6 +118,23 @@ def test_fp64_chunks_and_grids_do_not_change_the_result():
         assert _rel(r["X"], runs[0]["X"]) < 1e-12
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_gram_and_gemv_paths_agree(precision):
+    """u = (A A^T)_{:,i} from the precomputed Gram matrix (the practice note after
+    Algorithm 3) and u = A A_i^T streamed every iteration give the same rows, and
+    iterates equal to rounding (FP64) or to FP32 accuracy."""
+    A, B, C, _ = workloads.gaussian(333, 41, 29, 211, seed=14)
+    al = _alpha(B)
+    runs = [_gpu_run(A, B, C, "rgrbk", theta=0.6, alpha=al, seed=4, maxit=400, precision=precision,
+                     use_gram=ug, refresh_T=(64 if precision == "f32" else 0)) for ug in (1, -1)]
+    assert runs[0]["res"]["gram"] == 1 and runs[1]["res"]["gram"] == 0
+    if precision == "f64":
+        assert np.array_equal(runs[0]["rows"], runs[1]["rows"])
+        assert _rel(runs[0]["X"], runs[1]["X"]) < 1e-12
+    else:
+        assert _rel(runs[0]["X"], runs[1]["X"]) < 1e-4
+
+
 def test_fp64_refresh_keeps_parity():
     """Refreshing R = C - A X B every 64 iterations (FP64 GEMMs) keeps the row
     sequence and the iterate."""
