@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
+#include <algorithm>
 
 #include "grbk_internal.cuh"
 
@@ -253,14 +254,24 @@ __device__ __forceinline__ void split_f(float x, int terms, __nv_bfloat16* t)
     if (terms > 2) t[2] = __float2bfloat16_rn(r1 - __bfloat162float(l));
 }
 
-// D[M x N] = sum over term pairs of A_ta[M x K] * B_tb[N x K]^T; 256 threads:
-// warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM owner, warps 4-7 = epilogue.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// D[M x N] = sum over term pairs of A_ta[M x K] * B_tb[N x K]^T, persistent:
+// each CTA walks output tiles blockIdx.x, blockIdx.x + gridDim.x, ... (tile
+// index = m_block * n_blocks + n_block).  Two TMEM accumulators let the
+// epilogue of one tile run while the MMAs of the next are issued.
+// 256 threads: warp 0 = TMA producer, warp 1 = MMA issuer, warp 2 = TMEM owner,
+// warps 4-7 = epilogue.  Barriers: full/empty per smem stage, acc_full/acc_empty
+// per accumulator (acc_empty counts the 4 epilogue warps), done (all MMAs).
 template <int TERMS>
 __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, Args g)
 {
     constexpr int BN = Cfg<TERMS>::BN, B_TILE = Cfg<TERMS>::B_TILE, STAGE_BYTES = Cfg<TERMS>::STAGE_BYTES;
-    constexpr int TMEM_COLS = BN;
+    constexpr int TMEM_COLS = 2 * BN;
     constexpr uint32_t IDESC = idesc_for(BN);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -268,22 +279,28 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
     auto sA = [&](int s, int t) { return smem + s * STAGE_BYTES + t * A_TILE; };
     auto sB = [&](int s, int t) { return smem + s * STAGE_BYTES + TERMS * A_TILE + t * B_TILE; };
     uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+    const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
     __shared__ int s_abort;
 
     // a CTA that finds the error flag already set (an earlier CTA's wait
     // expired) leaves at once, before touching barriers or TMEM
     if (*(volatile int*)g.err != 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nkb = g.K / BK;
-    const int total = nkb;
+    const int n_blocks = (g.N + BN - 1) / BN, m_blocks = (g.M + BM - 1) / BM;
+    const int ntiles = n_blocks * m_blocks;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4);
         }
         mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -302,95 +319,118 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
 
     if (warp == 0 && lane == 0) {
         int issued = 0;
-        for (int it = 0; it < total; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-            if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; break; }
-            if (*(volatile int*)&s_abort) break;
-            const int kb = it;
-            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+            const int m0 = (tile / n_blocks) * BM, n0 = (tile % n_blocks) * BN;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int it = issued;
+                const int s = it % STAGES;
+                const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
 #pragma unroll
-            for (int t = 0; t < TERMS; ++t) {
-                tma_load_3d(smem_u32(sA(s, t)), &tmA, kb * BK, m0, t, full0 + 8 * s);
-                tma_load_3d(smem_u32(sB(s, t)), &tmB, kb * BK, n0, t, full0 + 8 * s);
+                for (int t = 0; t < TERMS; ++t) {
+                    tma_load_3d(smem_u32(sA(s, t)), &tmA, kb * BK, m0, t, full0 + 8 * s);
+                    tma_load_3d(smem_u32(sB(s, t)), &tmB, kb * BK, n0, t, full0 + 8 * s);
+                }
+                ++issued;
             }
-            ++issued;
         }
         // wait (bounded) for this CTA's copies still in flight before anyone leaves
         for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
             mbar_wait(full0 + 8 * (it % STAGES), (uint32_t)((it / STAGES) & 1));
     } else if (warp == 1 && lane == 0) {
-        for (int it = 0; it < total; ++it) {
-            const int s = it % STAGES;
-            const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-            if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; break; }
-            if (*(volatile int*)&s_abort) break;
+        int it = 0, lt = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            // the epilogue has drained this accumulator (first two tiles pass at once)
+            if (!mbar_wait(acce0 + 8 * acc, (uint32_t)(((lt >> 1) & 1) ^ 1))) { s_abort = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)(acc * BN);
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % STAGES;
+                const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int p = 0; p < Cfg<TERMS>::NPAIRS; ++p) {
-                int ta, tb;
-                pair_terms(TERMS, p, ta, tb);
-                const uint32_t a0 = smem_u32(sA(s, ta)), b0 = smem_u32(sB(s, tb));
+                for (int p = 0; p < Cfg<TERMS>::NPAIRS; ++p) {
+                    int ta, tb;
+                    pair_terms(TERMS, p, ta, tb);
+                    const uint32_t a0 = smem_u32(sA(s, ta)), b0 = smem_u32(sB(s, tb));
 #pragma unroll
-                for (int kk = 0; kk < BK / 16; ++kk)
-                    mma_bf16(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
-                             (it > 0 || p > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(dacc, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
+                                 (kb > 0 || p > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);
             }
-            mma_commit(empty0 + 8 * s);
+            if (!stop) mma_commit(accf0 + 8 * acc);  // this tile's accumulator is complete
         }
         mma_commit(done);  // arrives once every MMA issued above has completed
     } else if (warp >= 4) {
         const int e = warp - 4;
-        const bool ok = mbar_wait(done, 0);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = m0 + e * 32 + lane;
-        const bool write = ok && !*(volatile int*)&s_abort;
-        for (int cb = 0; cb < BN; cb += 32) {
-            uint32_t r[32];
-            tmem_ld32(tmem + ((uint32_t)(e * 32) << 16) + (uint32_t)cb, r);
-            if (!write || row >= g.M || n0 + cb >= g.N) continue;
-            const int col0 = n0 + cb;
-            const bool full = col0 + 32 <= g.N;
-            if (g.mode == EPI_RESID || g.mode == EPI_STORE) {
-                const bool resid = g.mode == EPI_RESID;
-                const float* ci = resid ? g.cin + (int64_t)row * g.ld + col0 : nullptr;
-                float* oi = g.out + (int64_t)row * g.ld + col0;
-                if (full) {
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const bool ok = mbar_wait(accf0 + 8 * acc, (uint32_t)((lt >> 1) & 1));
+            if (!ok || *(volatile int*)&s_abort) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int m0 = (tile / n_blocks) * BM, n0 = (tile % n_blocks) * BN;
+            const int row = m0 + e * 32 + lane;
+            for (int cb = 0; cb < BN; cb += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(acc * BN) + ((uint32_t)(e * 32) << 16) + (uint32_t)cb, r);
+                if (row >= g.M || n0 + cb >= g.N) continue;
+                const int col0 = n0 + cb;
+                const bool full = col0 + 32 <= g.N;
+                if (g.mode == EPI_RESID || g.mode == EPI_STORE) {
+                    const bool resid = g.mode == EPI_RESID;
+                    const float* ci = resid ? g.cin + (int64_t)row * g.ld + col0 : nullptr;
+                    float* oi = g.out + (int64_t)row * g.ld + col0;
+                    if (full) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        float4 ov;
-                        if (resid) {
-                            const float4 cv = __ldg(reinterpret_cast<const float4*>(ci + j));
-                            ov.x = cv.x - __uint_as_float(r[j]);
-                            ov.y = cv.y - __uint_as_float(r[j + 1]);
-                            ov.z = cv.z - __uint_as_float(r[j + 2]);
-                            ov.w = cv.w - __uint_as_float(r[j + 3]);
-                        } else {
-                            ov = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        for (int j = 0; j < 32; j += 4) {
+                            float4 ov;
+                            if (resid) {
+                                const float4 cv = __ldg(reinterpret_cast<const float4*>(ci + j));
+                                ov.x = cv.x - __uint_as_float(r[j]);
+                                ov.y = cv.y - __uint_as_float(r[j + 1]);
+                                ov.z = cv.z - __uint_as_float(r[j + 2]);
+                                ov.w = cv.w - __uint_as_float(r[j + 3]);
+                            } else {
+                                ov = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                 __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                            }
+                            *reinterpret_cast<float4*>(oi + j) = ov;
                         }
-                        *reinterpret_cast<float4*>(oi + j) = ov;
+                    } else {
+                        for (int j = 0; j < 32 && col0 + j < g.N; ++j)
+                            oi[j] = resid ? ci[j] - __uint_as_float(r[j]) : __uint_as_float(r[j]);
                     }
                 } else {
-                    for (int j = 0; j < 32 && col0 + j < g.N; ++j)
-                        oi[j] = resid ? ci[j] - __uint_as_float(r[j]) : __uint_as_float(r[j]);
-                }
-            } else {
-                for (int j = 0; j < 32 && col0 + j < g.N; ++j) {
-                    __nv_bfloat16 t[3];
-                    split_f(__uint_as_float(r[j]), g.out_terms, t);
-                    for (int tt = 0; tt < g.out_terms; ++tt)
-                        g.out_split[((int64_t)tt * g.out_rows + row) * g.out_ld + col0 + j] = t[tt];
+                    for (int j = 0; j < 32 && col0 + j < g.N; ++j) {
+                        __nv_bfloat16 t[3];
+                        split_f(__uint_as_float(r[j]), g.out_terms, t);
+                        for (int tt = 0; tt < g.out_terms; ++tt)
+                            g.out_split[((int64_t)tt * g.out_rows + row) * g.out_ld + col0 + j] = t[tt];
+                    }
                 }
             }
+            // hand the accumulator back to the MMA issuer
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * acc);
         }
-    }
-    if (threadIdx.x == 0 || (warp >= 4 && lane == 0)) {
-        if (*(volatile int*)&s_abort) atomicExch(g.err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&s_abort) atomicExch(g.err, 1);
     if (warp == 2) {
+        // every MMA this CTA issued has completed before the columns are freed
+        mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
@@ -454,6 +494,7 @@ struct SplitGemm {
     CUtensorMap tmA, tmXT, tmT1, tmBT;
     CUtensorMap tmAn;               // A's planes as the N-side operand (for A A^T)
     int* err;
+    int nsm;                        // persistent grid size
 };
 
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -492,6 +533,12 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     g->m = m; g->p = p; g->q = q; g->n = n; g->lda = lda; g->ldb = ldb; g->terms = terms;
     g->Kp = round_up(p, tc::BK);
     g->Kq = round_up(q, tc::BK);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (g->nsm < 1) g->nsm = 1;
+    }
     g->mr = round_up(m, tc::BN_MAX);   // A's planes also serve as the N-side operand of A A^T
     g->nr = round_up(n, tc::BN_MAX);
     g->qr = round_up(q, tc::BN_MAX);
@@ -552,8 +599,9 @@ grbk_status splitgemm_residual(SplitGemm* g, const double* X, int64_t ldx, const
     a2.M = (int)g->m; a2.N = (int)g->n; a2.K = (int)g->Kq;
     a2.mode = tc::EPI_RESID; a2.cin = C; a2.out = R; a2.ld = ldr; a2.err = g->err;
     const int bn = g->terms == 2 ? tc::Cfg<2>::BN : tc::Cfg<3>::BN;
-    dim3 g1((unsigned)((g->q + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
-    dim3 g2((unsigned)((g->n + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    const int64_t t1 = ((g->q + bn - 1) / bn) * ((g->m + tc::BM - 1) / tc::BM);
+    const int64_t t2 = ((g->n + bn - 1) / bn) * ((g->m + tc::BM - 1) / tc::BM);
+    dim3 g1((unsigned)std::min<int64_t>(t1, g->nsm)), g2((unsigned)std::min<int64_t>(t2, g->nsm));
     if (g->terms == 2) {
         tc::gemm_kernel<2><<<g1, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmXT, a1);
         GRBK_CK(cudaGetLastError());
@@ -574,7 +622,8 @@ grbk_status splitgemm_gram(SplitGemm* g, float* G, int64_t ldg, cudaStream_t st)
     a.M = (int)g->m; a.N = (int)g->m; a.K = (int)g->Kp;
     a.mode = tc::EPI_STORE; a.out = G; a.ld = ldg; a.err = g->err;
     const int bn = g->terms == 2 ? tc::Cfg<2>::BN : tc::Cfg<3>::BN;
-    dim3 grid((unsigned)((g->m + bn - 1) / bn), (unsigned)((g->m + tc::BM - 1) / tc::BM));
+    const int64_t tiles = ((g->m + bn - 1) / bn) * ((g->m + tc::BM - 1) / tc::BM);
+    dim3 grid((unsigned)std::min<int64_t>(tiles, g->nsm));
     if (g->terms == 2) tc::gemm_kernel<2><<<grid, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmAn, a);
     else tc::gemm_kernel<3><<<grid, 256, tc::SMEM_BYTES, st>>>(g->tmA, g->tmAn, a);
     GRBK_CK(cudaGetLastError());

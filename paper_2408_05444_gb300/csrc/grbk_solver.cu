@@ -687,6 +687,58 @@ __global__ void x_fold_kernel(double* X, int64_t p, int64_t q, const T* A, int64
     X[idx] += acc;
 }
 
+// FP32-mode fold: X (FP64) += sum_t c_t A_{i_t}^T w_t with the sum over the
+// chunk's terms formed in FP32 on 64 x 128 tiles of X staged in shared memory
+// (sa[t][r] = c_t A[i_t][r0 + r], sw[t][j] = w_t[j0 + j]), 64 terms at a time.
+constexpr int kFoldR = 64, kFoldC = 128, kFoldT = 64;
+
+__global__ void __launch_bounds__(512) x_fold_f32_kernel(double* X, int64_t p, int64_t q, const float* A,
+                                                         int64_t lda, const int* rows, const double* cs,
+                                                         const double* W, int nit)
+{
+    __shared__ float sa[kFoldT][kFoldR];
+    __shared__ float sw[kFoldT][kFoldC];
+    const int64_t r0 = (int64_t)blockIdx.y * kFoldR, j0 = (int64_t)blockIdx.x * kFoldC;
+    const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // rows 2tr, 2tr+1; columns tc + 16b
+    float acc[2][8];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    for (int t0 = 0; t0 < nit; t0 += kFoldT) {
+        const int nt = min(kFoldT, nit - t0);
+        for (int e = threadIdx.x; e < nt * kFoldR; e += 512) {
+            const int t = e / kFoldR, r = e % kFoldR;
+            sa[t][r] = (r0 + r < p) ? (float)(cs[t0 + t] * (double)__ldg(A + (int64_t)rows[t0 + t] * lda + r0 + r)) : 0.f;
+        }
+        for (int e = threadIdx.x; e < nt * kFoldC; e += 512) {
+            const int t = e / kFoldC, j = e % kFoldC;
+            sw[t][j] = (j0 + j < q) ? (float)W[(int64_t)(t0 + t) * q + j0 + j] : 0.f;
+        }
+        __syncthreads();
+        for (int t = 0; t < nt; ++t) {
+            const float a0 = sa[t][2 * tr], a1 = sa[t][2 * tr + 1];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const float wv = sw[t][tc + 16 * b];
+                acc[0][b] = fmaf(a0, wv, acc[0][b]);
+                acc[1][b] = fmaf(a1, wv, acc[1][b]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int64_t rr = r0 + 2 * tr + a;
+        if (rr >= p) continue;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int64_t j = j0 + tc + 16 * b;
+            if (j < q) X[rr * q + j] += (double)acc[a][b];
+        }
+    }
+}
+
 // power iteration pieces for ||B||_2^2 on the streaming helpers:
 // t = B^T x (column slabs, x staged in shared memory) ; y = B t (row blocks)
 template <typename T>
@@ -1267,9 +1319,11 @@ static grbk_status fold_x(grbk_ctx* c, int nit)
     if (c->prec == GRBK_F64)
         x_fold_kernel<double><<<blocks, 256, 0, c->stream>>>(c->X, c->p, c->q, (const double*)c->A, c->lda,
                                                             c->hist_rows, c->hist_c, c->hist_w, nit);
-    else
-        x_fold_kernel<float><<<blocks, 256, 0, c->stream>>>(c->X, c->p, c->q, (const float*)c->A, c->lda,
-                                                           c->hist_rows, c->hist_c, c->hist_w, nit);
+    else {
+        dim3 grid((unsigned)((c->q + kFoldC - 1) / kFoldC), (unsigned)((c->p + kFoldR - 1) / kFoldR));
+        x_fold_f32_kernel<<<grid, 512, 0, c->stream>>>(c->X, c->p, c->q, (const float*)c->A, c->lda, c->hist_rows,
+                                                       c->hist_c, c->hist_w, nit);
+    }
     GRBK_CK(cudaGetLastError());
     return GRBK_OK;
 }

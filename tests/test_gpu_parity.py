@@ -135,6 +135,19 @@ def test_gram_and_gemv_paths_agree(precision):
         assert _rel(runs[0]["X"], runs[1]["X"]) < 1e-4
 
 
+@pytest.mark.parametrize("terms", [2, 3])
+def test_fp32_gram_with_several_tiles_per_cta(terms):
+    """A A^T from the persistent tensor-core GEMM when the tile count exceeds the
+    SM count (each CTA reuses both of its TMEM accumulators): the solve with the
+    precomputed Gram matrix matches the one that streams A A_i^T."""
+    A, B, C, _ = workloads.gaussian(3000, 40, 20, 60, seed=21)
+    al = _alpha(B)
+    runs = [_gpu_run(A, B, C, "rgrbk", theta=0.5, alpha=al, seed=5, maxit=300, precision="f32",
+                     use_gram=ug, refresh_T=64, split_terms=terms, trace=False) for ug in (1, -1)]
+    assert runs[0]["res"]["gram"] == 1 and runs[1]["res"]["gram"] == 0
+    assert _rel(runs[0]["X"], runs[1]["X"]) < 1e-4
+
+
 def test_fp64_refresh_keeps_parity():
     """Refreshing R = C - A X B every 64 iterations (FP64 GEMMs) keeps the row
     sequence and the iterate."""
@@ -197,7 +210,7 @@ def test_nonzero_x0_and_limit():
 
 
 @pytest.mark.parametrize("terms,bound", [(3, 2e-6), (2, 6e-5)])
-@pytest.mark.parametrize("m,p,q,n", [(700, 130, 300, 517), (129, 64, 256, 256)])
+@pytest.mark.parametrize("m,p,q,n", [(700, 130, 300, 517), (129, 64, 256, 256), (9000, 64, 300, 1300)])
 def test_fp32_split_bf16_refresh(terms, bound, m, p, q, n):
     """The tensor-core refresh R = C - (A X) B with split-BF16 operands: every
     entry within `bound` of |A||X||B| + |C| (3 terms ~ FP32 rounding of the
