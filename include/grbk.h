@@ -85,7 +85,8 @@ typedef struct {
     int32_t check_every;  /* iterations per device chunk between host checks; 0 = refresh_T or 256 */
     int32_t use_gram;     /* form A A^T once and read u = (A A^T)_{:,i_k} from it (the practice note after
                              Algorithm 3): 1 on, -1 off (u = A A_{i_k}^T every iteration), 0 on when the
-                             m x m matrix takes at most 4 GB */
+                             m x m matrix takes at most 4 GB and, in FP64, forming it takes at most
+                             2 m^2 p = 1e11 flops (FP64 runs on the narrow FP64 pipe: about 80 ms) */
 } grbk_opts;
 
 typedef struct {

@@ -410,6 +410,27 @@ __global__ void __launch_bounds__(256, 1) gemm_kernel(const __grid_constant__ CU
                         for (int j = 0; j < 32 && col0 + j < g.N; ++j)
                             oi[j] = resid ? ci[j] - __uint_as_float(r[j]) : __uint_as_float(r[j]);
                     }
+                } else if (full) {
+                    // this lane's 32 columns of each term plane are 64 contiguous bytes
+                    // (the split planes have as many terms as the operands: out_terms == TERMS)
+#pragma unroll
+                    for (int tt = 0; tt < TERMS; ++tt) {
+                        uint4* dst = reinterpret_cast<uint4*>(g.out_split + ((int64_t)tt * g.out_rows + row) * g.out_ld +
+                                                              col0);
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; ++q4) {
+                            uint32_t w4[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                __nv_bfloat16 t0[3], t1[3];
+                                split_f(__uint_as_float(r[q4 * 8 + 2 * h]), TERMS, t0);
+                                split_f(__uint_as_float(r[q4 * 8 + 2 * h + 1]), TERMS, t1);
+                                w4[h] = (uint32_t)__bfloat16_as_ushort(t0[tt]) |
+                                        ((uint32_t)__bfloat16_as_ushort(t1[tt]) << 16);
+                            }
+                            dst[q4] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                        }
+                    }
                 } else {
                     for (int j = 0; j < 32 && col0 + j < g.N; ++j) {
                         __nv_bfloat16 t[3];

@@ -45,6 +45,12 @@ __device__ __forceinline__ float4 ldcg_v(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg_v(const double2* p) { return __ldcg(p); }
 __device__ __forceinline__ void stcg_v(float4* p, float4 v) { __stcg(p, v); }
 __device__ __forceinline__ void stcg_v(double2* p, double2 v) { __stcg(p, v); }
+// R is streamed once per iteration: evict-first loads and stores keep it from
+// pushing B, u and v out of L2
+__device__ __forceinline__ float4 ldcs_v(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ldcs_v(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ void stcs_v(float4* p, float4 v) { __stcs(p, v); }
+__device__ __forceinline__ void stcs_v(double2* p, double2 v) { __stcs(p, v); }
 
 // ----------------------------------------------------------------------------
 // kernel parameters
@@ -134,7 +140,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
                     const int64_t e = base + uu * 32 + lane;
-                    if (e < e1) rv[uu] = ldcg_v(Rrow + e);
+                    if (e < e1) rv[uu] = ldcs_v(Rrow + e);
                 }
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
@@ -156,7 +162,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
                                 acc_f = tk;
                             }
                         }
-                        if (UPDATE) stcg_v(Rrow + e, rv[uu]);
+                        if (UPDATE) stcs_v(Rrow + e, rv[uu]);
                     }
                 }
             }
@@ -1269,7 +1275,11 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
                              o.split_terms, st));
     // A A^T, formed once (the practice note after Algorithm 3)
     c->ldg = round_up(m, 32);
-    const bool want_gram = o.use_gram > 0 || (o.use_gram == 0 && (double)m * c->ldg * es <= 4.0e9);
+    // automatic choice: at most 4 GB, and in FP64 (SIMT, on the narrow FP64 pipe) at most
+    // 1e11 flops of set-up; the FP32 form builds it on the tensor cores in milliseconds
+    const double gram_flops = 2.0 * (double)m * (double)m * (double)p;
+    const bool want_gram = o.use_gram > 0 || (o.use_gram == 0 && (double)m * c->ldg * es <= 4.0e9 &&
+                                              (c->prec == GRBK_F32 || gram_flops <= 1.0e11));
     if (want_gram) {
         ALLOC(c->gram, (size_t)m * c->ldg * es);
         if (c->prec == GRBK_F64) {
