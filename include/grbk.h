@@ -61,6 +61,17 @@ typedef enum { GRBK_DT_F64 = 0, GRBK_DT_F32 = 1 } grbk_dtype;
  * iterations (X is folded in at those points).  NONE: run maxit iterations. */
 typedef enum { GRBK_STOP_NONE = 0, GRBK_STOP_RELRES = 1, GRBK_STOP_RSE = 2 } grbk_stop;
 
+/* How the residual is kept.  FULL: R = C - A X B, m x n, as in Algorithm 3.
+ * ROWSPACE: every residual row is a combination of the rows of B plus a part
+ * that the updates never change (each update of Algorithm 3 subtracts a
+ * multiple of R_{i_k} B^T B), so R = Z Bt + Rperp with Bt (r x n) an
+ * orthonormal basis of the row space of B (r = rank B) and Z = R Bt^T, m x r.
+ * The library keeps Z instead of R: s_i = ||Z_i||^2 + ||Rperp_i||^2 and the
+ * iterates are those of the full form up to rounding.  Set-up (pivoted
+ * Cholesky of B B^T, Z^0 and the Rperp row norms) costs O(m n q) and the
+ * residual shrinks by n / r.  Not part of the paper. */
+typedef enum { GRBK_FORM_FULL = 0, GRBK_FORM_ROWSPACE = 1 } grbk_form;
+
 /* A matrix argument.  `ptr` is a host pointer (on_device = 0) or a device
  * pointer (on_device = 1); the library never keeps it after the call returns. */
 typedef struct {
@@ -87,6 +98,9 @@ typedef struct {
                              Algorithm 3): 1 on, -1 off (u = A A_{i_k}^T every iteration), 0 on when the
                              m x m matrix takes at most 4 GB and, in FP64, forming it takes at most
                              2 m^2 p = 1e11 flops (FP64 runs on the narrow FP64 pipe: about 80 ms) */
+    int32_t form;         /* grbk_form; 0 = FULL */
+    double rank_tol;      /* ROWSPACE: pivots of B B^T at most rank_tol * max_i (B B^T)_ii end the
+                             basis (they set r); <= 0 selects 1e-12 (F64) or 1e-6 (F32) */
 } grbk_opts;
 
 typedef struct {
@@ -144,12 +158,18 @@ grbk_status grbk_solve(grbk_ctx* ctx, int32_t variant, double theta, const grbk_
 grbk_status grbk_residual(grbk_ctx* ctx, const grbk_mat* X, grbk_mat* R_out);
 
 /* Copies of the kept state after a solve: residual R (m x n) and row norms
- * ||R_i||^2 (m doubles, host or device per on_device). */
+ * ||R_i||^2 (m doubles, host or device per on_device).  grbk_residual and
+ * grbk_get_residual return GRBK_EINVAL for the ROWSPACE form, which keeps no
+ * m x n residual; its row norms include the fixed ||Rperp_i||^2. */
 grbk_status grbk_get_residual(grbk_ctx* ctx, grbk_mat* R_out);
 grbk_status grbk_get_rownorms(grbk_ctx* ctx, double* s_out, int32_t on_device);
 
-/* Problem sizes and the step in use. */
+/* Problem sizes (m, p, q, n of the caller's system) and the step in use. */
 grbk_status grbk_info(const grbk_ctx* ctx, int64_t dims[4], double* alpha);
+
+/* The residual form in use (grbk_form) and the columns of the kept residual:
+ * n for FULL, r = rank B for ROWSPACE.  Not part of the paper. */
+grbk_status grbk_form_info(const grbk_ctx* ctx, int32_t* form, int64_t* cols);
 
 void grbk_destroy(grbk_ctx* ctx);
 

@@ -25,6 +25,7 @@ VARIANTS = {"grbk": GRBK_GRBK, "rgrbk": GRBK_RGRBK, "mwrbk": GRBK_MWRBK, "rbk": 
 GRBK_F64, GRBK_F32 = 0, 1
 GRBK_DT_F64, GRBK_DT_F32 = 0, 1
 GRBK_STOP_NONE, GRBK_STOP_RELRES, GRBK_STOP_RSE = 0, 1, 2
+GRBK_FORM_FULL, GRBK_FORM_ROWSPACE = 0, 1
 
 
 class grbk_mat(ctypes.Structure):
@@ -38,7 +39,7 @@ class grbk_opts(ctypes.Structure):
                 ("x_ref", ctypes.POINTER(grbk_mat)), ("row_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("use_gram", ctypes.c_int32)]
+                ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double)]
 
 
 class grbk_result(ctypes.Structure):
@@ -61,7 +62,8 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_get_rownorms", "grbk_info", "grbk_destroy", "grbk_batch_create", "grbk_batch_solve",
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
-           "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest"]
+           "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
+           "grbk_form_info"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -90,6 +92,8 @@ def lib():
         L.grbk_get_rownorms.restype = i32
         L.grbk_info.argtypes = [vp, P(i64), P(dbl)]
         L.grbk_info.restype = i32
+        L.grbk_form_info.argtypes = [vp, P(i32), P(i64)]
+        L.grbk_form_info.restype = i32
         L.grbk_destroy.argtypes = [vp]
         L.grbk_destroy.restype = None
         L.grbk_batch_create.argtypes = [P(vp), i32, P(grbk_mat), P(grbk_mat), P(grbk_mat), P(grbk_opts)]
@@ -162,7 +166,8 @@ class _Keep:
 
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
-               x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None):
+               x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
+               form=None, rank_tol=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -181,6 +186,10 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.check_every = check_every
     if use_gram is not None:
         o.use_gram = {True: 1, False: -1}.get(use_gram, use_gram)
+    if form is not None:
+        o.form = {"full": GRBK_FORM_FULL, "rowspace": GRBK_FORM_ROWSPACE}.get(form, form)
+    if rank_tol is not None:
+        o.rank_tol = rank_tol
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     if x_ref is not None:
@@ -224,7 +233,8 @@ class Context:
 def grbk_create(A, B, C, opts=None, **kw) -> Context:
     """grbk_create(A, B, C, opts) -- set up one system; keyword options fill
     grbk_opts (precision='f64'|'f32', refresh_T, alpha, stop_kind, split_terms,
-    x_ref, trace_len, stream, grid_ctas, check_every)."""
+    x_ref, trace_len, stream, grid_ctas, check_every, use_gram, form='full'|'rowspace',
+    rank_tol)."""
     o, keep = _make_opts(opts, **kw)
     h = ctypes.c_void_p()
     mA, mB, mC = mat(A), mat(B), mat(C)
@@ -277,6 +287,16 @@ def grbk_info(ctx: Context):
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_info")
     return tuple(dims), al.value
+
+
+def grbk_form_info(ctx: Context):
+    """-> ('full' | 'rowspace', columns of the kept residual: n or rank B)."""
+    f = ctypes.c_int32()
+    cols = ctypes.c_int64()
+    st = lib().grbk_form_info(ctx.handle, ctypes.byref(f), ctypes.byref(cols))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_form_info")
+    return ("full", "rowspace")[f.value], cols.value
 
 
 def grbk_destroy(ctx: Context):

@@ -87,6 +87,7 @@ struct IterParams {
     int smem_arow;              // A_{i_k} staged in shared memory
     const T* G;                 // A A^T (m x ldg) or null
     int64_t ldg;
+    const double* soff;         // fixed row offsets added to s_i (row-space form) or null
 };
 
 // balanced contiguous row range of CTA c among G
@@ -183,6 +184,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             double sv = 0.0;
             for (int c = 0; c < nch; ++c) sv += sm_parts[rr * nch + c];
             const int64_t row = b0 + rr;
+            if (P.soff) sv += __ldg(P.soff + row);
             const double ai = __ldg(P.a + row);
             const double ri = (ai > 0.0) ? __ddiv_rn(sv, ai) : -INFINITY;
             __stcg(P.sr + row, make_double2(sv, ri));
@@ -865,6 +867,9 @@ struct grbk_ctx {
     size_t tmp_bytes;
     void* gram;             // A A^T (m x ldg) when used
     int64_t ldg;
+    int form;               // grbk_form
+    int64_t n_orig;         // columns of the caller's B and C (n is the kept residual's)
+    double* soff;           // row-space form: ||Rperp_i||^2
     cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
     long long launches;     // kernel launches issued (reset per solve)
 };
@@ -942,6 +947,7 @@ static IterParams<T> make_params(grbk_ctx* c)
     P.F = c->F; P.alpha = c->alpha;
     P.smem_v = c->smem_v; P.smem_arow = c->smem_arow;
     P.G = (const T*)c->gram; P.ldg = c->ldg;
+    P.soff = c->soff;
     P.stop_S = -1.0;
     return P;
 }
@@ -1019,7 +1025,7 @@ extern "C" void grbk_destroy(grbk_ctx* c)
     if (!c) return;
     void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->sr, c->X,
                     c->part, c->part_SJ, c->hist_rows, c->hist_c,
-                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram};
+                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -1169,10 +1175,13 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     if (o.split_terms == 0) o.split_terms = 2;
     if (o.split_terms != 2 && o.split_terms != 3) return GRBK_EINVAL;
     if (o.refresh_T < 0) return GRBK_EINVAL;
+    if (o.form != GRBK_FORM_FULL && o.form != GRBK_FORM_ROWSPACE) return GRBK_EINVAL;
 
     grbk_ctx* c = new grbk_ctx;
     memset(c, 0, sizeof(*c));
     c->m = m; c->p = p; c->q = q; c->n = n;
+    c->n_orig = n;
+    c->form = o.form;
     c->opts = o;
     c->prec = o.precision;
     c->esz = (c->prec == GRBK_F64) ? 8 : 4;
@@ -1225,6 +1234,39 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     if (badA || badB || badC) { grbk_destroy(c); return GRBK_ENONFINITE; }
     c->normC2 = ssC;
 
+    if (c->form == GRBK_FORM_ROWSPACE) {
+        // keep Z = R Bt^T (m x r) instead of R: solve the system (A, Lt, Chat) with
+        // the fixed row offsets ||Rperp_i||^2 (the derivation is in grbk_rowspace.cu)
+        const double tol = o.rank_tol > 0.0 ? o.rank_tol : (c->prec == GRBK_F64 ? 1e-12 : 1e-6);
+        RowspaceResult rs;
+        memset(&rs, 0, sizeof(rs));
+        TRY(rowspace_transform(c->prec == GRBK_F64, m, q, n, c->B, c->ldb, c->C, c->ldr, tol, st, &rs));
+        c->soff = rs.rperp;
+        const int64_t r = rs.r;
+        cudaFree(c->B); c->B = nullptr;
+        cudaFree(c->C); c->C = nullptr;
+        cudaFree(c->R); c->R = nullptr;
+        cudaFree(c->v); c->v = nullptr;
+        c->n = r;
+        c->ldb = round_up(r, 32);
+        c->ldr = c->ldb;
+        bool ok = cudaMalloc(&c->B, (size_t)q * c->ldb * es) == cudaSuccess &&
+                  cudaMalloc(&c->C, (size_t)m * c->ldr * es) == cudaSuccess &&
+                  cudaMalloc(&c->R, (size_t)m * c->ldr * es) == cudaSuccess &&
+                  cudaMalloc(&c->v, (size_t)c->ldr * es) == cudaSuccess;
+        if (ok)
+            ok = cudaMemsetAsync(c->B, 0, (size_t)q * c->ldb * es, st) == cudaSuccess &&
+                 cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, st) == cudaSuccess &&
+                 cudaMemsetAsync(c->R, 0, (size_t)m * c->ldr * es, st) == cudaSuccess &&
+                 cudaMemsetAsync(c->v, 0, (size_t)c->ldr * es, st) == cudaSuccess &&
+                 convert_matrix(c->B, dt, c->ldb, rs.Lt, dt, r, q, r, st) == cudaSuccess &&
+                 convert_matrix(c->C, dt, c->ldr, rs.Chat, dt, r, m, r, st) == cudaSuccess &&
+                 cudaStreamSynchronize(st) == cudaSuccess;
+        cudaFree(rs.Lt);
+        cudaFree(rs.Chat);
+        if (!ok) { grbk_destroy(c); return GRBK_ENOMEM; }
+    }
+
     // a_i, F and the RBK prefix (sequential, ascending rows)
     {
         const int threads = 256;
@@ -1271,7 +1313,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     ALLOC(c->hist_w, (size_t)c->chunk_cap * q * 8);
 
     if (c->prec == GRBK_F32)
-        TRY(splitgemm_create(&c->sg, m, p, q, n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
+        TRY(splitgemm_create(&c->sg, m, p, q, c->n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
                              o.split_terms, st));
     // A A^T, formed once (the practice note after Algorithm 3)
     c->ldg = round_up(m, 32);
@@ -1474,6 +1516,7 @@ extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, co
 extern "C" grbk_status grbk_residual(grbk_ctx* c, const grbk_mat* X, grbk_mat* R_out)
 {
     if (!c || !mat_ok(X) || X->rows != c->p || X->cols != c->q) return GRBK_EINVAL;
+    if (c->form != GRBK_FORM_FULL) return GRBK_EINVAL;
     if (!R_out || !R_out->ptr || R_out->rows != c->m || R_out->cols != c->n || R_out->ld < c->n) return GRBK_EINVAL;
     double* Xd = nullptr;
     void* Rd = nullptr;
@@ -1490,7 +1533,8 @@ extern "C" grbk_status grbk_residual(grbk_ctx* c, const grbk_mat* X, grbk_mat* R
 
 extern "C" grbk_status grbk_get_residual(grbk_ctx* c, grbk_mat* R_out)
 {
-    if (!c || !R_out || !R_out->ptr || R_out->rows != c->m || R_out->cols != c->n || R_out->ld < c->n) return GRBK_EINVAL;
+    if (!c || c->form != GRBK_FORM_FULL) return GRBK_EINVAL;
+    if (!R_out || !R_out->ptr || R_out->rows != c->m || R_out->cols != c->n || R_out->ld < c->n) return GRBK_EINVAL;
     grbk_status s = store_matrix(c, R_out, c->R, c->prec == GRBK_F64 ? GRBK_DT_F64 : GRBK_DT_F32, c->ldr);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess && s == GRBK_OK) s = GRBK_ECUDA;
     return s;
@@ -1545,10 +1589,18 @@ extern "C" grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream)
     return (grbk_status)h.status;
 }
 
+extern "C" grbk_status grbk_form_info(const grbk_ctx* c, int32_t* form, int64_t* cols)
+{
+    if (!c) return GRBK_EINVAL;
+    if (form) *form = c->form;
+    if (cols) *cols = c->n;
+    return GRBK_OK;
+}
+
 extern "C" grbk_status grbk_info(const grbk_ctx* c, int64_t dims[4], double* alpha)
 {
     if (!c) return GRBK_EINVAL;
-    if (dims) { dims[0] = c->m; dims[1] = c->p; dims[2] = c->q; dims[3] = c->n; }
+    if (dims) { dims[0] = c->m; dims[1] = c->p; dims[2] = c->q; dims[3] = c->n_orig; }
     if (alpha) *alpha = c->alpha;
     return GRBK_OK;
 }
