@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-rowspace", action="store_true")
     ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=2)
@@ -305,6 +306,44 @@ def native_arm(args):
         g.grbk_destroy(ctx64)
         del X64
 
+    # ---------------- row-space form: keeps Z = R Bt^T (m x rank B) ---------
+    # same iterates as the chosen form (FP32 + split-BF16 refresh every T), with
+    # the residual kept in an orthonormal basis of the row space of B
+    rowspace = None
+    if not args.no_rowspace:
+        barrier()
+        t0 = time.perf_counter()
+        ctxz = g.grbk_create(Ad, Bd, Cd, precision="f32", refresh_T=T, check_every=T, stream=stream,
+                             split_terms=args.split_terms, form="rowspace")
+        torch.cuda.synchronize(dev)
+        setup_s = time.perf_counter() - t0
+        r_cols = g.grbk_form_info(ctxz)[1]
+        Xz = torch.zeros(p, q, dtype=torch.float64, device=dev)
+        g.grbk_solve(ctxz, "grbk", X0=Xz, maxit=args.warmup * T, seed=1, X_out=Xz)
+        barrier()
+        kz = 4 * args.steps
+        ev0.record(stream)
+        stz, rz = g.grbk_solve(ctxz, "grbk", X0=Xz, maxit=kz * T, seed=2, X_out=Xz)
+        ev1.record(stream)
+        barrier()
+        msz = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([msz], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            msz = float(t.item())
+        kmz = rz["iter_kernel_ms"] / max(rz["iter_kernel_launches"], 1)
+        bz = iter_bytes(m, p, q, r_cols, 4, gram=bool(rz["gram"])) * T
+        rowspace = {"precision": "f32", "value": world * kz * T / (msz / 1e3), "unit": UNIT,
+                    "ms_per_step": msz / kz, "steps": kz, "kept_columns": r_cols, "setup_s": setup_s,
+                    "kernel_ms_per_launch": kmz, "kernel_GBs": bz / (kmz / 1e3) / 1e9,
+                    "kernel_frac_of_hbm": bz / (kmz / 1e3) / 1e9 / hbm_peak,
+                    "algorithmic_bytes_per_launch": bz,
+                    "note": "residual kept as Z = R Bt^T (m x rank B) plus fixed row offsets; same iterates as "
+                            "the chosen form; set-up (pivoted Cholesky of B B^T, Z^0, offsets) outside the timed "
+                            "region"}
+        g.grbk_destroy(ctxz)
+        del Xz
+
     # ---------------- end to end through the C ABI with host buffers --------
     e2e = None
     if not args.no_e2e:
@@ -353,6 +392,7 @@ def native_arm(args):
                          "kernel": "iterate_kernel<float> (persistent, %d iterations per launch)" % T,
                          "kernel_ms_per_launch": kern_ms, "peak_source": peak_src},
             "plain": plain,
+            "rowspace_form": rowspace,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "rse_after_timed_run": rse,
@@ -376,9 +416,13 @@ def time_to_target(args):
     stream = torch.cuda.current_stream(dev)
     out = {"mode": "time_to_target", "workload": args.workload, "variant": "ME-GRBK"}
 
-    def run(A, B, C, Xs, precision, tol, maxit, refresh_T, check):
+    def run(A, B, C, Xs, precision, tol, maxit, refresh_T, check, form="full"):
+        t0 = time.perf_counter()
         ctx = g.grbk_create(A, B, C, precision=precision, refresh_T=refresh_T, check_every=check,
-                            stop_kind="rse", x_ref=Xs, stream=stream, split_terms=args.split_terms, use_gram=1)
+                            stop_kind="rse", x_ref=Xs, stream=stream, split_terms=args.split_terms, use_gram=1,
+                            form=form)
+        torch.cuda.synchronize(dev)
+        setup_s = time.perf_counter() - t0
         X = torch.zeros(Xs.shape, dtype=torch.float64, device=dev)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -387,8 +431,9 @@ def time_to_target(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         g.grbk_destroy(ctx)
-        return {"precision": precision, "tol": tol, "status": g.grbk_strerror(st), "iters": res["iters"],
-                "seconds": ev0.elapsed_time(ev1) / 1e3, "rse": res["rse"], "refresh_T": refresh_T}
+        return {"precision": precision, "form": form, "tol": tol, "status": g.grbk_strerror(st),
+                "iters": res["iters"], "seconds": ev0.elapsed_time(ev1) / 1e3, "setup_s": setup_s,
+                "rse": res["rse"], "refresh_T": refresh_T}
 
     A1, B1, C1, X1 = workloads.config_small()
     out["small_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0, 4096)
@@ -397,10 +442,15 @@ def time_to_target(args):
     Xsd = torch.from_numpy(Xs).to(dev)
     del A, B, C
     out["chosen_f32_rse1e-4"] = run(Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, 64, 64)
+    if not args.no_rowspace:
+        out["rowspace_f32_rse1e-4"] = run(Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, 64, 64, form="rowspace")
     out["split_terms"] = args.split_terms
     if not args.no_plain:
         Ad64, Bd64, Cd64 = Ad.double(), Bd.double(), Cd.double()
         out["plain_f64_rse1e-4"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0, 256)
+        if not args.no_rowspace:
+            out["rowspace_f64_rse1e-4"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0, 256,
+                                              form="rowspace")
         if args.steps >= 2:
             out["plain_f64_rse1e-6"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-6, 4_000_000, 0, 256)
     print(json.dumps(out), flush=True)

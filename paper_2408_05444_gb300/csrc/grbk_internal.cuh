@@ -228,13 +228,15 @@ int splitgemm_launches(const SplitGemm* g);
 
 // Row-space form set-up (grbk_rowspace.cu): from B (q x n, ldb) and C (m x n,
 // ldc) in the working precision, the rank r of B, Lt (q x r, compact, with
-// Lt Lt^T = B B^T), Chat = C Bt^T (m x r, compact) and the FP64 row offsets
-// ||Rperp_i||^2 (m).  The three arrays are cudaMalloc'ed for the caller.
+// Lt Lt^T = B B^T), Chat = C Bt^T (m x r, compact), K = Lt^T Lt (r x r) and
+// the FP64 row offsets ||Rperp_i||^2 (m).  The four arrays are cudaMalloc'ed
+// for the caller.
 struct RowspaceResult {
     int64_t r;
     void* Lt;
     void* Chat;
     double* rperp;
+    void* K;        // Lt^T Lt (r x r, compact)
     long long launches;
 };
 grbk_status rowspace_transform(bool fp64, int64_t m, int64_t q, int64_t n, const void* B, int64_t ldb,

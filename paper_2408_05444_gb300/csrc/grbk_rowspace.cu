@@ -24,7 +24,9 @@
 // form): G = B B^T (FP64 output), Y = C B^T, Chat = Y M^T with
 // M[t][perm[s]] = L1^{-1}[t][s], Bt = M B, Rperp = C - Chat Bt (formed
 // explicitly, then its row norms in FP64, so that no difference of large
-// squared norms is taken).
+// squared norms is taken), and K = Lt^T Lt (r x r): the update vector of the
+// kept residual, (w Lt) with w = Z_{i_k} Lt^T, equals Z_{i_k} K, so an
+// iteration can form it from the selected row alone.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <math.h>
@@ -241,16 +243,18 @@ __global__ void __launch_bounds__(256) tri_inv_kernel(int64_t r, const double* L
 }
 
 // M (r x q, T): M[t][perm[s]] = LinvT[s][t] for s < r, 0 in the other columns.
-// Lt (q x r, T, ld ldlt): Lt[perm[j]][t] = L[j][t] for t <= j, else 0.
+// Lt (q x r, T): Lt[perm[j]][t] = L[j][t] for t <= j, else 0; LtT (r x q) its transpose.
 template <typename T>
 __global__ void build_factors_kernel(int64_t q, int64_t r, const double* L, int64_t ldl, const double* LinvT,
-                                     const int* perm, T* M, T* Lt)
+                                     const int* perm, T* M, T* Lt, T* LtT)
 {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= q * r) return;
     const int64_t a = e / r, b = e % r;  // a in [0, q), b in [0, r)
     // Lt row perm[a], column b
-    Lt[(int64_t)perm[a] * r + b] = (T)((b <= a) ? L[a * ldl + b] : 0.0);
+    const T l = (T)((b <= a) ? L[a * ldl + b] : 0.0);
+    Lt[(int64_t)perm[a] * r + b] = l;
+    LtT[b * q + perm[a]] = l;
     // M row b, column perm[a]
     M[b * q + perm[a]] = (T)((a < r) ? LinvT[a * r + b] : 0.0);
 }
@@ -347,9 +351,11 @@ grbk_status transform(int64_t m, int64_t q, int64_t n, const T* B, int64_t ldb, 
     tri_inv_kernel<<<(unsigned)((r * 32 + 255) / 256), 256, 0, st>>>(r, L, q, LinvT);
     RS_CK(cudaGetLastError());
 
-    T *M = nullptr, *Lt = nullptr, *Y = nullptr, *Bt = nullptr, *Chat = nullptr, *Rp = nullptr;
+    T *M = nullptr, *Lt = nullptr, *LtT = nullptr, *Y = nullptr, *Bt = nullptr, *Chat = nullptr, *Rp = nullptr;
+    T* K = nullptr;
     double* rperp = nullptr;
     RS_CK(tmp.alloc((void**)&M, (size_t)r * q * sizeof(T)));
+    RS_CK(tmp.alloc((void**)&LtT, (size_t)r * q * sizeof(T)));
     RS_CK(tmp.alloc((void**)&Y, (size_t)m * q * sizeof(T)));
     RS_CK(tmp.alloc((void**)&Bt, (size_t)r * n * sizeof(T)));
     RS_CK(tmp.alloc((void**)&Rp, (size_t)m * n * sizeof(T)));
@@ -357,14 +363,21 @@ grbk_status transform(int64_t m, int64_t q, int64_t n, const T* B, int64_t ldb, 
     RS_CK(cudaMalloc((void**)&Lt, (size_t)q * r * sizeof(T)));
     if (cudaMalloc((void**)&Chat, (size_t)m * r * sizeof(T)) != cudaSuccess) { cudaFree(Lt); return GRBK_ENOMEM; }
     if (cudaMalloc((void**)&rperp, (size_t)m * 8) != cudaSuccess) { cudaFree(Lt); cudaFree(Chat); return GRBK_ENOMEM; }
+    if (cudaMalloc((void**)&K, (size_t)r * r * sizeof(T)) != cudaSuccess) {
+        cudaFree(Lt); cudaFree(Chat); cudaFree(rperp);
+        return GRBK_ENOMEM;
+    }
     auto fail = [&](cudaError_t e, const char* what) {
         set_last_cuda_error(e, what, __FILE__, __LINE__);
-        cudaFree(Lt); cudaFree(Chat); cudaFree(rperp);
+        cudaFree(Lt); cudaFree(Chat); cudaFree(rperp); cudaFree(K);
         return GRBK_ECUDA;
     };
     cudaError_t e;
-    build_factors_kernel<T><<<(unsigned)((q * r + 255) / 256), 256, 0, st>>>(q, r, L, q, LinvT, perm, M, Lt);
+    build_factors_kernel<T><<<(unsigned)((q * r + 255) / 256), 256, 0, st>>>(q, r, L, q, LinvT, perm, M, Lt, LtT);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "build_factors_kernel");
+    // K = Lt^T Lt (r x r): R_{i_k} B^T B = Z_{i_k} K Bt, so v in the basis is Z_{i_k} K
+    if ((e = setup_gemm<T, T, true>(r, r, q, 1.0, LtT, q, LtT, q, 0.0, nullptr, 0, K, r, st)) != cudaSuccess)
+        return fail(e, "K = Lt^T Lt");
     // Y = C B^T (m x q); Chat = Y M^T (m x r); Bt = M B (r x n); Rp = C - Chat Bt
     if ((e = setup_gemm<T, T, true>(m, q, n, 1.0, C, ldc, B, ldb, 0.0, nullptr, 0, Y, q, st)) != cudaSuccess)
         return fail(e, "Y = C B^T");
@@ -381,7 +394,8 @@ grbk_status transform(int64_t m, int64_t q, int64_t n, const T* B, int64_t ldb, 
     out->Lt = Lt;
     out->Chat = Chat;
     out->rperp = rperp;
-    out->launches = 4 + 2 * q + 6;
+    out->K = K;
+    out->launches = 4 + 2 * q + 7;
     return GRBK_OK;
 }
 

@@ -88,6 +88,9 @@ struct IterParams {
     const T* G;                 // A A^T (m x ldg) or null
     int64_t ldg;
     const double* soff;         // fixed row offsets added to s_i (row-space form) or null
+    const T* K;                 // row-space form: Lt^T Lt (n x ldk); then v = R_{i_k} K and w is formed per chunk
+    int64_t ldk;
+    T* hist_z;                  // with K: per chunk the selected rows R_{i_k} (ldr per iteration)
 };
 
 // balanced contiguous row range of CTA c among G
@@ -572,29 +575,35 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
                 reinterpret_cast<V*>(sa)[e] = __ldg(reinterpret_cast<const V*>(Aik) + e);
         }
         __syncthreads();
-        {
-            // each CTA streams a contiguous block of rows of B (for w) and its own
-            // rows of A (for u, consumed by the same CTA in the fused pass)
+        // u holds the row coefficients c_k (A A_ik^T)_i of this CTA's rows, read from
+        // row i_k of the precomputed A A^T when there is one
+        if (P.G) {
+            const T* Gi = P.G + ik * P.ldg;
+            for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
+        } else {
+            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
+        }
+        if (P.K) {
+            // row-space form: the update vector is R_ik K (K = Lt^T Lt), one pass over
+            // K; the row itself is kept for the X update, w = R_ik Lt^T, formed per chunk
+            if (c == 0)
+                for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
+                    reinterpret_cast<V*>(P.hist_z + (int64_t)it * P.ldr)[e] = reinterpret_cast<const V*>(sv)[e];
+            cols_gemv<T>(P.K, P.ldk, P.n, sv, P.v, c, G, sm_parts);
+        } else {
+            // each CTA streams a contiguous block of rows of B for w; B is read last
+            // here, so the part of it still in L2 serves the v = w B phase that follows
             int64_t j0, j1;
             cta_rows(P.q, c, G, j0, j1);
-            // u first, then w: B is read last here, so the part of it still in L2 serves
-            // the v = w B phase that follows; u holds the row coefficients c_k (A A_ik^T)_i,
-            // read from row i_k of the precomputed A A^T when there is one
-            if (P.G) {
-                const T* Gi = P.G + ik * P.ldg;
-                for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
-            } else {
-                rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
-            }
             rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w, P.hist_w + (int64_t)it * P.q,
                         sm_parts);
-        }
-        if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
+            if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
 
-        // ---------------- V: v = w B (column slab of this CTA) ---------------
-        for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
-        __syncthreads();
-        cols_gemv<T>(P.B, P.ldb, P.q, sw, P.v, c, G, sm_parts);
+            // ---------------- V: v = w B (column slab of this CTA) -----------
+            for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
+            __syncthreads();
+            cols_gemv<T>(P.B, P.ldb, P.q, sw, P.v, c, G, sm_parts);
+        }
         if (!grid_sync(P.bar, P.st, 3, s_ok)) return;
 
         // ---------------- F: fused rank-1 update + row norms -----------------
@@ -698,6 +707,27 @@ __global__ void x_fold_kernel(double* X, int64_t p, int64_t q, const T* A, int64
 // FP32-mode fold: X (FP64) += sum_t c_t A_{i_t}^T w_t with the sum over the
 // chunk's terms formed in FP32 on 64 x 128 tiles of X staged in shared memory
 // (sa[t][r] = c_t A[i_t][r0 + r], sw[t][j] = w_t[j0 + j]), 64 terms at a time.
+// Row-space form: W[t][j] = Z_t . Lt_j for the chunk's selected rows Z_t (ldz
+// apart) and the rows of Lt (q x n, ldl) -- the w = R_{i_k} B^T of each
+// iteration, written as FP64 for the X fold.  One warp per (t, j).
+template <typename T>
+__global__ void chunk_w_kernel(int nit, int64_t q, int64_t n, const T* Z, int64_t ldz, const T* Lt, int64_t ldl,
+                               double* W)
+{
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (int64_t)nit * q) return;
+    const int64_t t = gw / q, j = gw % q;
+    const T* z = Z + t * ldz;
+    const T* l = Lt + j * ldl;
+    T acc = 0;
+    for (int64_t e = lane; e < n; e += 32) acc = fma(__ldg(z + e), __ldg(l + e), acc);
+    double tot;
+    if constexpr (sizeof(T) == 8) tot = warp_sum(acc);
+    else tot = (double)warp_sum_f(acc);
+    if (lane == 0) W[t * q + j] = tot;
+}
+
 constexpr int kFoldR = 64, kFoldC = 128, kFoldT = 64;
 
 __global__ void __launch_bounds__(512) x_fold_f32_kernel(double* X, int64_t p, int64_t q, const float* A,
@@ -870,6 +900,8 @@ struct grbk_ctx {
     int form;               // grbk_form
     int64_t n_orig;         // columns of the caller's B and C (n is the kept residual's)
     double* soff;           // row-space form: ||Rperp_i||^2
+    void* K;                // row-space form: Lt^T Lt (n x ldr), when the row fits in shared memory
+    void* hist_z;           // with K: the selected rows of a chunk (chunk_cap x ldr)
     cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
     long long launches;     // kernel launches issued (reset per solve)
 };
@@ -948,6 +980,7 @@ static IterParams<T> make_params(grbk_ctx* c)
     P.smem_v = c->smem_v; P.smem_arow = c->smem_arow;
     P.G = (const T*)c->gram; P.ldg = c->ldg;
     P.soff = c->soff;
+    P.K = (const T*)c->K; P.ldk = c->ldr; P.hist_z = (T*)c->hist_z;
     P.stop_S = -1.0;
     return P;
 }
@@ -1025,7 +1058,7 @@ extern "C" void grbk_destroy(grbk_ctx* c)
     if (!c) return;
     void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->sr, c->X,
                     c->part, c->part_SJ, c->hist_rows, c->hist_c,
-                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff};
+                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff, c->K, c->hist_z};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -1262,8 +1295,14 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
                  convert_matrix(c->B, dt, c->ldb, rs.Lt, dt, r, q, r, st) == cudaSuccess &&
                  convert_matrix(c->C, dt, c->ldr, rs.Chat, dt, r, m, r, st) == cudaSuccess &&
                  cudaStreamSynchronize(st) == cudaSuccess;
+        if (ok)
+            ok = cudaMalloc(&c->K, (size_t)r * c->ldr * es) == cudaSuccess &&
+                 cudaMemsetAsync(c->K, 0, (size_t)r * c->ldr * es, st) == cudaSuccess &&
+                 convert_matrix(c->K, dt, c->ldr, rs.K, dt, r, r, r, st) == cudaSuccess &&
+                 cudaStreamSynchronize(st) == cudaSuccess;
         cudaFree(rs.Lt);
         cudaFree(rs.Chat);
+        cudaFree(rs.K);
         if (!ok) { grbk_destroy(c); return GRBK_ENOMEM; }
     }
 
@@ -1311,6 +1350,14 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     ALLOC(c->hist_rows, (size_t)c->chunk_cap * 4);
     ALLOC(c->hist_c, (size_t)c->chunk_cap * 8);
     ALLOC(c->hist_w, (size_t)c->chunk_cap * q * 8);
+    if (c->K) {
+        if (c->smem_v) {
+            ALLOC(c->hist_z, (size_t)c->chunk_cap * c->ldr * es);
+        } else {  // the row does not fit in shared memory: w and v from Lt as in the full form
+            cudaFree(c->K);
+            c->K = nullptr;
+        }
+    }
 
     if (c->prec == GRBK_F32)
         TRY(splitgemm_create(&c->sg, m, p, q, c->n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
@@ -1366,6 +1413,19 @@ static grbk_status fold_x(grbk_ctx* c, int nit)
 {
     if (nit <= 0) return GRBK_OK;
     c->launches += 1;
+    if (c->K) {
+        // row-space form: w of each iteration from its kept row
+        c->launches += 1;
+        const int64_t warps = (int64_t)nit * c->q;
+        const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+        if (c->prec == GRBK_F64)
+            chunk_w_kernel<double><<<blocks, 256, 0, c->stream>>>(nit, c->q, c->n, (const double*)c->hist_z, c->ldr,
+                                                                 (const double*)c->B, c->ldb, c->hist_w);
+        else
+            chunk_w_kernel<float><<<blocks, 256, 0, c->stream>>>(nit, c->q, c->n, (const float*)c->hist_z, c->ldr,
+                                                                (const float*)c->B, c->ldb, c->hist_w);
+        GRBK_CK(cudaGetLastError());
+    }
     const int64_t tot = c->p * c->q;
     const unsigned blocks = (unsigned)((tot + 255) / 256);
     if (c->prec == GRBK_F64)
