@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     __shared__ double sm_red[2 * kWarps];
     __shared__ long long sm_redi[kWarps];
     __shared__ int s_ok;
-    __shared__ double s_S, s_rmax, s_t;
+    __shared__ double s_S, s_rmax, s_t, s_u;
     __shared__ long long s_imax, s_ik;
     __shared__ int s_stop;
     __shared__ double2 sm_sr[kSrCap];          // this CTA's (s_i, r_i) when it owns <= kSrCap rows
@@ -401,14 +401,33 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         if (warp == 0) {
             double S = 0.0, br = -INFINITY;
             long long bi = 0x7fffffffffffffffLL;
-            for (int cc = lane; cc < G; cc += 32) {
-                const double2* pp = reinterpret_cast<const double2*>(P.part + cc);
-                const double2 p0 = __ldcg(pp), p1 = __ldcg(pp + 1);
-                S += p0.x;
-                const double rr = p0.y;
-                const long long ii = __double_as_longlong(p1.x);
-                if (rr > br || (rr == br && ii < bi)) { br = rr; bi = ii; }
+            // all of this lane's partials (CTAs lane, lane + 32, ...) are requested
+            // before any is used: one L2 round trip per 32 * kSelRegs CTAs
+            constexpr int kSelRegs = 5;
+            for (int cb = 0; cb < G; cb += 32 * kSelRegs) {
+                double2 p0[kSelRegs], p1[kSelRegs];
+#pragma unroll
+                for (int j = 0; j < kSelRegs; ++j) {
+                    const int cc = cb + j * 32 + lane;
+                    if (cc < G) {
+                        const double2* pp = reinterpret_cast<const double2*>(P.part + cc);
+                        p0[j] = __ldcg(pp);
+                        p1[j] = __ldcg(pp + 1);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kSelRegs; ++j) {
+                    const int cc = cb + j * 32 + lane;
+                    if (cc < G) {
+                        S += p0[j].x;
+                        const double rr = p0[j].y;
+                        const long long ii = __double_as_longlong(p1[j].x);
+                        if (rr > br || (rr == br && ii < bi)) { br = rr; bi = ii; }
+                    }
+                }
             }
+            // the draw of this iteration, while the partials are in flight
+            if (lane == 0) s_u = philox_uniform(P.seed, (uint64_t)k, P.sys);
             S = warp_sum(S);
             warp_argmax(br, bi);
             if (lane == 0) {
@@ -464,7 +483,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
 #pragma unroll
                 for (int j = 0; j < kPartRegs; ++j) SJ += pv[j];
                 SJ = warp_sum(SJ);
-                const double u = philox_uniform(P.seed, (uint64_t)k, P.sys);
+                const double u = s_u;
                 const double target = __dmul_rn(u, SJ);
                 // owning CTA: first with inclusive prefix > target
                 double base = 0.0;
