@@ -159,12 +159,15 @@ def recorded_traffic(kernel):
         return None
 
 
-def iter_bytes(m, p, q, n, esz, gram=False):
+def iter_bytes(m, p, q, n, esz, gram=False, kpath=False):
     """Algorithmic bytes of one iteration: R read + written, B read twice
     (w = R_i B^T and v = w B), A read once for u = A A_i^T (or one row of the
-    precomputed A A^T), the vectors u, v, w and the row norms."""
+    precomputed A A^T), the vectors u, v, w and the row norms.  kpath: the
+    row-space form, whose update vector is R_i K with K = Lt^T Lt (n x n, read
+    once) instead of two passes over B (then n is the kept rank)."""
     u_bytes = m * esz if gram else m * p * esz
-    return 2 * m * n * esz + 2 * q * n * esz + u_bytes + (m + n + q) * esz + 3 * m * 8
+    b_bytes = n * n * esz if kpath else 2 * q * n * esz
+    return 2 * m * n * esz + b_bytes + u_bytes + (m + n + q) * esz + 3 * m * 8
 
 
 def cpu_baseline_oracle(target_seconds=12.0):
@@ -332,12 +335,14 @@ def native_arm(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             msz = float(t.item())
         kmz = rz["iter_kernel_ms"] / max(rz["iter_kernel_launches"], 1)
-        bz = iter_bytes(m, p, q, r_cols, 4, gram=bool(rz["gram"])) * T
+        bz = iter_bytes(m, p, q, r_cols, 4, gram=bool(rz["gram"]), kpath=True) * T
         rowspace = {"precision": "f32", "value": world * kz * T / (msz / 1e3), "unit": UNIT,
                     "ms_per_step": msz / kz, "steps": kz, "kept_columns": r_cols, "setup_s": setup_s,
                     "kernel_ms_per_launch": kmz, "kernel_GBs": bz / (kmz / 1e3) / 1e9,
                     "kernel_frac_of_hbm": bz / (kmz / 1e3) / 1e9 / hbm_peak,
                     "algorithmic_bytes_per_launch": bz,
+                    "traffic": (recorded_traffic("iterate_kernel<float>/rowspace")
+                                if (wl == "precision" and T == 64) else None),
                     "note": "residual kept as Z = R Bt^T (m x rank B) plus fixed row offsets; same iterates as "
                             "the chosen form; set-up (pivoted Cholesky of B B^T, Z^0, offsets) outside the timed "
                             "region"}
@@ -351,11 +356,14 @@ def native_arm(args):
         k_e2e = min(args.steps, 3)
         barrier()
         t0 = time.perf_counter()
+        step_s = []
         for s in range(k_e2e):
+            ts = time.perf_counter()
             c2 = g.grbk_create(Ah, Bh, Ch, precision="f32", refresh_T=T, check_every=T, stream=stream,
                                split_terms=args.split_terms)
             g.grbk_solve(c2, "grbk", X0=Xh, maxit=T, seed=s, X_out=Xh)
             g.grbk_destroy(c2)
+            step_s.append(time.perf_counter() - ts)
         barrier()
         e2e_s = time.perf_counter() - t0
         if world > 1:
@@ -364,7 +372,7 @@ def native_arm(args):
             e2e_s = float(t.item())
         e2e = {"value": world * k_e2e * T / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4 + Ch.numel() * 4),
-               "d2h_bytes_per_step": int(p * q * 8),
+               "d2h_bytes_per_step": int(p * q * 8), "step_seconds": step_s,
                "note": "per step: grbk_create from pinned host A, B, C (FP32), X0 from pinned host memory, "
                        "one refresh and 64 iterations, X copied back to pinned host memory, grbk_destroy"}
 

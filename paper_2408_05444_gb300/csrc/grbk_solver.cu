@@ -658,27 +658,63 @@ __global__ void row_sqnorm_kernel(const T* A, int64_t m, int64_t p, int64_t lda,
 
 // sum of squares (and non-finite count) of a matrix, per-block partials
 template <typename T>
-__global__ void sumsq_kernel(const T* M, int64_t rows, int64_t cols, int64_t ld, double* part,
-                             int* nonfinite)
+__global__ void __launch_bounds__(256) sumsq_kernel(const T* M, int64_t rows, int64_t cols, int64_t ld,
+                                                    double* part, int* nonfinite)
 {
-    __shared__ double red[32];
-    double acc = 0.0;
+    // one warp per row (grid-stride); FP32 rows: Kahan-compensated per-lane sums of squares
+    // combined in double-float arithmetic, FP64 rows: FP64 sums; a fixed order per launch shape
+    __shared__ double red[8];
+    using V = typename VecOf<T>::V;
+    constexpr int VN = VecOf<T>::N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * 8 + warp, nw = (int64_t)gridDim.x * 8;
+    const bool vec = (ld % VN) == 0;
+    double wacc = 0.0;
     int bad = 0;
-    const int64_t total = rows * cols;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / cols, j = e % cols;
-        const double x = (double)M[i * ld + j];
-        if (!isfinite(x)) bad = 1;
-        acc = fma(x, x, acc);
+    for (int64_t i = gw; i < rows; i += nw) {
+        const T* row = M + i * ld;
+        double acc_d = 0.0;
+        float acc_f = 0.f, comp_f = 0.f;
+        auto add = [&](T x) {
+            if (!isfinite(x)) bad = 1;
+            if constexpr (sizeof(T) == 8) {
+                acc_d = fma((double)x, (double)x, acc_d);
+            } else {
+                const float yk = fmaf((float)x, (float)x, -comp_f);
+                const float tk = acc_f + yk;
+                comp_f = (tk - acc_f) - yk;
+                acc_f = tk;
+            }
+        };
+        int64_t c0 = 0;
+        if (vec) {
+            const int64_t nv = cols / VN;
+            const V* rv = reinterpret_cast<const V*>(row);
+            for (int64_t e = lane; e < nv; e += 32) {
+                const V v = __ldg(rv + e);
+                const T* x = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                for (int c = 0; c < VN; ++c) add(x[c]);
+            }
+            c0 = nv * VN;
+        }
+        for (int64_t c = c0 + lane; c < cols; c += 32) add(row[c]);
+        double tot;
+        if constexpr (sizeof(T) == 8) {
+            tot = warp_sum(acc_d);
+        } else {
+            float hi = acc_f, lo = -comp_f;
+            warp_sum_df(hi, lo);
+            tot = (double)hi + (double)lo;
+        }
+        wacc += tot;
     }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    if (bad) atomicOr(nonfinite, 1);
+    if (lane == 0) red[warp] = wacc;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(nonfinite, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        for (int w = 0; w < 8; ++w) t += red[w];
         part[blockIdx.x] = t;
     }
 }
@@ -819,28 +855,66 @@ __global__ void __launch_bounds__(kBlock) b_t_kernel(const T* B, int64_t q, int6
 }
 
 // x <- y / ||y||, lambda = x.y (one block, FP64 sums)
+// One Lanczos step on B B^T (one CTA of 1024 threads): with y = B B^T v_j,
+// alpha_j = v_j . y, w = y - alpha_j v_j - beta_j v_{j-1}, beta_{j+1} = ||w||,
+// v_{j+1} = w / beta_{j+1}.  v and v_prev are kept in FP64; vt is v_{j+1} in the
+// bulk precision for the next product.  A step whose beta would vanish (an
+// invariant subspace) ends the recurrence: *nsteps stops growing.
 template <typename T>
-__global__ void power_normalize_kernel(T* x, const T* y, int64_t q, double* lambda)
+__global__ void __launch_bounds__(1024) lanczos_step_kernel(double* v, double* vprev, T* vt, const T* y, int64_t q,
+                                                            double* alpha, double* beta, int j, int* nsteps)
 {
-    __shared__ double red[2][32];
-    double xy = 0.0, yy = 0.0;
-    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) {
-        xy = fma((double)x[j], (double)y[j], xy);
-        yy = fma((double)y[j], (double)y[j], yy);
+    __shared__ double red[32];
+    __shared__ double s_val;
+    if (*nsteps != j) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto block_sum = [&](double x) {
+        x = warp_sum(x);
+        if (lane == 0) red[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 32; ++w) t += red[w];
+            s_val = t;
+        }
+        __syncthreads();
+        const double r = s_val;
+        __syncthreads();
+        return r;
+    };
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < q; i += 1024) a = fma(v[i], (double)y[i], a);
+    a = block_sum(a);
+    const double bj = (j > 0) ? beta[j] : 0.0;
+    double b2 = 0.0;
+    for (int64_t i = threadIdx.x; i < q; i += 1024) {
+        const double w = (double)y[i] - a * v[i] - bj * vprev[i];
+        b2 = fma(w, w, b2);
     }
-    xy = warp_sum(xy);
-    yy = warp_sum(yy);
-    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = xy; red[1][threadIdx.x >> 5] = yy; }
-    __syncthreads();
-    __shared__ double s_n;
+    b2 = block_sum(b2);
+    const double b = sqrt(b2);
+    if (threadIdx.x == 0) alpha[j] = a;
+    if (!(b > 1e-12 * fabs(a))) {
+        if (threadIdx.x == 0) *nsteps = -(j + 1);  // finished after this step
+        return;
+    }
+    for (int64_t i = threadIdx.x; i < q; i += 1024) {
+        const double w = (double)y[i] - a * v[i] - bj * vprev[i];
+        vprev[i] = v[i];
+        v[i] = w / b;
+        vt[i] = (T)(w / b);
+    }
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
-        *lambda = a;
-        s_n = sqrt(b);
+        beta[j + 1] = b;
+        *nsteps = j + 1;
     }
-    __syncthreads();
-    for (int64_t j = threadIdx.x; j < q; j += blockDim.x) x[j] = (T)((double)y[j] / s_n);
+}
+
+__global__ void lanczos_init_kernel(double* v, double* vprev, int64_t q, int* nsteps)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < q) { v[i] = 1.0 / sqrt((double)q); vprev[i] = 0.0; }
+    if (i == 0) *nsteps = 0;
 }
 
 template <typename T>
@@ -947,6 +1021,11 @@ static grbk_status load_matrix(grbk_ctx* c, const grbk_mat* M, void* dst, int dt
     const int es = dsize(M->dtype);
     if (M->on_device) {
         GRBK_CK(convert_matrix(dst, dtd, ldd, M->ptr, M->dtype, M->ld, rows, cols, c->stream));
+        return GRBK_OK;
+    }
+    if (M->dtype == dtd) {  // same element type: straight into the padded rows
+        GRBK_CK(cudaMemcpy2DAsync(dst, ldd * es, M->ptr, M->ld * es, cols * es, rows, cudaMemcpyHostToDevice,
+                                  c->stream));
         return GRBK_OK;
     }
     grbk_status s = ensure_tmp(c, (size_t)rows * cols * es);
@@ -1168,22 +1247,58 @@ static grbk_status setup_launch_shape(grbk_ctx* c)
     return GRBK_OK;
 }
 
-// lambda = ||B||_2^2 estimated by kPowerIters power iterations x <- B B^T x / ||.||
-// (Rayleigh quotient; a lower bound that converges to ||B||_2^2 from below)
-constexpr int kPowerIters = 100;
+// lambda = ||B||_2^2: the largest eigenvalue of the tridiagonal matrix of up to
+// kLanczosSteps Lanczos steps on B B^T from the normalised ones vector (the
+// extreme Ritz value converges first and is not disturbed by the loss of
+// orthogonality of plain Lanczos); bisection with Sturm counts on the host.
+constexpr int kLanczosSteps = 40;
+
+static double tridiag_max_eig(const std::vector<double>& al, const std::vector<double>& be)
+{
+    // al[0..k), be[1..k) off-diagonal (be[0] unused)
+    const int k = (int)al.size();
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? fabs(be[i]) : 0.0) + (i + 1 < k ? fabs(be[i + 1]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    auto count_below = [&](double x) {  // eigenvalues < x (Sturm sequence of T - x I)
+        int cnt = 0;
+        double d = 1.0;
+        for (int i = 0; i < k; ++i) {
+            const double b2 = (i > 0) ? be[i] * be[i] : 0.0;
+            d = (al[i] - x) - (i > 0 ? b2 / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0.0) ++cnt;
+        }
+        return cnt;
+    };
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * fabs(hi); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (count_below(mid) >= k) hi = mid; else lo = mid;
+    }
+    return hi;
+}
 
 template <typename T>
 static grbk_status power_iteration(grbk_ctx* c, double* lambda_out)
 {
     const int64_t q = c->q, ldb = c->ldb;
     cudaStream_t st = c->stream;
-    T *x = nullptr, *t = nullptr, *y = nullptr;
-    double* lam = nullptr;
-    if (cudaMalloc(&x, q * sizeof(T)) != cudaSuccess || cudaMalloc(&t, ldb * sizeof(T)) != cudaSuccess ||
-        cudaMalloc(&y, q * sizeof(T)) != cudaSuccess || cudaMalloc(&lam, 8) != cudaSuccess) {
-        cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+    T *vt = nullptr, *t = nullptr, *y = nullptr;
+    double *v = nullptr, *vprev = nullptr, *ab = nullptr;
+    int* nst = nullptr;
+    const int steps = (int)std::min<int64_t>(kLanczosSteps, q);
+    if (cudaMalloc(&vt, q * sizeof(T)) != cudaSuccess || cudaMalloc(&t, ldb * sizeof(T)) != cudaSuccess ||
+        cudaMalloc(&y, q * sizeof(T)) != cudaSuccess || cudaMalloc(&v, q * 8) != cudaSuccess ||
+        cudaMalloc(&vprev, q * 8) != cudaSuccess || cudaMalloc(&ab, (size_t)2 * (steps + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&nst, sizeof(int)) != cudaSuccess) {
+        cudaFree(vt); cudaFree(t); cudaFree(y); cudaFree(v); cudaFree(vprev); cudaFree(ab); cudaFree(nst);
         return GRBK_ENOMEM;
     }
+    double* alpha = ab;
+    double* beta = ab + steps + 1;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1195,19 +1310,33 @@ static grbk_status power_iteration(grbk_ctx* c, double* lambda_out)
     const int gcols = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, (ldb / (16 / (int64_t)sizeof(T)) + 31) / 32));
     const int grows = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, q));
     if (s == GRBK_OK) {
-        fill_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(x, q, 1.0 / sqrt((double)q));
-        for (int it = 0; it < kPowerIters; ++it) {
-            bt_x_kernel<T><<<gcols, kBlock, xs, st>>>((const T*)c->B, q, ldb, x, t);
+        lanczos_init_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(v, vprev, q, nst);
+        fill_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(vt, q, 1.0 / sqrt((double)q));
+        for (int j = 0; j < steps; ++j) {
+            bt_x_kernel<T><<<gcols, kBlock, xs, st>>>((const T*)c->B, q, ldb, vt, t);
             b_t_kernel<T><<<grows, kBlock, 0, st>>>((const T*)c->B, q, ldb, t, y);
-            power_normalize_kernel<T><<<1, 1024, 0, st>>>(x, y, q, lam);
+            lanczos_step_kernel<T><<<1, 1024, 0, st>>>(v, vprev, vt, y, q, alpha, beta, j, nst);
         }
-        double hl = 0.0;
-        if (cudaGetLastError() != cudaSuccess || cudaMemcpyAsync(&hl, lam, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess)
+        c->launches += 3 * steps;
+        int hn = 0;
+        std::vector<double> hab((size_t)2 * (steps + 1), 0.0);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&hn, nst, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hab.data(), ab, hab.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
             s = GRBK_ECUDA;
-        *lambda_out = hl;
+        } else {
+            const int k = hn < 0 ? -hn : hn;  // steps whose alpha was computed
+            if (k <= 0) {
+                *lambda_out = 0.0;
+            } else {
+                std::vector<double> al(hab.begin(), hab.begin() + k), be(k, 0.0);
+                for (int i = 1; i < k; ++i) be[i] = hab[steps + 1 + i];
+                *lambda_out = tridiag_max_eig(al, be);
+            }
+        }
     }
-    cudaFree(x); cudaFree(t); cudaFree(y); cudaFree(lam);
+    cudaFree(vt); cudaFree(t); cudaFree(y); cudaFree(v); cudaFree(vprev); cudaFree(ab); cudaFree(nst);
     return s;
 }
 

@@ -255,6 +255,20 @@ def test_torch_device_buffers_and_stream():
     assert _rel(Xt.cpu().numpy(), Xs) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("shape", [(37, 5, 7, 29), (200, 100, 80, 150), (2000, 200, 200, 2000), (60, 4, 1, 9)])
+def test_default_step_is_inverse_squared_spectral_norm(precision, shape):
+    """alpha = 1/||B||_2^2 (Section 5) from the library's Lanczos estimate of the
+    largest eigenvalue of B B^T, against numpy's SVD."""
+    m, p, q, n = shape
+    A, B, C, _ = workloads.gaussian(m, p, q, n, seed=q + n)
+    ctx = g.grbk_create(A, B, C, precision=precision)
+    _, al = g.grbk_info(ctx)
+    ref = 1.0 / np.linalg.norm(B, 2) ** 2
+    assert abs(al - ref) <= (1e-9 if precision == "f64" else 2e-6) * ref, (al, ref)
+    g.grbk_destroy(ctx)
+
+
 def test_edge_cases_and_errors():
     A, B, C, Xs = workloads.gaussian(20, 6, 5, 15, seed=11)
     ctx = g.grbk_create(A, B, C)
