@@ -445,6 +445,9 @@ def time_to_target(args):
 
     A1, B1, C1, X1 = workloads.config_small()
     out["small_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0, 4096)
+    if not args.no_rowspace:
+        out["small_rowspace_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0,
+                                                4096, form="rowspace")
     A, B, C, Xs = gen_inputs(args.workload)
     Ad, Bd, Cd = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev) for x in (A, B, C))
     Xsd = torch.from_numpy(Xs).to(dev)
