@@ -101,6 +101,10 @@ typedef struct {
     int32_t form;         /* grbk_form; 0 = FULL */
     double rank_tol;      /* ROWSPACE: pivots of B B^T at most rank_tol * max_i (B B^T)_ii end the
                              basis (they set r); <= 0 selects 1e-12 (F64) or 1e-6 (F32) */
+    int32_t band_limit;   /* batched solver: a system whose A and B have nonzeros only within half-bandwidths
+                             bA, bB <= band_limit of the diagonal (and 4 bA + 1 < m) takes the banded path,
+                             which forms w, u, v from the bands and updates only the rows within 2 bA of
+                             i_k (u_i = (A A_{i_k}^T)_i vanishes elsewhere); 0 = 64, -1 = always dense */
 } grbk_opts;
 
 typedef struct {
@@ -200,6 +204,11 @@ grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A,
 grbk_status grbk_batch_solve(grbk_batch* batch, int32_t variant, double theta, const grbk_mat* X0s,
                              double tol, const double* targets, int64_t maxit, uint64_t seed,
                              grbk_mat* X_outs, grbk_result* results);
+
+/* The path a batched system takes: the half-bandwidths of its A and B when it
+ * uses the banded path (opts.band_limit), -1 and -1 for the dense path.  Not
+ * part of the paper: a layout choice for banded (e.g. blur) matrices. */
+grbk_status grbk_batch_info(const grbk_batch* b, int32_t sys, int32_t* bandA, int32_t* bandB);
 
 void grbk_batch_destroy(grbk_batch* batch);
 

@@ -39,7 +39,8 @@ class grbk_opts(ctypes.Structure):
                 ("x_ref", ctypes.POINTER(grbk_mat)), ("row_trace", ctypes.POINTER(ctypes.c_int32)),
                 ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double)]
+                ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
+                ("band_limit", ctypes.c_int32)]
 
 
 class grbk_result(ctypes.Structure):
@@ -63,7 +64,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info"]
+           "grbk_form_info", "grbk_batch_info"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -101,6 +102,8 @@ def lib():
         L.grbk_batch_solve.argtypes = [vp, i32, dbl, P(grbk_mat), dbl, P(dbl), i64, u64, P(grbk_mat),
                                        P(grbk_result)]
         L.grbk_batch_solve.restype = i32
+        L.grbk_batch_info.argtypes = [vp, i32, P(i32), P(i32)]
+        L.grbk_batch_info.restype = i32
         L.grbk_batch_destroy.argtypes = [vp]
         L.grbk_batch_destroy.restype = None
         L.grbk_solve_small_noalloc.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, dbl, dbl, dbl, i64, u64, vp,
@@ -167,7 +170,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None):
+               form=None, rank_tol=None, band_limit=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -190,6 +193,8 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.form = {"full": GRBK_FORM_FULL, "rowspace": GRBK_FORM_ROWSPACE}.get(form, form)
     if rank_tol is not None:
         o.rank_tol = rank_tol
+    if band_limit is not None:
+        o.band_limit = band_limit
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     if x_ref is not None:
@@ -343,6 +348,15 @@ def grbk_batch_create(As, Bs, Cs, opts=None, trace_len=0, **kw) -> Batch:
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_batch_create")
     return Batch(h.value, keep)
+
+
+def grbk_batch_info(batch: Batch, sys: int):
+    """-> (half-bandwidth of A, of B) of a system on the banded path, (-1, -1) on the dense path."""
+    ba, bb = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().grbk_batch_info(batch.handle, int(sys), ctypes.byref(ba), ctypes.byref(bb))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_batch_info")
+    return ba.value, bb.value
 
 
 def grbk_batch_solve(batch: Batch, variant, theta=0.5, X0s=None, tol=0.0, targets=None, maxit=1000, seed=0,

@@ -24,10 +24,13 @@ namespace grbk {
 constexpr int kBB = 512;            // threads per CTA
 constexpr int kBW = kBB / 32;
 constexpr int kMaxSide = 1024;      // largest m, p, q, n of one system
+constexpr int kDefaultBandLimit = 64;
 
 struct SysDesc {
     int m, p, q, n;
     int lda, ldb, ldr;              // row strides (elements)
+    int bandA, bandB;               // banded path: A_ic = 0 for |c - i| > bandA, B_jl = 0 for |l - j| > bandB;
+                                    // -1: dense path
     int pad;
     long long offA, offB, offR, offX, offRow, offHist, offHistW;
     double F, alpha, stop_S;        // stop when S <= stop_S (< 0: never)
@@ -246,21 +249,94 @@ __device__ SetupOut system_setup(const float* A, int lda, const float* B, int ld
     return o;
 }
 
-// one CTA per system: scalars[s] = {F, ||C||^2, lambda, bad}
+// largest |c - i| over the nonzero entries M_ic (rows x cols, stride ld), by one CTA
+__device__ int half_bandwidth(const float* M, int ld, int rows, int cols, int* s_band)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) *s_band = 0;
+    __syncthreads();
+    int bw = 0;
+    for (int i = warp; i < rows; i += kBW)
+        for (int c = lane; c < cols; c += 32)
+            if (M[(long long)i * ld + c] != 0.f) bw = max(bw, abs(c - i));
+    for (int o = 16; o > 0; o >>= 1) bw = max(bw, __shfl_xor_sync(0xffffffffu, bw, o));
+    if (lane == 0) atomicMax(s_band, bw);
+    __syncthreads();
+    const int r = *s_band;
+    __syncthreads();
+    return r;
+}
+
+// one CTA per system: scalars[s] = {F, ||C||^2, lambda, bad, half-bandwidth of A, of B}
+constexpr int kSetupScalars = 6;
 __global__ void __launch_bounds__(kBB) batch_setup_kernel(const SysDesc* sys, const float* A, const float* B,
                                                           const float* C, double* a, double* pref, double* scalars)
 {
     __shared__ double x[kMaxSide], t[kMaxSide], y[kMaxSide];
     __shared__ double red[2 * kBW];
-    __shared__ int bad;
+    __shared__ int bad, band;
     const SysDesc d = sys[blockIdx.x];
     const SetupOut o = system_setup(A + d.offA, d.lda, B + d.offB, d.ldb, C + d.offR, d.ldr, d.m, d.p, d.q, d.n,
                                     a + d.offRow, pref + d.offRow, x, t, y, red, &bad);
+    const int bA = half_bandwidth(A + d.offA, d.lda, d.m, d.p, &band);
+    const int bB = half_bandwidth(B + d.offB, d.ldb, d.q, d.n, &band);
     if (threadIdx.x == 0) {
-        scalars[4 * blockIdx.x + 0] = o.F;
-        scalars[4 * blockIdx.x + 1] = o.normC2;
-        scalars[4 * blockIdx.x + 2] = o.lambda;
-        scalars[4 * blockIdx.x + 3] = (double)o.bad;
+        double* sc = scalars + (long long)kSetupScalars * blockIdx.x;
+        sc[0] = o.F;
+        sc[1] = o.normC2;
+        sc[2] = o.lambda;
+        sc[3] = (double)o.bad;
+        sc[4] = (double)bA;
+        sc[5] = (double)bB;
+    }
+}
+
+// R_i -= coef[i - rb] v for rows [rb, re), fused with the new s_i = ||R_i||^2
+// (Kahan FP32 per lane, double-float across lanes) and r_i = s_i / a_i; two rows
+// per warp, float4 columns.  v has ldr entries (padding zero).
+__device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int re, const float* coef,
+                                                  const float* v, const double* a, double* s_s, double* s_r)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const int nv = ldr / 4;
+    for (int i0 = rb + 2 * warp; i0 < re; i0 += 2 * kBW) {
+        float acc[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
+        float cf[2];
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) cf[k2] = (i0 + k2 < re) ? coef[i0 + k2 - rb] : 0.f;
+        for (int e = lane; e < nv; e += 32) {
+            float4 rv[2];
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2)
+                if (i0 + k2 < re) rv[k2] = reinterpret_cast<float4*>(R + (long long)(i0 + k2) * ldr)[e];
+            const float4 vv = v4[e];
+#pragma unroll
+            for (int k2 = 0; k2 < 2; ++k2) {
+                if (i0 + k2 >= re) continue;
+                float* x = reinterpret_cast<float*>(&rv[k2]);
+                const float* y = reinterpret_cast<const float*>(&vv);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    x[c] = fmaf(-cf[k2], y[c], x[c]);
+                    const float yk = fmaf(x[c], x[c], -comp[k2]);
+                    const float tk = acc[k2] + yk;
+                    comp[k2] = (tk - acc[k2]) - yk;
+                    acc[k2] = tk;
+                }
+                reinterpret_cast<float4*>(R + (long long)(i0 + k2) * ldr)[e] = rv[k2];
+            }
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < 2; ++k2) {
+            float hi = acc[k2], lo = -comp[k2];
+            warp_sum_df(hi, lo);
+            if (lane == 0 && i0 + k2 < re) {
+                const double tot = (double)hi + (double)lo;
+                s_s[i0 + k2] = tot;
+                s_r[i0 + k2] = a[i0 + k2] > 0.0 ? __ddiv_rn(tot, a[i0 + k2]) : -INFINITY;
+            }
+        }
     }
 }
 
@@ -461,97 +537,101 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             const double ck = aik > 0.0 ? __ddiv_rn(d.alpha, aik) : 0.0;
             if (threadIdx.x == 0 && k < P.trace_len) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
 
-            // ---- w = R_ik B^T, u = A A_ik^T (rows of B and A streamed as float4, 4 rows per warp)
-            {
-                const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
-                const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
-                for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
-                for (int e = threadIdx.x; e < d.lda / 4; e += kBB) reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
-            }
-            __syncthreads();
-            batch_rows_dot<4>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
-            batch_rows_dot<4>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
-            __syncthreads();
-            for (int i = threadIdx.x; i < d.m; i += kBB) s_u[i] = (float)(ck * (double)s_u[i]);  // coefficient c_k u_i
-            // ---- record the term, v = w B (vector columns, row classes reduced in shared memory)
-            if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
-            for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
-            {
-                const int nv4 = d.ldb / 4;
-                float4* red4 = reinterpret_cast<float4*>(fold_smem);  // [RG][cols] float4
-                for (int cb = 0; cb < nv4; cb += kBB) {
-                    const int ncols = min(kBB, nv4 - cb);
-                    const int RG = kBB / ncols;
-                    const int e = threadIdx.x % ncols, rg = threadIdx.x / ncols;
-                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (rg < RG) {
-                        const float4* col = reinterpret_cast<const float4*>(B) + cb + e;
-                        const int ldv = d.ldb / 4;
-#pragma unroll 8
-                        for (int j = rg; j < d.q; j += RG) {
-                            const float4 bv = __ldg(col + (long long)j * ldv);
-                            const float wj = s_w[j];
-                            acc.x = fmaf(wj, bv.x, acc.x);
-                            acc.y = fmaf(wj, bv.y, acc.y);
-                            acc.z = fmaf(wj, bv.z, acc.z);
-                            acc.w = fmaf(wj, bv.w, acc.w);
-                        }
-                        red4[rg * ncols + e] = acc;
-                    }
-                    __syncthreads();
-                    for (int t = threadIdx.x; t < ncols; t += kBB) {
-                        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-                        for (int r2 = 0; r2 < RG; ++r2) {
-                            const float4 v = red4[r2 * ncols + t];
-                            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-                        }
-                        reinterpret_cast<float4*>(s_vec)[cb + t] = sum;
-                    }
-                    __syncthreads();
+            if (d.bandA >= 0) {
+                // ---- banded A and B: u_i = (A A_ik^T)_i vanishes for |i - ik| > 2 bandA, so the
+                // update touches those rows only; w and v use the band of B
+                const int bA = d.bandA, bB = d.bandB;
+                {
+                    const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
+                    const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
+                    for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
+                    for (int e = threadIdx.x; e < d.lda / 4; e += kBB)
+                        reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
                 }
-            }
-            // ---- R -= c u v fused with the new row norms (float4, two rows per warp)
-            {
-                const float4* v4 = reinterpret_cast<const float4*>(s_vec);
-                const int nv = d.ldr / 4;
-                for (int i0 = 2 * warp; i0 < d.m; i0 += 2 * kBW) {
-                    float acc[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
-                    float coef[2];
-#pragma unroll
-                    for (int k2 = 0; k2 < 2; ++k2) coef[k2] = (i0 + k2 < d.m) ? s_u[i0 + k2] : 0.f;
-                    for (int e = lane; e < nv; e += 32) {
-                        float4 rv[2];
-#pragma unroll
-                        for (int k2 = 0; k2 < 2; ++k2)
-                            if (i0 + k2 < d.m) rv[k2] = reinterpret_cast<float4*>(R + (long long)(i0 + k2) * d.ldr)[e];
-                        const float4 vv = v4[e];
-#pragma unroll
-                        for (int k2 = 0; k2 < 2; ++k2) {
-                            if (i0 + k2 >= d.m) continue;
-                            float* x = reinterpret_cast<float*>(&rv[k2]);
-                            const float* y = reinterpret_cast<const float*>(&vv);
-#pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                x[c] = fmaf(-coef[k2], y[c], x[c]);
-                                const float yk = fmaf(x[c], x[c], -comp[k2]);
-                                const float tk = acc[k2] + yk;
-                                comp[k2] = (tk - acc[k2]) - yk;
-                                acc[k2] = tk;
+                __syncthreads();
+                // w_j = sum over |l - j| <= bB of R_ik,l B_jl (one warp per row of B)
+                for (int j = warp; j < d.q; j += kBW) {
+                    const int l0 = max(0, j - bB), l1 = min(d.n - 1, j + bB);
+                    float acc = 0.f;
+                    for (int l = l0 + lane; l <= l1; l += 32) acc = fmaf(s_vec[l], __ldg(B + (long long)j * d.ldb + l), acc);
+                    acc = warp_sum_f(acc);
+                    if (lane == 0) s_w[j] = acc;
+                }
+                // c_k u_i for |i - ik| <= 2 bA (one warp per row of A)
+                const int u0 = max(0, ik - 2 * bA), u1 = min(d.m - 1, ik + 2 * bA);
+                for (int i = u0 + warp; i <= u1; i += kBW) {
+                    const int c0 = max(0, max(i, ik) - bA), c1 = min(d.p - 1, min(i, ik) + bA);
+                    float acc = 0.f;
+                    for (int c = c0 + lane; c <= c1; c += 32) acc = fmaf(__ldg(A + (long long)i * d.lda + c), s_arow[c], acc);
+                    acc = warp_sum_f(acc);
+                    if (lane == 0) s_u[i - u0] = (float)(ck * (double)acc);
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
+                for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
+                // v_l = sum over |j - l| <= bB of w_j B_jl (padding columns 0)
+                for (int l = threadIdx.x; l < d.ldr; l += kBB) {
+                    float acc = 0.f;
+                    if (l < d.n) {
+                        const int j0 = max(0, l - bB), j1 = min(d.q - 1, l + bB);
+                        for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], __ldg(B + (long long)j * d.ldb + l), acc);
+                    }
+                    s_vec[l] = acc;
+                }
+                __syncthreads();
+                batch_update_rows(R, d.ldr, u0, u1 + 1, s_u, s_vec, a, s_s, s_r);
+            } else {
+                // ---- w = R_ik B^T, u = A A_ik^T (rows of B and A streamed as float4, 4 rows per warp)
+                {
+                    const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
+                    const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
+                    for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
+                    for (int e = threadIdx.x; e < d.lda / 4; e += kBB) reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
+                }
+                __syncthreads();
+                batch_rows_dot<4>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
+                batch_rows_dot<4>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
+                __syncthreads();
+                for (int i = threadIdx.x; i < d.m; i += kBB) s_u[i] = (float)(ck * (double)s_u[i]);  // coefficient c_k u_i
+                // ---- record the term, v = w B (vector columns, row classes reduced in shared memory)
+                if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
+                for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
+                {
+                    const int nv4 = d.ldb / 4;
+                    float4* red4 = reinterpret_cast<float4*>(fold_smem);  // [RG][cols] float4
+                    for (int cb = 0; cb < nv4; cb += kBB) {
+                        const int ncols = min(kBB, nv4 - cb);
+                        const int RG = kBB / ncols;
+                        const int e = threadIdx.x % ncols, rg = threadIdx.x / ncols;
+                        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (rg < RG) {
+                            const float4* col = reinterpret_cast<const float4*>(B) + cb + e;
+                            const int ldv = d.ldb / 4;
+    #pragma unroll 8
+                            for (int j = rg; j < d.q; j += RG) {
+                                const float4 bv = __ldg(col + (long long)j * ldv);
+                                const float wj = s_w[j];
+                                acc.x = fmaf(wj, bv.x, acc.x);
+                                acc.y = fmaf(wj, bv.y, acc.y);
+                                acc.z = fmaf(wj, bv.z, acc.z);
+                                acc.w = fmaf(wj, bv.w, acc.w);
                             }
-                            reinterpret_cast<float4*>(R + (long long)(i0 + k2) * d.ldr)[e] = rv[k2];
+                            red4[rg * ncols + e] = acc;
                         }
-                    }
-#pragma unroll
-                    for (int k2 = 0; k2 < 2; ++k2) {
-                        float hi = acc[k2], lo = -comp[k2];
-                        warp_sum_df(hi, lo);
-                        if (lane == 0 && i0 + k2 < d.m) {
-                            const double tot = (double)hi + (double)lo;
-                            s_s[i0 + k2] = tot;
-                            s_r[i0 + k2] = a[i0 + k2] > 0.0 ? __ddiv_rn(tot, a[i0 + k2]) : -INFINITY;
+                        __syncthreads();
+                        for (int t = threadIdx.x; t < ncols; t += kBB) {
+                            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+                            for (int r2 = 0; r2 < RG; ++r2) {
+                                const float4 v = red4[r2 * ncols + t];
+                                sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+                            }
+                            reinterpret_cast<float4*>(s_vec)[cb + t] = sum;
                         }
+                        __syncthreads();
                     }
                 }
+                // ---- R -= c u v fused with the new row norms
+                batch_update_rows(R, d.ldr, 0, d.m, s_u, s_vec, a, s_s, s_r);
             }
             ++k;
             ++nh;
@@ -696,22 +776,31 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     }
     // per-system set-up on the device (one CTA per system)
     {
-        std::vector<double> sc(4 * (size_t)nsys);
-        double* dsc = (double*)dmalloc(sizeof(double) * 4 * nsys);
+        std::vector<double> sc(kSetupScalars * (size_t)nsys);
+        double* dsc = (double*)dmalloc(sizeof(double) * kSetupScalars * nsys);
         if (!dsc) { grbk_batch_destroy(b); return GRBK_ENOMEM; }
         cudaError_t e = cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) {
             batch_setup_kernel<<<nsys, kBB, 0, st>>>(b->dsys, b->A, b->B, b->C, b->a, b->pref, dsc);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sc.data(), dsc, sizeof(double) * 4 * nsys, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(sc.data(), dsc, sizeof(double) * kSetupScalars * nsys, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaFree(dsc);
         if (e != cudaSuccess) { grbk_batch_destroy(b); return GRBK_ECUDA; }
         for (int s = 0; s < nsys; ++s) {
             SysDesc& d = b->hsys[s];
-            const double F = sc[4 * s], c2s = sc[4 * s + 1], lam = sc[4 * s + 2];
-            if (sc[4 * s + 3] != 0.0) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
+            const double* scs = sc.data() + (size_t)kSetupScalars * s;
+            const double F = scs[0], c2s = scs[1], lam = scs[2];
+            if (scs[3] != 0.0) { grbk_batch_destroy(b); return GRBK_ENONFINITE; }
+            // banded path when both half-bandwidths are within the limit and the rows an update
+            // touches (within 2 bandA of i_k) are a small part of R
+            const int limit = o.band_limit == 0 ? kDefaultBandLimit : o.band_limit;
+            const int bA = (int)scs[4], bB = (int)scs[5];
+            const bool banded = limit > 0 && bA <= limit && bB <= limit && 4 * (long long)bA + 1 < d.m;
+            d.bandA = banded ? bA : -1;
+            d.bandB = banded ? bB : -1;
             if (!(F > 0.0) || !(lam > 0.0)) { grbk_batch_destroy(b); return GRBK_EINVAL; }
             d.F = F;
             b->normC2[s] = c2s;
@@ -737,6 +826,14 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
         return GRBK_ECUDA;
     }
     *out = b;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_batch_info(const grbk_batch* b, int32_t sys, int32_t* bandA, int32_t* bandB)
+{
+    if (!b || sys < 0 || sys >= b->nsys) return GRBK_EINVAL;
+    if (bandA) *bandA = b->hsys[sys].bandA;
+    if (bandB) *bandB = b->hsys[sys].bandB;
     return GRBK_OK;
 }
 
@@ -940,6 +1037,7 @@ __global__ void __launch_bounds__(kBB) noalloc_setup_kernel(NoAllocScratch* S, c
         SysDesc& d = S->desc;
         d.m = m; d.p = p; d.q = q; d.n = n;
         d.lda = (p + 3) & ~3; d.ldb = (n + 3) & ~3; d.ldr = d.ldb;
+        d.bandA = -1; d.bandB = -1;
         d.pad = 0;
         d.offA = 0; d.offB = 0; d.offR = 0; d.offX = 0; d.offRow = 0; d.offHist = 0; d.offHistW = 0;
         d.F = o.F;

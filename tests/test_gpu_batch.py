@@ -23,10 +23,16 @@ def _systems():
     return workloads.blur_systems(n_images=3, min_side=48, max_side=112, noise=0.0, mild=True, seed=21)
 
 
-def test_batch_converges_to_clean_images():
+def _band(M):
+    i, c = np.nonzero(M)
+    return int(np.max(np.abs(c - i))) if len(i) else 0
+
+
+@pytest.mark.parametrize("band_limit", [0, -1])
+def test_batch_converges_to_clean_images(band_limit):
     sy = _systems()
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs, stop_kind="relres")
+    b = g.grbk_batch_create(As, Bs, Cs, stop_kind="relres", band_limit=band_limit)
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, "grbk", tol=1e-6, maxit=2_000_000, seed=3, X_outs=Xo)
     assert st == g.GRBK_OK
@@ -35,14 +41,18 @@ def test_batch_converges_to_clean_images():
         assert _rel(X, s["X"]) <= 1e-4
 
 
+@pytest.mark.parametrize("band_limit", [0, -1])
 @pytest.mark.parametrize("variant", ["mwrbk", "grbk", "rgrbk", "rbk", "bk"])
-def test_batch_matches_oracle_per_system(variant):
+def test_batch_matches_oracle_per_system(variant, band_limit):
     """Fixed 120 iterations per system: the selected rows agree with the FP64
     oracle's up to the first decision the oracle marks as closer than FP32
     resolves (relative margin 1e-5); with no such decision X agrees to 1e-4."""
     sy = _systems()
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120, band_limit=band_limit)
+    for sid, s in enumerate(sy):
+        want = (_band(s["A"]), _band(s["B"])) if band_limit == 0 else (-1, -1)
+        assert g.grbk_batch_info(b, sid) == want
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, variant, theta=0.7, maxit=120, seed=11, X_outs=Xo)
     assert st == g.GRBK_OK
@@ -60,3 +70,31 @@ def test_batch_matches_oracle_per_system(variant):
             assert _rel(X, orc["X"]) < 1e-4
             checked += 1
     assert checked >= 1
+
+
+def test_banded_and_dense_paths_agree():
+    """The banded path skips only exact zeros (rows of R with u_i = 0 are left as
+    they are, which the dense path reproduces bit for bit), so both paths select
+    the same rows while the decisions are wider than FP32 rounding and reach the
+    same X to FP32 accuracy; a matrix with a wide band stays dense."""
+    sy = workloads.blur_systems(n_images=2, min_side=64, max_side=160, noise=0.0, mild=True, seed=5)
+    As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
+    out = {}
+    for bl in (0, -1):
+        b = g.grbk_batch_create(As, Bs, Cs, trace_len=400, band_limit=bl)
+        Xo = [np.zeros_like(s["X"]) for s in sy]
+        st, res = g.grbk_batch_solve(b, "rgrbk", theta=0.8, maxit=400, seed=2, X_outs=Xo)
+        assert st == g.GRBK_OK
+        out[bl] = (b.row_trace.copy(), Xo)
+    for sid in range(len(sy)):
+        r0, r1 = out[0][0][sid], out[-1][0][sid]
+        diff = np.nonzero(r0 != r1)[0]
+        first = int(diff[0]) if len(diff) else 400
+        assert first >= 50, first
+        if first == 400:
+            assert _rel(out[0][1][sid], out[-1][1][sid]) < 1e-4
+    # a full A (band m - 1) keeps the dense path under the default limit
+    A = np.random.default_rng(1).standard_normal((40, 40))
+    b = g.grbk_batch_create([A, As[0]], [A, Bs[0]], [A @ A, Cs[0]])
+    assert g.grbk_batch_info(b, 0) == (-1, -1)
+    assert g.grbk_batch_info(b, 1)[0] >= 0

@@ -32,8 +32,8 @@ def test_noalloc_matches_batch_entry_point_twice(variant, tol):
     A, B, C = _system(31)
     alpha = 1.0 / np.linalg.norm(B, 2) ** 2
     maxit = 400 if tol == 0.0 else 200000
-    # the existing (allocating) entry point on the same single system
-    bt = g.grbk_batch_create([A], [B], [C], alpha=alpha, stop_kind="relres" if tol > 0 else "none")
+    # the existing (allocating) entry point on the same single system, on the same (dense) path
+    bt = g.grbk_batch_create([A], [B], [C], alpha=alpha, stop_kind="relres" if tol > 0 else "none", band_limit=-1)
     Xref = np.zeros((A.shape[1], B.shape[0]))
     st, res = g.grbk_batch_solve(bt, variant, theta=0.6, tol=tol, maxit=maxit, seed=9, X_outs=[Xref])
     assert st == g.GRBK_OK
