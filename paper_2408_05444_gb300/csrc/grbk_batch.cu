@@ -12,6 +12,7 @@
 #include <string.h>
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstddef>
 #include <mutex>
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
     __shared__ __align__(16) float s_u[kMaxSide];         // u
     extern __shared__ __align__(16) float fold_smem[];    // kFoldSmemBytes
     __shared__ double red[2 * kBW];
-    __shared__ long long redi[kBW];
+    __shared__ long long redi[2 * kBW];
     __shared__ int s_sys, s_first, s_last, s_stop;
     __shared__ double s_S, s_rmax, s_base_next;
     __shared__ long long s_imax;
@@ -440,26 +441,35 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
         for (;;) {
             // ---- totals and stop test
             {
-                double Sv = 0.0, br = -INFINITY;
-                long long bi = 0x7fffffffffffffffLL;
+                // r_i is >= 0 or -inf, so its largest value is the largest IEEE bit pattern read as
+                // a signed integer: the argmax runs on the integer pipe (ties: smallest row)
+                double Sv = 0.0;
+                long long bkey = LLONG_MIN, bi = 0x7fffffffffffffffLL;
                 for (int i = threadIdx.x; i < d.m; i += kBB) {
                     Sv += s_s[i];
-                    if (s_r[i] > br) { br = s_r[i]; bi = i; }
+                    const long long key = __double_as_longlong(s_r[i]);
+                    if (key > bkey) { bkey = key; bi = i; }
                 }
                 Sv = warp_sum(Sv);
-                warp_argmax(br, bi);
-                if (lane == 0) { red[warp] = Sv; red[kBW + warp] = br; redi[warp] = bi; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long ok = __shfl_xor_sync(0xffffffffu, bkey, o);
+                    const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (ok > bkey || (ok == bkey && oi < bi)) { bkey = ok; bi = oi; }
+                }
+                if (lane == 0) { red[warp] = Sv; redi[warp] = bi; redi[kBW + warp] = bkey; }
                 __syncthreads();
                 if (threadIdx.x == 0) {
-                    double S = 0.0, bb = -INFINITY;
-                    long long bbi = 0x7fffffffffffffffLL;
+                    double S = 0.0;
+                    long long bbk = LLONG_MIN, bbi = 0x7fffffffffffffffLL;
                     for (int w2 = 0; w2 < kBW; ++w2) {
                         S += red[w2];
-                        if (red[kBW + w2] > bb || (red[kBW + w2] == bb && redi[w2] < bbi)) {
-                            bb = red[kBW + w2];
+                        if (redi[kBW + w2] > bbk || (redi[kBW + w2] == bbk && redi[w2] < bbi)) {
+                            bbk = redi[kBW + w2];
                             bbi = redi[w2];
                         }
                     }
+                    const double bb = __longlong_as_double(bbk);
                     s_S = S; s_rmax = bb; s_imax = bbi;
                     int stop = 0;
                     if (!(S > 0.0)) stop = 2;
@@ -481,35 +491,45 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
                 double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, d.F)));
                 if (t > s_rmax) t = s_rmax;
-                double SJ = 0.0;
-                for (int i = threadIdx.x; i < d.m; i += kBB) SJ += (s_r[i] >= t) ? s_s[i] : 0.0;
-                SJ = block_sum_fixed(SJ, red);
-                const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), SJ);
+                // one block scan gives every prefix of the admitted s_i and S_J: thread T owns the
+                // contiguous rows [T K, T K + K); admission r_i >= t compares the IEEE bit patterns
+                // (r_i and t are >= 0 or -inf)
+                const double u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
+                const long long tkey = __double_as_longlong(t);
+                const int K = (d.m + kBB - 1) / kBB;
+                const int r0 = threadIdx.x * K, r1 = min(d.m, r0 + K);
+                double loc = 0.0;
+                int lastadm = -1;
+                for (int i = r0; i < r1; ++i)
+                    if (__double_as_longlong(s_r[i]) >= tkey) { loc += s_s[i]; lastadm = i; }
+                // warps without admitted rows (most of them when theta is large) skip the FP64 scan
+                const double incw = __any_sync(0xffffffffu, lastadm >= 0) ? warp_inclusive_scan(loc) : 0.0;
                 if (threadIdx.x == 0) { s_first = 0x7fffffff; s_last = -1; }
+                if (lane == 31) red[warp] = incw;
                 __syncthreads();
-                double base = 0.0;
-                for (int i0 = 0; i0 < d.m; i0 += kBB) {
-                    const int i = i0 + threadIdx.x;
-                    const bool adm = (i < d.m) && (s_r[i] >= t);
-                    const double val = adm ? s_s[i] : 0.0;
-                    const double incw = warp_inclusive_scan(val);
-                    if (lane == 31) red[warp] = incw;
-                    __syncthreads();
-                    if (warp == 0) {  // exclusive bases of the warps, and the chunk total
-                        const double wt = lane < kBW ? red[lane] : 0.0;
-                        const double inc = warp_inclusive_scan(wt);
-                        if (lane < kBW) red[kBW + lane] = base + inc - wt;
-                        const double tot = __shfl_sync(0xffffffffu, inc, kBW - 1);
-                        if (lane == 0) s_base_next = base + tot;
-                    }
-                    __syncthreads();
-                    const double wbase = red[kBW + warp];
-                    if (adm && wbase + incw > target) atomicMin(&s_first, i);
-                    if (adm) atomicMax(&s_last, i);
-                    __syncthreads();
-                    base = s_base_next;
-                    if (s_first != 0x7fffffff) break;
+                if (warp == 0) {  // exclusive bases of the warps and the total S_J
+                    const double wt = lane < kBW ? red[lane] : 0.0;
+                    const double inc = warp_inclusive_scan(wt);
+                    if (lane < kBW) red[kBW + lane] = inc - wt;
+                    if (lane == kBW - 1) s_base_next = inc;
                 }
+                __syncthreads();
+                const double target = __dmul_rn(u, s_base_next);
+                const double incl = red[kBW + warp] + incw;
+                if (lastadm >= 0) {
+                    atomicMax(&s_last, lastadm);
+                    if (incl > target) {  // the prefix crosses u S_J within or before these rows
+                        double run = incl - loc;
+                        int pick = lastadm;
+                        for (int i = r0; i < r1; ++i)
+                            if (__double_as_longlong(s_r[i]) >= tkey) {
+                                if (run + s_s[i] > target) { pick = i; break; }
+                                run += s_s[i];
+                            }
+                        atomicMin(&s_first, pick);
+                    }
+                }
+                __syncthreads();
                 ik = (s_first != 0x7fffffff) ? s_first : s_last;
             } else if (var == GRBK_MWRBK) {
                 ik = (int)s_imax;
@@ -549,22 +569,23 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                         reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
                 }
                 __syncthreads();
-                // w_j = sum over |l - j| <= bB of R_ik,l B_jl (one warp per row of B)
-                for (int j = warp; j < d.q; j += kBW) {
+                // w_j = sum over |l - j| <= bB of R_ik,l B_jl (one thread per row of B: the band is
+                // short, and the rows of B stay in L1 from one iteration to the next)
+                for (int j = threadIdx.x; j < d.q; j += kBB) {
                     const int l0 = max(0, j - bB), l1 = min(d.n - 1, j + bB);
+                    const float* Bj = B + (long long)j * d.ldb;
                     float acc = 0.f;
-                    for (int l = l0 + lane; l <= l1; l += 32) acc = fmaf(s_vec[l], __ldg(B + (long long)j * d.ldb + l), acc);
-                    acc = warp_sum_f(acc);
-                    if (lane == 0) s_w[j] = acc;
+                    for (int l = l0; l <= l1; ++l) acc = fmaf(s_vec[l], __ldg(Bj + l), acc);
+                    s_w[j] = acc;
                 }
-                // c_k u_i for |i - ik| <= 2 bA (one warp per row of A)
+                // c_k u_i for |i - ik| <= 2 bA (one thread per row of A)
                 const int u0 = max(0, ik - 2 * bA), u1 = min(d.m - 1, ik + 2 * bA);
-                for (int i = u0 + warp; i <= u1; i += kBW) {
+                for (int i = u0 + threadIdx.x; i <= u1; i += kBB) {
                     const int c0 = max(0, max(i, ik) - bA), c1 = min(d.p - 1, min(i, ik) + bA);
+                    const float* Ai = A + (long long)i * d.lda;
                     float acc = 0.f;
-                    for (int c = c0 + lane; c <= c1; c += 32) acc = fmaf(__ldg(A + (long long)i * d.lda + c), s_arow[c], acc);
-                    acc = warp_sum_f(acc);
-                    if (lane == 0) s_u[i - u0] = (float)(ck * (double)acc);
+                    for (int c = c0; c <= c1; ++c) acc = fmaf(__ldg(Ai + c), s_arow[c], acc);
+                    s_u[i - u0] = (float)(ck * (double)acc);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
