@@ -565,9 +565,9 @@ grbk_status splitgemm_create(SplitGemm** out, int64_t m, int64_t p, int64_t q, i
     g->qr = round_up(q, tc::BN_MAX);
     const size_t szA = (size_t)terms * g->mr * g->Kp * 2, szB = (size_t)terms * g->nr * g->Kq * 2;
     const size_t szX = (size_t)terms * g->qr * g->Kp * 2, szT = (size_t)terms * g->mr * g->Kq * 2;
-    if (cudaMalloc(&g->As, szA) != cudaSuccess || cudaMalloc(&g->BTs, szB) != cudaSuccess ||
-        cudaMalloc(&g->XTs, szX) != cudaSuccess || cudaMalloc(&g->T1s, szT) != cudaSuccess ||
-        cudaMalloc(&g->err, sizeof(int)) != cudaSuccess) {
+    if (dev_alloc((void**)&g->As, szA) != cudaSuccess || dev_alloc((void**)&g->BTs, szB) != cudaSuccess ||
+        dev_alloc((void**)&g->XTs, szX) != cudaSuccess || dev_alloc((void**)&g->T1s, szT) != cudaSuccess ||
+        dev_alloc((void**)&g->err, sizeof(int)) != cudaSuccess) {
         splitgemm_destroy(g);
         return GRBK_ENOMEM;
     }
@@ -666,7 +666,7 @@ void splitgemm_destroy(SplitGemm* g)
     if (!g) return;
     void* bufs[] = {g->As, g->BTs, g->XTs, g->T1s, g->err};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) dev_free(b);
     delete g;
 }
 

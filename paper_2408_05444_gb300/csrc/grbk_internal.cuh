@@ -27,6 +27,12 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Device blocks for contexts (grbk_alloc.cu): freed blocks are kept per device and
+// rounded size for the next request instead of returning to the driver.  A block
+// may be freed only when no queued work still uses it.
+cudaError_t dev_alloc(void** p, size_t bytes);
+void dev_free(void* p);
+
 // ----------------------------------------------------------------------------
 // device-side status (one per context / batch)
 // ----------------------------------------------------------------------------

@@ -995,6 +995,14 @@ struct grbk_ctx {
     double* soff;           // row-space form: ||Rperp_i||^2
     void* K;                // row-space form: Lt^T Lt (n x ldr), when the row fits in shared memory
     void* hist_z;           // with K: the selected rows of a chunk (chunk_cap x ldr)
+    cudaStream_t side;      // set-up only: the copy of a host C overlapped with the rest
+    cudaEvent_t side_done;
+    struct {                // set-up only: the Lanczos run for ||B||_2^2 (begun, then read back)
+        void *vt, *t, *y;
+        double *v, *vprev, *ab;
+        int* nst;
+        int steps;
+    } lz;
     cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
     long long launches;     // kernel launches issued (reset per solve)
 };
@@ -1002,10 +1010,10 @@ struct grbk_ctx {
 static grbk_status ensure_tmp(grbk_ctx* c, size_t bytes)
 {
     if (c->tmp_bytes >= bytes) return GRBK_OK;
-    if (c->tmp) cudaFree(c->tmp);
+    if (c->tmp) dev_free(c->tmp);
     c->tmp = nullptr;
     c->tmp_bytes = 0;
-    if (cudaMalloc(&c->tmp, bytes) != cudaSuccess) return GRBK_ENOMEM;
+    if (dev_alloc(&c->tmp, bytes) != cudaSuccess) return GRBK_ENOMEM;
     c->tmp_bytes = bytes;
     return GRBK_OK;
 }
@@ -1151,14 +1159,34 @@ extern "C" const char* grbk_strerror(int32_t s)
     }
 }
 
+// waits for and releases the set-up's side stream (a copy into c->C may be in flight)
+static void end_side(grbk_ctx* c)
+{
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        c->side = nullptr;
+    }
+    if (c->side_done) {
+        cudaEventDestroy(c->side_done);
+        c->side_done = nullptr;
+    }
+}
+
 extern "C" void grbk_destroy(grbk_ctx* c)
 {
     if (!c) return;
+    end_side(c);
     void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->sr, c->X,
                     c->part, c->part_SJ, c->hist_rows, c->hist_c,
                     c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff, c->K, c->hist_z};
+    // the blocks go back to the cache: let queued work on the context's stream finish first
+    cudaStreamSynchronize(c->stream);
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) dev_free(b);
+    void* lzb[] = {c->lz.vt, c->lz.t, c->lz.y, c->lz.v, c->lz.vprev, c->lz.ab, c->lz.nst};
+    for (void* b : lzb)
+        if (b) dev_free(b);
     if (c->st_host) cudaFreeHost(c->st_host);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -1169,7 +1197,7 @@ extern "C" void grbk_destroy(grbk_ctx* c)
 
 #define ALLOC(ptr, bytes)                                                     \
     do {                                                                      \
-        if (cudaMalloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16) != cudaSuccess) { \
+        if (dev_alloc((void**)&(ptr), (bytes) > 0 ? (bytes) : 16) != cudaSuccess) { \
             grbk_destroy(c);                                                  \
             return GRBK_ENOMEM;                                               \
         }                                                                     \
@@ -1281,63 +1309,81 @@ static double tridiag_max_eig(const std::vector<double>& al, const std::vector<d
     return hi;
 }
 
+// begin: the Lanczos steps are queued on the context's stream (no host wait)
 template <typename T>
-static grbk_status power_iteration(grbk_ctx* c, double* lambda_out)
+static grbk_status lanczos_begin(grbk_ctx* c)
 {
     const int64_t q = c->q, ldb = c->ldb;
     cudaStream_t st = c->stream;
-    T *vt = nullptr, *t = nullptr, *y = nullptr;
-    double *v = nullptr, *vprev = nullptr, *ab = nullptr;
-    int* nst = nullptr;
-    const int steps = (int)std::min<int64_t>(kLanczosSteps, q);
-    if (cudaMalloc(&vt, q * sizeof(T)) != cudaSuccess || cudaMalloc(&t, ldb * sizeof(T)) != cudaSuccess ||
-        cudaMalloc(&y, q * sizeof(T)) != cudaSuccess || cudaMalloc(&v, q * 8) != cudaSuccess ||
-        cudaMalloc(&vprev, q * 8) != cudaSuccess || cudaMalloc(&ab, (size_t)2 * (steps + 1) * 8) != cudaSuccess ||
-        cudaMalloc(&nst, sizeof(int)) != cudaSuccess) {
-        cudaFree(vt); cudaFree(t); cudaFree(y); cudaFree(v); cudaFree(vprev); cudaFree(ab); cudaFree(nst);
+    auto& L = c->lz;
+    L.steps = (int)std::min<int64_t>(kLanczosSteps, q);
+    if (dev_alloc(&L.vt, q * sizeof(T)) != cudaSuccess || dev_alloc(&L.t, ldb * sizeof(T)) != cudaSuccess ||
+        dev_alloc(&L.y, q * sizeof(T)) != cudaSuccess || dev_alloc((void**)&L.v, q * 8) != cudaSuccess ||
+        dev_alloc((void**)&L.vprev, q * 8) != cudaSuccess ||
+        dev_alloc((void**)&L.ab, (size_t)2 * (L.steps + 1) * 8) != cudaSuccess ||
+        dev_alloc((void**)&L.nst, sizeof(int)) != cudaSuccess)
         return GRBK_ENOMEM;
-    }
-    double* alpha = ab;
-    double* beta = ab + steps + 1;
+    double* alpha = L.ab;
+    double* beta = L.ab + L.steps + 1;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t xs = (size_t)q * sizeof(T);
-    grbk_status s = GRBK_OK;
     if (xs > 48 * 1024 &&
         cudaFuncSetAttribute(bt_x_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xs) != cudaSuccess)
-        s = GRBK_EINVAL;
+        return GRBK_EINVAL;
     const int gcols = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, (ldb / (16 / (int64_t)sizeof(T)) + 31) / 32));
     const int grows = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, q));
-    if (s == GRBK_OK) {
-        lanczos_init_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(v, vprev, q, nst);
-        fill_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(vt, q, 1.0 / sqrt((double)q));
-        for (int j = 0; j < steps; ++j) {
-            bt_x_kernel<T><<<gcols, kBlock, xs, st>>>((const T*)c->B, q, ldb, vt, t);
-            b_t_kernel<T><<<grows, kBlock, 0, st>>>((const T*)c->B, q, ldb, t, y);
-            lanczos_step_kernel<T><<<1, 1024, 0, st>>>(v, vprev, vt, y, q, alpha, beta, j, nst);
-        }
-        c->launches += 3 * steps;
-        int hn = 0;
-        std::vector<double> hab((size_t)2 * (steps + 1), 0.0);
-        if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(&hn, nst, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(hab.data(), ab, hab.size() * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) {
-            s = GRBK_ECUDA;
-        } else {
-            const int k = hn < 0 ? -hn : hn;  // steps whose alpha was computed
-            if (k <= 0) {
-                *lambda_out = 0.0;
-            } else {
-                std::vector<double> al(hab.begin(), hab.begin() + k), be(k, 0.0);
-                for (int i = 1; i < k; ++i) be[i] = hab[steps + 1 + i];
-                *lambda_out = tridiag_max_eig(al, be);
-            }
-        }
+    T* vt = (T*)L.vt;
+    lanczos_init_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(L.v, L.vprev, q, L.nst);
+    fill_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(vt, q, 1.0 / sqrt((double)q));
+    for (int j = 0; j < L.steps; ++j) {
+        bt_x_kernel<T><<<gcols, kBlock, xs, st>>>((const T*)c->B, q, ldb, vt, (T*)L.t);
+        b_t_kernel<T><<<grows, kBlock, 0, st>>>((const T*)c->B, q, ldb, (const T*)L.t, (T*)L.y);
+        lanczos_step_kernel<T><<<1, 1024, 0, st>>>(L.v, L.vprev, vt, (const T*)L.y, q, alpha, beta, j, L.nst);
     }
-    cudaFree(vt); cudaFree(t); cudaFree(y); cudaFree(v); cudaFree(vprev); cudaFree(ab); cudaFree(nst);
-    return s;
+    c->launches += 3 * L.steps;
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
+
+// end: read the tridiagonal back (waits for the stream), its largest eigenvalue
+static grbk_status lanczos_end(grbk_ctx* c, double* lambda_out)
+{
+    auto& L = c->lz;
+    cudaStream_t st = c->stream;
+    int hn = 0;
+    std::vector<double> hab((size_t)2 * (L.steps + 1), 0.0);
+    GRBK_CK(cudaMemcpyAsync(&hn, L.nst, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaMemcpyAsync(hab.data(), L.ab, hab.size() * 8, cudaMemcpyDeviceToHost, st));
+    GRBK_CK(cudaStreamSynchronize(st));
+    const int k = hn < 0 ? -hn : hn;  // steps whose alpha was computed
+    if (k <= 0) {
+        *lambda_out = 0.0;
+    } else {
+        std::vector<double> al(hab.begin(), hab.begin() + k), be(k, 0.0);
+        for (int i = 1; i < k; ++i) be[i] = hab[L.steps + 1 + i];
+        *lambda_out = tridiag_max_eig(al, be);
+    }
+    void* b[] = {L.vt, L.t, L.y, L.v, L.vprev, L.ab, L.nst};
+    for (void* x : b) dev_free(x);
+    memset(&L, 0, sizeof(L));
+    return GRBK_OK;
+}
+
+// the step from the estimate of ||B||_2^2: 1/lambda, or the caller's alpha when it is admissible
+static grbk_status set_step(grbk_ctx* c, double hl)
+{
+    c->lambda = hl;
+    if (!(hl > 0.0)) return GRBK_EINVAL;
+    if (c->opts.alpha > 0.0) {
+        // Lemma 2.2 / Theorems 4.2-4.6 need 0 < alpha < 2/||B||_2^2 (small slack for the estimate)
+        if (!(c->opts.alpha * hl < 2.0 * (1.0 + 1e-9))) return GRBK_EINVAL;
+        c->alpha = c->opts.alpha;
+    } else {
+        c->alpha = 1.0 / hl;
+    }
+    return GRBK_OK;
 }
 
 extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk_mat* B,
@@ -1392,9 +1438,13 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
 
     cudaStream_t st = c->stream;
+    // a host C of the working type is copied on a side stream while the set-up that
+    // needs only A and B runs (the Lanczos steps, the split planes, A A^T); the
+    // set-up's read-backs come before that copy starts or after that work
+    const bool c_async = c->form == GRBK_FORM_FULL && !C->on_device && C->dtype == dt;
     if (cudaMemsetAsync(c->A, 0, (size_t)m * c->lda * es, st) != cudaSuccess ||
         cudaMemsetAsync(c->B, 0, (size_t)q * c->ldb * es, st) != cudaSuccess ||
-        cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, st) != cudaSuccess ||
+        (!c_async && cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, st) != cudaSuccess) ||
         cudaMemsetAsync(c->R, 0, (size_t)m * c->ldr * es, st) != cudaSuccess ||
         cudaMemsetAsync(c->v, 0, (size_t)c->ldr * es, st) != cudaSuccess ||
         cudaMemsetAsync(c->bar, 0, sizeof(GridBarrier), st) != cudaSuccess ||
@@ -1404,14 +1454,15 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     }
     TRY(load_matrix(c, A, c->A, dt, c->lda));
     TRY(load_matrix(c, B, c->B, dt, c->ldb));
-    TRY(load_matrix(c, C, c->C, dt, c->ldr));
+    if (!c_async) TRY(load_matrix(c, C, c->C, dt, c->ldr));
 
-    // non-finite check and norms
-    double ssA, ssB, ssC;
-    int badA, badB, badC;
+
+    // non-finite check and norms (C's once it has arrived)
+    double ssA, ssB, ssC = 0.0;
+    int badA, badB, badC = 0;
     TRY(sumsq_nonfinite(c, c->A, m, p, c->lda, &ssA, &badA));
     TRY(sumsq_nonfinite(c, c->B, q, n, c->ldb, &ssB, &badB));
-    TRY(sumsq_nonfinite(c, c->C, m, n, c->ldr, &ssC, &badC));
+    if (!c_async) TRY(sumsq_nonfinite(c, c->C, m, n, c->ldr, &ssC, &badC));
     if (badA || badB || badC) { grbk_destroy(c); return GRBK_ENONFINITE; }
     c->normC2 = ssC;
 
@@ -1424,17 +1475,18 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
         TRY(rowspace_transform(c->prec == GRBK_F64, m, q, n, c->B, c->ldb, c->C, c->ldr, tol, st, &rs));
         c->soff = rs.rperp;
         const int64_t r = rs.r;
-        cudaFree(c->B); c->B = nullptr;
-        cudaFree(c->C); c->C = nullptr;
-        cudaFree(c->R); c->R = nullptr;
-        cudaFree(c->v); c->v = nullptr;
+        cudaStreamSynchronize(st);
+        dev_free(c->B); c->B = nullptr;
+        dev_free(c->C); c->C = nullptr;
+        dev_free(c->R); c->R = nullptr;
+        dev_free(c->v); c->v = nullptr;
         c->n = r;
         c->ldb = round_up(r, 32);
         c->ldr = c->ldb;
-        bool ok = cudaMalloc(&c->B, (size_t)q * c->ldb * es) == cudaSuccess &&
-                  cudaMalloc(&c->C, (size_t)m * c->ldr * es) == cudaSuccess &&
-                  cudaMalloc(&c->R, (size_t)m * c->ldr * es) == cudaSuccess &&
-                  cudaMalloc(&c->v, (size_t)c->ldr * es) == cudaSuccess;
+        bool ok = dev_alloc(&c->B, (size_t)q * c->ldb * es) == cudaSuccess &&
+                  dev_alloc(&c->C, (size_t)m * c->ldr * es) == cudaSuccess &&
+                  dev_alloc(&c->R, (size_t)m * c->ldr * es) == cudaSuccess &&
+                  dev_alloc(&c->v, (size_t)c->ldr * es) == cudaSuccess;
         if (ok)
             ok = cudaMemsetAsync(c->B, 0, (size_t)q * c->ldb * es, st) == cudaSuccess &&
                  cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, st) == cudaSuccess &&
@@ -1444,7 +1496,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
                  convert_matrix(c->C, dt, c->ldr, rs.Chat, dt, r, m, r, st) == cudaSuccess &&
                  cudaStreamSynchronize(st) == cudaSuccess;
         if (ok)
-            ok = cudaMalloc(&c->K, (size_t)r * c->ldr * es) == cudaSuccess &&
+            ok = dev_alloc(&c->K, (size_t)r * c->ldr * es) == cudaSuccess &&
                  cudaMemsetAsync(c->K, 0, (size_t)r * c->ldr * es, st) == cudaSuccess &&
                  convert_matrix(c->K, dt, c->ldr, rs.K, dt, r, r, r, st) == cudaSuccess &&
                  cudaStreamSynchronize(st) == cudaSuccess;
@@ -1474,20 +1526,23 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
             cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
     }
 
-    // ||B||_2^2 by power iteration on B B^T with a Rayleigh quotient
-    {
-        double hl = 0.0;
-        grbk_status ps = (c->prec == GRBK_F64) ? power_iteration<double>(c, &hl) : power_iteration<float>(c, &hl);
-        if (ps != GRBK_OK) { grbk_destroy(c); return ps; }
-        c->lambda = hl;
-        if (!(hl > 0.0)) { grbk_destroy(c); return GRBK_EINVAL; }
-        if (o.alpha > 0.0) {
-            // Lemma 2.2 / Theorems 4.2-4.6 need 0 < alpha < 2/||B||_2^2 (small slack for the estimate)
-            if (!(o.alpha * hl < 2.0 * (1.0 + 1e-9))) { grbk_destroy(c); return GRBK_EINVAL; }
-            c->alpha = o.alpha;
-        } else {
-            c->alpha = 1.0 / hl;
+    // ||B||_2^2 by Lanczos on B B^T; with a host C in flight its result is read after A A^T,
+    // so that no read-back waits behind the copy of C
+    TRY(c->prec == GRBK_F64 ? lanczos_begin<double>(c) : lanczos_begin<float>(c));
+    if (c_async) {
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->side_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMemsetAsync(c->C, 0, (size_t)m * c->ldr * es, c->side) != cudaSuccess ||
+            cudaMemcpy2DAsync(c->C, c->ldr * es, C->ptr, C->ld * es, n * es, m, cudaMemcpyHostToDevice,
+                              c->side) != cudaSuccess ||
+            cudaEventRecord(c->side_done, c->side) != cudaSuccess) {
+            grbk_destroy(c);
+            return GRBK_ECUDA;
         }
+    } else {
+        double hl = 0.0;
+        TRY(lanczos_end(c, &hl));
+        TRY(set_step(c, hl));
     }
 
     TRY(c->prec == GRBK_F64 ? setup_launch_shape<double>(c) : setup_launch_shape<float>(c));
@@ -1502,7 +1557,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
         if (c->smem_v) {
             ALLOC(c->hist_z, (size_t)c->chunk_cap * c->ldr * es);
         } else {  // the row does not fit in shared memory: w and v from Lt as in the full form
-            cudaFree(c->K);
+            dev_free(c->K);
             c->K = nullptr;
         }
     }
@@ -1528,6 +1583,16 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
             TRY(splitgemm_gram(c->sg, (float*)c->gram, c->ldg, st));
             TRY(splitgemm_check(c->sg, st));
         }
+    }
+    if (c_async) {
+        double hl = 0.0;
+        TRY(lanczos_end(c, &hl));
+        TRY(set_step(c, hl));
+        if (cudaStreamWaitEvent(st, c->side_done, 0) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
+        end_side(c);
+        TRY(sumsq_nonfinite(c, c->C, m, n, c->ldr, &ssC, &badC));
+        if (badC) { grbk_destroy(c); return GRBK_ENONFINITE; }
+        c->normC2 = ssC;
     }
     if (cudaStreamSynchronize(st) != cudaSuccess) { grbk_destroy(c); return GRBK_ECUDA; }
     *out = c;

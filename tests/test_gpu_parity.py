@@ -256,12 +256,20 @@ def test_torch_device_buffers_and_stream():
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("shape", [(37, 5, 7, 29), (200, 100, 80, 150), (2000, 200, 200, 2000), (60, 4, 1, 9)])
+@pytest.mark.parametrize("shape", [(37, 5, 7, 29), (200, 100, 80, 150), (2000, 200, 200, 2000), (60, 4, 1, 9),
+                                   "rank_deficient"])
 def test_default_step_is_inverse_squared_spectral_norm(precision, shape):
     """alpha = 1/||B||_2^2 (Section 5) from the library's Lanczos estimate of the
-    largest eigenvalue of B B^T, against numpy's SVD."""
-    m, p, q, n = shape
-    A, B, C, _ = workloads.gaussian(m, p, q, n, seed=q + n)
+    largest eigenvalue of B B^T, against numpy's SVD (also for a B whose 40 rows
+    span only 12 dimensions: the recurrence ends early)."""
+    if shape == "rank_deficient":
+        rng = np.random.default_rng(3)
+        B = rng.standard_normal((40, 12)) @ rng.standard_normal((12, 70))
+        A = rng.standard_normal((30, 9))
+        C = A @ rng.standard_normal((9, 40)) @ B
+    else:
+        m, p, q, n = shape
+        A, B, C, _ = workloads.gaussian(m, p, q, n, seed=q + n)
     ctx = g.grbk_create(A, B, C, precision=precision)
     _, al = g.grbk_info(ctx)
     ref = 1.0 / np.linalg.norm(B, 2) ** 2

@@ -174,3 +174,17 @@ def test_rowspace_keeps_no_full_residual():
     with pytest.raises(g.GrbkError):
         g.grbk_residual(ctx, np.zeros((6, 5)), np.zeros((40, 30)))
     g.grbk_destroy(ctx)
+
+
+def test_rowspace_fp32_three_terms_from_nonzero_x0():
+    """FP32 row-space form with the 3-term split refresh, started from X0 != 0 (its
+    first residual is the transformed refresh Chat - A X0 Lt): RSE <= 1e-4."""
+    A, B, C, Xs = workloads.config_precision(2000, 200, 200, 2000)
+    X0 = Xs + 0.1 * np.random.default_rng(4).standard_normal(Xs.shape)
+    ctx = g.grbk_create(A, B, C, precision="f32", stop_kind="rse", x_ref=Xs, refresh_T=64, split_terms=3,
+                        form="rowspace")
+    X = np.zeros_like(Xs)
+    st, res = g.grbk_solve(ctx, "rgrbk", theta=0.5, X0=X0, tol=1e-4, maxit=2_000_000, seed=3, X_out=X)
+    assert st == g.GRBK_OK, res
+    assert _rel(X, Xs) <= 1e-4
+    assert res["iters"] > 0
