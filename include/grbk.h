@@ -168,6 +168,11 @@ grbk_status grbk_residual(grbk_ctx* ctx, const grbk_mat* X, grbk_mat* R_out);
 grbk_status grbk_get_residual(grbk_ctx* ctx, grbk_mat* R_out);
 grbk_status grbk_get_rownorms(grbk_ctx* ctx, double* s_out, int32_t on_device);
 
+/* Device blocks of destroyed contexts are kept (per device and size, at most 64 GB)
+ * for the next grbk_create; this returns every kept block to the driver, e.g.
+ * before another allocator in the process needs the memory.  Not part of the paper. */
+void grbk_trim_cache(void);
+
 /* Problem sizes (m, p, q, n of the caller's system) and the step in use. */
 grbk_status grbk_info(const grbk_ctx* ctx, int64_t dims[4], double* alpha);
 

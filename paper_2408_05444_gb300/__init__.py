@@ -64,7 +64,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info", "grbk_batch_info"]
+           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -93,6 +93,8 @@ def lib():
         L.grbk_get_rownorms.restype = i32
         L.grbk_info.argtypes = [vp, P(i64), P(dbl)]
         L.grbk_info.restype = i32
+        L.grbk_trim_cache.argtypes = []
+        L.grbk_trim_cache.restype = None
         L.grbk_form_info.argtypes = [vp, P(i32), P(i64)]
         L.grbk_form_info.restype = i32
         L.grbk_destroy.argtypes = [vp]
@@ -302,6 +304,11 @@ def grbk_form_info(ctx: Context):
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_form_info")
     return ("full", "rowspace")[f.value], cols.value
+
+
+def grbk_trim_cache():
+    """Return the device blocks kept from destroyed contexts to the driver."""
+    lib().grbk_trim_cache()
 
 
 def grbk_destroy(ctx: Context):

@@ -18,7 +18,7 @@
 
 namespace grbk {
 
-namespace {
+namespace {  // the cache's state
 
 struct Block {
     size_t bytes;
@@ -112,3 +112,9 @@ void dev_free(void* p)
 }
 
 }  // namespace grbk
+
+extern "C" void grbk_trim_cache(void)
+{
+    std::lock_guard<std::mutex> lk(grbk::g_mu);
+    grbk::release_kept_locked();
+}

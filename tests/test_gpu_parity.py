@@ -326,3 +326,18 @@ def test_zero_rows_of_A_are_skipped():
         _assert_same_rows(gpu["rows"], orc)
         if variant != "bk":
             assert not set(gpu["rows"].tolist()) & {0, 7, 39}
+
+
+def test_block_cache_reuse_and_trim():
+    """A destroyed context's device blocks serve the next create of the same sizes
+    (same results), and grbk_trim_cache returns them to the driver."""
+    A, B, C, _ = workloads.gaussian(3000, 60, 50, 900, seed=12)
+    al = _alpha(B)
+    free0 = torch.cuda.mem_get_info()[0]
+    r1 = _gpu_run(A, B, C, "grbk", alpha=al, seed=2, maxit=200, precision="f32", refresh_T=64, trace=False)
+    held = free0 - torch.cuda.mem_get_info()[0]
+    r2 = _gpu_run(A, B, C, "grbk", alpha=al, seed=2, maxit=200, precision="f32", refresh_T=64, trace=False)
+    assert np.array_equal(r1["X"], r2["X"])
+    assert free0 - torch.cuda.mem_get_info()[0] <= held + (8 << 20)   # the second create reused the blocks
+    g.grbk_trim_cache()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
