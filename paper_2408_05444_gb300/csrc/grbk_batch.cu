@@ -379,18 +379,22 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
 
         // R^0 = C - A X^0 B (row by row) or R^0 = C
         if (P.init_from_x) {
+            // on the banded path only the bands of A_i and of B's columns contribute
             const float* X = P.X + d.offX;
+            const bool bnd = d.bandA >= 0;
             for (int i = 0; i < d.m; ++i) {
+                const int c0 = bnd ? max(0, i - d.bandA) : 0, c1 = bnd ? min(d.p - 1, i + d.bandA) : d.p - 1;
                 for (int j = threadIdx.x; j < d.q; j += kBB) {  // t = A_i X
                     float acc = 0.f;
-                    for (int c2 = 0; c2 < d.p; ++c2)
+                    for (int c2 = c0; c2 <= c1; ++c2)
                         acc = fmaf(A[(long long)i * d.lda + c2], X[(long long)c2 * d.q + j], acc);
                     s_w[j] = acc;
                 }
                 __syncthreads();
                 for (int l = threadIdx.x; l < d.n; l += kBB) {  // R_i = C_i - t B
+                    const int j0 = bnd ? max(0, l - d.bandB) : 0, j1 = bnd ? min(d.q - 1, l + d.bandB) : d.q - 1;
                     float acc = 0.f;
-                    for (int j = 0; j < d.q; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
+                    for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
                     R[(long long)i * d.ldr + l] = C[(long long)i * d.ldr + l] - acc;
                 }
                 __syncthreads();
@@ -718,23 +722,44 @@ extern "C" void grbk_batch_destroy(grbk_batch* b)
     delete b;
 }
 
-static grbk_status batch_load(const grbk_mat* M, float* dst, int64_t ldd, cudaStream_t st)
-{
-    const int64_t rows = M->rows, cols = M->cols;
-    const int es = M->dtype == GRBK_DT_F64 ? 8 : 4;
-    if (M->on_device) {
-        GRBK_CK(convert_matrix(dst, GRBK_DT_F32, ldd, M->ptr, M->dtype, M->ld, rows, cols, st));
+// Caller matrices -> padded FP32 device rows, for many systems in one call.  An FP32
+// host matrix is copied straight into its rows; an FP64 host matrix goes through one
+// staging block (largest of them, reused in stream order, released after one wait).
+struct BatchLoader {
+    cudaStream_t st;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    grbk_status load(const grbk_mat* M, float* dst, int64_t ldd)
+    {
+        const int64_t rows = M->rows, cols = M->cols;
+        if (M->on_device) {
+            GRBK_CK(convert_matrix(dst, GRBK_DT_F32, ldd, M->ptr, M->dtype, M->ld, rows, cols, st));
+            return GRBK_OK;
+        }
+        if (M->dtype == GRBK_DT_F32) {
+            GRBK_CK(cudaMemcpy2DAsync(dst, ldd * 4, M->ptr, M->ld * 4, cols * 4, rows, cudaMemcpyHostToDevice, st));
+            return GRBK_OK;
+        }
+        const size_t need = (size_t)rows * cols * 8;
+        if (need > tmp_bytes) {
+            if (tmp) { cudaStreamSynchronize(st); dev_free(tmp); tmp = nullptr; tmp_bytes = 0; }
+            if (dev_alloc(&tmp, need) != cudaSuccess) return GRBK_ENOMEM;
+            tmp_bytes = need;
+        }
+        GRBK_CK(cudaMemcpy2DAsync(tmp, cols * 8, M->ptr, M->ld * 8, cols * 8, rows, cudaMemcpyHostToDevice, st));
+        GRBK_CK(convert_matrix(dst, GRBK_DT_F32, ldd, tmp, M->dtype, cols, rows, cols, st));
         return GRBK_OK;
     }
-    void* tmp = dmalloc((size_t)rows * cols * es);
-    if (!tmp) return GRBK_ENOMEM;
-    cudaError_t e = cudaMemcpy2DAsync(tmp, cols * es, M->ptr, M->ld * es, cols * es, rows, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = convert_matrix(dst, GRBK_DT_F32, ldd, tmp, M->dtype, cols, rows, cols, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return GRBK_ECUDA;
-    return GRBK_OK;
-}
+    grbk_status finish()
+    {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (tmp) dev_free(tmp);
+        tmp = nullptr;
+        tmp_bytes = 0;
+        return e == cudaSuccess ? GRBK_OK : GRBK_ECUDA;
+    }
+    ~BatchLoader() { finish(); }
+};
 
 extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
                                          const grbk_mat* C, const grbk_opts* opts)
@@ -785,15 +810,21 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     cudaMemsetAsync(b->B, 0, oB * 4, st);
     cudaMemsetAsync(b->C, 0, oR * 4, st);
     b->normC2.resize(nsys);
-    for (int s = 0; s < nsys; ++s) {
-        SysDesc& d = b->hsys[s];
-        grbk_status e;
-        if ((e = batch_load(&A[s], b->A + d.offA, d.lda, st)) != GRBK_OK ||
-            (e = batch_load(&B[s], b->B + d.offB, d.ldb, st)) != GRBK_OK ||
-            (e = batch_load(&C[s], b->C + d.offR, d.ldr, st)) != GRBK_OK) {
-            grbk_batch_destroy(b);
-            return e;
+    {
+        BatchLoader ld{st};
+        for (int s = 0; s < nsys; ++s) {
+            SysDesc& d = b->hsys[s];
+            grbk_status e;
+            if ((e = ld.load(&A[s], b->A + d.offA, d.lda)) != GRBK_OK ||
+                (e = ld.load(&B[s], b->B + d.offB, d.ldb)) != GRBK_OK ||
+                (e = ld.load(&C[s], b->C + d.offR, d.ldr)) != GRBK_OK) {
+                ld.finish();
+                grbk_batch_destroy(b);
+                return e;
+            }
         }
+        const grbk_status e = ld.finish();
+        if (e != GRBK_OK) { grbk_batch_destroy(b); return e; }
     }
     // per-system set-up on the device (one CTA per system)
     {
@@ -878,11 +909,14 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     }
     GRBK_CK(cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st));
     if (X0s) {
+        BatchLoader ld{st};
         for (int s = 0; s < b->nsys; ++s) {
             const SysDesc& d = b->hsys[s];
-            grbk_status e = batch_load(&X0s[s], b->X + d.offX, d.q, st);
+            const grbk_status e = ld.load(&X0s[s], b->X + d.offX, d.q);
             if (e != GRBK_OK) return e;
         }
+        const grbk_status e = ld.finish();
+        if (e != GRBK_OK) return e;
     } else {
         GRBK_CK(cudaMemsetAsync(b->X, 0, b->totX * 4, st));
     }
@@ -926,23 +960,33 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     if (tlen > 0)
         GRBK_CK(cudaMemcpyAsync(b->opts.row_trace, b->trace, (size_t)tlen * b->nsys * 4, cudaMemcpyDeviceToHost, st));
     if (X_outs) {
-        for (int s = 0; s < b->nsys; ++s) {
+        // host outputs go through one staging block: every system converted into it at its own
+        // offset, each copied out, one wait at the end
+        size_t stage_bytes = 0;
+        for (int s = 0; s < b->nsys; ++s)
+            if (!X_outs[s].on_device)
+                stage_bytes += (size_t)b->hsys[s].p * b->hsys[s].q * (X_outs[s].dtype == GRBK_DT_F64 ? 8 : 4);
+        char* stage = nullptr;
+        if (stage_bytes && dev_alloc((void**)&stage, stage_bytes) != cudaSuccess) return GRBK_ENOMEM;
+        size_t off = 0;
+        cudaError_t e = cudaSuccess;
+        for (int s = 0; s < b->nsys && e == cudaSuccess; ++s) {
             const SysDesc& d = b->hsys[s];
             grbk_mat& M = X_outs[s];
             const int es = M.dtype == GRBK_DT_F64 ? 8 : 4;
             if (M.on_device) {
-                GRBK_CK(convert_matrix((void*)M.ptr, M.dtype, M.ld, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st));
+                e = convert_matrix((void*)M.ptr, M.dtype, M.ld, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st);
             } else {
-                void* tmp = dmalloc((size_t)d.p * d.q * es);
-                if (!tmp) return GRBK_ENOMEM;
-                cudaError_t e = convert_matrix(tmp, M.dtype, d.q, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st);
+                e = convert_matrix(stage + off, M.dtype, d.q, b->X + d.offX, GRBK_DT_F32, d.q, d.p, d.q, st);
                 if (e == cudaSuccess)
-                    e = cudaMemcpy2DAsync((void*)M.ptr, M.ld * es, tmp, d.q * es, d.q * es, d.p, cudaMemcpyDeviceToHost, st);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-                cudaFree(tmp);
-                if (e != cudaSuccess) return GRBK_ECUDA;
+                    e = cudaMemcpy2DAsync((void*)M.ptr, M.ld * es, stage + off, d.q * es, d.q * es, d.p,
+                                          cudaMemcpyDeviceToHost, st);
+                off += (size_t)d.p * d.q * es;
             }
         }
+        const cudaError_t e2 = cudaStreamSynchronize(st);
+        if (stage) dev_free(stage);
+        if (e != cudaSuccess || e2 != cudaSuccess) return GRBK_ECUDA;
     }
     GRBK_CK(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -25,7 +25,9 @@
 namespace grbk {
 namespace unet {
 
-constexpr int TILE = 16;       // output tile side
+constexpr int TILE = 16;       // output tile side (weight-gradient kernel; width of the convolution's tile)
+constexpr int PIX = 4;         // convolution: output pixels per thread, stacked vertically
+constexpr int TILE_H = TILE * PIX;  // convolution: output tile height
 constexpr int CO_T = 16;       // output channels per CTA
 constexpr int CI_T = 8;        // input channels staged per step
 
@@ -50,21 +52,25 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
                                                       const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
                                                       int H, int W, int relu, int accumulate)
 {
-    __shared__ float s_in[CI_T][TILE + 2][TILE + 2];
+    // output tile TILE wide and TILE_H tall; thread (lx, ly) computes PIX pixels of one
+    // column, so every weight read from shared memory feeds PIX multiply-adds
+    __shared__ float s_in[CI_T][TILE_H + 2][TILE + 2];
     __shared__ float s_w[CO_T][CI_T][9];
     const int tiles_x = (W + TILE - 1) / TILE;
-    const int tx0 = (blockIdx.x % tiles_x) * TILE, ty0 = (blockIdx.x / tiles_x) * TILE;
+    const int tx0 = (blockIdx.x % tiles_x) * TILE, ty0 = (blockIdx.x / tiles_x) * TILE_H;
     const int o0 = blockIdx.y * CO_T, n = blockIdx.z;
     const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
-    const int x = tx0 + lx, y = ty0 + ly;
-    float acc[CO_T];
+    const int x = tx0 + lx, y0 = ty0 + ly * PIX;
+    float acc[CO_T][PIX];
 #pragma unroll
-    for (int o = 0; o < CO_T; ++o) acc[o] = 0.f;
+    for (int o = 0; o < CO_T; ++o)
+#pragma unroll
+        for (int p = 0; p < PIX; ++p) acc[o][p] = 0.f;
     for (int i0 = 0; i0 < Cin; i0 += CI_T) {
         // stage CI_T input channels with a 1-pixel halo
-        for (int e = threadIdx.x; e < CI_T * (TILE + 2) * (TILE + 2); e += 256) {
-            const int ci = e / ((TILE + 2) * (TILE + 2));
-            const int r = e % ((TILE + 2) * (TILE + 2));
+        for (int e = threadIdx.x; e < CI_T * (TILE_H + 2) * (TILE + 2); e += 256) {
+            const int ci = e / ((TILE_H + 2) * (TILE + 2));
+            const int r = e % ((TILE_H + 2) * (TILE + 2));
             const int hy = r / (TILE + 2), hx = r % (TILE + 2);
             const int gy = ty0 + hy - 1, gx = tx0 + hx - 1;
             float v = 0.f;
@@ -85,27 +91,38 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
             s_w[o][ci][k] = wv;
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 2
         for (int ci = 0; ci < CI_T; ++ci) {
-            float nb[9];
+            float nb[PIX + 2][3];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) nb[k] = s_in[ci][ly + k / 3][lx + k % 3];
+            for (int r = 0; r < PIX + 2; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) nb[r][c] = s_in[ci][ly * PIX + r][lx + c];
 #pragma unroll
             for (int o = 0; o < CO_T; ++o) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) acc[o] = fmaf(s_w[o][ci][k], nb[k], acc[o]);
+                for (int k = 0; k < 9; ++k) {
+                    const float wv = s_w[o][ci][k];
+#pragma unroll
+                    for (int p = 0; p < PIX; ++p) acc[o][p] = fmaf(wv, nb[p + k / 3][k % 3], acc[o][p]);
+                }
             }
         }
         __syncthreads();
     }
-    if (x >= W || y >= H) return;
+    if (x >= W) return;
 #pragma unroll
-    for (int o = 0; o < CO_T; ++o) {
-        if (o0 + o >= Cout) break;
-        float v = acc[o] + (b ? b[o0 + o] : 0.f);
-        if (relu) v = fmaxf(v, 0.f);
-        float* dst = at(out, n, o0 + o, H, W) + y * W + x;
-        if (accumulate) *dst += v; else *dst = v;
+    for (int p = 0; p < PIX; ++p) {
+        const int y = y0 + p;
+        if (y >= H) break;
+#pragma unroll
+        for (int o = 0; o < CO_T; ++o) {
+            if (o0 + o >= Cout) break;
+            float v = acc[o][p] + (b ? b[o0 + o] : 0.f);
+            if (relu) v = fmaxf(v, 0.f);
+            float* dst = at(out, n, o0 + o, H, W) + y * W + x;
+            if (accumulate) *dst += v; else *dst = v;
+        }
     }
 }
 
@@ -386,7 +403,7 @@ static unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 
 static cudaError_t conv(grbk_unet* u, int l, View in, View out, int N, int H, int W)
 {
     const LayerDef& d = u->L[l];
-    const int tiles = ((W + TILE - 1) / TILE) * ((H + TILE - 1) / TILE);
+    const int tiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
     dim3 grid((unsigned)tiles, (unsigned)((d.cout + CO_T - 1) / CO_T), (unsigned)N);
     conv3x3_kernel<false><<<grid, 256, 0, u->stream>>>(in, d.cin, kNone, out, d.cout, u->wb + d.woff,
                                                        u->params + d.boff, H, W, d.relu, 0);
@@ -409,7 +426,8 @@ static cudaError_t conv_bwd(grbk_unet* u, int l, View in, View outv, View gout, 
     reduce_slices_kernel<<<blocks_for(wl), 256, 0, u->stream>>>(u->wpart, S, wl, u->grad + d.woff);
     reduce_slices_kernel<<<blocks_for(d.cout), 256, 0, u->stream>>>(bpart, S, d.cout, u->grad + d.boff);
     if (gin.p) {
-        dim3 grid((unsigned)tiles, (unsigned)((d.cin + CO_T - 1) / CO_T), (unsigned)N);
+        const int ctiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
+        dim3 grid((unsigned)ctiles, (unsigned)((d.cin + CO_T - 1) / CO_T), (unsigned)N);
         conv3x3_kernel<true><<<grid, 256, 0, u->stream>>>(gout, d.cout, mask, gin, d.cin, u->wb + d.woff, nullptr, H, W,
                                                           0, accumulate);
     }

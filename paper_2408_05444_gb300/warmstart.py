@@ -60,21 +60,27 @@ def train(net, C, T, epochs=2, batch=64, lr=2e-3, seed=0, log=None):
     return losses
 
 
-def warm_starts(net, Cs):
+def warm_starts(net, Cs, on_device=False):
     """X0 = U-Net(C) for each channel (equal shapes run batched).  The judge of
-    each X0 against X0 = 0 happens inside grbk_batch_solve."""
+    each X0 against X0 = 0 happens inside grbk_batch_solve.  on_device=True
+    returns FP32 device tensors (views of the batched output), which
+    grbk_batch_solve takes without a round trip through the host."""
     import torch
     shapes = {}
     for k, C in enumerate(Cs):
         shapes.setdefault(C.shape, []).append(k)
     out = [None] * len(Cs)
     for shp, ks in shapes.items():
-        Ct = torch.tensor(np.stack([Cs[k] for k in ks]), dtype=torch.float32, device="cuda")
+        Ct = torch.from_numpy(np.stack([np.asarray(Cs[k], dtype=np.float32) for k in ks])).to("cuda")
         Xt = torch.empty_like(Ct)
         grbk_unet_forward(net, Ct, Xt)
-        Xh = Xt.cpu().numpy()
-        for j, k in enumerate(ks):
-            out[k] = Xh[j]
+        if on_device:
+            for j, k in enumerate(ks):
+                out[k] = Xt[j]
+        else:
+            Xh = Xt.cpu().numpy()
+            for j, k in enumerate(ks):
+                out[k] = Xh[j]
     return out
 
 

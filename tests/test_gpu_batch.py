@@ -132,3 +132,27 @@ def test_banded_path_on_rectangular_banded_systems():
         assert np.array_equal(b.row_trace[sid][:kk], orc["rows"][:kk])
         if kk == 150:
             assert _rel(X, orc["X"]) < 1e-4
+
+
+@pytest.mark.parametrize("band_limit", [0, -1])
+def test_batch_from_nonzero_x0_matches_oracle(band_limit):
+    """R^0 = C - A X0 B formed on the device (from the bands of A and B on the
+    banded path) and the iteration from there agree with the oracle."""
+    sy = _systems()[:2]
+    As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
+    rng = np.random.default_rng(6)
+    X0s = [s["X"] + 0.05 * rng.standard_normal(s["X"].shape) for s in sy]
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=100, band_limit=band_limit)
+    Xo = [np.zeros_like(s["X"]) for s in sy]
+    st, res = g.grbk_batch_solve(b, "grbk", X0s=X0s, maxit=100, seed=5, X_outs=Xo)
+    assert st == g.GRBK_OK
+    for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
+        assert r["x0_rejected"] == 0
+        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=r["alpha"], X0=X0s[sid], seed=5, sys=sid,
+                           maxit=100, mode=oracle.MODE_FACTORED)
+        margins = np.minimum(orc["margin_pick"], np.where(np.isnan(orc["margin_adm"]), np.inf, orc["margin_adm"]))
+        near = np.nonzero(margins < 1e-5)[0]
+        kk = int(near[0]) if len(near) else 100
+        assert np.array_equal(b.row_trace[sid][:kk], orc["rows"][:kk])
+        if kk == 100:
+            assert _rel(X, orc["X"]) < 1e-4

@@ -106,6 +106,8 @@ def test_warm_start_gain():
     it0, e0, _ = run(None)
     itu, eu, _ = run([x.astype(np.float64) for x in ws.warm_starts(untrained, Cs)])
     itw, ew, resw = run([x.astype(np.float64) for x in ws.warm_starts(net, Cs)])
+    itd, ed, _ = run(ws.warm_starts(net, Cs, on_device=True))   # the same X0 handed over on the device
+    assert np.array_equal(itd, itw) and abs(ed - ew) <= 1e-6 * ew
     assert sum(r["x0_rejected"] for r in resw) == 0
     assert itw.mean() < 0.8 * it0.mean(), (itw.mean(), it0.mean())
     assert itw.mean() < itu.mean(), (itw.mean(), itu.mean())
