@@ -35,7 +35,7 @@ struct SysDesc {
     int pad;
     long long offA, offB, offR, offX, offRow, offHist, offHistW;
     double F, alpha, stop_S;        // stop when S <= stop_S (< 0: never)
-    double normC2;                  // ||C||_F^2 (judge of a caller's X0)
+    double normC2;                  // ||C||_F^2 (the test of a caller's X0)
 };
 
 struct BatchParams {
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             }
             __syncthreads();
             if (!P.init_from_x || pass == 1) break;
-            // judge the caller's X0 against X0 = 0: keep it only if ||C - A X0 B|| < ||C||
+            // test the caller's X0 against X0 = 0: keep it only if ||C - A X0 B|| < ||C||
             double S0 = 0.0;
             for (int i = threadIdx.x; i < d.m; i += kBB) S0 += s_s[i];
             S0 = block_sum_fixed(S0, red);

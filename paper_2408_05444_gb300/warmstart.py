@@ -1,7 +1,7 @@
 """Learned warm start for batched colour-image restoration (Section 6 solves one
 A X B = C system per channel): train the library's U-Net on (blurred channel,
 restoration) pairs produced by the solver itself, then start each solve from
-X0 = U-Net(C) with X0 = 0 as the fallback and judge.
+X0 = U-Net(C), with X0 = 0 as the fallback and the reference it must beat.
 
 Every numerical step runs in the library's kernels (grbk_unet_* and
 grbk_batch_*); this module only orders the calls.
@@ -61,7 +61,7 @@ def train(net, C, T, epochs=2, batch=64, lr=2e-3, seed=0, log=None):
 
 
 def warm_starts(net, Cs, on_device=False):
-    """X0 = U-Net(C) for each channel (equal shapes run batched).  The judge of
+    """X0 = U-Net(C) for each channel (equal shapes run batched).  The check of
     each X0 against X0 = 0 happens inside grbk_batch_solve.  on_device=True
     returns FP32 device tensors (views of the batched output), which
     grbk_batch_solve takes without a round trip through the host."""
