@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-rowspace", action="store_true")
-    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch"],
+    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=2)
     ap.add_argument("--train-images", type=int, default=20000)
@@ -583,8 +583,32 @@ def batch_bench(args):
     print(json.dumps(out), flush=True)
 
 
+def unet_bench(args):
+    """Warm-start network inference: the U-Net (width 20, random weights) on a batch
+    of 16 channels of 512 x 512 already on the device; three untimed forwards,
+    then one timed with CUDA events."""
+    import torch
+    import paper_2408_05444_gb300 as g
+    from paper_2408_05444_gb300 import warmstart as ws
+    net = ws.make_net(width=20, seed=0)
+    C = torch.rand(16, 512, 512, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    X = torch.empty_like(C)
+    for _ in range(3):
+        g.grbk_unet_forward(net, C, X)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    g.grbk_unet_forward(net, C, X)
+    ev1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "unet", "channels": 16, "side": 512, "forward_ms": ev0.elapsed_time(ev1)}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "unet":
+        unet_bench(args)
+        return
     if args.mode == "batch":
         batch_bench(args)
         return
