@@ -47,27 +47,28 @@ __device__ __forceinline__ float* at(const View& v, int n, int c, int H, int W)
 //   FLIP = false: w(o, i, k) = W[o][i][k]         (forward)
 //   FLIP = true : w(o, i, k) = W[i][o][8 - k]     (gradient w.r.t. the input)
 // mask (optional): the input is multiplied by (mask > 0) (ReLU derivative).
-template <bool FLIP>
+template <bool FLIP, int COT>
 __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mask, View out, int Cout,
                                                       const __nv_bfloat16* __restrict__ Wt, const float* __restrict__ b,
                                                       int H, int W, int relu, int accumulate)
 {
-    // output tile TILE wide and TILE_H tall; thread (lx, ly) computes PIX pixels of one
-    // column, so every weight read from shared memory feeds PIX multiply-adds
+    // output tile TILE wide and TILE_H tall, COT output channels; thread (lx, ly) computes
+    // PIX pixels of one column, so every weight read from shared memory feeds PIX
+    // multiply-adds.
     __shared__ float s_in[CI_T][TILE_H + 2][TILE + 2];
-    __shared__ float s_w[CO_T][CI_T][9];
+    __shared__ float s_w[COT][CI_T][9];
     const int tiles_x = (W + TILE - 1) / TILE;
     const int tx0 = (blockIdx.x % tiles_x) * TILE, ty0 = (blockIdx.x / tiles_x) * TILE_H;
-    const int o0 = blockIdx.y * CO_T, n = blockIdx.z;
+    const int o0 = blockIdx.y * COT, n = blockIdx.z;
     const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
     const int x = tx0 + lx, y0 = ty0 + ly * PIX;
-    float acc[CO_T][PIX];
+    float acc[COT][PIX];
 #pragma unroll
-    for (int o = 0; o < CO_T; ++o)
+    for (int o = 0; o < COT; ++o)
 #pragma unroll
         for (int p = 0; p < PIX; ++p) acc[o][p] = 0.f;
     for (int i0 = 0; i0 < Cin; i0 += CI_T) {
-        // stage CI_T input channels with a 1-pixel halo
+        // stage CI_T input channels with a 1-pixel halo (zeros past Cin)
         for (int e = threadIdx.x; e < CI_T * (TILE_H + 2) * (TILE + 2); e += 256) {
             const int ci = e / ((TILE_H + 2) * (TILE + 2));
             const int r = e % ((TILE_H + 2) * (TILE + 2));
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
             }
             s_in[ci][hy][hx] = v;
         }
-        for (int e = threadIdx.x; e < CO_T * CI_T * 9; e += 256) {
+        for (int e = threadIdx.x; e < COT * CI_T * 9; e += 256) {
             const int o = e / (CI_T * 9), r = e % (CI_T * 9), ci = r / 9, k = r % 9;
             float wv = 0.f;
             if (o0 + o < Cout && i0 + ci < Cin) {
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
 #pragma unroll
                 for (int c = 0; c < 3; ++c) nb[r][c] = s_in[ci][ly * PIX + r][lx + c];
 #pragma unroll
-            for (int o = 0; o < CO_T; ++o) {
+            for (int o = 0; o < COT; ++o) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     const float wv = s_w[o][ci][k];
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
         const int y = y0 + p;
         if (y >= H) break;
 #pragma unroll
-        for (int o = 0; o < CO_T; ++o) {
+        for (int o = 0; o < COT; ++o) {
             if (o0 + o >= Cout) break;
             float v = acc[o][p] + (b ? b[o0 + o] : 0.f);
             if (relu) v = fmaxf(v, 0.f);
@@ -404,9 +405,15 @@ static cudaError_t conv(grbk_unet* u, int l, View in, View out, int N, int H, in
 {
     const LayerDef& d = u->L[l];
     const int tiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
-    dim3 grid((unsigned)tiles, (unsigned)((d.cout + CO_T - 1) / CO_T), (unsigned)N);
-    conv3x3_kernel<false><<<grid, 256, 0, u->stream>>>(in, d.cin, kNone, out, d.cout, u->wb + d.woff,
-                                                       u->params + d.boff, H, W, d.relu, 0);
+    if (d.cout == 1) {  // the output layer: one channel per CTA instead of CO_T mostly empty ones
+        dim3 grid((unsigned)tiles, 1u, (unsigned)N);
+        conv3x3_kernel<false, 1><<<grid, 256, 0, u->stream>>>(in, d.cin, kNone, out, d.cout, u->wb + d.woff,
+                                                              u->params + d.boff, H, W, d.relu, 0);
+    } else {
+        dim3 grid((unsigned)tiles, (unsigned)((d.cout + CO_T - 1) / CO_T), (unsigned)N);
+        conv3x3_kernel<false, CO_T><<<grid, 256, 0, u->stream>>>(in, d.cin, kNone, out, d.cout, u->wb + d.woff,
+                                                                 u->params + d.boff, H, W, d.relu, 0);
+    }
     return cudaGetLastError();
 }
 
@@ -428,7 +435,7 @@ static cudaError_t conv_bwd(grbk_unet* u, int l, View in, View outv, View gout, 
     if (gin.p) {
         const int ctiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
         dim3 grid((unsigned)ctiles, (unsigned)((d.cin + CO_T - 1) / CO_T), (unsigned)N);
-        conv3x3_kernel<true><<<grid, 256, 0, u->stream>>>(gout, d.cout, mask, gin, d.cin, u->wb + d.woff, nullptr, H, W,
+        conv3x3_kernel<true, CO_T><<<grid, 256, 0, u->stream>>>(gout, d.cout, mask, gin, d.cin, u->wb + d.woff, nullptr, H, W,
                                                           0, accumulate);
     }
     return cudaGetLastError();
