@@ -1010,7 +1010,10 @@ struct grbk_ctx {
 static grbk_status ensure_tmp(grbk_ctx* c, size_t bytes)
 {
     if (c->tmp_bytes >= bytes) return GRBK_OK;
-    if (c->tmp) dev_free(c->tmp);
+    if (c->tmp) {  // queued copies may still use the old block
+        cudaStreamSynchronize(c->stream);
+        dev_free(c->tmp);
+    }
     c->tmp = nullptr;
     c->tmp_bytes = 0;
     if (dev_alloc(&c->tmp, bytes) != cudaSuccess) return GRBK_ENOMEM;
