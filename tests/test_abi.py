@@ -69,3 +69,20 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(g, "_lib", None)
     with pytest.raises(RuntimeError):
         g.lib()
+
+
+def test_option_marshalling_without_gpu(built):
+    """The binding's keyword options land in the grbk_opts fields the header
+    declares, and the library's defaults are the documented ones."""
+    o = g.grbk_default_opts()
+    assert (o.precision, o.refresh_T, o.alpha, o.stop_kind, o.split_terms) == (g.GRBK_F64, 0, 0.0, 0, 2)
+    assert (o.use_gram, o.form, o.rank_tol, o.band_limit) == (0, g.GRBK_FORM_FULL, 0.0, 0)
+    o, keep = g._make_opts(None, precision="f32", refresh_T=64, split_terms=3, use_gram=False, form="rowspace",
+                           rank_tol=1e-9, band_limit=-1, stop_kind="relres", check_every=128, grid_ctas=7,
+                           trace_len=5)
+    assert (o.precision, o.refresh_T, o.split_terms, o.use_gram) == (g.GRBK_F32, 64, 3, -1)
+    assert (o.form, o.rank_tol, o.band_limit) == (g.GRBK_FORM_ROWSPACE, 1e-9, -1)
+    assert (o.stop_kind, o.check_every, o.grid_ctas, o.trace_len) == (g.GRBK_STOP_RELRES, 128, 7, 5)
+    assert keep.rows.shape == (5,) and keep.S.shape == (5,)
+    o2, _ = g._make_opts(None, use_gram=True)
+    assert o2.use_gram == 1
