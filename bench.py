@@ -470,7 +470,7 @@ def time_to_target(args):
 def warmstart_bench(args):
     """Learned warm start on batched colour-image restoration: generate
     train-images seeded images (train-side^2, 3 channels each), restore every
-    channel with ME-GRBK (theta 0.8) to the discrepancy stop, train the U-Net
+    channel with ME-GRBK (theta fixed at 1/2) to the discrepancy stop, train the U-Net
     (width 20) on (blurred channel, restoration) pairs, then restore
     eval-images held-out eval-side^2 RGB images (seeds disjoint from training)
     from X0 = 0 and from X0 = U-Net(C): iterations, device time, PSNR."""
@@ -493,7 +493,7 @@ def warmstart_bench(args):
         gen_s += time.perf_counter() - t0
         t0 = time.perf_counter()
         Xr, res = ws.restore([q["A"] for q in sy], [q["B"] for q in sy], [q["C"] for q in sy],
-                             [np.linalg.norm(q["E"]) for q in sy], theta=0.8, seed=c0)
+                             [np.linalg.norm(q["E"]) for q in sy], seed=c0)
         solve_s += time.perf_counter() - t0
         n_iters_train += sum(r["iters"] for r in res)
         Cs_t.append(torch.tensor(np.stack([q["C"] for q in sy]), dtype=torch.float32, device=dev))
@@ -525,7 +525,7 @@ def warmstart_bench(args):
         targets = ws.DISCREPANCY_TAU * np.asarray(nn_)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        st, res = g.grbk_batch_solve(b, "grbk", theta=0.8, X0s=X0s, targets=targets, maxit=5_000_000, seed=7,
+        st, res = g.grbk_batch_solve(b, "grbk", X0s=X0s, targets=targets, maxit=5_000_000, seed=7,
                                      X_outs=X)
         el = time.perf_counter() - t0
         return X, res, el
@@ -557,7 +557,7 @@ def warmstart_bench(args):
 def batch_bench(args):
     """Batched colour-image restoration: batch-images seeded RGB images of uneven
     sides in [128, 512] (3 systems each), all solved in one persistent launch
-    with ME-GRBK (theta 0.8) to the discrepancy stop ||R_s|| <= 1.05 ||E_s||
+    with ME-GRBK (theta fixed at 1/2) to the discrepancy stop ||R_s|| <= 1.05 ||E_s||
     (or batch-maxit iterations).  Reports aggregate iterations per second."""
     import torch
     import paper_2408_05444_gb300 as g
@@ -568,10 +568,10 @@ def batch_bench(args):
     targets = ws.DISCREPANCY_TAU * np.array([np.linalg.norm(q["E"]) for q in sy])
     b = g.grbk_batch_create(As, Bs, Cs)
     X = [np.zeros((A.shape[1], B.shape[0])) for A, B in zip(As, Bs)]
-    g.grbk_batch_solve(b, "grbk", theta=0.8, targets=targets, maxit=min(args.batch_maxit, 64), seed=1, X_outs=X)
+    g.grbk_batch_solve(b, "grbk", targets=targets, maxit=min(args.batch_maxit, 64), seed=1, X_outs=X)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    st, res = g.grbk_batch_solve(b, "grbk", theta=0.8, targets=targets, maxit=args.batch_maxit, seed=1, X_outs=X)
+    st, res = g.grbk_batch_solve(b, "grbk", targets=targets, maxit=args.batch_maxit, seed=1, X_outs=X)
     el = time.perf_counter() - t0
     its = np.array([r["iters"] for r in res])
     work = np.array([A.shape[0] * B.shape[1] for A, B in zip(As, Bs)])

@@ -34,7 +34,8 @@ def init_params(width: int, seed: int = 0) -> np.ndarray:
 
 def restore(As, Bs, Cs, noise_norms, variant="grbk", theta=0.8, maxit=2_000_000, seed=0, X0s=None):
     """Batched solve of every system to the discrepancy stop ||R_s|| <= 1.05 ||E_s||;
-    returns (X list, result list)."""
+    returns (X list, result list).  theta is the relaxation of variant "rgrbk"
+    (0.8 is the paper's image setting, Section 6); ME-GRBK fixes it at 1/2."""
     b = grbk_batch_create(As, Bs, Cs)
     Xs = [np.zeros((A.shape[1], B.shape[0])) for A, B in zip(As, Bs)]
     targets = DISCREPANCY_TAU * np.asarray(noise_norms, dtype=np.float64)
