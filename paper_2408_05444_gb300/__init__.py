@@ -139,19 +139,62 @@ def _is_torch(x):
     return type(x).__module__.startswith("torch")
 
 
-def mat(x) -> grbk_mat:
-    """Describe a 2-D numpy array or torch tensor (row-major, unit column stride)."""
+def mat(x, out=False) -> grbk_mat:
+    """Describe a 2-D FP32 or FP64 numpy array or torch tensor for the C ABI.
+
+    The library trusts a descriptor (pointer, rows, cols, row stride), so
+    everything it cannot express is refused here, before a pointer leaves
+    Python: other ranks or dtypes, a column stride other than 1, a row stride
+    below the column count (flipped views, broadcast or expanded rows), and,
+    for an output (out=True), a read-only numpy array."""
     if _is_torch(x):
         import torch
-        assert x.dim() == 2 and (x.stride(1) == 1 or x.shape[1] <= 1), "need unit column stride"
-        assert x.dtype in (torch.float64, torch.float32)
-        return grbk_mat(x.data_ptr(), x.shape[0], x.shape[1], max(x.stride(0), x.shape[1]),
-                        GRBK_DT_F64 if x.dtype == torch.float64 else GRBK_DT_F32, 1 if x.is_cuda else 0)
-    a = x
-    assert isinstance(a, np.ndarray) and a.ndim == 2 and a.dtype in (np.float64, np.float32)
-    assert a.flags["C_CONTIGUOUS"] or a.strides[1] == a.itemsize, "need unit column stride"
-    return grbk_mat(a.ctypes.data, a.shape[0], a.shape[1], max(a.strides[0] // a.itemsize, a.shape[1]),
-                    GRBK_DT_F64 if a.dtype == np.float64 else GRBK_DT_F32, 0)
+        if x.dim() != 2:
+            raise ValueError(f"need a 2-D tensor, got {x.dim()}-D")
+        if x.dtype not in (torch.float64, torch.float32):
+            raise TypeError(f"need a float32 or float64 tensor, got {x.dtype}")
+        rows, cols = x.shape
+        rs, cs = x.stride()
+        ptr, f64, dev = x.data_ptr(), x.dtype == torch.float64, 1 if x.is_cuda else 0
+    elif isinstance(x, np.ndarray):
+        if x.ndim != 2:
+            raise ValueError(f"need a 2-D array, got {x.ndim}-D")
+        if x.dtype not in (np.dtype(np.float64), np.dtype(np.float32)):
+            raise TypeError(f"need a native float32 or float64 array, got {x.dtype}")
+        if out and not x.flags.writeable:
+            raise ValueError("output array is read-only")
+        rows, cols = x.shape
+        it = x.itemsize
+        if x.strides[0] % it or x.strides[1] % it:
+            raise ValueError("strides are not whole elements")
+        rs, cs = x.strides[0] // it, x.strides[1] // it
+        ptr, f64, dev = x.ctypes.data, x.dtype == np.float64, 0
+    else:
+        raise TypeError(f"need a numpy array or a torch tensor, got {type(x).__name__}")
+    if cols > 1 and cs != 1:
+        raise ValueError("need unit column stride (row-major rows)")
+    if rows > 1 and rs < cols:
+        raise ValueError(f"row stride {rs} is below the column count {cols} (flipped, broadcast or expanded rows)")
+    ld = rs if rows > 1 else cols
+    return grbk_mat(ptr, rows, cols, max(ld, cols), GRBK_DT_F64 if f64 else GRBK_DT_F32, dev)
+
+
+def _stream_ptr(stream):
+    return 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def _cuda_f32_tensor(t, name, ndim):
+    """Pointer of a contiguous FP32 CUDA tensor of rank ndim (raises otherwise)."""
+    if not _is_torch(t):
+        raise TypeError(f"{name}: need a torch tensor, got {type(t).__name__}")
+    import torch
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name}: need float32, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: need a CUDA tensor")
+    if t.dim() != ndim or not t.is_contiguous():
+        raise ValueError(f"{name}: need a contiguous {ndim}-D tensor, got shape {tuple(t.shape)}")
+    return t.data_ptr()
 
 
 def grbk_strerror(status: int) -> str:
@@ -256,7 +299,7 @@ def grbk_solve(ctx: Context, variant, theta=0.5, X0=None, tol=0.0, maxit=1000, s
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     res = grbk_result()
     m0 = mat(X0) if X0 is not None else None
-    mo = mat(X_out) if X_out is not None else None
+    mo = mat(X_out, out=True) if X_out is not None else None
     st = lib().grbk_solve(ctx.handle, v, float(theta), ctypes.byref(m0) if m0 is not None else None, float(tol),
                           int(maxit), int(seed), ctypes.byref(mo) if mo is not None else None, ctypes.byref(res))
     if st not in (GRBK_OK, GRBK_ENOTCONV):
@@ -265,24 +308,36 @@ def grbk_solve(ctx: Context, variant, theta=0.5, X0=None, tol=0.0, maxit=1000, s
 
 
 def grbk_residual(ctx: Context, X, R_out):
-    mx, mr = mat(X), mat(R_out)
+    mx, mr = mat(X), mat(R_out, out=True)
     st = lib().grbk_residual(ctx.handle, ctypes.byref(mx), ctypes.byref(mr))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_residual")
 
 
 def grbk_get_residual(ctx: Context, R_out):
-    mr = mat(R_out)
+    mr = mat(R_out, out=True)
     st = lib().grbk_get_residual(ctx.handle, ctypes.byref(mr))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_get_residual")
 
 
 def grbk_get_rownorms(ctx: Context, s_out):
+    """s_out <- s_i = ||R_i||^2 (i < m): a contiguous FP64 array or tensor
+    (host or CUDA) with at least m entries."""
+    m = grbk_info(ctx)[0][0]
     if _is_torch(s_out):
-        st = lib().grbk_get_rownorms(ctx.handle, s_out.data_ptr(), 1 if s_out.is_cuda else 0)
+        import torch
+        if s_out.dtype != torch.float64 or not s_out.is_contiguous() or s_out.numel() < m:
+            raise ValueError(f"s_out: need a contiguous float64 tensor of at least {m} entries")
+        ptr, dev = s_out.data_ptr(), 1 if s_out.is_cuda else 0
+    elif isinstance(s_out, np.ndarray):
+        if (s_out.dtype != np.float64 or not s_out.flags.c_contiguous or not s_out.flags.writeable
+                or s_out.size < m):
+            raise ValueError(f"s_out: need a writable contiguous float64 array of at least {m} entries")
+        ptr, dev = s_out.ctypes.data, 0
     else:
-        st = lib().grbk_get_rownorms(ctx.handle, s_out.ctypes.data, 0)
+        raise TypeError(f"s_out: need a numpy array or a torch tensor, got {type(s_out).__name__}")
+    st = lib().grbk_get_rownorms(ctx.handle, ptr, dev)
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_get_rownorms")
 
@@ -335,10 +390,10 @@ class Batch:
             self.handle = None
 
 
-def _mat_array(xs):
+def _mat_array(xs, out=False):
     arr = (grbk_mat * len(xs))()
     for i, x in enumerate(xs):
-        arr[i] = mat(x)
+        arr[i] = mat(x, out=out)
     return arr
 
 
@@ -372,7 +427,7 @@ def grbk_batch_solve(batch: Batch, variant, theta=0.5, X0s=None, tol=0.0, target
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     n = len(X_outs) if X_outs is not None else (len(X0s) if X0s is not None else None)
     x0 = _mat_array(X0s) if X0s is not None else None
-    xo = _mat_array(X_outs) if X_outs is not None else None
+    xo = _mat_array(X_outs, out=True) if X_outs is not None else None
     tg = None
     if targets is not None:
         tgt = np.ascontiguousarray(targets, dtype=np.float64)
@@ -395,19 +450,20 @@ def grbk_batch_destroy(batch: Batch):
 
 def grbk_solve_small_noalloc(A, B, C, X_out, variant="grbk", theta=0.5, alpha=0.0, tol=0.0, maxit=1000, seed=0,
                              stream=None):
-    """grbk_solve_small_noalloc -> (status, iters, relres).  A, B, C, X_out are
-    contiguous FP32 CUDA tensors; nothing is allocated by the library."""
-    for t in (A, B, C, X_out):
-        assert _is_torch(t) and t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4
-    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    """grbk_solve_small_noalloc -> (status, iters, relres).  A (m x p), B (q x n),
+    C (m x n) and X_out (p x q) are contiguous FP32 CUDA tensors; nothing is
+    allocated by the library."""
+    ptrs = [_cuda_f32_tensor(t, name, 2) for t, name in ((A, "A"), (B, "B"), (C, "C"), (X_out, "X_out"))]
     m, p = A.shape
     q, n = B.shape
+    if tuple(C.shape) != (m, n) or tuple(X_out.shape) != (p, q):
+        raise ValueError(f"need C {m}x{n} and X_out {p}x{q}, got {tuple(C.shape)} and {tuple(X_out.shape)}")
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     it = ctypes.c_int64(0)
     rr = ctypes.c_double(0.0)
-    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    st = lib().grbk_solve_small_noalloc(A.data_ptr(), B.data_ptr(), C.data_ptr(), m, p, q, n, v, float(theta),
-                                        float(alpha), float(tol), int(maxit), int(seed), X_out.data_ptr(),
-                                        ctypes.byref(it), ctypes.byref(rr), sp)
+    st = lib().grbk_solve_small_noalloc(ptrs[0], ptrs[1], ptrs[2], m, p, q, n, v, float(theta), float(alpha),
+                                        float(tol), int(maxit), int(seed), ptrs[3], ctypes.byref(it),
+                                        ctypes.byref(rr), _stream_ptr(stream))
     return st, it.value, rr.value
 
 
@@ -428,15 +484,9 @@ class UNetHandle:
             self.handle = None
 
 
-def _cuda_f32(t):
-    assert _is_torch(t) and t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4 and t.dim() == 3
-    return t.data_ptr()
-
-
 def grbk_unet_create(width=20, stream=None) -> UNetHandle:
     h = ctypes.c_void_p()
-    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    st = lib().grbk_unet_create(ctypes.byref(h), int(width), sp)
+    st = lib().grbk_unet_create(ctypes.byref(h), int(width), _stream_ptr(stream))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_create")
     return UNetHandle(h.value, width)
@@ -447,10 +497,18 @@ def grbk_unet_num_params(net: UNetHandle) -> int:
 
 
 def grbk_unet_set_params(net: UNetHandle, params):
+    """params: the network's flat FP32 parameter vector (grbk_unet_num_params
+    entries), a host array or a host or CUDA tensor."""
+    npar = grbk_unet_num_params(net)
     if _is_torch(params):
+        import torch
+        if params.dtype != torch.float32 or not params.is_contiguous() or params.numel() != npar:
+            raise ValueError(f"params: need a contiguous float32 tensor of {npar} entries")
         st = lib().grbk_unet_set_params(net.handle, params.data_ptr(), 1 if params.is_cuda else 0)
     else:
         a = np.ascontiguousarray(params, dtype=np.float32)
+        if a.size != npar:
+            raise ValueError(f"params: need {npar} entries, got {a.size}")
         st = lib().grbk_unet_set_params(net.handle, a.ctypes.data, 0)
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_set_params")
@@ -464,19 +522,28 @@ def grbk_unet_get_params(net: UNetHandle) -> np.ndarray:
     return out
 
 
+def _same_shape(C, T, name):
+    if tuple(T.shape) != tuple(C.shape):
+        raise ValueError(f"{name}: need shape {tuple(C.shape)}, got {tuple(T.shape)}")
+
+
 def grbk_unet_forward(net: UNetHandle, C, X0):
     """C, X0: contiguous FP32 CUDA tensors [n, h, w]."""
+    pc, px = _cuda_f32_tensor(C, "C", 3), _cuda_f32_tensor(X0, "X0", 3)
+    _same_shape(C, X0, "X0")
     n, h, w = C.shape
-    st = lib().grbk_unet_forward(net.handle, _cuda_f32(C), n, h, w, _cuda_f32(X0))
+    st = lib().grbk_unet_forward(net.handle, pc, n, h, w, px)
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_forward")
 
 
 def grbk_unet_loss_grad(net: UNetHandle, C, T, want_grad=True):
+    pc, pt = _cuda_f32_tensor(C, "C", 3), _cuda_f32_tensor(T, "T", 3)
+    _same_shape(C, T, "T")
     n, h, w = C.shape
     loss = ctypes.c_double(0.0)
     g = np.zeros(grbk_unet_num_params(net), dtype=np.float32) if want_grad else None
-    st = lib().grbk_unet_loss_grad(net.handle, _cuda_f32(C), _cuda_f32(T), n, h, w, ctypes.byref(loss),
+    st = lib().grbk_unet_loss_grad(net.handle, pc, pt, n, h, w, ctypes.byref(loss),
                                    g.ctypes.data if g is not None else None, 0)
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_loss_grad")
@@ -484,9 +551,11 @@ def grbk_unet_loss_grad(net: UNetHandle, C, T, want_grad=True):
 
 
 def grbk_unet_train_step(net: UNetHandle, C, T, lr) -> float:
+    pc, pt = _cuda_f32_tensor(C, "C", 3), _cuda_f32_tensor(T, "T", 3)
+    _same_shape(C, T, "T")
     n, h, w = C.shape
     loss = ctypes.c_double(0.0)
-    st = lib().grbk_unet_train_step(net.handle, _cuda_f32(C), _cuda_f32(T), n, h, w, float(lr), ctypes.byref(loss))
+    st = lib().grbk_unet_train_step(net.handle, pc, pt, n, h, w, float(lr), ctypes.byref(loss))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_train_step")
     return loss.value
@@ -500,5 +569,4 @@ def grbk_unet_destroy(net: UNetHandle):
 
 def grbk_barrier_selftest(absent_cta=-1, stream=None) -> int:
     """Status of one bounded grid barrier; absent_cta >= 0 leaves that CTA out."""
-    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    return int(lib().grbk_barrier_selftest(int(absent_cta), sp))
+    return int(lib().grbk_barrier_selftest(int(absent_cta), _stream_ptr(stream)))

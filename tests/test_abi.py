@@ -86,3 +86,57 @@ def test_option_marshalling_without_gpu(built):
     assert keep.rows.shape == (5,) and keep.S.shape == (5,)
     o2, _ = g._make_opts(None, use_gram=True)
     assert o2.use_gram == 1
+
+
+def test_matrix_descriptors_are_checked_before_the_library():
+    """The library trusts (pointer, rows, cols, row stride); views it cannot
+    read in that form are refused in Python, with no library call."""
+    import numpy as np
+    import torch
+    a = np.arange(60, dtype=np.float64).reshape(6, 10)
+    d = g.mat(a)
+    assert (d.rows, d.cols, d.ld, d.dtype, d.on_device) == (6, 10, 10, g.GRBK_DT_F64, 0)
+    d = g.mat(a[1:, :4])  # row slice of wider rows: row stride stays 10
+    assert (d.rows, d.cols, d.ld) == (5, 4, 10) and d.ptr == a[1:].ctypes.data
+    assert g.mat(a[2:3, :]).ld == 10
+    for bad in (np.flipud(a), np.broadcast_to(a[0], (6, 10)), a.T, a[:, ::2]):
+        with pytest.raises(ValueError):
+            g.mat(bad)
+    with pytest.raises(TypeError):
+        g.mat(a.astype(np.int32))
+    with pytest.raises(TypeError):
+        g.mat(a.astype(">f8"))
+    with pytest.raises(ValueError):
+        g.mat(a[0])
+    ro = a.copy()
+    ro.flags.writeable = False
+    g.mat(ro)
+    with pytest.raises(ValueError):
+        g.mat(ro, out=True)
+    with pytest.raises(TypeError):
+        g.mat(a.tolist())
+    t = torch.zeros(4, 6, dtype=torch.float32)
+    d = g.mat(t)
+    assert (d.rows, d.cols, d.ld, d.dtype) == (4, 6, 6, g.GRBK_DT_F32)
+    assert g.mat(torch.zeros(4, 9)[:, :6]).ld == 9
+    for bad in (torch.zeros(1, 6).expand(4, 6), torch.zeros(6, 4).t(), torch.zeros(4, 6, 2)):
+        with pytest.raises(ValueError):
+            g.mat(bad)
+    with pytest.raises(TypeError):
+        g.mat(torch.zeros(4, 6, dtype=torch.int32))
+
+
+def test_device_only_entry_points_check_their_tensors():
+    """The no-allocation solver and the U-Net entry points take contiguous FP32
+    CUDA tensors of matching shapes; anything else is refused in Python."""
+    import torch
+    A, B, C, X = torch.zeros(8, 4), torch.zeros(3, 5), torch.zeros(8, 5), torch.zeros(4, 3)
+    with pytest.raises(ValueError):  # host tensors
+        g.grbk_solve_small_noalloc(A, B, C, X)
+    with pytest.raises(TypeError):
+        g.grbk_solve_small_noalloc(A.double(), B, C, X)
+    net = g.UNetHandle(None, 4)
+    with pytest.raises(ValueError):
+        g.grbk_unet_forward(net, torch.zeros(2, 16, 16), torch.zeros(2, 16, 16))
+    with pytest.raises(TypeError):
+        g.grbk_unet_train_step(net, torch.zeros(2, 16, 16, dtype=torch.int32), torch.zeros(2, 16, 16), 1e-3)
