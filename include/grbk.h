@@ -192,6 +192,10 @@ void grbk_destroy(grbk_ctx* ctx);
  * discrepancy rule via grbk_batch_solve's `targets`.  opts->row_trace, when
  * set, must hold nsys * trace_len entries: system s writes its first
  * trace_len selected rows at row_trace[s * trace_len + k] (s_trace unused).
+ * Every side m, p, q, n of a system is at most 1024 (larger systems belong to
+ * grbk_create).  Errors: EINVAL (nsys <= 0, NULL pointers, C_s not m x n, a
+ * side outside [1, 1024], a row stride below the column count, a dtype other
+ * than F32/F64), ENOMEM, ECUDA.
  */
 grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
                               const grbk_mat* C, const grbk_opts* opts);
@@ -204,7 +208,9 @@ grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A,
  * absolute residual targets ||R_s||_F <= targets[s] (discrepancy principle);
  * when given they replace tol.  X_outs: nsys caller matrices (written).
  * results: NULL or nsys entries.  Returns OK when every system stopped by its
- * rule, ENOTCONV when some reached maxit.
+ * rule, ENOTCONV when some reached maxit; EINVAL for a bad variant, theta or
+ * maxit, or an X0s / X_outs entry that is not p_s x q_s with row stride >= q_s
+ * and dtype F32/F64.
  */
 grbk_status grbk_batch_solve(grbk_batch* batch, int32_t variant, double theta, const grbk_mat* X0s,
                              double tol, const double* targets, int64_t maxit, uint64_t seed,

@@ -761,6 +761,14 @@ struct BatchLoader {
     ~BatchLoader() { finish(); }
 };
 
+static bool dtype_ok(int32_t dt) { return dt == GRBK_DT_F64 || dt == GRBK_DT_F32; }
+
+// an X^0 or X output descriptor the copies can follow: p x q, row stride >= q, FP32 or FP64
+static bool x_desc_ok(const grbk_mat& M, int p, int q)
+{
+    return M.ptr && M.rows == p && M.cols == q && M.ld >= q && dtype_ok(M.dtype);
+}
+
 extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
                                          const grbk_mat* C, const grbk_opts* opts)
 {
@@ -774,6 +782,7 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
         if (m <= 0 || p <= 0 || q <= 0 || n <= 0 || C[s].rows != m || C[s].cols != n) return GRBK_EINVAL;
         if (m > kMaxSide || p > kMaxSide || q > kMaxSide || n > kMaxSide) return GRBK_EINVAL;
         if (A[s].ld < p || B[s].ld < n || C[s].ld < n) return GRBK_EINVAL;
+        if (!dtype_ok(A[s].dtype) || !dtype_ok(B[s].dtype) || !dtype_ok(C[s].dtype)) return GRBK_EINVAL;
     }
     grbk_batch* b = new grbk_batch();
     b->nsys = nsys;
@@ -901,8 +910,8 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     cudaStream_t st = b->stream;
     for (int s = 0; s < b->nsys; ++s) {
         SysDesc& d = b->hsys[s];
-        if (X0s && (X0s[s].rows != d.p || X0s[s].cols != d.q || !X0s[s].ptr)) return GRBK_EINVAL;
-        if (X_outs && (X_outs[s].rows != d.p || X_outs[s].cols != d.q || !X_outs[s].ptr)) return GRBK_EINVAL;
+        if (X0s && !x_desc_ok(X0s[s], d.p, d.q)) return GRBK_EINVAL;
+        if (X_outs && !x_desc_ok(X_outs[s], d.p, d.q)) return GRBK_EINVAL;
         if (targets) d.stop_S = targets[s] * targets[s];
         else if (b->opts.stop_kind == GRBK_STOP_RELRES) d.stop_S = tol * tol * b->normC2[s];
         else d.stop_S = -1.0;
