@@ -143,6 +143,13 @@ def gen_inputs(wl):
     return A, B, C, Xs
 
 
+def workload_label(wl, T):
+    """config.workload of both arms: the timed system and the form the native arm runs."""
+    d = WORKLOADS[wl]
+    return (f"{wl}: A {d['m']}x{d['p']}, B {d['q']}x{d['n']} N(0,1/cols), X* N(0,1), C = A X* B; "
+            f"chosen form FP32 + split-BF16 refresh every {T}")
+
+
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None when the
     kernel's sources changed since the counters were taken."""
@@ -210,7 +217,7 @@ def reference_arm(args):
     oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=0, mode=oracle.MODE_FACTORED, trace=False)
     t_setup = time.perf_counter() - t0
     n_it = 10
-    d, full = WORKLOADS["precision_slice"], WORKLOADS["precision"]
+    d, full = WORKLOADS["precision_slice"], WORKLOADS[args.workload]
     work = lambda w: w["m"] * w["n"] + w["m"] * w["p"] + 2 * w["q"] * w["n"] + w["p"] * w["q"]
     scale = work(d) / work(full)
     for _ in range(args.warmup):
@@ -225,8 +232,9 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "precision: A 20000x2000, B 2000x20000 N(0,1/cols), "
-                                                        "C = A X* B", "sample": "2000x200/200x2000 slice"},
+            "data": "synthetic", "config": {"workload": workload_label(args.workload, args.iters_per_step),
+                                            "iters_per_step": args.iters_per_step, "variant": "ME-GRBK",
+                                            "sample": "2000x200/200x2000 slice"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{n_it} ME-GRBK iterations per step on the 2000x200/200x2000 slice, "
                                        f"scaled by the per-iteration element work ratio {scale:.4g}"},
@@ -387,8 +395,7 @@ def native_arm(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{wl}: A {m}x{p}, B {q}x{n} N(0,1/cols), X* N(0,1), C = A X* B; "
-                                   f"chosen form FP32 + split-BF16 refresh every {T}",
+            "config": {"workload": workload_label(wl, T),
                        "iters_per_step": T, "variant": "ME-GRBK", "parallelism": f"replicas{world}",
                        "split_terms": args.split_terms, "gram": bool(res["gram"]),
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},

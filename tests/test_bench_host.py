@@ -52,3 +52,22 @@ def test_recorded_traffic_follows_the_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("other_kernel") is None
     (tmp_path / "k.cu").write_bytes(b"kernel v2")
     assert bench.recorded_traffic("iterate_kernel<float>") is None
+
+
+def test_reference_arm_prints_the_contract_line():
+    """--impl reference times the oracle on the CPU and prints one JSON line on
+    the native arm's workload label, metric and unit."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=300, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["config"]["workload"] == bench.workload_label("precision", 64)
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
