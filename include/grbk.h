@@ -84,7 +84,9 @@ typedef struct {
 typedef struct {
     int32_t precision;    /* grbk_precision */
     int32_t refresh_T;    /* recompute R = C - A X B every refresh_T iterations; 0 = never */
-    double alpha;         /* step; <= 0 selects 1/||B||_2^2 (power iteration on B B^T) */
+    double alpha;         /* step; <= 0 selects 1/||B||_2^2 estimated on the device (grbk_create: largest
+                             Ritz value of up to 40 Lanczos steps on B B^T; batched solvers: power
+                             iteration per system) */
     int32_t stop_kind;    /* grbk_stop */
     int32_t split_terms;  /* F32 refresh: 2 (hi+lo, default) or 3 (hi+mid+lo) BF16 terms; 0 = 2 */
     const grbk_mat* x_ref;/* reference solution for GRBK_STOP_RSE and result.rse; may be NULL */
