@@ -134,7 +134,7 @@ void grbk_default_opts(grbk_opts* opts);
  * Copies A (m x p), B (q x n), C (m x n) into library-owned device memory in
  * the precision of opts->precision; the caller may free its buffers at once.
  * Computes ||A_i||^2, ||A||_F^2, ||C||_F^2 and alpha (Section 5 uses
- * alpha = 1/||B||_2^2; Lemma 2.2 and Theorems 4.2-4.6 need 0 < alpha < 2/||B||_2^2).
+ * alpha = 1/||B||_2^2; Lemma 2.2 and Theorems 4.2, 4.5, 4.8 need 0 < alpha < 2/||B||_2^2).
  * Errors: EINVAL (NULL pointers, shape mismatch, m == 0, explicit alpha not in
  * (0, 2/||B||_2^2), non-finite input -> ENONFINITE), ENOMEM, ECUDA.
  */

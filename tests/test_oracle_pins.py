@@ -5,8 +5,9 @@ paper proves, a library routine, a hand-built case or brute-force statistics.
 Paper references: Eq. (2.2) least-norm solution and the full-rank formulas of
 Section 2; Lemma 3.2 / Eq. (3.1) invariant; Theorem 3.3 ME-BK limit;
 Eqs. (3.4)-(3.6) per-step error identity; Remark 4.1 non-empty admitted set;
-Remark 4.4 theta = 1/2; Theorem 4.6 / Eq. (4.18) MWRBK contraction;
-Lemma 2.2 / Eq. (2.3) and Theorem 4.2 / Eq. (4.3) expected-rate bounds;
+Remark 4.4 theta = 1/2; Theorem 4.8 / Eq. (4.18) MWRBK contraction;
+Lemma 2.2 / Eq. (2.3), Theorem 4.2 / Eq. (4.3) and Theorem 4.5 / Eqs. (4.13),
+(4.15) expected-rate bounds;
 Algorithms 1-5 for the selection rules.
 """
 import numpy as np
@@ -153,7 +154,7 @@ def test_per_step_error_identity():
 
 
 def test_mwrbk_contraction():
-    """Theorem 4.6 / Eq. (4.18): every ME-MWRBK step contracts the error by at
+    """Theorem 4.8 / Eq. (4.18): every ME-MWRBK step contracts the error by at
     least 1 - (2 alpha - alpha^2 ||B||_2^2) sigma_min^2(A) sigma_min^2(B) / gamma_k."""
     A, B, C, _ = workloads.gaussian(25, 6, 5, 18, seed=5)
     Xs = pinv(A) @ C @ pinv(B)
@@ -309,6 +310,60 @@ def test_expected_rate_bounds():
                                       mode=oracle.MODE_FACTORED)["err2"] for sd in range(200)])
         mean = errs.mean(axis=0)
         assert np.all(mean <= bound * mean[0] * (1 + 1e-9))
+
+
+def _rate_constants(A, B, alpha):
+    sa = np.linalg.svd(A, compute_uv=False)[-1]
+    sb = np.linalg.svd(B, compute_uv=False)[-1]
+    nb2 = np.linalg.norm(B, 2) ** 2
+    FA = np.sum(A * A)
+    # kappa_{F,2}^2(B^T (x) A) = ||A||_F^2 ||B||_F^2 / (sigma_min(A) sigma_min(B))^2, so
+    # rho_0 = 1 - (2 alpha - alpha^2 ||B||_2^2) ||B||_F^2 / kappa^2 = 1 - (...) sigma^2 sigma^2 / ||A||_F^2
+    return 1 - (2 * alpha - alpha ** 2 * nb2) * sa ** 2 * sb ** 2 / FA
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_rgrbk_first_step_expectation_exact(theta):
+    """Theorem 4.5 / Eq. (4.13) for ME-RGRBK, with the expectation taken
+    exactly: the oracle's X^1 for every row it picks (seeds 0..599), weighted by
+    Algorithm 4's probabilities s_i / S_J over the admitted set built here from
+    R^0 = C; every admitted row must occur, no other row may, and the expected
+    error must not exceed rho_0 ||X^0 - X_*||^2."""
+    A, B, C, _ = workloads.gaussian(12, 4, 3, 10, seed=21)
+    Xs = pinv(A) @ C @ pinv(B)
+    alpha = _alpha(B)
+    a = np.sum(A * A, axis=1)
+    s = np.sum(C * C, axis=1)
+    r = s / a
+    t = min(theta * r.max() + (1 - theta) * s.sum() / a.sum(), r.max())
+    J = np.nonzero(r >= t)[0]
+    X1 = {}
+    for sd in range(600):
+        out = oracle.solve(A, B, C, "rgrbk", theta=theta, alpha=alpha, seed=sd, maxit=1)
+        X1.setdefault(int(out["rows"][0]), out["X"])
+    assert sorted(X1) == sorted(int(i) for i in J)
+    E = sum(s[i] / s[J].sum() * np.sum((X1[int(i)] - Xs) ** 2) for i in J)
+    assert E <= _rate_constants(A, B, alpha) * np.sum(Xs ** 2)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.8])
+def test_rgrbk_expected_rate_bound(theta):
+    """Theorem 4.5 / Eq. (4.15) for ME-RGRBK: every factor rho_{l,theta} is at
+    most rho_0 (Remark 4.6; equal to it while no residual row vanishes, when
+    phi_l = ||B||_F^2), so the mean of ||X^k - X_*||^2 over 200 seeds stays
+    below rho_0^k ||X^0 - X_*||^2."""
+    A, B, C, _ = workloads.gaussian(16, 5, 4, 12, seed=9)
+    Xs = pinv(A) @ C @ pinv(B)
+    alpha = _alpha(B)
+    rho = _rate_constants(A, B, alpha)
+    K = 60
+    errs = []
+    for sd in range(200):
+        out = oracle.solve(A, B, C, "rgrbk", theta=theta, alpha=alpha, seed=sd, maxit=K, Xref=Xs,
+                           mode=oracle.MODE_FACTORED)
+        errs.append(out["err2"])
+    mean = np.mean(errs, axis=0)
+    assert np.all(mean <= rho ** np.arange(K + 1) * mean[0] * (1 + 1e-9))
 
 
 def test_greedy_needs_fewer_iterations_than_rbk_loose():
