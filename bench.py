@@ -12,9 +12,14 @@ the whole hot path (select, W/U, V, fused residual pass) plus one refresh of
 R = C - A X B and the stop check.  R (1.6 GB) is far larger than L2, so no
 flush is needed between steps.
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the 2000x200 / 200x2000 slice of the same recipe, scaled to the full
-size by the ratio of per-iteration element work) and prints the same line.
+--impl reference times the FP64 CPU oracle (its OpenMP timing build, on every
+host core) on the same system: each step is a few ME-GRBK iterations of the
+selected workload itself, so the line needs no scaling.
+
+The default run also measures, at N = 1, time to a solution-error target
+("ttt"): the 20000x2000 / 2000x20000 system to RSE <= 1e-4 in the chosen form,
+the row-space form and the plain FP64 form, and the 200x100 / 80x150 system to
+RSE <= 1e-6 in FP64 (about four minutes in all; --no-ttt skips it).
 """
 from __future__ import annotations
 
@@ -59,6 +64,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-rowspace", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target legs of the default run")
+    ap.add_argument("--cpu-iters", type=int, default=20,
+                    help="oracle iterations of the full system timed for cpu_baseline")
     ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=2)
@@ -177,33 +185,46 @@ def iter_bytes(m, p, q, n, esz, gram=False, kpath=False):
     return 2 * m * n * esz + b_bytes + u_bytes + (m + n + q) * esz + 3 * m * 8
 
 
-def cpu_baseline_oracle(target_seconds=12.0):
-    """The FP64 oracle (single thread) on the 2000x200/200x2000 slice of the same
-    recipe: iterations per second, then scaled by the per-iteration element
-    work ratio to the full 20000x2000/2000x20000 size."""
+def _alpha_estimate(B, iters=30):
+    """1/||B||_2^2 from a few power iterations (the oracle's timing does not
+    depend on the step's last digits)."""
+    x = np.ones(B.shape[0]) / np.sqrt(B.shape[0])
+    lam = 1.0
+    for _ in range(iters):
+        y = B @ (B.T @ x)
+        lam = float(x @ y)
+        x = y / np.linalg.norm(y)
+    return 1.0 / lam
+
+
+def _oracle_rate(A, B, C, alpha, n_it, omp):
+    """Iterations per second of the FP64 oracle (FACTORED mode: the rank-1
+    update with A A_i^T and (R_i B^T) B formed per iteration) on this system,
+    from the oracle's own clock around its iteration loop (set-up excluded)."""
     import oracle
-    d = WORKLOADS["precision_slice"]
-    A, B, C, Xs = gen_inputs("precision_slice")
-    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
-    t0 = time.perf_counter()
-    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=0, mode=oracle.MODE_FACTORED, trace=False)
-    t_setup = time.perf_counter() - t0
-    n_it = 20
-    t0 = time.perf_counter()
-    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
-    per_it = max((time.perf_counter() - t0 - t_setup) / n_it, 1e-6)
-    n_it = max(20, int(target_seconds / per_it))
-    t0 = time.perf_counter()
-    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
-    el = time.perf_counter() - t0 - t_setup
-    slice_rate = n_it / el
-    full = WORKLOADS["precision"]
-    work = lambda w: w["m"] * w["n"] + w["m"] * w["p"] + 2 * w["q"] * w["n"] + w["p"] * w["q"]
-    scale = work(d) / work(full)
-    return {"value": slice_rate * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle, single thread, {n_it} ME-GRBK iterations on the 2000x200/200x2000 slice "
-                      f"in {el:.1f} s ({slice_rate:.1f} iters/s), scaled by the per-iteration element work "
-                      f"ratio {scale:.4g} to 20000x2000/2000x20000"}
+    r = oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, seed=1, mode=oracle.MODE_FACTORED, trace=False,
+                     omp=omp)
+    el = max(r["loop_seconds"], 1e-9)
+    return r["iters"] / el, el
+
+
+def cpu_baseline_oracle(A, B, C, wl, n_it):
+    """The FP64 oracle on the benchmark's own system (no slice, no scaling):
+    n_it ME-GRBK iterations on every host core (OpenMP timing build, the
+    reported value) and single-threaded (the tests' build)."""
+    import oracle
+    d = WORKLOADS[wl]
+    alpha = _alpha_estimate(B)
+    nproc = os.cpu_count() or 1
+    rate_all, el_all = _oracle_rate(A, B, C, alpha, n_it, True)
+    rate_one, el_one = _oracle_rate(A, B, C, alpha, n_it, False)
+    thr = oracle.threads(True)
+    return {"value": rate_all, "unit": UNIT, "cores": thr, "kind": "oracle", "nproc": nproc,
+            "single_thread": {"value": rate_one, "unit": UNIT, "cores": 1, "seconds": el_one},
+            "sample": f"FP64 oracle (FACTORED mode), {n_it} ME-GRBK iterations of the full {d['m']}x{d['p']} / "
+                      f"{d['q']}x{d['n']} system from X0 = 0: {el_all:.2f} s on {thr} threads (OpenMP build over "
+                      f"rows; host nproc {nproc}), {el_one:.2f} s on one thread; the oracle's set-up (R^0 = C, "
+                      f"||A_i||^2, ||C||_F) is outside its timed loop"}
 
 
 def reference_arm(args):
@@ -211,33 +232,31 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    A, B, C, Xs = gen_inputs("precision_slice")
-    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
-    t0 = time.perf_counter()
-    oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=0, mode=oracle.MODE_FACTORED, trace=False)
-    t_setup = time.perf_counter() - t0
-    n_it = 10
-    d, full = WORKLOADS["precision_slice"], WORKLOADS[args.workload]
-    work = lambda w: w["m"] * w["n"] + w["m"] * w["p"] + 2 * w["q"] * w["n"] + w["p"] * w["q"]
-    scale = work(d) / work(full)
+    A, B, C, Xs = gen_inputs(args.workload)
+    alpha = _alpha_estimate(B)
+    d = WORKLOADS[args.workload]
+    # iterations per step: about 0.3 s of the oracle's loop on every core at the full size
+    n_it = max(4, int(4 * 20000 * 20000 / (d["m"] * d["n"])))
+    run = lambda s: oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, seed=s, mode=oracle.MODE_FACTORED,
+                                 trace=False, omp=True)
     for _ in range(args.warmup):
-        oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, mode=oracle.MODE_FACTORED, trace=False)
-    times = []
-    for s in range(args.steps):
-        t0 = time.perf_counter()
-        oracle.solve(A, B, C, "grbk", alpha=alpha, maxit=n_it, seed=s, mode=oracle.MODE_FACTORED, trace=False)
-        times.append(max(time.perf_counter() - t0 - t_setup, 1e-9))
+        run(0)
+    times = [max(run(s)["loop_seconds"], 1e-9) for s in range(args.steps)]
     tot = sum(times)
-    value = args.steps * n_it / tot * scale
+    value = args.steps * n_it / tot
+    thr = oracle.threads(True)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_label(args.workload, args.iters_per_step),
-                                            "iters_per_step": args.iters_per_step, "variant": "ME-GRBK",
-                                            "sample": "2000x200/200x2000 slice"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_it} ME-GRBK iterations per step on the 2000x200/200x2000 slice, "
-                                       f"scaled by the per-iteration element work ratio {scale:.4g}"},
+                                            "iters_per_step": n_it, "variant": "ME-GRBK",
+                                            "sample": f"{n_it} iterations per step of the full system"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                             "nproc": os.cpu_count(),
+                             "sample": f"FP64 oracle (OpenMP timing build, {thr} threads, FACTORED mode), {n_it} "
+                                       f"ME-GRBK iterations per step of the {d['m']}x{d['p']} / {d['q']}x{d['n']} "
+                                       f"system itself, timed by the oracle's clock around its iteration loop "
+                                       f"(its set-up excluded)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -262,7 +281,9 @@ def native_arm(args):
     A, B, C, Xs = gen_inputs(wl)
     Ah, Bh, Ch = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory() for x in (A, B, C))
     Ad, Bd, Cd = (x.to(dev) for x in (Ah, Bh, Ch))
-    del A, B, C
+    keep_host = rank == 0 and world == 1 and not args.no_cpu_baseline
+    if not keep_host:
+        del A, B, C
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -311,8 +332,16 @@ def native_arm(args):
         barrier()
         ms64 = ev0.elapsed_time(ev1)
         km64 = r64["iter_kernel_ms"] / max(r64["iter_kernel_launches"], 1)
+        gbs64 = iter_bytes(m, p, q, n, 8, gram=bool(r64["gram"])) * T / (km64 / 1e3) / 1e9
+        # FP64 roof: two FMAs per element of R per iteration (the update and the square)
+        dfma_peak, probe_ms = g.grbk_fp64_probe(stream=stream)
+        dfma64 = 2.0 * m * n * T / (km64 / 1e3)
         plain = {"precision": "f64", "value": k64 * T / (ms64 / 1e3), "unit": UNIT,
-                 "kernel_GBs": iter_bytes(m, p, q, n, 8, gram=bool(r64["gram"])) * T / (km64 / 1e3) / 1e9,
+                 "kernel_GBs": gbs64, "kernel_frac_of_hbm": gbs64 / hbm_peak,
+                 "kernel_fp64_fma_per_s": dfma64,
+                 "fp64_fma_peak_measured": dfma_peak, "kernel_frac_of_fp64": dfma64 / dfma_peak,
+                 "fp64_probe": f"grbk_fp64_probe: 8 independent FMA chains per thread, 8 x 256-thread blocks per "
+                               f"SM, {probe_ms:.2f} ms timed launch",
                  "note": "FP64 residual pass, X0 = 0, no refresh (R^0 = C); A A^T formed at set-up (outside the timed region)"}
         g.grbk_destroy(ctx64)
         del X64
@@ -384,9 +413,15 @@ def native_arm(args):
                "note": "per step: grbk_create from pinned host A, B, C (FP32), X0 from pinned host memory, "
                        "one refresh and 64 iterations, X copied back to pinned host memory, grbk_destroy"}
 
+    clocks = clk.summary()
+    ttt = None
+    if rank == 0 and world == 1 and not args.no_ttt:
+        ttt = ttt_legs(args, g, torch, dev, stream, Ad, Bd, Cd, Xs)
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_oracle()
+    if keep_host:
+        cpu = cpu_baseline_oracle(A, B, C, wl, args.cpu_iters)
+        del A, B, C
 
     # solution error reached by the timed run (context for the metric)
     rse = float(torch.linalg.norm(Xd.cpu() - torch.from_numpy(Xs)) / np.linalg.norm(Xs))
@@ -410,8 +445,9 @@ def native_arm(args):
             "rowspace_form": rowspace,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "ttt": ttt,
             "rse_after_timed_run": rse,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "gpu_launches": int(res["launches"]),
         }
         print(json.dumps(line), flush=True)
@@ -420,57 +456,75 @@ def native_arm(args):
         dist.destroy_process_group()
 
 
+def _ttt_run(g, torch, dev, stream, A, B, C, Xs, precision, tol, maxit, refresh_T, check, split_terms,
+             form="full"):
+    """One solve from X0 = 0 to ||X - X*|| <= tol ||X*||: set-up wall time
+    (grbk_create from device buffers) and the solve's device time (CUDA events
+    on the launch stream around grbk_solve)."""
+    t0 = time.perf_counter()
+    ctx = g.grbk_create(A, B, C, precision=precision, refresh_T=refresh_T, check_every=check, stop_kind="rse",
+                        x_ref=Xs, stream=stream, split_terms=split_terms, use_gram=1, form=form)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    X = torch.zeros(Xs.shape, dtype=torch.float64, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    st, res = g.grbk_solve(ctx, "grbk", tol=tol, maxit=maxit, seed=1, X_out=X)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    g.grbk_destroy(ctx)
+    return {"precision": precision, "form": form, "tol": tol, "status": g.grbk_strerror(st),
+            "iters": res["iters"], "seconds": ev0.elapsed_time(ev1) / 1e3, "setup_s": setup_s,
+            "rse": res["rse"], "refresh_T": refresh_T}
+
+
+def ttt_legs(args, g, torch, dev, stream, Ad, Bd, Cd, Xs):
+    """Time to target in the default run: the selected system to RSE <= 1e-4
+    (chosen FP32 + split-BF16 refresh, row-space FP32, plain FP64), and the
+    200x100 / 80x150 system to RSE <= 1e-6 in FP64 (the metric's target)."""
+    Xsd = torch.from_numpy(Xs).to(dev)
+    T = args.iters_per_step
+    out = {"variant": "ME-GRBK", "stop": "||X - X*||_F <= tol ||X*||_F, tested every check_every iterations"}
+    out["chosen_f32_rse1e-4"] = _ttt_run(g, torch, dev, stream, Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, T, T,
+                                         args.split_terms)
+    out["rowspace_f32_rse1e-4"] = _ttt_run(g, torch, dev, stream, Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, T, T,
+                                           args.split_terms, form="rowspace")
+    Ad64, Bd64, Cd64 = Ad.double(), Bd.double(), Cd.double()
+    out["plain_f64_rse1e-4"] = _ttt_run(g, torch, dev, stream, Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0,
+                                        256, args.split_terms)
+    del Ad64, Bd64, Cd64
+    A1, B1, C1, X1 = workloads.config_small()
+    out["small_f64_rse1e-6"] = _ttt_run(g, torch, dev, stream, A1, B1, C1, torch.from_numpy(X1).to(dev), "f64",
+                                        1e-6, 5_000_000, 0, 4096, args.split_terms)
+    ch, pl, rs = out["chosen_f32_rse1e-4"], out["plain_f64_rse1e-4"], out["rowspace_f32_rse1e-4"]
+    out["chosen_over_plain_speedup"] = pl["seconds"] / ch["seconds"] if ch["seconds"] > 0 else None
+    out["rowspace_over_plain_speedup"] = pl["seconds"] / rs["seconds"] if rs["seconds"] > 0 else None
+    out["chosen_faster_than_plain"] = bool(ch["status"] == "ok" and pl["status"] == "ok"
+                                           and ch["seconds"] < pl["seconds"])
+    return out
+
+
 def time_to_target(args):
-    """Wall time (device events around one grbk_solve) until ||X - X*|| <= tol ||X*||
-    for the chosen form (FP32 + split-BF16 refresh every 64, tol 1e-4), the plain
-    FP64 form (tol 1e-4 and 1e-6) on the selected workload, and for the
-    200x100 / 80x150 system in FP64 (tol 1e-6)."""
+    """--mode ttt: the time-to-target legs alone, plus the row-space FP64 form
+    and (with --steps >= 2) the plain FP64 form to RSE <= 1e-6."""
     import torch
     import paper_2408_05444_gb300 as g
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
-    out = {"mode": "time_to_target", "workload": args.workload, "variant": "ME-GRBK"}
-
-    def run(A, B, C, Xs, precision, tol, maxit, refresh_T, check, form="full"):
-        t0 = time.perf_counter()
-        ctx = g.grbk_create(A, B, C, precision=precision, refresh_T=refresh_T, check_every=check,
-                            stop_kind="rse", x_ref=Xs, stream=stream, split_terms=args.split_terms, use_gram=1,
-                            form=form)
-        torch.cuda.synchronize(dev)
-        setup_s = time.perf_counter() - t0
-        X = torch.zeros(Xs.shape, dtype=torch.float64, device=dev)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        ev0.record(stream)
-        st, res = g.grbk_solve(ctx, "grbk", tol=tol, maxit=maxit, seed=1, X_out=X)
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        g.grbk_destroy(ctx)
-        return {"precision": precision, "form": form, "tol": tol, "status": g.grbk_strerror(st),
-                "iters": res["iters"], "seconds": ev0.elapsed_time(ev1) / 1e3, "setup_s": setup_s,
-                "rse": res["rse"], "refresh_T": refresh_T}
-
-    A1, B1, C1, X1 = workloads.config_small()
-    out["small_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0, 4096)
-    if not args.no_rowspace:
-        out["small_rowspace_f64_rse1e-6"] = run(A1, B1, C1, torch.from_numpy(X1).to(dev), "f64", 1e-6, 5_000_000, 0,
-                                                4096, form="rowspace")
     A, B, C, Xs = gen_inputs(args.workload)
     Ad, Bd, Cd = (torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev) for x in (A, B, C))
-    Xsd = torch.from_numpy(Xs).to(dev)
     del A, B, C
-    out["chosen_f32_rse1e-4"] = run(Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, 64, 64)
-    if not args.no_rowspace:
-        out["rowspace_f32_rse1e-4"] = run(Ad, Bd, Cd, Xsd, "f32", 1e-4, 2_000_000, 64, 64, form="rowspace")
+    out = {"mode": "time_to_target", "workload": args.workload}
+    out.update(ttt_legs(args, g, torch, dev, stream, Ad, Bd, Cd, Xs))
+    Xsd = torch.from_numpy(Xs).to(dev)
+    Ad64, Bd64, Cd64 = Ad.double(), Bd.double(), Cd.double()
+    out["rowspace_f64_rse1e-4"] = _ttt_run(g, torch, dev, stream, Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0,
+                                           256, args.split_terms, form="rowspace")
+    if args.steps >= 2:
+        out["plain_f64_rse1e-6"] = _ttt_run(g, torch, dev, stream, Ad64, Bd64, Cd64, Xsd, "f64", 1e-6, 4_000_000, 0,
+                                            256, args.split_terms)
     out["split_terms"] = args.split_terms
-    if not args.no_plain:
-        Ad64, Bd64, Cd64 = Ad.double(), Bd.double(), Cd.double()
-        out["plain_f64_rse1e-4"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0, 256)
-        if not args.no_rowspace:
-            out["rowspace_f64_rse1e-4"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-4, 2_000_000, 0, 256,
-                                              form="rowspace")
-        if args.steps >= 2:
-            out["plain_f64_rse1e-6"] = run(Ad64, Bd64, Cd64, Xsd, "f64", 1e-6, 4_000_000, 0, 256)
     print(json.dumps(out), flush=True)
 
 

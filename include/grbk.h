@@ -107,6 +107,9 @@ typedef struct {
                              bA, bB <= band_limit of the diagonal (and 4 bA + 1 < m) takes the banded path,
                              which forms w, u, v from the bands and updates only the rows within 2 bA of
                              i_k (u_i = (A A_{i_k}^T)_i vanishes elsewhere); 0 = 64, -1 = always dense */
+    const double* alphas; /* batched and sparse solvers: host array of nsys steps, one per system, each in
+                             (0, 2/||B_s||_2^2) (checked against the device estimate of ||B_s||_2^2); it
+                             replaces `alpha`.  NULL: `alpha` (when > 0) or 1/||B_s||_2^2 for every system */
 } grbk_opts;
 
 typedef struct {
@@ -228,9 +231,9 @@ void grbk_batch_destroy(grbk_batch* batch);
 /*
  * grbk_solve_small_noalloc -- one small system A X B = C in FP32 solved with no
  * device or host allocation.  The paper has no counterpart: this entry point
- * exists for callers that cannot allocate, e.g. code that runs while a CUDA
- * graph is being captured, processes whose device memory comes from a fixed
- * pool they do not own, or loops where the cost and device-wide
+ * exists for callers that cannot allocate, e.g. processes whose device memory
+ * comes from a fixed pool they do not own (a framework's caching allocator, a
+ * service with a hard memory budget), or loops where the cost and device-wide
  * synchronisation of cudaMalloc/cudaFree are not acceptable.
  *
  * It runs the batched kernel on a single system (system index 0 for the
@@ -258,7 +261,8 @@ void grbk_batch_destroy(grbk_batch* batch);
  * work overlaps on the GPU (other streams, other host threads) race on the
  * array and must be serialised by the caller.
  * Errors: EINVAL (NULL pointer, size outside [1, GRBK_NOALLOC_MAX_SIDE],
- * variant, theta, alpha), ENONFINITE (NaN/Inf input or residual), ECUDA.
+ * variant, theta, a non-finite alpha or tol, an alpha outside
+ * (0, 2/||B||_2^2)), ENONFINITE (NaN/Inf input or residual), ECUDA.
  */
 #define GRBK_NOALLOC_MAX_SIDE 512
 #define GRBK_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
@@ -313,6 +317,19 @@ void grbk_unet_destroy(grbk_unet* net);
  * stays usable.  Nothing faults or hangs in either case.
  */
 grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream);
+
+/*
+ * grbk_fp64_probe -- no counterpart in the paper: measures the FP64 fused
+ * multiply-add rate of the current device, the roof of the FP64 residual pass
+ * (two FMAs per element of R: the rank-1 update and the square of the new
+ * value; Algorithm 3's update of R and the row norms of the next iteration).
+ * Launches blocks_per_sm x (SM count) blocks of 256 threads, each thread
+ * running 8 independent FMA chains for `iters` steps; one untimed launch, then
+ * one timed with CUDA events on `stream`.  Outputs (host pointers, may be
+ * NULL): FMAs per second and the timed launch's milliseconds.
+ * Errors: EINVAL (iters <= 0, blocks_per_sm outside [1, 64]), ENOMEM, ECUDA.
+ */
+grbk_status grbk_fp64_probe(int64_t iters, int32_t blocks_per_sm, double* dfma_per_s, double* ms, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* grbk_strerror(int32_t status);

@@ -6,6 +6,10 @@ package, and this package never imports the product library.
 
 ``build()`` compiles the C file with gcc (-O2 -ffp-contract=off) into
 ``oracle/_build/libgrbk_oracle.so``; ``lib()`` loads it, building on demand.
+``build_omp()`` compiles the same source with -fopenmp into
+``libgrbk_oracle_omp.so`` for timing the oracle on every host core
+(``solve(..., omp=True)``); it computes the same bits as the single-thread
+build and no test of the oracle's values uses it.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "grbk_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_OUT_DIR, "libgrbk_oracle.so")
+_SO_OMP = os.path.join(_OUT_DIR, "libgrbk_oracle_omp.so")
 
 GRBK, RGRBK, MWRBK, RBK, BK = 0, 1, 2, 3, 4
 VARIANTS = {"grbk": GRBK, "rgrbk": RGRBK, "mwrbk": MWRBK, "rbk": RBK, "bk": BK}
@@ -30,12 +35,12 @@ _libs = {}
 _override = None
 
 
-def compile_c(src: str, so: str) -> str:
+def compile_c(src: str, so: str, openmp: bool = False) -> str:
     """gcc -O2 -ffp-contract=off a C source into a shared object (atomic rename)."""
     os.makedirs(os.path.dirname(so), exist_ok=True)
     tmp = so + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-o", tmp, src, "-lm"])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared"]
+                          + (["-fopenmp"] if openmp else []) + ["-o", tmp, src, "-lm"])
     os.replace(tmp, so)
     return so
 
@@ -44,6 +49,12 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         compile_c(_SRC, _SO)
     return _SO
+
+
+def build_omp(force: bool = False) -> str:
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC):
+        compile_c(_SRC, _SO_OMP, openmp=True)
+    return _SO_OMP
 
 
 class use_library:
@@ -63,10 +74,10 @@ class use_library:
         _override = self._prev
 
 
-def lib():
+def lib(omp: bool = False):
     # GRBK_ORACLE_SO lets the mutation test point a child process at a build of
     # a deliberately broken copy of the oracle source.
-    path = _override or os.environ.get("GRBK_ORACLE_SO") or build()
+    path = build_omp() if omp else (_override or os.environ.get("GRBK_ORACLE_SO") or build())
     if path not in _libs:
         L = ctypes.CDLL(path)
         i64, u64, dbl, vp = ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
@@ -84,6 +95,10 @@ def lib():
                                    ctypes.c_int, ctypes.c_int, dbl, vp, vp, vp, vp, vp, vp, vp,
                                    vp, vp, ctypes.POINTER(ctypes.c_int)]
         L.oracle_solve.restype = i64
+        L.oracle_last_loop_seconds.argtypes = []
+        L.oracle_last_loop_seconds.restype = dbl
+        L.oracle_threads.argtypes = []
+        L.oracle_threads.restype = ctypes.c_int
         _libs[path] = L
     return _libs[path]
 
@@ -129,10 +144,16 @@ def spectral_norm_sq(B, iters=500):
     return lib().oracle_spectral_norm_sq(B.shape[0], B.shape[1], _ptr(B), int(iters))
 
 
+def threads(omp: bool = False) -> int:
+    """Threads the oracle's row loops run on (1 for the tests' build)."""
+    return int(lib(omp).oracle_threads())
+
+
 def solve(A, B, C, variant="grbk", theta=0.5, alpha=None, X0=None, seed=0, sys=0, maxit=1000,
-          mode=MODE_GRAM, stop=STOP_NONE, tol=0.0, Xref=None, trace=True, want_R=False):
+          mode=MODE_GRAM, stop=STOP_NONE, tol=0.0, Xref=None, trace=True, want_R=False, omp=False):
     """Run the oracle; returns a dict with X, iters, status and (if trace) the
-    per-iteration traces rows, S, t, margin_adm, margin_pick, err2."""
+    per-iteration traces rows, S, t, margin_adm, margin_pick, err2.  omp=True
+    runs the OpenMP build (same results, every host core; timing only)."""
     A, B, C = map(_f64, (A, B, C))
     m, p = A.shape
     q, n = B.shape
@@ -153,11 +174,12 @@ def solve(A, B, C, variant="grbk", theta=0.5, alpha=None, X0=None, seed=0, sys=0
     R = np.empty((m, n)) if want_R else None
     s = np.empty(m) if want_R else None
     st = ctypes.c_int(0)
-    it = lib().oracle_solve(_ptr(dims), _ptr(A), _ptr(B), _ptr(C), _ptr(X), v, float(theta),
+    it = lib(omp).oracle_solve(_ptr(dims), _ptr(A), _ptr(B), _ptr(C), _ptr(X), v, float(theta),
                             float(alpha), int(seed), int(sys), int(maxit), int(mode), int(stop),
                             float(tol), _ptr(Xr), _ptr(rows), _ptr(S), _ptr(t), _ptr(madm),
                             _ptr(mpick), _ptr(err2), _ptr(R), _ptr(s), ctypes.byref(st))
-    out = dict(X=X, iters=int(it), status=int(st.value), alpha=float(alpha))
+    out = dict(X=X, iters=int(it), status=int(st.value), alpha=float(alpha),
+               loop_seconds=float(lib(omp).oracle_last_loop_seconds()))
     if trace:
         out.update(rows=rows[:it], S=S[:it], t=t[:it], margin_adm=madm[:it],
                    margin_pick=mpick[:it])

@@ -7,8 +7,13 @@
  * or constant with the CUDA library; the two only share the seeded input
  * generators.
  *
- * Everything is row-major FP64, single-threaded, with index-ascending loops.
- * Built with -ffp-contract=off so that x86-64 and aarch64 round identically.
+ * Everything is row-major FP64 with index-ascending loops.  The build the
+ * tests use is single-threaded, with -ffp-contract=off so that x86-64 and
+ * aarch64 round identically.  A second build with -fopenmp (used only to time
+ * the oracle on every host core) runs the loops marked "omp" below with their
+ * rows (or columns) split across threads: every output element is still
+ * computed by one thread in the same order, and every sum over rows (S, ||C||)
+ * stays a serial ascending loop, so both builds give the same bits.
  *
  * Notation (paper, Section 2 and Algorithms 1-5):
  *   A in R^{m x p}, B in R^{q x n}, C in R^{m x n}, X in R^{p x q};
@@ -28,6 +33,32 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Wall time of the iteration loop of the last oracle_solve call (set-up
+ * excluded), for timing the oracle; not thread-safe. */
+static double g_loop_seconds = 0.0;
+double oracle_last_loop_seconds(void) { return g_loop_seconds; }
+
+static double wall_seconds(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* Threads the "omp" loops run on: 1 in the tests' build. */
+int oracle_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x64-10 counter-based generator, written from Salmon, Moraes, Dror,
@@ -237,16 +268,18 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
     if (Xref)
         for (int64_t i = 0; i < p * q; ++i) normXref2 += Xref[i] * Xref[i];
 
+    const double t_loop = wall_seconds();
     int64_t k = 0;
     for (;; ++k) {
         /* row norms and Frobenius norm of the current residual */
-        double S = 0.0;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < m; ++i) {
             double acc = 0.0;
             for (int64_t l = 0; l < n; ++l) acc += R[i * n + l] * R[i * n + l];
             s[i] = acc;
-            S += acc;
         }
+        double S = 0.0;
+        for (int64_t i = 0; i < m; ++i) S += s[i];
         double err2 = NAN;
         if (Xref) {
             err2 = 0.0;
@@ -328,12 +361,14 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
         const double c = alpha / a[ik];
 
         /* w = R_{i_k} B^T  (1 x q) */
+#pragma omp parallel for schedule(static)
         for (int64_t j = 0; j < q; ++j) {
             double acc = 0.0;
             for (int64_t l = 0; l < n; ++l) acc += R[ik * n + l] * B[j * n + l];
             w[j] = acc;
         }
         /* X^{k+1} = X^k + c A_{i_k}^T w */
+#pragma omp parallel for schedule(static)
         for (int64_t row = 0; row < p; ++row)
             for (int64_t j = 0; j < q; ++j) X[row * q + j] += c * A[ik * p + row] * w[j];
 
@@ -349,11 +384,13 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
                 h[l] = acc;
             }
         } else {
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < m; ++i) { /* A A_{i_k}^T */
                 double acc = 0.0;
                 for (int64_t cc = 0; cc < p; ++cc) acc += A[i * p + cc] * A[ik * p + cc];
                 g[i] = acc;
             }
+#pragma omp parallel for schedule(static)
             for (int64_t l = 0; l < n; ++l) { /* (R_{i_k} B^T) B */
                 double acc = 0.0;
                 for (int64_t j = 0; j < q; ++j) acc += w[j] * B[j * n + l];
@@ -361,10 +398,12 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
             }
         }
         /* R^{k+1} = R^k - c g h  (Algorithm 3, last step) */
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < m; ++i)
             for (int64_t l = 0; l < n; ++l) R[i * n + l] -= c * g[i] * h[l];
     }
 
+    g_loop_seconds = wall_seconds() - t_loop;
     if (R_out) memcpy(R_out, R, sizeof(double) * (size_t)(m * n));
     if (s_out) memcpy(s_out, s, sizeof(double) * (size_t)m);
     if (status) *status = st;

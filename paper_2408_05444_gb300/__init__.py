@@ -40,7 +40,7 @@ class grbk_opts(ctypes.Structure):
                 ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
-                ("band_limit", ctypes.c_int32)]
+                ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double))]
 
 
 class grbk_result(ctypes.Structure):
@@ -64,7 +64,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache"]
+           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -129,6 +129,8 @@ def lib():
         L.grbk_unet_destroy.restype = None
         L.grbk_barrier_selftest.argtypes = [i32, vp]
         L.grbk_barrier_selftest.restype = i32
+        L.grbk_fp64_probe.argtypes = [i64, i32, P(dbl), P(dbl), vp]
+        L.grbk_fp64_probe.restype = i32
         L.grbk_strerror.argtypes = [i32]
         L.grbk_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -215,7 +217,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None, band_limit=None):
+               form=None, rank_tol=None, band_limit=None, alphas=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -240,6 +242,9 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.rank_tol = rank_tol
     if band_limit is not None:
         o.band_limit = band_limit
+    if alphas is not None:
+        keep.alphas = np.ascontiguousarray(alphas, dtype=np.float64)
+        o.alphas = keep.alphas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     if stream is not None:
         o.stream = stream if isinstance(stream, int) else stream.cuda_stream
     if x_ref is not None:
@@ -399,7 +404,10 @@ def _mat_array(xs, out=False):
 
 def grbk_batch_create(As, Bs, Cs, opts=None, trace_len=0, **kw) -> Batch:
     """Batched systems; trace_len > 0 records each system's first trace_len rows
-    (available as batch.row_trace, shape nsys x trace_len)."""
+    (available as batch.row_trace, shape nsys x trace_len); alphas: one step per
+    system (grbk_opts.alphas)."""
+    if kw.get("alphas") is not None and len(kw["alphas"]) != len(As):
+        raise ValueError(f"alphas needs {len(As)} entries, got {len(kw['alphas'])}")
     o, keep = _make_opts(opts, trace_len=trace_len * len(As), **kw)
     if trace_len > 0:
         o.trace_len = trace_len
@@ -570,3 +578,12 @@ def grbk_unet_destroy(net: UNetHandle):
 def grbk_barrier_selftest(absent_cta=-1, stream=None) -> int:
     """Status of one bounded grid barrier; absent_cta >= 0 leaves that CTA out."""
     return int(lib().grbk_barrier_selftest(int(absent_cta), _stream_ptr(stream)))
+
+
+def grbk_fp64_probe(iters=1 << 16, blocks_per_sm=8, stream=None):
+    """grbk_fp64_probe -> (FP64 FMAs per second, milliseconds of the timed launch)."""
+    r, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib().grbk_fp64_probe(int(iters), int(blocks_per_sm), ctypes.byref(r), ctypes.byref(ms), _stream_ptr(stream))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_fp64_probe")
+    return r.value, ms.value

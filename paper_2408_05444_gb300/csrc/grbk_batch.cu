@@ -45,7 +45,9 @@ struct BatchParams {
     int* queue;                     // next queue slot
     const float* A;
     const float* B;
-    const float* C;
+    const float* C;                 // may alias R when init_from_x == 0 (the no-allocation entry point keeps
+                                    // C's copy in R): then C is read only by the R^0 = C copy, which skips
+                                    // the copy when the two are the same array
     float* R;
     float* X;
     const double* a;                // ||A_i||^2 per row
@@ -399,7 +401,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 }
                 __syncthreads();
             }
-        } else {
+        } else if (C != R) {
             const float4* C4 = reinterpret_cast<const float4*>(C);
             float4* R4 = reinterpret_cast<float4*>(R);
             for (long long e = threadIdx.x; e < (long long)d.m * d.ldr / 4; e += kBB) R4[e] = __ldg(C4 + e);
@@ -776,8 +778,10 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     *out = nullptr;
     grbk_opts o;
     if (opts) o = *opts; else grbk_default_opts(&o);
+    if (!std::isfinite(o.alpha)) return GRBK_EINVAL;
     for (int s = 0; s < nsys; ++s) {
         const int64_t m = A[s].rows, p = A[s].cols, q = B[s].rows, n = B[s].cols;
+        if (o.alphas && !(std::isfinite(o.alphas[s]) && o.alphas[s] > 0.0)) return GRBK_EINVAL;
         if (!A[s].ptr || !B[s].ptr || !C[s].ptr) return GRBK_EINVAL;
         if (m <= 0 || p <= 0 || q <= 0 || n <= 0 || C[s].rows != m || C[s].cols != n) return GRBK_EINVAL;
         if (m > kMaxSide || p > kMaxSide || q > kMaxSide || n > kMaxSide) return GRBK_EINVAL;
@@ -866,9 +870,11 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
             d.F = F;
             b->normC2[s] = c2s;
             d.normC2 = c2s;
-            if (o.alpha > 0.0) {
-                if (!(o.alpha * lam < 2.0 * (1.0 + 1e-9))) { grbk_batch_destroy(b); return GRBK_EINVAL; }
-                d.alpha = o.alpha;
+            const double a_in = o.alphas ? o.alphas[s] : o.alpha;
+            if (o.alphas || a_in > 0.0) {
+                // Lemma 2.2 / Theorems 4.2-4.8 need 0 < alpha < 2/||B||_2^2 (small slack for the estimate)
+                if (!(a_in > 0.0 && a_in * lam < 2.0 * (1.0 + 1e-9))) { grbk_batch_destroy(b); return GRBK_EINVAL; }
+                d.alpha = a_in;
             } else {
                 d.alpha = 1.0 / lam;
             }
@@ -906,12 +912,13 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     if (!b) return GRBK_EINVAL;
     if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
     if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
-    if (maxit < 0) return GRBK_EINVAL;
+    if (maxit < 0 || !std::isfinite(tol)) return GRBK_EINVAL;
     cudaStream_t st = b->stream;
     for (int s = 0; s < b->nsys; ++s) {
         SysDesc& d = b->hsys[s];
         if (X0s && !x_desc_ok(X0s[s], d.p, d.q)) return GRBK_EINVAL;
         if (X_outs && !x_desc_ok(X_outs[s], d.p, d.q)) return GRBK_EINVAL;
+        if (targets && !(std::isfinite(targets[s]) && targets[s] >= 0.0)) return GRBK_EINVAL;
         if (targets) d.stop_S = targets[s] * targets[s];
         else if (b->opts.stop_kind == GRBK_STOP_RELRES) d.stop_S = tol * tol * b->normC2[s];
         else d.stop_S = -1.0;
@@ -1022,11 +1029,11 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
 // ============================================================================
 // grbk_solve_small_noalloc: one small FP32 system, no allocation at all.
 //
-// Some callers cannot allocate device memory: code running while a CUDA graph
-// is being captured, processes whose device memory is handed out by a fixed
-// pool they do not own, or latency-critical loops where a cudaMalloc /
-// cudaFree (and the device-wide synchronisation cudaFree implies) is not
-// acceptable.  For them this entry point runs the batch kernel above on one
+// Some callers cannot allocate device memory: processes whose device memory
+// is handed out by a fixed pool they do not own (a framework's caching
+// allocator or a service's memory budget), or latency-critical loops where a
+// cudaMalloc / cudaFree (and the device-wide synchronisation cudaFree implies)
+// is not acceptable.  For them this entry point runs the batch kernel above on one
 // system with every working buffer (residual, row norms, recorded terms,
 // queue, outputs) taken from the file-scope array below.  The array lives as
 // long as the library is loaded on a device; every call shares it.
@@ -1163,7 +1170,7 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
         return GRBK_EINVAL;
     if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
     if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
-    if (maxit < 0) return GRBK_EINVAL;
+    if (maxit < 0 || !std::isfinite(alpha) || !std::isfinite(tol)) return GRBK_EINVAL;
     void* base = nullptr;
     grbk_status s = noalloc_scratch_address(&base);
     if (s != GRBK_OK) return s;
@@ -1179,7 +1186,8 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
     P.sys = &S->desc;
     P.order = &S->order;
     P.queue = &S->queue;
-    P.A = S->A; P.B = S->B; P.C = S->R;   // R starts as the padded copy of C
+    // R starts as the padded copy of C: C aliases R, which the kernel allows when init_from_x == 0
+    P.A = S->A; P.B = S->B; P.C = S->R;
     P.R = S->R;
     P.X = X_out;
     P.a = S->a;

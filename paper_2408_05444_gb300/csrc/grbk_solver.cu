@@ -18,6 +18,7 @@
 #include <string.h>
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 #include "grbk_internal.cuh"
@@ -1402,6 +1403,7 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     grbk_opts o;
     if (opts) o = *opts; else grbk_default_opts(&o);
     if (o.precision != GRBK_F64 && o.precision != GRBK_F32) return GRBK_EINVAL;
+    if (!std::isfinite(o.alpha) || !std::isfinite(o.rank_tol)) return GRBK_EINVAL;
     if (o.split_terms == 0) o.split_terms = 2;
     if (o.split_terms != 2 && o.split_terms != 3) return GRBK_EINVAL;
     if (o.refresh_T < 0) return GRBK_EINVAL;
@@ -1676,7 +1678,7 @@ extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, co
     if (!c) return GRBK_EINVAL;
     if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
     if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
-    if (maxit < 0) return GRBK_EINVAL;
+    if (maxit < 0 || !std::isfinite(tol)) return GRBK_EINVAL;
     if (X0 && (!mat_ok(X0) || X0->rows != c->p || X0->cols != c->q)) return GRBK_EINVAL;
     if (X_out && (!X_out->ptr || X_out->rows != c->p || X_out->cols != c->q || X_out->ld < c->q)) return GRBK_EINVAL;
     const grbk_opts& o = c->opts;

@@ -55,3 +55,21 @@ def test_fixture_cyclic_rows():
     """ME-BK visits the rows in order 0, 1, ..., m-1, 0, ... (Section 3)."""
     case = next(c for c in _load()["cases"] if c["variant"] == "bk")
     assert case["rows"] == [k % 200 for k in range(200)]
+
+
+def test_openmp_timing_build_gives_the_same_bits():
+    """The OpenMP build that times the oracle on every host core splits only
+    loops whose elements are independent and keeps every sum over rows serial,
+    so it must reproduce the single-thread build exactly."""
+    import numpy as np
+    import workloads
+    A, B, C, Xs = workloads.config_small()
+    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
+    for variant in ("grbk", "mwrbk"):
+        one = oracle.solve(A, B, C, variant, alpha=alpha, seed=3, maxit=150, mode=oracle.MODE_FACTORED, want_R=True)
+        allc = oracle.solve(A, B, C, variant, alpha=alpha, seed=3, maxit=150, mode=oracle.MODE_FACTORED,
+                            want_R=True, omp=True)
+        assert np.array_equal(one["rows"], allc["rows"])
+        assert np.array_equal(one["X"], allc["X"]) and np.array_equal(one["R"], allc["R"])
+        assert np.array_equal(one["S"], allc["S"])
+    assert oracle.threads(False) == 1

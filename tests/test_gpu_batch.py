@@ -6,6 +6,7 @@ import pytest
 
 import oracle
 import workloads
+from parity_rows import compare_rows
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -21,6 +22,12 @@ def _rel(a, b):
 
 def _systems():
     return workloads.blur_systems(n_images=3, min_side=48, max_side=112, noise=0.0, mild=True, seed=21)
+
+
+def _alphas(Bs):
+    """alpha_s = 1 / ||B_s||_2^2 from numpy's SVD (Section 5's step), given to
+    both the library and the oracle so neither side takes the other's step."""
+    return np.array([1.0 / np.linalg.norm(B, 2) ** 2 for B in Bs])
 
 
 def _band(M):
@@ -46,30 +53,29 @@ def test_batch_converges_to_clean_images(band_limit):
 def test_batch_matches_oracle_per_system(variant, band_limit):
     """Fixed 120 iterations per system: the selected rows agree with the FP64
     oracle's up to the first decision the oracle marks as closer than FP32
-    resolves (relative margin 1e-5); with no such decision X agrees to 1e-4."""
+    resolves (relative margin 1e-5), and every system agrees at least up to
+    its first decision within 1e-6; where all 120 agree X agrees to 1e-4."""
     sy = _systems()
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120, band_limit=band_limit)
+    alphas = _alphas(Bs)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120, band_limit=band_limit, alphas=alphas)
     for sid, s in enumerate(sy):
         want = (_band(s["A"]), _band(s["B"])) if band_limit == 0 else (-1, -1)
         assert g.grbk_batch_info(b, sid) == want
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, variant, theta=0.7, maxit=120, seed=11, X_outs=Xo)
     assert st == g.GRBK_OK
-    checked = 0
+    compared = []
     for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
         assert r["iters"] == 120
-        orc = oracle.solve(s["A"], s["B"], s["C"], variant, theta=0.7, alpha=r["alpha"], seed=11, sys=sid,
+        assert r["alpha"] == alphas[sid]
+        orc = oracle.solve(s["A"], s["B"], s["C"], variant, theta=0.7, alpha=alphas[sid], seed=11, sys=sid,
                            maxit=120, mode=oracle.MODE_FACTORED)
-        margins = np.minimum(orc["margin_pick"], np.where(np.isnan(orc["margin_adm"]), np.inf, orc["margin_adm"]))
-        near = np.nonzero(margins < 1e-5)[0]
-        kk = int(near[0]) if len(near) else 120
-        rows = b.row_trace[sid]
-        assert np.array_equal(rows[:kk], orc["rows"][:kk]), (sid, kk, rows[:kk], orc["rows"][:kk])
+        kk = compare_rows(b.row_trace[sid], orc, 120)
         if kk == 120:
             assert _rel(X, orc["X"]) < 1e-4
-            checked += 1
-    assert checked >= 1
+        compared.append(kk)
+    assert sum(compared) >= 0.9 * 120 * len(sy), compared
 
 
 def test_banded_and_dense_paths_agree():
@@ -117,19 +123,17 @@ def test_banded_path_on_rectangular_banded_systems():
         Xs = rng.standard_normal((p, q))
         sy.append(dict(A=A, B=B, C=A @ Xs @ B, X=Xs, ba=ba, bb=bb))
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs, trace_len=150)
+    alphas = _alphas(Bs)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=150, alphas=alphas)
     for sid, s in enumerate(sy):
         assert g.grbk_batch_info(b, sid) == (_band(s["A"]), _band(s["B"]))
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, "grbk", maxit=150, seed=4, X_outs=Xo)
     assert st == g.GRBK_OK
     for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
-        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=r["alpha"], seed=4, sys=sid, maxit=150,
+        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=alphas[sid], seed=4, sys=sid, maxit=150,
                            mode=oracle.MODE_FACTORED)
-        margins = np.minimum(orc["margin_pick"], np.where(np.isnan(orc["margin_adm"]), np.inf, orc["margin_adm"]))
-        near = np.nonzero(margins < 1e-5)[0]
-        kk = int(near[0]) if len(near) else 150
-        assert np.array_equal(b.row_trace[sid][:kk], orc["rows"][:kk])
+        kk = compare_rows(b.row_trace[sid], orc, 150)
         if kk == 150:
             assert _rel(X, orc["X"]) < 1e-4
 
@@ -142,17 +146,15 @@ def test_batch_from_nonzero_x0_matches_oracle(band_limit):
     As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
     rng = np.random.default_rng(6)
     X0s = [s["X"] + 0.05 * rng.standard_normal(s["X"].shape) for s in sy]
-    b = g.grbk_batch_create(As, Bs, Cs, trace_len=100, band_limit=band_limit)
+    alphas = _alphas(Bs)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=100, band_limit=band_limit, alphas=alphas)
     Xo = [np.zeros_like(s["X"]) for s in sy]
     st, res = g.grbk_batch_solve(b, "grbk", X0s=X0s, maxit=100, seed=5, X_outs=Xo)
     assert st == g.GRBK_OK
     for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
         assert r["x0_rejected"] == 0
-        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=r["alpha"], X0=X0s[sid], seed=5, sys=sid,
+        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=alphas[sid], X0=X0s[sid], seed=5, sys=sid,
                            maxit=100, mode=oracle.MODE_FACTORED)
-        margins = np.minimum(orc["margin_pick"], np.where(np.isnan(orc["margin_adm"]), np.inf, orc["margin_adm"]))
-        near = np.nonzero(margins < 1e-5)[0]
-        kk = int(near[0]) if len(near) else 100
-        assert np.array_equal(b.row_trace[sid][:kk], orc["rows"][:kk])
+        kk = compare_rows(b.row_trace[sid], orc, 100)
         if kk == 100:
             assert _rel(X, orc["X"]) < 1e-4

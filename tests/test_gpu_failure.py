@@ -39,6 +39,30 @@ def test_invalid_inputs_are_reported_not_crashed():
     with pytest.raises(g.GrbkError) as e:
         g.grbk_create(A, B, C, refresh_T=-1)
     assert e.value.status == g.GRBK_EINVAL
+    nan = float("nan")
+    for kw in (dict(alpha=nan), dict(alpha=float("inf")), dict(rank_tol=nan)):
+        with pytest.raises(g.GrbkError) as e:
+            g.grbk_create(A, B, C, **kw)
+        assert e.value.status == g.GRBK_EINVAL, kw
+    for kw in (dict(alpha=nan), dict(alphas=[nan]), dict(alphas=[-1.0]), dict(alphas=[1e6])):
+        with pytest.raises(g.GrbkError) as e:
+            g.grbk_batch_create([A], [B], [C], **kw)
+        assert e.value.status == g.GRBK_EINVAL, kw
+    ctx = g.grbk_create(A, B, C)
+    X = np.zeros((4, 3))
+    with pytest.raises(g.GrbkError) as e:
+        g.grbk_solve(ctx, "grbk", tol=nan, maxit=5, X_out=X)
+    assert e.value.status == g.GRBK_EINVAL
+    with pytest.raises(g.GrbkError) as e:
+        g.grbk_solve(ctx, "rgrbk", theta=nan, maxit=5, X_out=X)
+    assert e.value.status == g.GRBK_EINVAL
+    g.grbk_destroy(ctx)
+    b = g.grbk_batch_create([A], [B], [C])
+    for kw in (dict(tol=nan), dict(targets=[nan])):
+        with pytest.raises(g.GrbkError) as e:
+            g.grbk_batch_solve(b, "grbk", maxit=5, X_outs=[X], **kw)
+        assert e.value.status == g.GRBK_EINVAL, kw
+    g.grbk_batch_destroy(b)
     Cinf = C.copy()
     Cinf[0, 0] = np.inf
     with pytest.raises(g.GrbkError) as e:

@@ -132,7 +132,9 @@ def test_row_sharded_exchange_matches_oracle(tmp_path, world, variant, theta):
     mp.spawn(_worker, args=(world, _free_port(), str(tmp_path), variant, theta, maxit), nprocs=world, join=True)
     got = np.load(tmp_path / "shard.npz")
     A, B, C, _ = workloads.config_small()
-    orc = oracle.solve(A, B, C, variant, theta=theta, alpha=float(got["alpha"]), seed=7, maxit=maxit,
+    alpha = 1.0 / np.linalg.norm(B, 2) ** 2
+    assert float(got["alpha"]) == alpha
+    orc = oracle.solve(A, B, C, variant, theta=theta, alpha=alpha, seed=7, maxit=maxit,
                        mode=oracle.MODE_FACTORED)
     live = np.nonzero(orc["S"] <= 1e-20 * orc["S"][0])[0]
     n = int(live[0]) if len(live) else maxit

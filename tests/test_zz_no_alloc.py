@@ -1,6 +1,7 @@
 """grbk_solve_small_noalloc: the entry point for callers that cannot allocate
-(work inside a CUDA graph capture, memory handed out by a fixed pool, loops
-that cannot afford cudaMalloc/cudaFree).  It must give what the allocating
+(a process whose device memory is handed out by a fixed pool it does not own,
+loops that cannot afford cudaMalloc/cudaFree and the synchronisation cudaFree
+implies).  It must give what the allocating
 batched entry point gives for the same single system, on two calls in a row
 (the second call reuses the static working array the first one left behind).
 
@@ -62,3 +63,10 @@ def test_noalloc_default_step_and_limits():
     Xs = torch.zeros(4, 4, dtype=torch.float32, device=dev)
     st, _, _ = g.grbk_solve_small_noalloc(big, Bs, Cs, Xs, "grbk", maxit=5)
     assert st == g.GRBK_EINVAL
+    # non-finite step, tolerance or relaxation: rejected on the host before any work
+    nan = float("nan")
+    for kw in (dict(alpha=nan), dict(alpha=float("inf")), dict(tol=nan), dict(variant="rgrbk", theta=nan)):
+        args = dict(variant="grbk", maxit=5)
+        args.update(kw)
+        st, _, _ = g.grbk_solve_small_noalloc(At, Bt, Ct, X, **args)
+        assert st == g.GRBK_EINVAL, kw
