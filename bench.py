@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target legs of the default run")
     ap.add_argument("--cpu-iters", type=int, default=20,
                     help="oracle iterations of the full system timed for cpu_baseline")
-    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet"],
+    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet", "sparse", "colour"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=2)
     ap.add_argument("--train-images", type=int, default=20000)
@@ -644,6 +644,85 @@ def batch_bench(args):
     print(json.dumps(out), flush=True)
 
 
+def sparse_bench(args):
+    """Sparse A and B (CSR, FP64): the paper's four sprandn-shaped sets (Tables 3
+    and 5, sets 3 and 6) in one launch, every variant for a fixed 1e5 iterations
+    per system, timed with CUDA events; the FP64 oracle's single-thread rate on
+    the same dense systems for comparison."""
+    import torch
+    import oracle
+    import paper_2408_05444_gb300 as g
+    names = sorted(workloads.SPARSE_SETS)
+    sets = [workloads.sparse_set(nm) for nm in names]
+    K = 100_000
+    out = {"mode": "sparse", "systems": names, "iters_per_system": K, "dtype": "f64", "variants": {}}
+    sp = g.grbk_sparse_create([s_[0] for s_ in sets], [s_[1] for s_ in sets], [s_[2] for s_ in sets])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for variant, theta in [("rbk", 0.5), ("grbk", 0.5), ("rgrbk", 0.8), ("mwrbk", 1.0)]:
+        X = [np.zeros((s_[0].shape[1], s_[1].shape[0])) for s_ in sets]
+        g.grbk_sparse_solve(sp, variant, theta=theta, maxit=100, seed=1, X_outs=X)
+        torch.cuda.synchronize()
+        ev0.record()
+        st, res = g.grbk_sparse_solve(sp, variant, theta=theta, maxit=K, seed=1)
+        ev1.record()
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        out["variants"][f"{variant}_theta{theta}"] = {
+            "seconds": sec, "system_iters_per_s": len(sets) * K / sec,
+            "us_per_iteration_longest": 1e6 * sec / K,
+            "relres": [r["relres"] for r in res]}
+    for nm, (A, B, C, Xs) in zip(names, sets):
+        gn, al = g.grbk_sparse_info(sp, names.index(nm))
+        out.setdefault("gram_nnz", {})[nm] = gn
+    # oracle rate on the largest set (dense FACTORED, single thread)
+    A, B, C, Xs = sets[names.index("table5_set6")]
+    r = oracle.solve(A, B, C, "grbk", alpha=1.0 / np.linalg.norm(B, 2) ** 2, maxit=2000, mode=oracle.MODE_FACTORED,
+                     trace=False)
+    out["oracle_table5_set6_iters_per_s"] = r["iters"] / max(r["loop_seconds"], 1e-9)
+    g.grbk_sparse_destroy(sp)
+    print(json.dumps(out), flush=True)
+
+
+def colour_bench(args):
+    """Section 6's colour model B = A X A_c^T + E on synthetic images of the
+    paper's four sizes (92x92, 96x96, 125x120, 240x192; 5 x 5 Gaussian blur with
+    sigma 6, zero boundary, A_c of Section 6, noise N(0, 1e-3^2)), one system
+    per image, all four in one launch; ME-RBK, ME-GRBK, ME-RGRBK (theta 0.8) and
+    ME-MWRBK for 1.5e5 iterations (the largest count of Section 6) from X^0 = 0:
+    device time, PSNR and SSIM as in Table 9."""
+    import torch
+    import scipy.sparse as sps
+    import paper_2408_05444_gb300 as g
+    from paper_2408_05444_gb300 import quality as Q
+    names = list(workloads.COLOUR_SIZES)
+    ds = [workloads.colour_model(h, w, seed=5, index=i, noise=1e-3)
+          for i, (h, w) in enumerate(workloads.COLOUR_SIZES.values())]
+    As = [sps.csr_matrix((d["A"][2], d["A"][1], d["A"][0]), shape=(d["h"] * d["w"],) * 2) for d in ds]
+    sp = g.grbk_sparse_create(As, [d["B"] for d in ds], [d["C"] for d in ds])
+    K = 150_000
+    out = {"mode": "colour", "images": names, "iterations": K, "dtype": "f64", "blurred": {}, "variants": {}}
+    for nm, d in zip(names, ds):
+        bl = workloads.unvec_image(d["C"], d["h"], d["w"])
+        out["blurred"][nm] = {"psnr": Q.psnr(bl, d["image"]), "ssim": Q.ssim(bl, d["image"])}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for variant, theta in [("rbk", 0.5), ("grbk", 0.5), ("rgrbk", 0.8), ("mwrbk", 1.0)]:
+        X = [np.zeros((d["h"] * d["w"], 3)) for d in ds]
+        torch.cuda.synchronize()
+        ev0.record()
+        st, res = g.grbk_sparse_solve(sp, variant, theta=theta, maxit=K, seed=3, X_outs=X)
+        ev1.record()
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        per = {}
+        for nm, d, x in zip(names, ds, X):
+            img = workloads.unvec_image(x, d["h"], d["w"])
+            per[nm] = {"psnr": Q.psnr(img, d["image"]), "ssim": Q.ssim(img, d["image"])}
+        out["variants"][f"{variant}_theta{theta}"] = {"seconds_incl_copies": sec,
+                                                       "us_per_iteration_longest": 1e6 * sec / K, "images": per}
+    g.grbk_sparse_destroy(sp)
+    print(json.dumps(out), flush=True)
+
+
 def unet_bench(args):
     """Warm-start network inference: the U-Net (width 20, random weights) on a batch
     of 16 channels of 512 x 512 already on the device; three untimed forwards,
@@ -669,6 +748,12 @@ def main():
     args = parse()
     if args.mode == "unet":
         unet_bench(args)
+        return
+    if args.mode == "sparse":
+        sparse_bench(args)
+        return
+    if args.mode == "colour":
+        colour_bench(args)
         return
     if args.mode == "batch":
         batch_bench(args)

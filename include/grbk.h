@@ -229,6 +229,66 @@ grbk_status grbk_batch_info(const grbk_batch* b, int32_t sys, int32_t* bandA, in
 void grbk_batch_destroy(grbk_batch* batch);
 
 /*
+ * Sparse A and B: nsys independent systems A_s X_s B_s = C_s with A_s and B_s
+ * in compressed sparse rows, R dense, all arithmetic FP64 (the paper's
+ * precision).  Section 5 draws A and B from sparse test matrices (the sprandn
+ * sets of Tables 3, 5 and 7); Section 6's colour model B = A X A_c^T + E has a
+ * blur A of mn x mn with a few dozen nonzeros per row and B = A_c^T (3 x 3),
+ * one system per image with the three channels as the columns of X.
+ *
+ * Per iteration the library touches only what the sparsity allows: w =
+ * R_{i_k} B^T over the rows of B, X += c A_{i_k}^T w over the nonzeros of
+ * A_{i_k}, v = w B over the columns of B, and R -= c (A A_{i_k}^T) v only on
+ * the rows k with (A A^T)_{k,i_k} != 0 (the sparse Gram matrix A A^T is formed
+ * once on the device at set-up, the practice note after Algorithm 3).  The
+ * threshold, the admitted set and the pick are those of Algorithms 1-5, with
+ * the totals kept as per-block summaries of 256 rows.  X^0 = 0 (Section 6
+ * starts from the zero matrix).
+ */
+typedef struct {
+    int64_t rows, cols, nnz;
+    const int64_t* rowptr;  /* rows + 1 host offsets: rowptr[0] = 0, rowptr[rows] = nnz, non-decreasing */
+    const int32_t* colind;  /* nnz host column indices, strictly ascending within each row */
+    const double* val;      /* nnz host values (finite) */
+} grbk_csr;
+
+typedef struct grbk_sparse grbk_sparse;
+
+/*
+ * grbk_sparse_create -- copies A[s] (m x p CSR), B[s] (q x n CSR) and C[s]
+ * (m x n dense, host or device, FP32/FP64) for s < nsys into library-owned
+ * device memory, forms the CSC of B and A A^T, ||A_i||^2, ||A||_F^2, ||C||_F^2
+ * and the step (opts->alphas, opts->alpha, else 1/||B||_2^2 from 200 power
+ * iterations on B B^T).  Limits: m <= 262144, q and n <= 1024.
+ * opts: stop_kind (NONE or RELRES), row_trace / s_trace (host, nsys * trace_len
+ * entries: system s at [s * trace_len + k]), stream, grid_ctas.
+ * Errors: EINVAL (NULL, malformed CSR: offsets, column range or order; shapes;
+ * limits; inadmissible alpha), ENONFINITE, ENOMEM, ECUDA.
+ */
+grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const grbk_csr* A, const grbk_csr* B,
+                               const grbk_mat* C, const grbk_opts* opts);
+
+/*
+ * grbk_sparse_solve -- every system from X^0 = 0 until its stop rule holds or
+ * maxit: RELRES with tol, or targets[s] (absolute ||R_s||_F, the discrepancy
+ * principle) when targets is not NULL.  X_outs: NULL or nsys caller matrices
+ * p_s x q_s (host or device, FP32/FP64, row stride >= q_s).  results: NULL or
+ * nsys entries.  Returns OK, or ENOTCONV when some system with a stop rule
+ * reached maxit; EINVAL for a bad variant, theta, tol, target or output.
+ */
+grbk_status grbk_sparse_solve(grbk_sparse* sp, int32_t variant, double theta, double tol, const double* targets,
+                              int64_t maxit, uint64_t seed, grbk_mat* X_outs, grbk_result* results);
+
+/* Entries of the sparse Gram matrix A_s A_s^T and the step of system `sys`. */
+grbk_status grbk_sparse_info(const grbk_sparse* sp, int32_t sys, int64_t* gram_nnz, double* alpha);
+
+/* The kept residual R_s (m x n FP64, row-major) and its row norms ||R_i||^2
+ * (m doubles) after a solve, into host buffers (either may be NULL). */
+grbk_status grbk_sparse_get_residual(const grbk_sparse* sp, int32_t sys, double* R_out, double* s_out);
+
+void grbk_sparse_destroy(grbk_sparse* sp);
+
+/*
  * grbk_solve_small_noalloc -- one small system A X B = C in FP32 solved with no
  * device or host allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate, e.g. processes whose device memory

@@ -43,6 +43,11 @@ class grbk_opts(ctypes.Structure):
                 ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double))]
 
 
+class grbk_csr(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
 class grbk_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("relres", ctypes.c_double), ("rse", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("alpha", ctypes.c_double), ("iter_kernel_ms", ctypes.c_double),
@@ -64,7 +69,8 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe"]
+           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_sparse_create",
+           "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -129,6 +135,16 @@ def lib():
         L.grbk_unet_destroy.restype = None
         L.grbk_barrier_selftest.argtypes = [i32, vp]
         L.grbk_barrier_selftest.restype = i32
+        L.grbk_sparse_create.argtypes = [P(vp), i32, P(grbk_csr), P(grbk_csr), P(grbk_mat), P(grbk_opts)]
+        L.grbk_sparse_create.restype = i32
+        L.grbk_sparse_solve.argtypes = [vp, i32, dbl, dbl, P(dbl), i64, u64, P(grbk_mat), P(grbk_result)]
+        L.grbk_sparse_solve.restype = i32
+        L.grbk_sparse_info.argtypes = [vp, i32, P(i64), P(dbl)]
+        L.grbk_sparse_info.restype = i32
+        L.grbk_sparse_get_residual.argtypes = [vp, i32, vp, vp]
+        L.grbk_sparse_get_residual.restype = i32
+        L.grbk_sparse_destroy.argtypes = [vp]
+        L.grbk_sparse_destroy.restype = None
         L.grbk_fp64_probe.argtypes = [i64, i32, P(dbl), P(dbl), vp]
         L.grbk_fp64_probe.restype = i32
         L.grbk_strerror.argtypes = [i32]
@@ -587,3 +603,122 @@ def grbk_fp64_probe(iters=1 << 16, blocks_per_sm=8, stream=None):
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_fp64_probe")
     return r.value, ms.value
+
+
+# ---------------------------------------------------------------------------
+# sparse A and B (CSR)
+# ---------------------------------------------------------------------------
+def csr_arrays(M):
+    """(rows, cols, rowptr int64, colind int32, val float64) of a scipy.sparse
+    matrix or a dense 2-D array (its nonzeros, row by row, ascending columns)."""
+    if hasattr(M, "tocsr"):
+        M = M.tocsr()
+        M.sum_duplicates()
+        M.sort_indices()
+        return (int(M.shape[0]), int(M.shape[1]), np.ascontiguousarray(M.indptr, dtype=np.int64),
+                np.ascontiguousarray(M.indices, dtype=np.int32), np.ascontiguousarray(M.data, dtype=np.float64))
+    D = np.asarray(M, dtype=np.float64)
+    if D.ndim != 2:
+        raise ValueError("need a 2-D matrix")
+    nz = D != 0
+    rowptr = np.concatenate([[0], np.cumsum(nz.sum(axis=1))]).astype(np.int64)
+    r, c = np.nonzero(nz)
+    return (D.shape[0], D.shape[1], rowptr, np.ascontiguousarray(c, dtype=np.int32),
+            np.ascontiguousarray(D[r, c], dtype=np.float64))
+
+
+def _csr(M, keep):
+    rows, cols, rp, ci, v = csr_arrays(M)
+    keep.append((rp, ci, v))
+    return grbk_csr(rows, cols, len(v), rp.ctypes.data, ci.ctypes.data if len(ci) else None,
+                    v.ctypes.data if len(v) else None)
+
+
+class Sparse:
+    def __init__(self, handle, keep, nsys, trace_len):
+        self.handle = handle
+        self.keep = keep
+        self.nsys = nsys
+        self.trace_len = trace_len
+
+    @property
+    def row_trace(self):
+        rows = getattr(self.keep, "rows", None)
+        return None if rows is None else rows.reshape(self.nsys, self.trace_len)
+
+    @property
+    def s_trace(self):
+        S = getattr(self.keep, "S", None)
+        return None if S is None else S.reshape(self.nsys, self.trace_len)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().grbk_sparse_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def grbk_sparse_create(As, Bs, Cs, opts=None, trace_len=0, **kw) -> Sparse:
+    """Systems with sparse A_s, B_s (scipy.sparse or dense arrays, sent as CSR)
+    and dense C_s; trace_len > 0 records each system's first trace_len rows
+    and ||R^k||_F^2 (sparse.row_trace, sparse.s_trace: nsys x trace_len)."""
+    n = len(As)
+    if kw.get("alphas") is not None and len(kw["alphas"]) != n:
+        raise ValueError(f"alphas needs {n} entries, got {len(kw['alphas'])}")
+    o, keep = _make_opts(opts, trace_len=trace_len * n, **kw)
+    if trace_len > 0:
+        o.trace_len = trace_len
+    held = []
+    a = (grbk_csr * n)(*[_csr(M, held) for M in As])
+    b = (grbk_csr * n)(*[_csr(M, held) for M in Bs])
+    keep.csr = held
+    c = _mat_array(Cs)
+    h = ctypes.c_void_p()
+    st = lib().grbk_sparse_create(ctypes.byref(h), n, a, b, c, ctypes.byref(o))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_sparse_create")
+    return Sparse(h.value, keep, n, trace_len)
+
+
+def grbk_sparse_solve(sp: Sparse, variant, theta=0.5, tol=0.0, targets=None, maxit=1000, seed=0, X_outs=None):
+    """grbk_sparse_solve -> (status, list of result dicts); X_outs written in place."""
+    v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    xo = _mat_array(X_outs, out=True) if X_outs is not None else None
+    tg = None
+    if targets is not None:
+        tgt = np.ascontiguousarray(targets, dtype=np.float64)
+        if len(tgt) != sp.nsys:
+            raise ValueError(f"targets needs {sp.nsys} entries")
+        tg = tgt.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    res = (grbk_result * sp.nsys)()
+    st = lib().grbk_sparse_solve(sp.handle, v, float(theta), float(tol), tg, int(maxit), int(seed), xo, res)
+    if st not in (GRBK_OK, GRBK_ENOTCONV):
+        raise GrbkError(st, "grbk_sparse_solve")
+    return st, [r.as_dict() for r in res]
+
+
+def grbk_sparse_info(sp: Sparse, sys: int):
+    """-> (entries of A_s A_s^T, step alpha_s)."""
+    nnz, al = ctypes.c_int64(), ctypes.c_double()
+    st = lib().grbk_sparse_info(sp.handle, int(sys), ctypes.byref(nnz), ctypes.byref(al))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_sparse_info")
+    return nnz.value, al.value
+
+
+def grbk_sparse_get_residual(sp: Sparse, sys: int, m: int, n: int):
+    """-> (R (m x n), row norms (m)) of system `sys` after a solve."""
+    R = np.empty((m, n))
+    s = np.empty(m)
+    st = lib().grbk_sparse_get_residual(sp.handle, int(sys), R.ctypes.data, s.ctypes.data)
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_sparse_get_residual")
+    return R, s
+
+
+def grbk_sparse_destroy(sp: Sparse):
+    if sp.handle:
+        lib().grbk_sparse_destroy(sp.handle)
+        sp.handle = None

@@ -88,9 +88,18 @@ def test_fp64_matches_oracle_at_scale(rank_deficient, variant, theta):
     assert np.max(np.abs(got["R"] - orc["R"])) <= 1e-9 * np.max(np.abs(C))
     assert np.max(np.abs(got["s"] - orc["s"]) / np.maximum(orc["s"], 1e-300)) < 1e-9
     if rank_deficient:
-        # Lemma 3.2 with X^0 = 0: X^k - A^+ A X^k B B^+ stays 0
-        Pa = np.linalg.pinv(A) @ A
-        Pb = B @ np.linalg.pinv(B)
+        # Lemma 3.2 with X^0 = 0: X^k - A^+ A X^k B B^+ stays 0.  A^+ A and B B^+ are the
+        # projectors onto the row space of A and the column space of B, formed from the
+        # singular vectors of the singular values above 1e-10 sigma_max (A and B have
+        # exactly 600 and 500 such values; the others are at the rounding level)
+        def proj(V, sv):
+            r = int(np.sum(sv > 1e-10 * sv[0]))
+            return V[:, :r] @ V[:, :r].T, r
+        _, sa, Vta = np.linalg.svd(A, full_matrices=False)
+        Ub, sb, _ = np.linalg.svd(B, full_matrices=False)
+        Pa, ra = proj(Vta.T, sa)
+        Pb, rb = proj(Ub, sb)
+        assert (ra, rb) == (600, 500)
         X = got["X"]
         assert np.linalg.norm(X - Pa @ X @ Pb) <= 1e-9 * np.linalg.norm(X)
 

@@ -227,3 +227,120 @@ def blur_systems(n_images=64, seed=4, min_side=128, max_side=512, noise=1e-3, mi
     for (idx, *_), pr in zip(jobs, params):
         out += _systems_from(idx, seed, noise, mild, pr)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Sparse test matrices (Section 5, Tables 3, 5, 7: MATLAB sprandn sets)
+# ---------------------------------------------------------------------------
+
+def sprand_gaussian(g, rows, cols, density, full_rank=True, tries=50):
+    """rows x cols matrix with about density * rows * cols N(0,1) nonzeros at
+    uniformly random positions (a stand-in for MATLAB's sprandn, whose random
+    stream and condition-number construction are not reproduced); with
+    full_rank, redrawn until its rank is min(rows, cols).  Dense numpy array."""
+    for _ in range(tries):
+        M = np.where(g.random((rows, cols)) < density, g.standard_normal((rows, cols)), 0.0)
+        if not full_rank or np.linalg.matrix_rank(M) == min(rows, cols):
+            return M
+    raise RuntimeError("no full-rank draw")
+
+
+# (A shape, A density), (B shape, B density) of the paper's sprandn sets
+SPARSE_SETS = {
+    "table3_set3": ((210, 20, 0.05), (40, 270, 0.05)),
+    "table3_set6": ((160, 35, 0.05), (25, 150, 0.08)),
+    "table5_set3": ((25, 205, 0.08), (125, 40, 0.05)),
+    "table5_set6": ((130, 320, 0.05), (435, 170, 0.02)),
+}
+
+
+def sparse_set(name, seed=6):
+    """A, B (dense arrays with the set's sparsity), X* N(0,1), C = A X* B."""
+    (m, p, da), (q, n, db) = SPARSE_SETS[name]
+    g = rng(7000 + seed + 17 * sorted(SPARSE_SETS).index(name))
+    A = sprand_gaussian(g, m, p, da)
+    B = sprand_gaussian(g, q, n, db)
+    Xs = g.standard_normal((p, q))
+    return A, B, A @ Xs @ B, Xs
+
+
+# ---------------------------------------------------------------------------
+# Section 6 colour model: B = A X A_c^T + E, X = (vec X_r, vec X_g, vec X_b)
+# ---------------------------------------------------------------------------
+
+# cross-channel blur of Section 6
+A_CROSS = np.array([[0.9, 0.05, 0.05],
+                    [0.0, 0.9, 0.1],
+                    [0.05, 0.1, 0.85]])
+
+# the four test images' sizes in Section 6 (face, bird, mandril, barbara)
+COLOUR_SIZES = {"face": (92, 92), "bird": (96, 96), "mandril": (125, 120), "barbara": (240, 192)}
+
+
+def gaussian_psf(size=5, sigma=6.0):
+    """size x size taps exp(-(x^2 + y^2) / (2 sigma^2)), x, y centred, summing to 1
+    (the G(5, 6) blur of Section 6: 5 x 5 with sigma 6)."""
+    h = size // 2
+    x = np.arange(-h, h + 1)
+    P = np.exp(-(x[:, None] ** 2 + x[None, :] ** 2) / (2.0 * sigma ** 2))
+    return P / P.sum()
+
+
+def blur_operator(h, w, psf):
+    """The within-channel blur A (hw x hw) acting on vec(X) (columns stacked, pixel
+    (r, c) at index c h + r) as the 2-D convolution with the (symmetric) psf
+    under zero boundary conditions, as CSR arrays (rowptr, colind, val) with
+    ascending columns; scipy is not needed."""
+    k = psf.shape[0] // 2
+    rows, cols, vals = [], [], []
+    rr, cc = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    idx = (cc * h + rr).ravel()
+    r0, c0 = rr.ravel(), cc.ravel()
+    for dc in range(-k, k + 1):          # neighbour columns first: ascending column index within a row
+        for dr in range(-k, k + 1):
+            r1, c1 = r0 + dr, c0 + dc
+            ok = (r1 >= 0) & (r1 < h) & (c1 >= 0) & (c1 < w)
+            rows.append(idx[ok])
+            cols.append((c1 * h + r1)[ok])
+            vals.append(np.full(int(ok.sum()), psf[dr + k, dc + k]))
+    rows, cols, vals = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(h * w + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr).astype(np.int64), cols.astype(np.int32), vals
+
+
+def csr_to_dense(rowptr, colind, val, cols):
+    D = np.zeros((len(rowptr) - 1, cols))
+    for i in range(len(rowptr) - 1):
+        D[i, colind[rowptr[i]:rowptr[i + 1]]] = val[rowptr[i]:rowptr[i + 1]]
+    return D
+
+
+def csr_matvec(rowptr, colind, val, X):
+    """A X for CSR A and dense X (rows of X gathered per nonzero)."""
+    out = np.zeros((len(rowptr) - 1,) + X.shape[1:])
+    rows = np.repeat(np.arange(len(rowptr) - 1), np.diff(rowptr))
+    np.add.at(out, rows, val[:, None] * X[colind] if X.ndim == 2 else val * X[colind])
+    return out
+
+
+def colour_model(h, w, seed=9, index=0, noise=0.0, psf=None):
+    """One synthetic colour image (h x w x 3, as color_image) and Section 6's
+    model: A = blur_operator (CSR), B = A_c^T, X = (vec X_r, vec X_g, vec X_b)
+    (hw x 3), C = A X B + N(0, noise^2).  Returns a dict with A (CSR triple), B,
+    C, X, E, image, h, w."""
+    g = np.random.default_rng([BASE_SEED, 600 + int(seed), int(index)])
+    img = color_image(g, h, w)
+    X = np.stack([img[:, :, c].T.ravel() for c in range(3)], axis=1)   # vec stacks columns
+    A = blur_operator(h, w, gaussian_psf() if psf is None else psf)
+    B = A_CROSS.T.copy()
+    E = g.standard_normal((h * w, 3)) * noise
+    C = csr_matvec(*A, X) @ B + E
+    return dict(A=A, B=B, C=C, X=X, E=E, image=img, h=h, w=w)
+
+
+def unvec_image(X, h, w):
+    """h x w x 3 image from the hw x 3 matrix of stacked columns."""
+    return np.stack([X[:, c].reshape(w, h).T for c in range(3)], axis=2)
