@@ -110,6 +110,8 @@ typedef struct {
     const double* alphas; /* batched and sparse solvers: host array of nsys steps, one per system, each in
                              (0, 2/||B_s||_2^2) (checked against the device estimate of ||B_s||_2^2); it
                              replaces `alpha`.  NULL: `alpha` (when > 0) or 1/||B_s||_2^2 for every system */
+    int32_t extended;     /* sparse solver: 1 = least-squares extension for inconsistent systems (Eq. 2.1;
+                             see grbk_sparse_create); 0 = the paper's iteration */
 } grbk_opts;
 
 typedef struct {
@@ -244,6 +246,17 @@ void grbk_batch_destroy(grbk_batch* batch);
  * threshold, the admitted set and the pick are those of Algorithms 1-5, with
  * the totals kept as per-block summaries of 256 rows.  X^0 = 0 (Section 6
  * starts from the zero matrix).
+ *
+ * opts->extended = 1 solves inconsistent systems in the least-squares sense
+ * (Eq. 2.1, whose target the paper defines but does not solve), as the
+ * randomized extended Kaczmarz method of Zouzias and Freris (2013) does for
+ * A x = b: an auxiliary Y (m x n, Y^0 = C) is driven to (I - A A^+) C by one
+ * column projection per iteration, Y -= A_{:,j} (A_{:,j}^T Y) / ||A_{:,j}||^2
+ * with column j drawn with probability ||A_{:,j}||^2 / ||A||_F^2 (Philox
+ * counter (k, system, 1, 0)), and the row step of the chosen variant runs on
+ * R = C - Y - A X B.  With B of full column rank (B^+ B = I) X^k tends to the
+ * least-norm least-squares solution A^+ C B^+.  R^0 = 0, so the extension runs
+ * a fixed number of iterations (stop_kind NONE, no targets; otherwise EINVAL).
  */
 typedef struct {
     int64_t rows, cols, nnz;

@@ -93,7 +93,9 @@ def lib(omp: bool = False):
         L.oracle_spectral_norm_sq.restype = dbl
         L.oracle_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int, dbl, dbl, u64, u64, i64,
                                    ctypes.c_int, ctypes.c_int, dbl, vp, vp, vp, vp, vp, vp, vp,
-                                   vp, vp, ctypes.POINTER(ctypes.c_int)]
+                                   vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, vp]
+        L.oracle_uniform_column.argtypes = [u64, u64, u64]
+        L.oracle_uniform_column.restype = dbl
         L.oracle_solve.restype = i64
         L.oracle_last_loop_seconds.argtypes = []
         L.oracle_last_loop_seconds.restype = dbl
@@ -123,6 +125,10 @@ def uniform(seed, k, sys=0):
     return lib().oracle_uniform(int(seed), int(k), int(sys))
 
 
+def uniform_column(seed, k, sys=0):
+    return lib().oracle_uniform_column(int(seed), int(k), int(sys))
+
+
 def residual(A, X, B, C):
     A, X, B, C = map(_f64, (A, X, B, C))
     m, p = A.shape
@@ -150,10 +156,13 @@ def threads(omp: bool = False) -> int:
 
 
 def solve(A, B, C, variant="grbk", theta=0.5, alpha=None, X0=None, seed=0, sys=0, maxit=1000,
-          mode=MODE_GRAM, stop=STOP_NONE, tol=0.0, Xref=None, trace=True, want_R=False, omp=False):
+          mode=MODE_GRAM, stop=STOP_NONE, tol=0.0, Xref=None, trace=True, want_R=False, omp=False,
+          extended=False):
     """Run the oracle; returns a dict with X, iters, status and (if trace) the
     per-iteration traces rows, S, t, margin_adm, margin_pick, err2.  omp=True
-    runs the OpenMP build (same results, every host core; timing only)."""
+    runs the OpenMP build (same results, every host core; timing only).
+    extended=True: the least-squares extension (column steps on Y; want_R
+    also returns the final Y)."""
     A, B, C = map(_f64, (A, B, C))
     m, p = A.shape
     q, n = B.shape
@@ -173,11 +182,13 @@ def solve(A, B, C, variant="grbk", theta=0.5, alpha=None, X0=None, seed=0, sys=0
     Xr = None if Xref is None else _f64(Xref)
     R = np.empty((m, n)) if want_R else None
     s = np.empty(m) if want_R else None
+    Y = np.empty((m, n)) if (want_R and extended) else None
     st = ctypes.c_int(0)
     it = lib(omp).oracle_solve(_ptr(dims), _ptr(A), _ptr(B), _ptr(C), _ptr(X), v, float(theta),
                             float(alpha), int(seed), int(sys), int(maxit), int(mode), int(stop),
                             float(tol), _ptr(Xr), _ptr(rows), _ptr(S), _ptr(t), _ptr(madm),
-                            _ptr(mpick), _ptr(err2), _ptr(R), _ptr(s), ctypes.byref(st))
+                            _ptr(mpick), _ptr(err2), _ptr(R), _ptr(s), ctypes.byref(st), int(bool(extended)),
+                            _ptr(Y))
     out = dict(X=X, iters=int(it), status=int(st.value), alpha=float(alpha),
                loop_seconds=float(lib(omp).oracle_last_loop_seconds()))
     if trace:
@@ -187,4 +198,6 @@ def solve(A, B, C, variant="grbk", theta=0.5, alpha=None, X0=None, seed=0, sys=0
             out["err2"] = err2[:it + 1]
     if want_R:
         out.update(R=R, s=s)
+        if extended:
+            out["Y"] = Y
     return out

@@ -97,6 +97,14 @@ double oracle_uniform(uint64_t seed, uint64_t k, uint64_t sys)
     return (double)(out[0] >> 11) * 0x1.0p-53;
 }
 
+/* The extended method's column draw of iteration k: counter (k, sys, 1, 0). */
+double oracle_uniform_column(uint64_t seed, uint64_t k, uint64_t sys)
+{
+    uint64_t ctr[4] = {k, sys, 1, 0}, key[2] = {seed, 0}, out[4];
+    oracle_philox4x64_10(ctr, key, out);
+    return (double)(out[0] >> 11) * 0x1.0p-53;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense helpers (plain triple loops, ascending index order).               */
 /* ------------------------------------------------------------------------ */
@@ -207,6 +215,22 @@ enum { OR_RAN_MAXIT = 0, OR_TOL_MET = 1, OR_EXACT = 2, OR_NOT_CONVERGED = 3 };
  *             (for MWRBK: (r_max - second largest r) / r_max)
  *   tr_err2   ||X^k - Xref||_F^2, length maxit + 1 (needs Xref)
  * R_out (m x n) and s_out (m) receive the final residual and row norms.
+ *
+ * extended = 1: the inconsistent (least-squares, Eq. 2.1) extension, which the
+ * paper defines the target of but does not solve.  As in the randomized
+ * extended Kaczmarz method of Zouzias and Freris (SIAM J. Matrix Anal. Appl.,
+ * 2013) an auxiliary Y (m x n, Y^0 = C) is driven to (I - A A^+) C by column
+ * projections, and the row steps run on the residual R = C - Y - A X B of the
+ * consistent system A X B = C - Y:
+ *   at the start of iteration k < maxit, j_k = first column (ascending) whose
+ *   running sum of ||A_{:,j}||^2 exceeds u'_k ||A||_F^2, u'_k =
+ *   oracle_uniform_column(seed, k, sys); z = A_{:,j}^T Y (1 x n), g = z /
+ *   ||A_{:,j}||^2; Y -= A_{:,j} g and R += A_{:,j} g (R = C - Y - A X B);
+ *   then s_i, S, the stop tests (no stop on S = 0: R^0 = -A X^0 B may vanish
+ *   while Y still moves) and the row step of `variant` on R.
+ * When B has full column rank (B^+ B = I), X^k tends to A^+ C B^+ + (the part
+ * of X^0 in the null space), the least-squares solution of least norm.
+ * Y_out (m x n) receives the final Y (extended only).
  * Returns the number of iterations performed; *status gets OR_* status.
  */
 int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, const double* C,
@@ -214,7 +238,7 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
                      uint64_t sys, int64_t maxit, int mode, int stop_kind, double tol,
                      const double* Xref, int64_t* tr_rows, double* tr_S, double* tr_t,
                      double* tr_madm, double* tr_mpick, double* tr_err2, double* R_out,
-                     double* s_out, int* status)
+                     double* s_out, int* status, int extended, double* Y_out)
 {
     const int64_t m = dims[0], p = dims[1], q = dims[2], n = dims[3];
     if (variant == OR_GRBK) theta = 0.5;
@@ -228,6 +252,10 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
     double* h = (double*)malloc(sizeof(double) * (size_t)n);
     double* GA = NULL;
     double* GB = NULL;
+    double* Y = NULL;       /* extended: Y (m x n) */
+    double* cn = NULL;      /* extended: ||A_{:,j}||^2 */
+    double* zz = NULL;      /* extended: z / ||A_{:,j}||^2 (1 x n) */
+    double Fc = 0.0;        /* extended: sum_j ||A_{:,j}||^2 */
 
     oracle_row_sqnorms(m, p, A, a);
     double F = 0.0;
@@ -260,6 +288,20 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
         memcpy(R, C, sizeof(double) * (size_t)(m * n));
     else
         oracle_residual(m, p, q, n, A, X, B, C, R);
+    if (extended) {
+        /* Y^0 = C, R^0 = C - Y^0 - A X^0 B */
+        Y = (double*)malloc(sizeof(double) * (size_t)(m * n));
+        cn = (double*)malloc(sizeof(double) * (size_t)p);
+        zz = (double*)malloc(sizeof(double) * (size_t)n);
+        memcpy(Y, C, sizeof(double) * (size_t)(m * n));
+        for (int64_t i = 0; i < m * n; ++i) R[i] -= Y[i];
+        for (int64_t j = 0; j < p; ++j) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < m; ++i) acc += A[i * p + j] * A[i * p + j];
+            cn[j] = acc;
+            Fc += acc;
+        }
+    }
 
     int st =(stop_kind == OR_STOP_NONE) ? OR_RAN_MAXIT : OR_NOT_CONVERGED;
     double normC2 = 0.0;
@@ -271,6 +313,28 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
     const double t_loop = wall_seconds();
     int64_t k = 0;
     for (;; ++k) {
+        if (extended && k < maxit) {
+            /* column step: Y -= A_{:,j} (A_{:,j}^T Y) / ||A_{:,j}||^2, R moves the other way */
+            double target = oracle_uniform_column(seed, (uint64_t)k, sys) * Fc, run = 0.0;
+            int64_t j = -1, lastj = -1;
+            for (int64_t c = 0; c < p; ++c) {
+                if (cn[c] <= 0.0) continue;
+                run += cn[c];
+                lastj = c;
+                if (run > target) { j = c; break; }
+            }
+            if (j < 0) j = lastj;
+            for (int64_t l = 0; l < n; ++l) {
+                double acc = 0.0;
+                for (int64_t i = 0; i < m; ++i) acc += A[i * p + j] * Y[i * n + l];
+                zz[l] = acc / cn[j];
+            }
+            for (int64_t i = 0; i < m; ++i)
+                for (int64_t l = 0; l < n; ++l) {
+                    Y[i * n + l] -= A[i * p + j] * zz[l];
+                    R[i * n + l] += A[i * p + j] * zz[l];
+                }
+        }
         /* row norms and Frobenius norm of the current residual */
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < m; ++i) {
@@ -289,7 +353,7 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
             }
             if (tr_err2) tr_err2[k] = err2;
         }
-        if (S == 0.0) { st = OR_EXACT; break; }
+        if (S == 0.0 && !extended) { st = OR_EXACT; break; }
         if (stop_kind == OR_STOP_RELRES && sqrt(S) <= tol * sqrt(normC2)) { st = OR_TOL_MET; break; }
         if (stop_kind == OR_STOP_RSE && Xref && sqrt(err2) <= tol * sqrt(normXref2)) { st = OR_TOL_MET; break; }
         if (k >= maxit) break;
@@ -374,6 +438,8 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
 
         if (mode == OR_MODE_LITERAL) {
             oracle_residual(m, p, q, n, A, X, B, C, R);
+            if (extended)
+                for (int64_t i = 0; i < m * n; ++i) R[i] -= Y[i];
             continue;
         }
         if (mode == OR_MODE_GRAM) {
@@ -406,8 +472,9 @@ int64_t oracle_solve(const int64_t* dims, const double* A, const double* B, cons
     g_loop_seconds = wall_seconds() - t_loop;
     if (R_out) memcpy(R_out, R, sizeof(double) * (size_t)(m * n));
     if (s_out) memcpy(s_out, s, sizeof(double) * (size_t)m);
+    if (Y_out && Y) memcpy(Y_out, Y, sizeof(double) * (size_t)(m * n));
     if (status) *status = st;
     free(R); free(a); free(s); free(r); free(w); free(g); free(h);
-    free(GA); free(GB);
+    free(GA); free(GB); free(Y); free(cn); free(zz);
     return k;
 }

@@ -40,7 +40,8 @@ class grbk_opts(ctypes.Structure):
                 ("s_trace", ctypes.POINTER(ctypes.c_double)), ("trace_len", ctypes.c_int64),
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
-                ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double))]
+                ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double)),
+                ("extended", ctypes.c_int32)]
 
 
 class grbk_csr(ctypes.Structure):
@@ -233,7 +234,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None, band_limit=None, alphas=None):
+               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -258,6 +259,8 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.rank_tol = rank_tol
     if band_limit is not None:
         o.band_limit = band_limit
+    if extended is not None:
+        o.extended = int(bool(extended))
     if alphas is not None:
         keep.alphas = np.ascontiguousarray(alphas, dtype=np.float64)
         o.alphas = keep.alphas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

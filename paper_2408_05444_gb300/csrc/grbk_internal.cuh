@@ -114,13 +114,14 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
 
 // ----------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): key (seed, 0), counter
-// (k, sys, 0, 0); u = top 53 bits of the first output word times 2^-53.
+// (k, sys, stream, 0); u = top 53 bits of the first output word times 2^-53.
+// Stream 0 draws the row picks, stream 1 the extended method's columns.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t k, uint64_t sys)
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t k, uint64_t sys, uint64_t stream = 0)
 {
     const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
     const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-    uint64_t x0 = k, x1 = sys, x2 = 0, x3 = 0, k0 = seed, k1 = 0;
+    uint64_t x0 = k, x1 = sys, x2 = stream, x3 = 0, k0 = seed, k1 = 0;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint64_t hi0 = __umul64hi(M0, x0), lo0 = M0 * x0;

@@ -15,7 +15,10 @@
 //     nonzeros of A_{i_k} only, v = w B over the columns of B (CSC);
 //   * R -= c (A A_{i_k}^T) v touches only the rows k with (A A^T)_{k,i_k} != 0,
 //     read from the precomputed sparse Gram matrix A A^T (the practice note
-//     after Algorithm 3), and their s_k, r_k are recomputed.
+//     after Algorithm 3), and their s_k, r_k are recomputed;
+//   * the least-squares extension (Eq. 2.1) first projects column j of A out of
+//     an auxiliary Y, Y -= A_{:,j} (A_{:,j}^T Y) / ||A_{:,j}||^2, over the
+//     nonzeros of that column (CSC of A), and moves R = C - Y - A X B with it.
 // Every product and sum of w, v, u, the X and R updates, a_i and s_i is taken
 // in the oracle's order with explicitly rounded operations (no fused
 // multiply-add), so R, X and s follow the FP64 oracle bit for bit while the
@@ -50,8 +53,10 @@ struct SpDesc {
     long long bRow, bNz;       // B: CSR rowptr base (q + 1), entry base
     long long bCol;            // B: CSC colptr base (n + 1); CSC entries share bNz
     long long gRow, gNz;       // A A^T: rowptr base (m + 1), entry base
-    long long offR, offX, offRow, offBlk;
+    long long aCol;            // A: CSC colptr base (p + 1); CSC entries share aNz
+    long long offR, offX, offRow, offBlk, offCol;
     double F, alpha, stop_S, normC2;
+    double Fc;                 // sum of the column norms ||A_{:,j}||^2 (extended method)
 };
 
 struct SpParams {
@@ -63,6 +68,11 @@ struct SpParams {
     const long long* b_rowptr; const int* b_col; const double* b_val;     // CSR of B
     const long long* bc_colptr; const int* bc_row; const double* bc_val;  // CSC of B
     const long long* g_rowptr; const int* g_col; const double* g_val;     // A A^T (CSR)
+    const long long* ac_colptr; const int* ac_row; const double* ac_val;  // CSC of A
+    const double* cn;          // ||A_{:,j}||^2
+    const double* cpref;       // running sums of the nonzero column norms
+    double* Y;                 // extended method: Y (m x n)
+    int extended;
     const double* C;
     double* R;
     double* X;
@@ -231,9 +241,9 @@ __global__ void __launch_bounds__(kSpT) sp_gram_kernel(const long long* rowptr, 
 // One CTA per system: a_i = sum_c A_ic^2 (ascending, rounded products), their
 // running sums and F, ||C||_F^2, ||B||_2^2 by 200 power iterations on B B^T
 // (Rayleigh quotient; B^T x over the CSC, B t over the CSR), a non-finite flag.
-constexpr int kSpSetupScalars = 4;  // F, ||C||^2, lambda, bad
+constexpr int kSpSetupScalars = 5;  // F, ||C||^2, lambda, bad, sum of the column norms
 __global__ void __launch_bounds__(kSpT) sp_setup_kernel(SpParams P, double* a_out, double* pref_out,
-                                                        double* scalars)
+                                                        double* cn_out, double* cpref_out, double* scalars)
 {
     __shared__ double x[kSpMaxSide], t[kSpMaxSide], y[kSpMaxSide];
     __shared__ double red[kSpW + 1], red2[kSpW];
@@ -286,6 +296,26 @@ __global__ void __launch_bounds__(kSpT) sp_setup_kernel(SpParams P, double* a_ou
         }
         scalars[kSpSetupScalars * blockIdx.x + 0] = run;
         scalars[kSpSetupScalars * blockIdx.x + 1] = tt;
+    }
+    // ||A_{:,j}||^2 over the CSC of A (ascending rows) and their running sums
+    {
+        const long long* acp = P.ac_colptr + d.aCol;
+        const double* acv = P.ac_val + d.aNz;
+        double* cn = cn_out + d.offCol;
+        for (int j = threadIdx.x; j < d.p; j += kSpT) {
+            double acc = 0.0;
+            for (long long e = acp[j]; e < acp[j + 1]; ++e) acc = __dadd_rn(acc, __dmul_rn(acv[e], acv[e]));
+            cn[j] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double run = 0.0;
+            for (int j = 0; j < d.p; ++j) {
+                if (cn[j] > 0.0) run = __dadd_rn(run, cn[j]);
+                cpref_out[d.offCol + j] = run;
+            }
+            scalars[kSpSetupScalars * blockIdx.x + 4] = run;
+        }
     }
     for (int j = threadIdx.x; j < d.q; j += kSpT) x[j] = 1.0 / sqrt((double)d.q);
     __syncthreads();
@@ -368,7 +398,15 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
     const SpDesc d = P.sys[blockIdx.x];
     const double* C = P.C + d.offR;
     double* R = P.R + d.offR;
-    for (long long e = threadIdx.x; e < (long long)d.m * d.n; e += kSpT) R[e] = C[e];
+    if (P.extended) {   // Y^0 = C, R^0 = C - Y^0 (X^0 = 0)
+        double* Y = P.Y + d.offR;
+        for (long long e = threadIdx.x; e < (long long)d.m * d.n; e += kSpT) {
+            Y[e] = C[e];
+            R[e] = __dsub_rn(C[e], C[e]);
+        }
+    } else {
+        for (long long e = threadIdx.x; e < (long long)d.m * d.n; e += kSpT) R[e] = C[e];
+    }
     double* X = P.X + d.offX;
     for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += kSpT) X[e] = 0.0;
     __syncthreads();
@@ -389,7 +427,7 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
 __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
 {
     __shared__ double s_row[kSpMaxSide];      // R_{i_k}, then v
-    __shared__ double s_w[kSpMaxSide];
+    __shared__ double s_w[kSpMaxSide];        // w; the extended method's z / ||A_{:,j}||^2
     __shared__ double s_sj[kSpMaxBlocks];     // admitted sum per block
     __shared__ int s_anz_c[kSpMaxRowNnz];     // nonzeros of A_{i_k}
     __shared__ double s_anz_v[kSpMaxRowNnz];
@@ -397,7 +435,7 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
     __shared__ double red[kSpW + 1];
     __shared__ long long redk[kSpW];
     __shared__ int reda[kSpW];
-    __shared__ int s_sys, s_stop, s_pick, s_first_blk, s_last_blk;
+    __shared__ int s_sys, s_stop, s_pick, s_first_blk, s_last_blk, s_col;
     __shared__ double s_S, s_rmax, s_target;
     __shared__ int s_imax;
 
@@ -437,6 +475,72 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
         long long k = 0;
         int flag = FLAG_RUNNING;
         for (;;) {
+            // ---- extended method: project column j of A out of Y; R = C - Y - A X B follows
+            if (P.extended && k < P.maxit) {
+                if (threadIdx.x == 0) {
+                    const double* cpref = P.cpref + d.offCol;
+                    const double* cn = P.cn + d.offCol;
+                    const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid, 1), d.Fc);
+                    int lo = 0, hi = d.p;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (cpref[mid] > target) hi = mid; else lo = mid + 1;
+                    }
+                    if (lo >= d.p) {
+                        lo = d.p - 1;
+                        while (lo > 0 && !(cn[lo] > 0.0)) --lo;
+                    }
+                    s_col = lo;
+                }
+                __syncthreads();
+                const int j = s_col;
+                const long long cb = P.ac_colptr[d.aCol + j], ce = P.ac_colptr[d.aCol + j + 1];
+                const int* crw = P.ac_row + d.aNz;
+                const double* cvl = P.ac_val + d.aNz;
+                double* Y = P.Y + d.offR;
+                const double cnj = P.cn[d.offCol + j];
+                for (int l = threadIdx.x; l < d.n; l += kSpT) {
+                    double acc = 0.0;
+                    for (long long e = cb; e < ce; ++e)
+                        acc = __dadd_rn(acc, __dmul_rn(cvl[e], Y[(long long)crw[e] * d.n + l]));
+                    s_w[l] = __ddiv_rn(acc, cnj);
+                }
+                __syncthreads();
+                for (long long e = cb + threadIdx.x; e < ce; e += kSpT) {
+                    const int i = crw[e];
+                    const double av = cvl[e];
+                    double* Yi = Y + (long long)i * d.n;
+                    double* Ri = R + (long long)i * d.n;
+                    double acc = 0.0;
+                    for (int l = 0; l < d.n; ++l) {
+                        const double gl = __dmul_rn(av, s_w[l]);
+                        Yi[l] = __dsub_rn(Yi[l], gl);
+                        const double v = __dadd_rn(Ri[l], gl);
+                        Ri[l] = v;
+                        acc = __dadd_rn(acc, __dmul_rn(v, v));
+                    }
+                    s[i] = acc;
+                    r[i] = a[i] > 0.0 ? __ddiv_rn(acc, a[i]) : -INFINITY;
+                    const int b = i / kSpBlk;
+                    atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
+                }
+                __syncthreads();
+                {
+                    const int nw = (d.nb + 31) / 32;
+                    for (int wi = 0; wi < nw; ++wi) {
+                        unsigned bits = s_dirty[wi];
+                        int idx = 0;
+                        while (bits) {
+                            const int bit = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit);
+                            ++idx;
+                        }
+                    }
+                }
+                __syncthreads();
+                for (int b = threadIdx.x; b < (d.nb + 31) / 32; b += kSpT) s_dirty[b] = 0u;
+            }
             // ---- totals from the block summaries (fixed order) and the stop test
             {
                 double Sv = 0.0;
@@ -469,7 +573,7 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                     s_rmax = __longlong_as_double(bk);
                     s_imax = ba;
                     int stop = 0;
-                    if (!(S > 0.0)) stop = 2;
+                    if (!(S > 0.0) && !P.extended) stop = 2;   // the extension's R^0 = 0 while Y moves
                     else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
                     else if (k >= P.maxit) stop = 4;
                     s_stop = stop;
@@ -514,13 +618,13 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                     double SJ = 0.0;
                     int last = -1;
                     for (int b = 0; b < d.nb; ++b)
-                        if (s_sj[b] > 0.0) { SJ += s_sj[b]; last = b; }
+                        if (blk_key[b] >= tkey) { SJ += s_sj[b]; last = b; }
                     const double u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
                     const double target = __dmul_rn(u, SJ);
                     double run = 0.0;
                     int fb = -1;
                     for (int b = 0; b < d.nb; ++b) {
-                        if (!(s_sj[b] > 0.0)) continue;
+                        if (blk_key[b] < tkey) continue;
                         if (run + s_sj[b] > target) { fb = b; break; }
                         run += s_sj[b];
                     }
@@ -706,6 +810,9 @@ struct grbk_sparse {
     long long *a_rowptr = nullptr, *b_rowptr = nullptr, *bc_colptr = nullptr, *g_rowptr = nullptr;
     int *a_col = nullptr, *b_col = nullptr, *bc_row = nullptr, *g_col = nullptr;
     double *a_val = nullptr, *b_val = nullptr, *bc_val = nullptr, *g_val = nullptr;
+    long long* ac_colptr = nullptr;
+    int* ac_row = nullptr;
+    double *ac_val = nullptr, *cn = nullptr, *cpref = nullptr, *Y = nullptr;
     double *C = nullptr, *R = nullptr, *X = nullptr, *a = nullptr, *pref = nullptr, *s = nullptr, *r = nullptr;
     double* blk_sum = nullptr;
     long long* blk_key = nullptr;
@@ -724,7 +831,7 @@ extern "C" void grbk_sparse_destroy(grbk_sparse* b)
     void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->a_rowptr, b->b_rowptr, b->bc_colptr, b->g_rowptr,
                     b->a_col, b->b_col, b->bc_row, b->g_col, b->a_val, b->b_val, b->bc_val, b->g_val, b->C,
                     b->R, b->X, b->a, b->pref, b->s, b->r, b->blk_sum, b->blk_key, b->blk_arg, b->iters, b->S,
-                    b->flags, b->trace, b->traceS};
+                    b->flags, b->trace, b->traceS, b->ac_colptr, b->ac_row, b->ac_val, b->cn, b->cpref, b->Y};
     for (void* p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -773,14 +880,16 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
     b->opts = o;
     b->stream = (cudaStream_t)o.stream;
     b->hsys.resize(nsys);
-    long long oAR = 0, oAN = 0, oBR = 0, oBN = 0, oBC = 0, oGR = 0, oR = 0, oX = 0, oRow = 0, oBlk = 0;
+    long long oAR = 0, oAN = 0, oBR = 0, oBN = 0, oBC = 0, oGR = 0, oR = 0, oX = 0, oRow = 0, oBlk = 0, oAC = 0;
+    long long oCol = 0;
     for (int s = 0; s < nsys; ++s) {
         SpDesc& d = b->hsys[s];
         memset(&d, 0, sizeof(d));
         d.m = (int)A[s].rows; d.p = (int)A[s].cols; d.q = (int)B[s].rows; d.n = (int)B[s].cols;
         d.nb = (d.m + kSpBlk - 1) / kSpBlk;
         d.aRow = oAR; d.aNz = oAN; d.bRow = oBR; d.bNz = oBN; d.bCol = oBC; d.gRow = oGR;
-        d.offR = oR; d.offX = oX; d.offRow = oRow; d.offBlk = oBlk;
+        d.offR = oR; d.offX = oX; d.offRow = oRow; d.offBlk = oBlk; d.aCol = oAC; d.offCol = oCol;
+        oAC += d.p + 1; oCol += d.p;
         oAR += d.m + 1; oAN += A[s].nnz; oBR += d.q + 1; oBN += B[s].nnz; oBC += d.n + 1; oGR += d.m + 1;
         oR += (long long)d.m * d.n; oX += (long long)d.p * d.q; oRow += d.m; oBlk += d.nb;
     }
@@ -792,6 +901,8 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
               sp_alloc(&b->g_rowptr, oGR) && sp_alloc(&b->C, oR) && sp_alloc(&b->R, oR) && sp_alloc(&b->X, oX) &&
               sp_alloc(&b->a, oRow) && sp_alloc(&b->pref, oRow) && sp_alloc(&b->s, oRow) && sp_alloc(&b->r, oRow) &&
               sp_alloc(&b->blk_sum, oBlk) && sp_alloc(&b->blk_key, oBlk) && sp_alloc(&b->blk_arg, oBlk) &&
+              sp_alloc(&b->ac_colptr, oAC) && sp_alloc(&b->ac_row, oAN) && sp_alloc(&b->ac_val, oAN) &&
+              sp_alloc(&b->cn, oCol) && sp_alloc(&b->cpref, oCol) && (!o.extended || sp_alloc(&b->Y, oR)) &&
               sp_alloc(&b->dsys, nsys) && sp_alloc(&b->dorder, nsys) && sp_alloc(&b->dqueue, 1) &&
               sp_alloc(&b->iters, nsys) && sp_alloc(&b->S, nsys) && sp_alloc(&b->flags, nsys);
     if (!ok) { grbk_sparse_destroy(b); return GRBK_ENOMEM; }
@@ -804,13 +915,9 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
     long long maxdim = 1;
     for (int s = 0; s < nsys; ++s) maxdim = std::max<long long>({maxdim, (long long)A[s].cols + 1, (long long)A[s].rows + 1,
                                                                (long long)B[s].cols + 1});
-    std::vector<long long*> a_colptr(nsys, nullptr);
-    std::vector<int*> a_crow(nsys, nullptr);
-    std::vector<double*> a_cval(nsys, nullptr);
     grbk_status err = GRBK_OK;
     auto fail = [&](grbk_status e) {
         cudaStreamSynchronize(st);
-        for (int s = 0; s < nsys; ++s) { cudaFree(a_colptr[s]); cudaFree(a_crow[s]); cudaFree(a_cval[s]); }
         cudaFree(cnt);
         cudaFree(fill);
         grbk_sparse_destroy(b);
@@ -858,20 +965,21 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
         sp_csc_fill_kernel<<<grid, 256, 0, st>>>(b->b_rowptr + d.bRow, b->b_col + d.bNz, b->b_val + d.bNz, d.q,
                                                   b->bc_colptr + d.bCol, fill, b->bc_row + d.bNz, b->bc_val + d.bNz);
         sp_csc_sort_kernel<<<grid, 256, 0, st>>>(b->bc_colptr + d.bCol, d.n, b->bc_row + d.bNz, b->bc_val + d.bNz);
-        // A^T
-        if (!sp_alloc(&a_colptr[s], d.p + 1) || !sp_alloc(&a_crow[s], A[s].nnz) || !sp_alloc(&a_cval[s], A[s].nnz))
-            return fail(GRBK_ENOMEM);
+        // A^T (kept: the Gram matrix below and the extended method's column steps read it)
+        long long* a_colptr = b->ac_colptr + d.aCol;
+        int* a_crow = b->ac_row + d.aNz;
+        double* a_cval = b->ac_val + d.aNz;
         cudaMemsetAsync(cnt, 0, 8 * (d.p + 1), st);
         cudaMemsetAsync(fill, 0, 8 * (d.p + 1), st);
         sp_colcount_kernel<<<grid, 256, 0, st>>>(b->a_col + d.aNz, A[s].nnz, cnt);
-        sp_scan_kernel<<<1, kSpT, 0, st>>>(cnt, d.p, a_colptr[s]);
+        sp_scan_kernel<<<1, kSpT, 0, st>>>(cnt, d.p, a_colptr);
         sp_csc_fill_kernel<<<grid, 256, 0, st>>>(b->a_rowptr + d.aRow, b->a_col + d.aNz, b->a_val + d.aNz, d.m,
-                                                  a_colptr[s], fill, a_crow[s], a_cval[s]);
-        sp_csc_sort_kernel<<<grid, 256, 0, st>>>(a_colptr[s], d.p, a_crow[s], a_cval[s]);
+                                                  a_colptr, fill, a_crow, a_cval);
+        sp_csc_sort_kernel<<<grid, 256, 0, st>>>(a_colptr, d.p, a_crow, a_cval);
         // A A^T: entries per row, their offsets
         const int gb = std::max(1, std::min(1024, (d.m + kSpW - 1) / kSpW));
         sp_gram_kernel<<<gb, kSpT, 0, st>>>(b->a_rowptr + d.aRow, b->a_col + d.aNz, b->a_val + d.aNz, d.m,
-                                            a_colptr[s], a_crow[s], cnt, nullptr, nullptr, nullptr, 0);
+                                            a_colptr, a_crow, cnt, nullptr, nullptr, nullptr, 0);
         sp_scan_kernel<<<1, kSpT, 0, st>>>(cnt, d.m, b->g_rowptr + d.gRow);
         if (cudaGetLastError() != cudaSuccess) return fail(GRBK_ECUDA);
         long long gn = 0;
@@ -887,7 +995,7 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
         const SpDesc& d = b->hsys[s];
         const int gb = std::max(1, std::min(1024, (d.m + kSpW - 1) / kSpW));
         sp_gram_kernel<<<gb, kSpT, 0, st>>>(b->a_rowptr + d.aRow, b->a_col + d.aNz, b->a_val + d.aNz, d.m,
-                                            a_colptr[s], a_crow[s], nullptr, b->g_rowptr + d.gRow,
+                                            b->ac_colptr + d.aCol, b->ac_row + d.aNz, nullptr, b->g_rowptr + d.gRow,
                                             b->g_col + d.gNz, b->g_val + d.gNz, 1);
     }
     if (cudaGetLastError() != cudaSuccess) return fail(GRBK_ECUDA);
@@ -898,19 +1006,19 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
     P.a_rowptr = b->a_rowptr; P.a_col = b->a_col; P.a_val = b->a_val;
     P.b_rowptr = b->b_rowptr; P.b_col = b->b_col; P.b_val = b->b_val;
     P.bc_colptr = b->bc_colptr; P.bc_row = b->bc_row; P.bc_val = b->bc_val;
+    P.ac_colptr = b->ac_colptr; P.ac_row = b->ac_row; P.ac_val = b->ac_val;
     P.C = b->C;
     std::vector<double> sc(kSpSetupScalars * (size_t)nsys);
     double* dsc = nullptr;
     if (!sp_alloc(&dsc, sc.size())) return fail(GRBK_ENOMEM);
     cudaError_t e = cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SpDesc) * nsys, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
-        sp_setup_kernel<<<nsys, kSpT, 0, st>>>(P, b->a, b->pref, dsc);
+        sp_setup_kernel<<<nsys, kSpT, 0, st>>>(P, b->a, b->pref, b->cn, b->cpref, dsc);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc.data(), dsc, 8 * sc.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dsc);
-    for (int s = 0; s < nsys; ++s) { cudaFree(a_colptr[s]); cudaFree(a_crow[s]); cudaFree(a_cval[s]); a_colptr[s] = nullptr; a_crow[s] = nullptr; a_cval[s] = nullptr; }
     if (e != cudaSuccess) return fail(GRBK_ECUDA);
     for (int s = 0; s < nsys; ++s) {
         SpDesc& d = b->hsys[s];
@@ -920,6 +1028,7 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
         if (!(F > 0.0) || !(lam > 0.0)) return fail(GRBK_EINVAL);
         d.F = F;
         d.normC2 = x[1];
+        d.Fc = x[4];
         const double a_in = o.alphas ? o.alphas[s] : o.alpha;
         if (o.alphas || a_in > 0.0) {
             // Lemma 2.2 / Theorems 4.2-4.8 need 0 < alpha < 2/||B||_2^2
@@ -962,6 +1071,8 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
     if (variant < GRBK_GRBK || variant > GRBK_BK) return GRBK_EINVAL;
     if (variant == GRBK_RGRBK && !(theta > 0.0 && theta <= 1.0)) return GRBK_EINVAL;
     if (maxit < 0 || !std::isfinite(tol)) return GRBK_EINVAL;
+    // the extension's residual starts at zero: it runs a fixed number of iterations
+    if (b->opts.extended && (targets || b->opts.stop_kind != GRBK_STOP_NONE)) return GRBK_EINVAL;
     cudaStream_t st = b->stream;
     for (int s = 0; s < b->nsys; ++s) {
         SpDesc& d = b->hsys[s];
@@ -984,6 +1095,8 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
     P.b_rowptr = b->b_rowptr; P.b_col = b->b_col; P.b_val = b->b_val;
     P.bc_colptr = b->bc_colptr; P.bc_row = b->bc_row; P.bc_val = b->bc_val;
     P.g_rowptr = b->g_rowptr; P.g_col = b->g_col; P.g_val = b->g_val;
+    P.ac_colptr = b->ac_colptr; P.ac_row = b->ac_row; P.ac_val = b->ac_val;
+    P.cn = b->cn; P.cpref = b->cpref; P.Y = b->Y; P.extended = b->opts.extended ? 1 : 0;
     P.C = b->C; P.R = b->R; P.X = b->X; P.a = b->a; P.pref = b->pref; P.s = b->s; P.r = b->r;
     P.blk_sum = b->blk_sum; P.blk_key = b->blk_key; P.blk_arg = b->blk_arg;
     P.iters = b->iters; P.S_out = b->S; P.flag_out = b->flags;

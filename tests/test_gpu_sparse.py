@@ -48,14 +48,15 @@ def _live(orc, floor=1e-20):
     return int(dead[0]) if len(dead) else len(S)
 
 
-def _check_parity(A_sp, Ad, B, C, variant, theta, K=1000, seed=5):
-    """A_sp: what the library gets for A (CSR triple or dense), Ad its dense copy."""
+def _check_parity(A_sp, Ad, B_sp, B, C, variant, theta, K=1000, seed=5):
+    """A_sp, B_sp: what the library gets (scipy CSR, a CSR triple or dense); Ad, B
+    their dense copies for the oracle."""
     al = 1.0 / np.linalg.norm(B, 2) ** 2
     if isinstance(A_sp, tuple):
         import scipy.sparse as sps
         rp, ci, v = A_sp
         A_sp = sps.csr_matrix((v, ci, rp), shape=Ad.shape)
-    sp = g.grbk_sparse_create([A_sp], [B], [C], alphas=[al], trace_len=K)
+    sp = g.grbk_sparse_create([A_sp], [B_sp], [C], alphas=[al], trace_len=K)
     X = np.zeros((Ad.shape[1], B.shape[0]))
     st, res = g.grbk_sparse_solve(sp, variant, theta=theta, maxit=K, seed=seed, X_outs=[X])
     assert st == g.GRBK_OK and res[0]["iters"] == K and res[0]["alpha"] == al
@@ -80,7 +81,7 @@ def _check_parity(A_sp, Ad, B, C, variant, theta, K=1000, seed=5):
 def test_sparse_sets_match_oracle(name, variant, theta):
     A, B, C, Xs = workloads.sparse_set(name)
     import scipy.sparse as sps
-    _check_parity(sps.csr_matrix(A), A, sps.csr_matrix(B), C, variant, theta)
+    _check_parity(sps.csr_matrix(A), A, sps.csr_matrix(B), B, C, variant, theta)
 
 
 def test_sparse_sets_reach_the_least_norm_solution():
@@ -104,7 +105,7 @@ def test_sparse_sets_reach_the_least_norm_solution():
 def test_colour_model_small_image_matches_oracle(variant, theta):
     d = workloads.colour_model(24, 20, seed=3, noise=1e-3)
     Ad = workloads.csr_to_dense(*d["A"], 24 * 20)
-    _check_parity(d["A"], Ad, d["B"], d["C"], variant, theta)
+    _check_parity(d["A"], Ad, d["B"], d["B"], d["C"], variant, theta)
 
 
 def test_colour_model_at_the_papers_sizes():
@@ -135,3 +136,62 @@ def test_colour_model_at_the_papers_sizes():
         print(f"\n{d['h']}x{d['w']}: PSNR {p0:.2f} -> {p1:.2f} dB, SSIM {s0:.3f} -> {s1:.3f}")
         assert p1 > p0 + 3.0
         assert -1.0 <= s1 <= 1.0
+
+
+def _ls_sparse_system(seed=0, noise=0.05):
+    """An inconsistent sparse system: A 210 x 20 at 5 % (Table 3 set 3's A:
+    full column rank, m > p) and B 125 x 40 at 5 % (Table 5 set 3's B: full
+    column rank, so B^+ B = I), C = A X* B + noise N(0, noise^2) -- the noise
+    leaves the range of A, so no X solves A X B = C (Eq. 2.1)."""
+    g0 = np.random.default_rng(900 + seed)
+    A = workloads.sprand_gaussian(g0, 210, 20, 0.05)
+    B = workloads.sprand_gaussian(g0, 125, 40, 0.05)
+    Xs = g0.standard_normal((20, 125))
+    C = A @ Xs @ B + noise * g0.standard_normal((210, 40))
+    return A, B, C
+
+
+@pytest.mark.parametrize("variant,theta", VARIANTS)
+def test_extended_matches_oracle(variant, theta):
+    """The least-squares extension against the oracle's restatement of it: the
+    same rows, column draws (Philox counter (k, system, 1, 0)) and, to the last
+    bits, X, R = C - Y - A X B and the row norms over 1000 iterations."""
+    import scipy.sparse as sps
+    A, B, C = _ls_sparse_system()
+    al = 1.0 / np.linalg.norm(B, 2) ** 2
+    K = 1000
+    sp = g.grbk_sparse_create([sps.csr_matrix(A)], [sps.csr_matrix(B)], [C], alphas=[al], trace_len=K,
+                              extended=True)
+    X = np.zeros((20, 125))
+    st, res = g.grbk_sparse_solve(sp, variant, theta=theta, maxit=K, seed=8, X_outs=[X])
+    assert st == g.GRBK_OK and res[0]["iters"] == K
+    R, s = g.grbk_sparse_get_residual(sp, 0, 210, 40)
+    rows = sp.row_trace[0].astype(np.int64)
+    Sg = sp.s_trace[0]
+    g.grbk_sparse_destroy(sp)
+    orc = oracle.solve(A, B, C, variant, theta=theta, alpha=al, seed=8, maxit=K, mode=oracle.MODE_FACTORED,
+                       want_R=True, extended=True)
+    assert np.array_equal(rows, orc["rows"])
+    ok = orc["S"] > 0
+    assert np.max(np.abs(Sg[ok] - orc["S"][ok]) / orc["S"][ok]) < 1e-12
+    assert _rel(X, orc["X"]) < 1e-12
+    assert _rel(R, orc["R"]) < 1e-12
+    assert _rel(s, orc["s"]) < 1e-12
+
+
+def test_extended_reaches_least_squares_solution():
+    """With B of full column rank the extension tends to the least-squares
+    solution of least norm A^+ C B^+ (numpy's pinv); the paper's iteration on
+    the same inconsistent system stalls at an error floor."""
+    import scipy.sparse as sps
+    A, B, C = _ls_sparse_system(seed=1)
+    Xls = np.linalg.pinv(A) @ C @ np.linalg.pinv(B)
+    out = {}
+    for ext in (True, False):
+        sp = g.grbk_sparse_create([sps.csr_matrix(A)], [sps.csr_matrix(B)], [C], extended=ext)
+        X = np.zeros((20, 125))
+        g.grbk_sparse_solve(sp, "grbk", maxit=100_000, seed=3, X_outs=[X])
+        g.grbk_sparse_destroy(sp)
+        out[ext] = np.linalg.norm(X - Xls) / np.linalg.norm(Xls)
+    assert out[True] < 1e-8, out
+    assert out[False] > 1e-4, out

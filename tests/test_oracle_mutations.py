@@ -27,7 +27,11 @@ MUTANTS = {
     "gram_offdiagonal_halved": ("acc += A[i * p + c] * A[j * p + c];\n                GA[i * m + j] = acc;",
                                 "acc += A[i * p + c] * A[j * p + c] * (i == j ? 1.0 : 0.5);\n                GA[i * m + j] = acc;"),
     "philox_swapped_words": ("uint64_t y0 = hi1 ^ x1 ^ k0;", "uint64_t y0 = hi0 ^ x1 ^ k0;"),
-    "uniform_low_bits": ("(double)(out[0] >> 11) * 0x1.0p-53", "(double)(out[1] >> 11) * 0x1.0p-53"),
+    "uniform_low_bits": ("(double)(out[0] >> 11) * 0x1.0p-53;\n}\n\n/* The extended",
+                         "(double)(out[1] >> 11) * 0x1.0p-53;\n}\n\n/* The extended"),
+    "extended_residual_sign": ("R[i * n + l] += A[i * p + j] * zz[l];", "R[i * n + l] -= A[i * p + j] * zz[l];"),
+    "extended_column_step_sign": ("Y[i * n + l] -= A[i * p + j] * zz[l];", "Y[i * n + l] += A[i * p + j] * zz[l];"),
+    "extended_column_stream": ("uint64_t ctr[4] = {k, sys, 1, 0}", "uint64_t ctr[4] = {k, sys, 0, 0}"),
     "pick_first_not_exceeding": ("if (ik < 0 && run > target) ik = i;\n            }\n            if (ik < 0) ik = last;\n        } else if (variant == OR_MWRBK)",
                                  "if (ik < 0 && run >= 0.5 * target) ik = i;\n            }\n            if (ik < 0) ik = last;\n        } else if (variant == OR_MWRBK)"),
 }

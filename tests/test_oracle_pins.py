@@ -390,3 +390,66 @@ def test_stop_rules():
     assert np.linalg.norm(C - A @ r["X"] @ B) <= 1e-8 * np.linalg.norm(C) * (1 + 1e-6)
     r0 = oracle.solve(A, B, np.zeros_like(C), "grbk", alpha=_alpha(B), maxit=10)
     assert r0["status"] == oracle.EXACT and r0["iters"] == 0
+
+
+# ------------------------------------------- least-squares extension (Eq. 2.1)
+
+def _ls_system(seed=0, noise=0.1):
+    """A 60x20 (full column rank), B 30x10 (full column rank, so B^+ B = I),
+    C = A X* B + noise E with E generic: inconsistent on the side of A."""
+    g = np.random.default_rng(700 + seed)
+    A = g.standard_normal((60, 20))
+    B = g.standard_normal((30, 10))
+    Xs = g.standard_normal((20, 30))
+    C = A @ Xs @ B + noise * g.standard_normal((60, 10))
+    return A, B, C
+
+
+def test_column_draw_matches_numpy_random():
+    """The extended method's column draw is numpy's Philox block for counter
+    (k, sys, 1, 0) -- word 2 of the counter selects the second stream."""
+    for seed, k, sys in [(5, 0, 0), (99, 1234, 7), (2**40 + 3, 77, 191)]:
+        c = k | (sys << 64) | (1 << 128)
+        prev = (c - 1) % (1 << 256)
+        words = np.array([(prev >> (64 * i)) & (2**64 - 1) for i in range(4)], dtype=np.uint64)
+        bg = np.random.Philox(counter=words, key=np.array([seed, 0], dtype=np.uint64))
+        want = (int(bg.random_raw(4)[0]) >> 11) * 2.0 ** -53
+        assert oracle.uniform_column(seed, k, sys) == want
+
+
+@pytest.mark.parametrize("variant,theta", [("grbk", 0.5), ("rgrbk", 0.8), ("mwrbk", 1.0), ("rbk", 0.5)])
+def test_extended_reaches_least_squares_solution(variant, theta):
+    """Eq. 2.1: with B of full column rank the extended iteration tends to the
+    least-squares solution of least norm A^+ C B^+ (numpy's pinv), while the
+    plain iteration on the same inconsistent system stalls at an error floor."""
+    A, B, C = _ls_system()
+    Xls = pinv(A) @ C @ pinv(B)
+    ext = oracle.solve(A, B, C, variant, theta=theta, alpha=_alpha(B), seed=3, maxit=60000,
+                       mode=oracle.MODE_FACTORED, extended=True, trace=False, want_R=True)
+    assert _rel(ext["X"], Xls) < 1e-8
+    # the auxiliary matrix is the part of C outside the range of A: (I - A A^+) C
+    assert _rel(ext["Y"], C - A @ pinv(A) @ C) < 1e-8
+    plain = oracle.solve(A, B, C, variant, theta=theta, alpha=_alpha(B), seed=3, maxit=60000,
+                         mode=oracle.MODE_FACTORED, trace=False)
+    assert _rel(plain["X"], Xls) > 1e-3
+
+
+def test_extended_residual_definition_and_consistent_case():
+    """The kept residual of the extended iteration is C - Y - A X B (recursive
+    and literal modes agree row for row); on a consistent system it reaches the
+    solution like the plain method and Y tends to zero."""
+    A, B, C = _ls_system(seed=1)
+    for maxit in (1, 7, 300):
+        f = oracle.solve(A, B, C, "grbk", alpha=_alpha(B), seed=4, maxit=maxit, mode=oracle.MODE_FACTORED,
+                         extended=True, want_R=True)
+        lit = oracle.solve(A, B, C, "grbk", alpha=_alpha(B), seed=4, maxit=maxit, mode=oracle.MODE_LITERAL,
+                           extended=True, want_R=True)
+        assert np.array_equal(f["rows"], lit["rows"])
+        assert np.max(np.abs(f["R"] - (C - f["Y"] - A @ f["X"] @ B))) < 1e-12 * np.max(np.abs(C))
+        assert np.max(np.abs(f["R"] - lit["R"])) < 1e-12 * np.max(np.abs(C))
+    A, B, C0 = _ls_system(seed=2, noise=0.0)
+    Xs = pinv(A) @ C0 @ pinv(B)
+    ext = oracle.solve(A, B, C0, "grbk", alpha=_alpha(B), seed=5, maxit=60000, mode=oracle.MODE_FACTORED,
+                       extended=True, want_R=True, trace=False)
+    assert _rel(ext["X"], Xs) < 1e-8
+    assert np.linalg.norm(ext["Y"]) < 1e-8 * np.linalg.norm(C0)
