@@ -627,20 +627,34 @@ def batch_bench(args):
     sy = workloads.blur_systems(n_images=args.batch_images, min_side=128, max_side=512, seed=13, processes=procs)
     As, Bs, Cs = [q["A"] for q in sy], [q["B"] for q in sy], [q["C"] for q in sy]
     targets = ws.DISCREPANCY_TAU * np.array([np.linalg.norm(q["E"]) for q in sy])
-    b = g.grbk_batch_create(As, Bs, Cs)
-    X = [np.zeros((A.shape[1], B.shape[0])) for A, B in zip(As, Bs)]
-    g.grbk_batch_solve(b, "grbk", targets=targets, maxit=min(args.batch_maxit, 64), seed=1, X_outs=X)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st, res = g.grbk_batch_solve(b, "grbk", targets=targets, maxit=args.batch_maxit, seed=1, X_outs=X)
-    el = time.perf_counter() - t0
-    its = np.array([r["iters"] for r in res])
     work = np.array([A.shape[0] * B.shape[1] for A, B in zip(As, Bs)])
-    psnr = np.mean([10 * np.log10(1.0 / np.mean((np.clip(x, 0, 1) - q["X"]) ** 2)) for x, q in zip(X, sy)])
-    out = {"mode": "batch", "systems": len(sy), "status": g.grbk_strerror(st), "seconds": el,
-           "iters_total": int(its.sum()), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
-           "system_iters_per_s": float(its.sum() / el), "residual_elements_per_s": float((its * work).sum() / el),
-           "stopped_by_rule": int(sum(1 for r in res if r["status"] == 0)), "psnr_db": float(psnr)}
+
+    def timed(tune):
+        t0 = time.perf_counter()
+        b = g.grbk_batch_create(As, Bs, Cs, tune=tune)
+        create_s = time.perf_counter() - t0
+        X = [np.zeros((A.shape[1], B.shape[0])) for A, B in zip(As, Bs)]
+        g.grbk_batch_solve(b, "grbk", targets=targets, maxit=min(args.batch_maxit, 64), seed=1, X_outs=X)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, res = g.grbk_batch_solve(b, "grbk", targets=targets, maxit=args.batch_maxit, seed=1, X_outs=X)
+        el = time.perf_counter() - t0
+        its = np.array([r["iters"] for r in res])
+        psnr = np.mean([10 * np.log10(1.0 / np.mean((np.clip(x, 0, 1) - q["X"]) ** 2)) for x, q in zip(X, sy)])
+        variants = [g.grbk_batch_variant(b, s)[0] for s in range(len(sy))]
+        tune_s = g.grbk_batch_variant(b, 0)[1]
+        g.grbk_batch_destroy(b)
+        return {"status": g.grbk_strerror(st), "seconds": el, "create_s": create_s, "tune_s": tune_s,
+                "iters_total": int(its.sum()), "iters_mean": float(its.mean()), "iters_max": int(its.max()),
+                "system_iters_per_s": float(its.sum() / el), "residual_elements_per_s": float((its * work).sum() / el),
+                "stopped_by_rule": int(sum(1 for r in res if r["status"] == 0)), "psnr_db": float(psnr),
+                "variants_used": {str(v): variants.count(v) for v in sorted(set(variants))}}
+
+    g.grbk_tune_clear()
+    default = timed(False)
+    tuned = timed(True)
+    out = {"mode": "batch", "systems": len(sy), "variants": g.grbk_tune_variants(), "default": default,
+           "autotuned": tuned, "speedup": default["seconds"] / tuned["seconds"]}
     print(json.dumps(out), flush=True)
 
 

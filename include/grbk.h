@@ -112,6 +112,9 @@ typedef struct {
                              replaces `alpha`.  NULL: `alpha` (when > 0) or 1/||B_s||_2^2 for every system */
     int32_t extended;     /* sparse solver: 1 = least-squares extension for inconsistent systems (Eq. 2.1;
                              see grbk_sparse_create); 0 = the paper's iteration */
+    int32_t tune;         /* batched solver: 1 = choose each system's kernel variant by timing the compiled
+                             variants on it (grbk_tune_*; choices kept per system shape for the process);
+                             0 = the default variant (512 threads, two rows per warp) for every system */
 } grbk_opts;
 
 typedef struct {
@@ -229,6 +232,37 @@ grbk_status grbk_batch_solve(grbk_batch* batch, int32_t variant, double theta, c
 grbk_status grbk_batch_info(const grbk_batch* b, int32_t sys, int32_t* bandA, int32_t* bandB);
 
 void grbk_batch_destroy(grbk_batch* batch);
+
+/*
+ * Batch autotuner (not part of the paper; Section 6's application solves many
+ * systems of uneven sizes).  The batched kernel is compiled in several
+ * variants (threads per CTA, rows of R per warp in the fused update pass) that
+ * compute the same iteration and differ only in the summation order of the
+ * FP64 totals.  With opts.tune = 1, grbk_batch_create times every variant on
+ * one system of each class (sides rounded up to multiples of 64, exact
+ * half-bandwidths) not yet in the process-wide cache -- ME-GRBK, 48
+ * iterations from R = C, CUDA events -- and keeps the fastest (a variant
+ * within 2 % of it that uses fewer threads wins).  Solves then launch one
+ * kernel per variant in use, side by side on the batch's own streams.
+ *
+ * grbk_tune_num_variants / grbk_tune_variant_info: the compiled variants.
+ * grbk_tune_choose: the rule applied to one class's timings (ms[v] for each of
+ *   the grbk_tune_num_variants() variants; entries <= 0 or non-finite are
+ *   ignored); returns the variant, or -1 for a wrong count.
+ * grbk_tune_lookup / grbk_tune_store / grbk_tune_clear: the cache (variant -1
+ *   when the class is absent).  Thread-safe.
+ * grbk_batch_variant: the variant a system of a batch runs and the seconds
+ *   the batch's tuning took.
+ */
+int32_t grbk_tune_num_variants(void);
+grbk_status grbk_tune_variant_info(int32_t variant, int32_t* threads, int32_t* rows_per_warp);
+int32_t grbk_tune_choose(const double* ms, int32_t nvariants);
+grbk_status grbk_tune_lookup(int32_t m, int32_t p, int32_t q, int32_t n, int32_t bandA, int32_t bandB,
+                             int32_t* variant);
+grbk_status grbk_tune_store(int32_t m, int32_t p, int32_t q, int32_t n, int32_t bandA, int32_t bandB,
+                            int32_t variant);
+void grbk_tune_clear(void);
+grbk_status grbk_batch_variant(const grbk_batch* batch, int32_t sys, int32_t* variant, double* tune_seconds);
 
 /*
  * Sparse A and B: nsys independent systems A_s X_s B_s = C_s with A_s and B_s

@@ -41,7 +41,7 @@ class grbk_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
                 ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double)),
-                ("extended", ctypes.c_int32)]
+                ("extended", ctypes.c_int32), ("tune", ctypes.c_int32)]
 
 
 class grbk_csr(ctypes.Structure):
@@ -71,7 +71,9 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
            "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_sparse_create",
-           "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy"]
+           "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy",
+           "grbk_tune_num_variants", "grbk_tune_variant_info", "grbk_tune_choose", "grbk_tune_lookup",
+           "grbk_tune_store", "grbk_tune_clear", "grbk_batch_variant"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -146,6 +148,20 @@ def lib():
         L.grbk_sparse_get_residual.restype = i32
         L.grbk_sparse_destroy.argtypes = [vp]
         L.grbk_sparse_destroy.restype = None
+        L.grbk_tune_num_variants.argtypes = []
+        L.grbk_tune_num_variants.restype = i32
+        L.grbk_tune_variant_info.argtypes = [i32, P(i32), P(i32)]
+        L.grbk_tune_variant_info.restype = i32
+        L.grbk_tune_choose.argtypes = [P(dbl), i32]
+        L.grbk_tune_choose.restype = i32
+        L.grbk_tune_lookup.argtypes = [i32, i32, i32, i32, i32, i32, P(i32)]
+        L.grbk_tune_lookup.restype = i32
+        L.grbk_tune_store.argtypes = [i32, i32, i32, i32, i32, i32, i32]
+        L.grbk_tune_store.restype = i32
+        L.grbk_tune_clear.argtypes = []
+        L.grbk_tune_clear.restype = None
+        L.grbk_batch_variant.argtypes = [vp, i32, P(i32), P(dbl)]
+        L.grbk_batch_variant.restype = i32
         L.grbk_fp64_probe.argtypes = [i64, i32, P(dbl), P(dbl), vp]
         L.grbk_fp64_probe.restype = i32
         L.grbk_strerror.argtypes = [i32]
@@ -234,7 +250,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None):
+               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None, tune=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -261,6 +277,8 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.band_limit = band_limit
     if extended is not None:
         o.extended = int(bool(extended))
+    if tune is not None:
+        o.tune = int(bool(tune))
     if alphas is not None:
         keep.alphas = np.ascontiguousarray(alphas, dtype=np.float64)
         o.alphas = keep.alphas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -725,3 +743,48 @@ def grbk_sparse_destroy(sp: Sparse):
     if sp.handle:
         lib().grbk_sparse_destroy(sp.handle)
         sp.handle = None
+
+
+# ---------------------------------------------------------------------------
+# batch autotuner
+# ---------------------------------------------------------------------------
+def grbk_tune_variants():
+    """-> list of (threads per CTA, rows per warp) of the compiled batched-kernel variants."""
+    out = []
+    for v in range(lib().grbk_tune_num_variants()):
+        t, r = ctypes.c_int32(), ctypes.c_int32()
+        lib().grbk_tune_variant_info(v, ctypes.byref(t), ctypes.byref(r))
+        out.append((t.value, r.value))
+    return out
+
+
+def grbk_tune_choose(ms):
+    a = np.ascontiguousarray(ms, dtype=np.float64)
+    return int(lib().grbk_tune_choose(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(a)))
+
+
+def grbk_tune_lookup(m, p, q, n, bandA=-1, bandB=-1):
+    v = ctypes.c_int32()
+    st = lib().grbk_tune_lookup(m, p, q, n, bandA, bandB, ctypes.byref(v))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_tune_lookup")
+    return v.value
+
+
+def grbk_tune_store(m, p, q, n, bandA, bandB, variant):
+    st = lib().grbk_tune_store(m, p, q, n, bandA, bandB, int(variant))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_tune_store")
+
+
+def grbk_tune_clear():
+    lib().grbk_tune_clear()
+
+
+def grbk_batch_variant(batch: Batch, sys: int):
+    """-> (variant index of system `sys`, seconds the batch's tuning took)."""
+    v, t = ctypes.c_int32(), ctypes.c_double()
+    st = lib().grbk_batch_variant(batch.handle, int(sys), ctypes.byref(v), ctypes.byref(t))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_batch_variant")
+    return v.value, t.value

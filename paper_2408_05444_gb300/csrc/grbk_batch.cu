@@ -15,6 +15,7 @@
 #include <climits>
 #include <cmath>
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -70,7 +71,8 @@ struct BatchParams {
 };
 
 // block-wide sum in a fixed order; one thread adds the warp partials (FP64 is
-// 1/64 of the FP32 rate here, so it is kept off the other 511 threads)
+// 1/64 of the FP32 rate here, so it is kept off the other threads)
+template <int NW = kBW>
 __device__ __forceinline__ double block_sum_fixed(double v, double* red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -80,23 +82,31 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red)
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kBW; ++w) t += red[w];
-        red[kBW] = t;
+        for (int w = 0; w < NW; ++w) t += red[w];
+        red[NW] = t;
     }
     __syncthreads();
-    const double t = red[kBW];
+    const double t = red[NW];
     __syncthreads();
     return t;
 }
 
 // X += sum_t c_t A_{i_t}^T w_t over the recorded terms (FP32), as a small GEMM
-// over tiles of 64 rows x 128 columns of X with the chunk's terms staged in
-// shared memory: sa[t][r] = c_t A[i_t][r0 + r], sw[t][j] = w_t[j0 + j].
-constexpr int kFoldRows = 64, kFoldCols = 128, kMaxChunk = 64;
-constexpr int kFoldSmemBytes = kMaxChunk * (kFoldRows + kFoldCols) * 4;
+// over tiles of NT/8 rows x 128 columns of X (each thread two rows and eight
+// columns) with the chunk's terms staged in shared memory:
+// sa[t][r] = c_t A[i_t][r0 + r], sw[t][j] = w_t[j0 + j].  Every element of X
+// sums its terms in the same order t = 0, 1, ... for every CTA size.
+constexpr int kFoldCols = 128, kMaxChunk = 64;
+template <int NT> struct FoldCfg {
+    static constexpr int ROWS = NT / 8;
+    static constexpr int SMEM_BYTES = kMaxChunk * (ROWS + kFoldCols) * 4;
+};
+constexpr int kFoldSmemBytes = FoldCfg<kBB>::SMEM_BYTES;
 
+template <int NT>
 __device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh, float* fsm)
 {
+    constexpr int kFoldRows = FoldCfg<NT>::ROWS;
     if (nh <= 0) return;
     const float* A = P.A + d.offA;
     const int* hr = P.hist_rows + d.offHist;
@@ -108,12 +118,12 @@ __device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh, float
     const int tr = threadIdx.x / 16, tcol = threadIdx.x % 16;  // rows 2tr, 2tr+1; cols tcol + 16k
     __syncthreads();
     for (int r0 = 0; r0 < d.p; r0 += kFoldRows) {
-        for (int e = threadIdx.x; e < nh * kFoldRows; e += kBB) {
+        for (int e = threadIdx.x; e < nh * kFoldRows; e += NT) {
             const int t = e / kFoldRows, r = e % kFoldRows;
             sa[e] = (r0 + r < d.p) ? hc[t] * A[(long long)hr[t] * d.lda + r0 + r] : 0.f;
         }
         for (int j0 = 0; j0 < d.q; j0 += kFoldCols) {
-            for (int e = threadIdx.x; e < nh * kFoldCols; e += kBB) {
+            for (int e = threadIdx.x; e < nh * kFoldCols; e += NT) {
                 const int t = e / kFoldCols, j = e % kFoldCols;
                 sw[e] = (j0 + j < d.q) ? hw[(long long)t * d.q + j0 + j] : 0.f;
             }
@@ -150,12 +160,12 @@ __device__ void batch_fold(const BatchParams& P, const SysDesc& d, int nh, float
 // dst[r] = X_r . y for rows r < rows (rows of nv float4 vectors, stride ldx
 // floats); y in shared memory.  Each warp takes RP rows at a time, so a lane
 // has RP independent vector loads in flight per step.
-template <int RP>
+template <int RP, int NW>
 __device__ __forceinline__ void batch_rows_dot(const float* X, int ldx, int rows, int nv, const float* y, float* dst)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* y4 = reinterpret_cast<const float4*>(y);
-    for (int r0 = warp * RP; r0 < rows; r0 += kBW * RP) {
+    for (int r0 = warp * RP; r0 < rows; r0 += NW * RP) {
         float acc[RP];
 #pragma unroll
         for (int k = 0; k < RP; ++k) acc[k] = 0.f;
@@ -295,27 +305,29 @@ __global__ void __launch_bounds__(kBB) batch_setup_kernel(const SysDesc* sys, co
 }
 
 // R_i -= coef[i - rb] v for rows [rb, re), fused with the new s_i = ||R_i||^2
-// (Kahan FP32 per lane, double-float across lanes) and r_i = s_i / a_i; two rows
-// per warp, float4 columns.  v has ldr entries (padding zero).
+// (Kahan FP32 per lane, double-float across lanes) and r_i = s_i / a_i; RPW rows
+// per warp at a time, float4 columns.  v has ldr entries (padding zero).
+template <int NW, int RPW>
 __device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int re, const float* coef,
                                                   const float* v, const double* a, double* s_s, double* s_r)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* v4 = reinterpret_cast<const float4*>(v);
     const int nv = ldr / 4;
-    for (int i0 = rb + 2 * warp; i0 < re; i0 += 2 * kBW) {
-        float acc[2] = {0.f, 0.f}, comp[2] = {0.f, 0.f};
-        float cf[2];
+    for (int i0 = rb + RPW * warp; i0 < re; i0 += RPW * NW) {
+        float acc[RPW], comp[RPW], cf[RPW];
 #pragma unroll
-        for (int k2 = 0; k2 < 2; ++k2) cf[k2] = (i0 + k2 < re) ? coef[i0 + k2 - rb] : 0.f;
+        for (int k2 = 0; k2 < RPW; ++k2) { acc[k2] = 0.f; comp[k2] = 0.f; }
+#pragma unroll
+        for (int k2 = 0; k2 < RPW; ++k2) cf[k2] = (i0 + k2 < re) ? coef[i0 + k2 - rb] : 0.f;
         for (int e = lane; e < nv; e += 32) {
-            float4 rv[2];
+            float4 rv[RPW];
 #pragma unroll
-            for (int k2 = 0; k2 < 2; ++k2)
+            for (int k2 = 0; k2 < RPW; ++k2)
                 if (i0 + k2 < re) rv[k2] = reinterpret_cast<float4*>(R + (long long)(i0 + k2) * ldr)[e];
             const float4 vv = v4[e];
 #pragma unroll
-            for (int k2 = 0; k2 < 2; ++k2) {
+            for (int k2 = 0; k2 < RPW; ++k2) {
                 if (i0 + k2 >= re) continue;
                 float* x = reinterpret_cast<float*>(&rv[k2]);
                 const float* y = reinterpret_cast<const float*>(&vv);
@@ -331,7 +343,7 @@ __device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int
             }
         }
 #pragma unroll
-        for (int k2 = 0; k2 < 2; ++k2) {
+        for (int k2 = 0; k2 < RPW; ++k2) {
             float hi = acc[k2], lo = -comp[k2];
             warp_sum_df(hi, lo);
             if (lane == 0 && i0 + k2 < re) {
@@ -343,8 +355,10 @@ __device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int
     }
 }
 
-__global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
+template <int NT, int RPW>
+__global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
 {
+    constexpr int NW = NT / 32;
     __shared__ double s_s[kMaxSide];                      // ||R_i||^2
     __shared__ double s_r[kMaxSide];                      // s_i / a_i
     __shared__ __align__(16) float s_vec[kMaxSide];       // R_{i_k} row, then v
@@ -352,8 +366,8 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
     __shared__ __align__(16) float s_w[kMaxSide];         // w
     __shared__ __align__(16) float s_u[kMaxSide];         // u
     extern __shared__ __align__(16) float fold_smem[];    // kFoldSmemBytes
-    __shared__ double red[2 * kBW];
-    __shared__ long long redi[2 * kBW];
+    __shared__ double red[2 * 32];
+    __shared__ long long redi[2 * 32];
     __shared__ int s_sys, s_first, s_last, s_stop;
     __shared__ double s_S, s_rmax, s_base_next;
     __shared__ long long s_imax;
@@ -386,14 +400,14 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             const bool bnd = d.bandA >= 0;
             for (int i = 0; i < d.m; ++i) {
                 const int c0 = bnd ? max(0, i - d.bandA) : 0, c1 = bnd ? min(d.p - 1, i + d.bandA) : d.p - 1;
-                for (int j = threadIdx.x; j < d.q; j += kBB) {  // t = A_i X
+                for (int j = threadIdx.x; j < d.q; j += NT) {  // t = A_i X
                     float acc = 0.f;
                     for (int c2 = c0; c2 <= c1; ++c2)
                         acc = fmaf(A[(long long)i * d.lda + c2], X[(long long)c2 * d.q + j], acc);
                     s_w[j] = acc;
                 }
                 __syncthreads();
-                for (int l = threadIdx.x; l < d.n; l += kBB) {  // R_i = C_i - t B
+                for (int l = threadIdx.x; l < d.n; l += NT) {  // R_i = C_i - t B
                     const int j0 = bnd ? max(0, l - d.bandB) : 0, j1 = bnd ? min(d.q - 1, l + d.bandB) : d.q - 1;
                     float acc = 0.f;
                     for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
@@ -404,13 +418,13 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
         } else if (C != R) {
             const float4* C4 = reinterpret_cast<const float4*>(C);
             float4* R4 = reinterpret_cast<float4*>(R);
-            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr / 4; e += kBB) R4[e] = __ldg(C4 + e);
+            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr / 4; e += NT) R4[e] = __ldg(C4 + e);
         }
         __syncthreads();
 
         // row norms of R^0: warp per row (Kahan FP32 lanes, FP64 across lanes)
         for (int pass = 0; pass < 2; ++pass) {
-            for (int i = warp; i < d.m; i += kBW) {
+            for (int i = warp; i < d.m; i += NW) {
                 float acc = 0.f, comp = 0.f;
                 for (int l = lane; l < d.n; l += 32) {
                     const float x = R[(long long)i * d.ldr + l];
@@ -431,14 +445,14 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
             if (!P.init_from_x || pass == 1) break;
             // test the caller's X0 against X0 = 0: keep it only if ||C - A X0 B|| < ||C||
             double S0 = 0.0;
-            for (int i = threadIdx.x; i < d.m; i += kBB) S0 += s_s[i];
-            S0 = block_sum_fixed(S0, red);
+            for (int i = threadIdx.x; i < d.m; i += NT) S0 += s_s[i];
+            S0 = block_sum_fixed<NW>(S0, red);
             const bool reject = !(S0 < d.normC2);
             if (threadIdx.x == 0 && P.x0_rejected) P.x0_rejected[sid] = reject ? 1 : 0;
             if (!reject) break;
             float* X = P.X + d.offX;
-            for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += kBB) X[e] = 0.f;
-            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += kBB) R[e] = C[e];
+            for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += NT) X[e] = 0.f;
+            for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += NT) R[e] = C[e];
             __syncthreads();
         }
 
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 // a signed integer: the argmax runs on the integer pipe (ties: smallest row)
                 double Sv = 0.0;
                 long long bkey = LLONG_MIN, bi = 0x7fffffffffffffffLL;
-                for (int i = threadIdx.x; i < d.m; i += kBB) {
+                for (int i = threadIdx.x; i < d.m; i += NT) {
                     Sv += s_s[i];
                     const long long key = __double_as_longlong(s_r[i]);
                     if (key > bkey) { bkey = key; bi = i; }
@@ -463,15 +477,15 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     if (ok > bkey || (ok == bkey && oi < bi)) { bkey = ok; bi = oi; }
                 }
-                if (lane == 0) { red[warp] = Sv; redi[warp] = bi; redi[kBW + warp] = bkey; }
+                if (lane == 0) { red[warp] = Sv; redi[warp] = bi; redi[NW + warp] = bkey; }
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     double S = 0.0;
                     long long bbk = LLONG_MIN, bbi = 0x7fffffffffffffffLL;
-                    for (int w2 = 0; w2 < kBW; ++w2) {
+                    for (int w2 = 0; w2 < NW; ++w2) {
                         S += red[w2];
-                        if (redi[kBW + w2] > bbk || (redi[kBW + w2] == bbk && redi[w2] < bbi)) {
-                            bbk = redi[kBW + w2];
+                        if (redi[NW + w2] > bbk || (redi[NW + w2] == bbk && redi[w2] < bbi)) {
+                            bbk = redi[NW + w2];
                             bbi = redi[w2];
                         }
                     }
@@ -502,7 +516,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 // (r_i and t are >= 0 or -inf)
                 const double u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
                 const long long tkey = __double_as_longlong(t);
-                const int K = (d.m + kBB - 1) / kBB;
+                const int K = (d.m + NT - 1) / NT;
                 const int r0 = threadIdx.x * K, r1 = min(d.m, r0 + K);
                 double loc = 0.0;
                 int lastadm = -1;
@@ -514,14 +528,14 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 if (lane == 31) red[warp] = incw;
                 __syncthreads();
                 if (warp == 0) {  // exclusive bases of the warps and the total S_J
-                    const double wt = lane < kBW ? red[lane] : 0.0;
+                    const double wt = lane < NW ? red[lane] : 0.0;
                     const double inc = warp_inclusive_scan(wt);
-                    if (lane < kBW) red[kBW + lane] = inc - wt;
-                    if (lane == kBW - 1) s_base_next = inc;
+                    if (lane < NW) red[NW + lane] = inc - wt;
+                    if (lane == NW - 1) s_base_next = inc;
                 }
                 __syncthreads();
                 const double target = __dmul_rn(u, s_base_next);
-                const double incl = red[kBW + warp] + incw;
+                const double incl = red[NW + warp] + incw;
                 if (lastadm >= 0) {
                     atomicMax(&s_last, lastadm);
                     if (incl > target) {  // the prefix crosses u S_J within or before these rows
@@ -570,14 +584,14 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 {
                     const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
                     const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
-                    for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
-                    for (int e = threadIdx.x; e < d.lda / 4; e += kBB)
+                    for (int e = threadIdx.x; e < d.ldr / 4; e += NT) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
+                    for (int e = threadIdx.x; e < d.lda / 4; e += NT)
                         reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
                 }
                 __syncthreads();
                 // w_j = sum over |l - j| <= bB of R_ik,l B_jl (one thread per row of B: the band is
                 // short, and the rows of B stay in L1 from one iteration to the next)
-                for (int j = threadIdx.x; j < d.q; j += kBB) {
+                for (int j = threadIdx.x; j < d.q; j += NT) {
                     const int l0 = max(0, j - bB), l1 = min(d.n - 1, j + bB);
                     const float* Bj = B + (long long)j * d.ldb;
                     float acc = 0.f;
@@ -586,7 +600,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 }
                 // c_k u_i for |i - ik| <= 2 bA (one thread per row of A)
                 const int u0 = max(0, ik - 2 * bA), u1 = min(d.m - 1, ik + 2 * bA);
-                for (int i = u0 + threadIdx.x; i <= u1; i += kBB) {
+                for (int i = u0 + threadIdx.x; i <= u1; i += NT) {
                     const int c0 = max(0, max(i, ik) - bA), c1 = min(d.p - 1, min(i, ik) + bA);
                     const float* Ai = A + (long long)i * d.lda;
                     float acc = 0.f;
@@ -595,9 +609,9 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
-                for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
+                for (int j = threadIdx.x; j < d.q; j += NT) hw[(long long)nh * d.q + j] = s_w[j];
                 // v_l = sum over |j - l| <= bB of w_j B_jl (padding columns 0)
-                for (int l = threadIdx.x; l < d.ldr; l += kBB) {
+                for (int l = threadIdx.x; l < d.ldr; l += NT) {
                     float acc = 0.f;
                     if (l < d.n) {
                         const int j0 = max(0, l - bB), j1 = min(d.q - 1, l + bB);
@@ -606,29 +620,29 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     s_vec[l] = acc;
                 }
                 __syncthreads();
-                batch_update_rows(R, d.ldr, u0, u1 + 1, s_u, s_vec, a, s_s, s_r);
+                batch_update_rows<NW, RPW>(R, d.ldr, u0, u1 + 1, s_u, s_vec, a, s_s, s_r);
             } else {
                 // ---- w = R_ik B^T, u = A A_ik^T (rows of B and A streamed as float4, 4 rows per warp)
                 {
                     const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
                     const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
-                    for (int e = threadIdx.x; e < d.ldr / 4; e += kBB) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
-                    for (int e = threadIdx.x; e < d.lda / 4; e += kBB) reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
+                    for (int e = threadIdx.x; e < d.ldr / 4; e += NT) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
+                    for (int e = threadIdx.x; e < d.lda / 4; e += NT) reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
                 }
                 __syncthreads();
-                batch_rows_dot<4>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
-                batch_rows_dot<4>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
+                batch_rows_dot<4, NW>(B, d.ldb, d.q, d.ldb / 4, s_vec, s_w);
+                batch_rows_dot<4, NW>(A, d.lda, d.m, d.lda / 4, s_arow, s_u);
                 __syncthreads();
-                for (int i = threadIdx.x; i < d.m; i += kBB) s_u[i] = (float)(ck * (double)s_u[i]);  // coefficient c_k u_i
+                for (int i = threadIdx.x; i < d.m; i += NT) s_u[i] = (float)(ck * (double)s_u[i]);  // coefficient c_k u_i
                 // ---- record the term, v = w B (vector columns, row classes reduced in shared memory)
                 if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
-                for (int j = threadIdx.x; j < d.q; j += kBB) hw[(long long)nh * d.q + j] = s_w[j];
+                for (int j = threadIdx.x; j < d.q; j += NT) hw[(long long)nh * d.q + j] = s_w[j];
                 {
                     const int nv4 = d.ldb / 4;
                     float4* red4 = reinterpret_cast<float4*>(fold_smem);  // [RG][cols] float4
-                    for (int cb = 0; cb < nv4; cb += kBB) {
-                        const int ncols = min(kBB, nv4 - cb);
-                        const int RG = kBB / ncols;
+                    for (int cb = 0; cb < nv4; cb += NT) {
+                        const int ncols = min(NT, nv4 - cb);
+                        const int RG = NT / ncols;
                         const int e = threadIdx.x % ncols, rg = threadIdx.x / ncols;
                         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (rg < RG) {
@@ -646,7 +660,7 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                             red4[rg * ncols + e] = acc;
                         }
                         __syncthreads();
-                        for (int t = threadIdx.x; t < ncols; t += kBB) {
+                        for (int t = threadIdx.x; t < ncols; t += NT) {
                             float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
                             for (int r2 = 0; r2 < RG; ++r2) {
                                 const float4 v = red4[r2 * ncols + t];
@@ -658,17 +672,17 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
                     }
                 }
                 // ---- R -= c u v fused with the new row norms
-                batch_update_rows(R, d.ldr, 0, d.m, s_u, s_vec, a, s_s, s_r);
+                batch_update_rows<NW, RPW>(R, d.ldr, 0, d.m, s_u, s_vec, a, s_s, s_r);
             }
             ++k;
             ++nh;
             if (nh == P.chunk) {
-                batch_fold(P, d, nh, fold_smem);
+                batch_fold<NT>(P, d, nh, fold_smem);
                 nh = 0;
             }
             __syncthreads();
         }
-        batch_fold(P, d, nh, fold_smem);
+        batch_fold<NT>(P, d, nh, fold_smem);
         if (threadIdx.x == 0) {
             P.iters[sid] = k;
             P.S_out[sid] = s_S;
@@ -676,6 +690,31 @@ __global__ void __launch_bounds__(kBB) batch_kernel(BatchParams P)
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Batch autotuner: the compiled variants of the batched kernel (threads per
+// CTA, rows per warp of the fused update pass).  All variants compute the same
+// iteration; they differ in how the work of one system is spread over the CTA
+// (and so in how many CTAs fit on an SM) and only in the summation order of
+// the FP64 totals.  A system's variant is chosen by timing every variant on it
+// and kept per system shape for the rest of the process.
+// ---------------------------------------------------------------------------
+struct BatchVariant {
+    int threads, rpw;
+    void (*kern)(BatchParams);
+    int smem;
+};
+static const BatchVariant kVariants[] = {
+    {256, 1, batch_kernel_t<256, 1>, FoldCfg<256>::SMEM_BYTES},
+    {256, 2, batch_kernel_t<256, 2>, FoldCfg<256>::SMEM_BYTES},
+    {256, 4, batch_kernel_t<256, 4>, FoldCfg<256>::SMEM_BYTES},
+    {512, 1, batch_kernel_t<512, 1>, FoldCfg<512>::SMEM_BYTES},
+    {512, 2, batch_kernel_t<512, 2>, FoldCfg<512>::SMEM_BYTES},
+    {512, 4, batch_kernel_t<512, 4>, FoldCfg<512>::SMEM_BYTES},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+constexpr int kDefaultVariant = 4;   // 512 threads, two rows per warp
+constexpr int kTuneIters = 48;       // iterations of one timed trial
 
 }  // namespace grbk
 
@@ -705,6 +744,12 @@ struct grbk_batch {
     int* rejected;
     int chunk;
     long long totA, totB, totR, totX, totRow, totHist, totHistW;
+    std::vector<int> variant;        // kernel variant of each system
+    int goff[grbk::kNumVariants] = {}, gcnt[grbk::kNumVariants] = {};   // systems of each variant in dorder
+    int* dids = nullptr;             // system ids 0 .. nsys-1 (one-system tuning launches)
+    cudaStream_t side[grbk::kNumVariants] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[grbk::kNumVariants] = {};
+    double tune_seconds = 0.0;
 };
 
 static void* dmalloc(size_t bytes)
@@ -714,13 +759,95 @@ static void* dmalloc(size_t bytes)
     return p;
 }
 
+// ---- autotuner bookkeeping (host only) -------------------------------------
+// A system's class: its sides rounded up to multiples of 64 and its exact
+// half-bandwidths (-1 on the dense path).
+struct TuneKey {
+    int m, p, q, n, bandA, bandB;
+    bool operator<(const TuneKey& o) const
+    {
+        const int a[6] = {m, p, q, n, bandA, bandB}, b[6] = {o.m, o.p, o.q, o.n, o.bandA, o.bandB};
+        return std::lexicographical_compare(a, a + 6, b, b + 6);
+    }
+};
+static std::map<TuneKey, int> g_tune_cache;
+static std::mutex g_tune_mu;
+
+static TuneKey tune_key(int m, int p, int q, int n, int bandA, int bandB)
+{
+    auto r64 = [](int x) { return (x + 63) / 64 * 64; };
+    return TuneKey{r64(m), r64(p), r64(q), r64(n), bandA, bandB};
+}
+
+// The fastest variant; a variant within 2 % of the fastest that uses fewer
+// threads wins (more CTAs fit on an SM, which helps the other systems).
+static int tune_choose(const double* ms, int nv)
+{
+    int best = -1;
+    for (int v = 0; v < nv; ++v)
+        if (ms[v] > 0.0 && std::isfinite(ms[v]) && (best < 0 || ms[v] < ms[best])) best = v;
+    if (best < 0) return kDefaultVariant;
+    int pick = best;
+    for (int v = 0; v < nv; ++v)
+        if (ms[v] > 0.0 && std::isfinite(ms[v]) && ms[v] <= 1.02 * ms[best] &&
+            kVariants[v].threads < kVariants[pick].threads)
+            pick = v;
+    return pick;
+}
+
+extern "C" int32_t grbk_tune_num_variants(void) { return kNumVariants; }
+
+extern "C" grbk_status grbk_tune_variant_info(int32_t v, int32_t* threads, int32_t* rows_per_warp)
+{
+    if (v < 0 || v >= kNumVariants) return GRBK_EINVAL;
+    if (threads) *threads = kVariants[v].threads;
+    if (rows_per_warp) *rows_per_warp = kVariants[v].rpw;
+    return GRBK_OK;
+}
+
+extern "C" int32_t grbk_tune_choose(const double* ms, int32_t nv)
+{
+    if (!ms || nv != kNumVariants) return -1;
+    return tune_choose(ms, nv);
+}
+
+extern "C" grbk_status grbk_tune_lookup(int32_t m, int32_t p, int32_t q, int32_t n, int32_t bandA, int32_t bandB,
+                                        int32_t* variant)
+{
+    if (!variant) return GRBK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto it = g_tune_cache.find(tune_key(m, p, q, n, bandA, bandB));
+    *variant = it == g_tune_cache.end() ? -1 : it->second;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_tune_store(int32_t m, int32_t p, int32_t q, int32_t n, int32_t bandA, int32_t bandB,
+                                       int32_t variant)
+{
+    if (variant < 0 || variant >= kNumVariants) return GRBK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[tune_key(m, p, q, n, bandA, bandB)] = variant;
+    return GRBK_OK;
+}
+
+extern "C" void grbk_tune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
+}
+
 extern "C" void grbk_batch_destroy(grbk_batch* b)
 {
     if (!b) return;
     void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->A, b->B, b->C, b->R, b->X, b->a, b->pref,
-                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags, b->trace, b->rejected};
+                    b->hist_rows, b->hist_c, b->hist_w, b->iters, b->S, b->flags, b->trace, b->rejected, b->dids};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (b->side[v]) cudaStreamDestroy(b->side[v]);
+        if (b->ev_join[v]) cudaEventDestroy(b->ev_join[v]);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     delete b;
 }
 
@@ -771,6 +898,85 @@ static bool x_desc_ok(const grbk_mat& M, int p, int q)
     return M.ptr && M.rows == p && M.cols == q && M.ld >= q && dtype_ok(M.dtype);
 }
 
+// The kernel parameters of a launch over the systems order[0 .. n) (queue counter at queue).
+static BatchParams batch_params(grbk_batch* b, const int* order, int n, int* queue)
+{
+    BatchParams P;
+    memset(&P, 0, sizeof(P));
+    P.nsys = n; P.sys = b->dsys; P.order = order; P.queue = queue;
+    P.A = b->A; P.B = b->B; P.C = b->C; P.R = b->R; P.X = b->X; P.a = b->a; P.rbk_prefix = b->pref;
+    P.hist_rows = b->hist_rows; P.hist_c = b->hist_c; P.hist_w = b->hist_w;
+    P.iters = b->iters; P.S_out = b->S; P.flag_out = b->flags;
+    P.chunk = b->chunk;
+    P.x0_rejected = b->rejected;
+    return P;
+}
+
+static grbk_status launch_variant(int v, const BatchParams& P, int nsys_launch, int grid_cap, cudaStream_t st)
+{
+    const BatchVariant& V = kVariants[v];
+    int dev = 0, nsm = 0, per_sm = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    GRBK_CK(cudaFuncSetAttribute(V.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
+    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.kern, V.threads, V.smem));
+    int grid = nsm * (per_sm > 0 ? per_sm : 1);
+    if (grid_cap > 0) grid = std::min(grid, grid_cap);
+    grid = std::min(grid, nsys_launch);
+    V.kern<<<grid, V.threads, V.smem, st>>>(P);
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
+
+// Time every variant on one system of each class not yet in the cache (ME-GRBK,
+// kTuneIters iterations from R = C, one untimed and one timed launch each) and
+// keep the choice.  The systems' R and X are left as the trials leave them;
+// every solve starts them afresh.
+static grbk_status batch_autotune(grbk_batch* b)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = b->stream;
+    std::vector<int> ids(b->nsys);
+    for (int s = 0; s < b->nsys; ++s) ids[s] = s;
+    b->dids = (int*)dmalloc(4 * b->nsys);
+    if (!b->dids) return GRBK_ENOMEM;
+    GRBK_CK(cudaMemcpyAsync(b->dids, ids.data(), 4 * b->nsys, cudaMemcpyHostToDevice, st));
+    GRBK_CK(cudaMemcpyAsync(b->dsys, b->hsys.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GRBK_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GRBK_ECUDA; }
+    grbk_status res = GRBK_OK;
+    for (int s : b->order) {
+        const SysDesc& d = b->hsys[s];
+        int32_t v = -1;
+        grbk_tune_lookup(d.m, d.p, d.q, d.n, d.bandA, d.bandB, &v);
+        if (v >= 0) { b->variant[s] = v; continue; }
+        double ms[kNumVariants];
+        BatchParams P = batch_params(b, b->dids + s, 1, b->dqueue);
+        P.variant = GRBK_GRBK; P.theta = 0.5; P.seed = 1; P.maxit = kTuneIters;
+        for (int vv = 0; vv < kNumVariants && res == GRBK_OK; ++vv) {
+            float el = 0.f;
+            for (int rep = 0; rep < 2 && res == GRBK_OK; ++rep) {
+                if (cudaMemsetAsync(b->dqueue, 0, 4, st) != cudaSuccess) { res = GRBK_ECUDA; break; }
+                if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) { res = GRBK_ECUDA; break; }
+                res = launch_variant(vv, P, 1, 1, st);
+                if (res == GRBK_OK && rep == 1 && cudaEventRecord(e1, st) != cudaSuccess) res = GRBK_ECUDA;
+            }
+            if (res == GRBK_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
+                res = GRBK_ECUDA;
+            ms[vv] = el;
+        }
+        if (res != GRBK_OK) break;
+        v = tune_choose(ms, kNumVariants);
+        grbk_tune_store(d.m, d.p, d.q, d.n, d.bandA, d.bandB, v);
+        b->variant[s] = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tune_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return res;
+}
+
 extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const grbk_mat* A, const grbk_mat* B,
                                          const grbk_mat* C, const grbk_opts* opts)
 {
@@ -810,7 +1016,7 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     b->a = (double*)dmalloc(oRow * 8); b->pref = (double*)dmalloc(oRow * 8);
     b->hist_rows = (int*)dmalloc(oH * 4); b->hist_c = (float*)dmalloc(oH * 4); b->hist_w = (float*)dmalloc(oHW * 4);
     b->dsys = (SysDesc*)dmalloc(sizeof(SysDesc) * nsys); b->dorder = (int*)dmalloc(4 * nsys);
-    b->dqueue = (int*)dmalloc(4); b->iters = (long long*)dmalloc(8 * nsys); b->S = (double*)dmalloc(8 * nsys);
+    b->dqueue = (int*)dmalloc(4 * kNumVariants); b->iters = (long long*)dmalloc(8 * nsys); b->S = (double*)dmalloc(8 * nsys);
     b->flags = (int*)dmalloc(4 * nsys);
     b->rejected = (int*)dmalloc(4 * nsys);
     if (!b->rejected || !b->A || !b->B || !b->C || !b->R || !b->X || !b->a || !b->pref || !b->hist_rows || !b->hist_c ||
@@ -887,12 +1093,35 @@ extern "C" grbk_status grbk_batch_create(grbk_batch** out, int32_t nsys, const g
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
         return (long long)b->hsys[x].m * b->hsys[x].n > (long long)b->hsys[y].m * b->hsys[y].n;
     });
+    // kernel variant of every system: the default, or the autotuner's choice
+    b->variant.assign(nsys, kDefaultVariant);
+    if (o.tune) {
+        const grbk_status e = batch_autotune(b);
+        if (e != GRBK_OK) { grbk_batch_destroy(b); return e; }
+    }
+    // queue order: systems grouped by variant, longest first within a group
+    std::vector<int> grouped;
+    for (int v = 0; v < kNumVariants; ++v) {
+        b->goff[v] = (int)grouped.size();
+        for (int s : b->order)
+            if (b->variant[s] == v) grouped.push_back(s);
+        b->gcnt[v] = (int)grouped.size() - b->goff[v];
+    }
+    b->order = grouped;
     if (cudaMemcpyAsync(b->dorder, b->order.data(), 4 * nsys, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         grbk_batch_destroy(b);
         return GRBK_ECUDA;
     }
     *out = b;
+    return GRBK_OK;
+}
+
+extern "C" grbk_status grbk_batch_variant(const grbk_batch* b, int32_t sys, int32_t* variant, double* tune_seconds)
+{
+    if (!b || sys < 0 || sys >= b->nsys) return GRBK_EINVAL;
+    if (variant) *variant = b->variant[sys];
+    if (tune_seconds) *tune_seconds = b->tune_seconds;
     return GRBK_OK;
 }
 
@@ -936,7 +1165,7 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     } else {
         GRBK_CK(cudaMemsetAsync(b->X, 0, b->totX * 4, st));
     }
-    GRBK_CK(cudaMemsetAsync(b->dqueue, 0, 4, st));
+    GRBK_CK(cudaMemsetAsync(b->dqueue, 0, 4 * kNumVariants, st));
     GRBK_CK(cudaMemsetAsync(b->rejected, 0, 4 * b->nsys, st));
     BatchParams P;
     memset(&P, 0, sizeof(P));
@@ -956,16 +1185,36 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
     }
     P.init_from_x = X0s != nullptr;
     P.x0_rejected = b->rejected;
-    int dev = 0, nsm = 0, per_sm = 0;
-    GRBK_CK(cudaGetDevice(&dev));
-    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    GRBK_CK(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemBytes));
-    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBB, kFoldSmemBytes));
-    int grid = nsm * (per_sm > 0 ? per_sm : 1);
-    if (b->opts.grid_ctas > 0) grid = b->opts.grid_ctas;
-    if (grid > b->nsys) grid = b->nsys;
-    batch_kernel<<<grid, kBB, kFoldSmemBytes, st>>>(P);
-    GRBK_CK(cudaGetLastError());
+    // one launch per kernel variant in use, each over its own systems; with more
+    // than one, the launches run side by side on the batch's side streams
+    int ngroups = 0;
+    for (int v = 0; v < kNumVariants; ++v) ngroups += b->gcnt[v] > 0;
+    if (ngroups > 1 && !b->ev_fork) {
+        GRBK_CK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+        for (int v = 0; v < kNumVariants; ++v) {
+            GRBK_CK(cudaStreamCreateWithFlags(&b->side[v], cudaStreamNonBlocking));
+            GRBK_CK(cudaEventCreateWithFlags(&b->ev_join[v], cudaEventDisableTiming));
+        }
+    }
+    if (ngroups > 1) GRBK_CK(cudaEventRecord(b->ev_fork, st));
+    for (int v = 0; v < kNumVariants; ++v) {
+        if (!b->gcnt[v]) continue;
+        BatchParams Pv = P;
+        Pv.nsys = b->gcnt[v];
+        Pv.order = b->dorder + b->goff[v];
+        Pv.queue = b->dqueue + v;
+        cudaStream_t sv = st;
+        if (ngroups > 1) {
+            sv = b->side[v];
+            GRBK_CK(cudaStreamWaitEvent(sv, b->ev_fork, 0));
+        }
+        const grbk_status e = launch_variant(v, Pv, b->gcnt[v], b->opts.grid_ctas, sv);
+        if (e != GRBK_OK) return e;
+        if (ngroups > 1) {
+            GRBK_CK(cudaEventRecord(b->ev_join[v], sv));
+            GRBK_CK(cudaStreamWaitEvent(st, b->ev_join[v], 0));
+        }
+    }
     std::vector<long long> it(b->nsys);
     std::vector<double> S(b->nsys);
     std::vector<int> fl(b->nsys), rej(b->nsys);
@@ -1149,7 +1398,7 @@ static grbk_status noalloc_scratch_address(void** out)
     if (!g_noalloc_ptr[dev]) {
         void* ptr = nullptr;
         GRBK_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        GRBK_CK(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemBytes));
+        GRBK_CK(cudaFuncSetAttribute(batch_kernel_t<kBB, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFoldSmemBytes));
         g_noalloc_ptr[dev] = ptr;
     }
     *out = g_noalloc_ptr[dev];
@@ -1204,7 +1453,7 @@ extern "C" grbk_status grbk_solve_small_noalloc(const float* A, const float* B, 
     P.maxit = maxit;
     P.chunk = kNoAllocChunk;
     P.init_from_x = 0;
-    batch_kernel<<<1, kBB, kFoldSmemBytes, st>>>(P);
+    batch_kernel_t<kBB, 2><<<1, kBB, kFoldSmemBytes, st>>>(P);
     GRBK_CK(cudaGetLastError());
     struct {
         long long iters;

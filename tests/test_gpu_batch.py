@@ -158,3 +158,43 @@ def test_batch_from_nonzero_x0_matches_oracle(band_limit):
         kk = compare_rows(b.row_trace[sid], orc, 100)
         if kk == 100:
             assert _rel(X, orc["X"]) < 1e-4
+
+
+@pytest.mark.parametrize("band_limit", [0, -1])
+def test_autotuned_batch_matches_oracle(band_limit):
+    """With the autotuner on, each system runs the variant timed fastest on its
+    class (possibly different variants side by side on separate streams); the
+    rows still follow the FP64 oracle's and every system's variant is recorded
+    and cached."""
+    g.grbk_tune_clear()
+    sy = _systems()
+    As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
+    alphas = _alphas(Bs)
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=120, band_limit=band_limit, alphas=alphas, tune=True)
+    nv = len(g.grbk_tune_variants())
+    chosen = []
+    for sid, s in enumerate(sy):
+        v, secs = g.grbk_batch_variant(b, sid)
+        assert 0 <= v < nv and secs > 0
+        bA, bB = g.grbk_batch_info(b, sid)
+        m, p = s["A"].shape
+        q, n = s["B"].shape
+        assert g.grbk_tune_lookup(m, p, q, n, bA, bB) == v
+        chosen.append(v)
+    Xo = [np.zeros_like(s["X"]) for s in sy]
+    st, res = g.grbk_batch_solve(b, "grbk", maxit=120, seed=11, X_outs=Xo)
+    assert st == g.GRBK_OK
+    compared = []
+    for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
+        assert r["iters"] == 120
+        orc = oracle.solve(s["A"], s["B"], s["C"], "grbk", alpha=alphas[sid], seed=11, sys=sid, maxit=120,
+                           mode=oracle.MODE_FACTORED)
+        kk = compare_rows(b.row_trace[sid], orc, 120)
+        if kk == 120:
+            assert _rel(X, orc["X"]) < 1e-4
+        compared.append(kk)
+    assert sum(compared) >= 0.9 * 120 * len(sy), compared
+    # a second batch of the same shapes takes every choice from the cache
+    b2 = g.grbk_batch_create(As, Bs, Cs, band_limit=band_limit, tune=True)
+    assert [g.grbk_batch_variant(b2, sid)[0] for sid in range(len(sy))] == chosen
+    g.grbk_tune_clear()
