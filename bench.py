@@ -746,16 +746,32 @@ def unet_bench(args):
     from paper_2408_05444_gb300 import warmstart as ws
     net = ws.make_net(width=20, seed=0)
     C = torch.rand(16, 512, 512, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-    X = torch.empty_like(C)
-    for _ in range(3):
-        g.grbk_unet_forward(net, C, X)
-    torch.cuda.synchronize()
+    out = {"mode": "unet", "channels": 16, "side": 512, "width": 20}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    X = {}
+    for tc in (True, False):
+        g.grbk_unet_use_tensor_cores(net, tc)
+        X[tc] = torch.empty_like(C)
+        for _ in range(3):
+            g.grbk_unet_forward(net, C, X[tc])
+        torch.cuda.synchronize()
+        ev0.record()
+        g.grbk_unet_forward(net, C, X[tc])
+        ev1.record()
+        torch.cuda.synchronize()
+        out["forward_ms_tensor_cores" if tc else "forward_ms_simt"] = ev0.elapsed_time(ev1)
+    out["speedup"] = out["forward_ms_simt"] / out["forward_ms_tensor_cores"]
+    out["max_rel_diff"] = float((X[True] - X[False]).abs().max() / (X[False] - C).abs().max())
+    # 192 channels of 512^2 (64 RGB images, the warm start's evaluation) in batches of 16
+    g.grbk_unet_use_tensor_cores(net, True)
+    torch.cuda.synchronize()
     ev0.record()
-    g.grbk_unet_forward(net, C, X)
+    for _ in range(12):
+        g.grbk_unet_forward(net, C, X[True])
     ev1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "unet", "channels": 16, "side": 512, "forward_ms": ev0.elapsed_time(ev1)}), flush=True)
+    out["forward_ms_192_channels_tensor_cores"] = ev0.elapsed_time(ev1)
+    print(json.dumps(out), flush=True)
 
 
 def main():

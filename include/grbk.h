@@ -412,6 +412,16 @@ grbk_status grbk_unet_loss_grad(grbk_unet* net, const float* C, const float* T, 
 /* one Adam step on mean((X0 - T)^2); loss (host, may be NULL) is the loss before the step */
 grbk_status grbk_unet_train_step(grbk_unet* net, const float* C, const float* T, int32_t n, int32_t h, int32_t w,
                                  float lr, double* loss);
+/* Convolution path (not part of the paper): on = 1 (the default) runs every
+ * convolution with 16 to 128 output channels and at least 16 input channels
+ * of the forward pass on the tensor cores -- an implicit GEMM (tcgen05.mma,
+ * TMEM accumulators, TMA loads whose out-of-range coordinates give the zero
+ * padding) over a three-term BF16 split of the FP32 activations and the BF16
+ * weights, accumulated in FP32; on = 0 keeps every convolution on the SIMT
+ * kernel.  The backward passes always use the SIMT kernels.  A bounded wait
+ * of the tensor-core kernel that expires makes the next forward, loss or
+ * training call return GRBK_ETIMEOUT. */
+grbk_status grbk_unet_use_tensor_cores(grbk_unet* net, int32_t on);
 void grbk_unet_destroy(grbk_unet* net);
 
 /*

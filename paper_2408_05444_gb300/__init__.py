@@ -73,7 +73,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_sparse_create",
            "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy",
            "grbk_tune_num_variants", "grbk_tune_variant_info", "grbk_tune_choose", "grbk_tune_lookup",
-           "grbk_tune_store", "grbk_tune_clear", "grbk_batch_variant"]
+           "grbk_tune_store", "grbk_tune_clear", "grbk_batch_variant", "grbk_unet_use_tensor_cores"]
 GRBK_NOALLOC_MAX_SIDE = 512
 
 _lib = None
@@ -134,6 +134,8 @@ def lib():
         L.grbk_unet_loss_grad.restype = i32
         L.grbk_unet_train_step.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, P(dbl)]
         L.grbk_unet_train_step.restype = i32
+        L.grbk_unet_use_tensor_cores.argtypes = [vp, i32]
+        L.grbk_unet_use_tensor_cores.restype = i32
         L.grbk_unet_destroy.argtypes = [vp]
         L.grbk_unet_destroy.restype = None
         L.grbk_barrier_selftest.argtypes = [i32, vp]
@@ -604,6 +606,12 @@ def grbk_unet_train_step(net: UNetHandle, C, T, lr) -> float:
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_train_step")
     return loss.value
+
+
+def grbk_unet_use_tensor_cores(net: UNetHandle, on: bool = True):
+    st = lib().grbk_unet_use_tensor_cores(net.handle, int(bool(on)))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_unet_use_tensor_cores")
 
 
 def grbk_unet_destroy(net: UNetHandle):

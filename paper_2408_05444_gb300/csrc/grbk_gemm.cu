@@ -501,6 +501,203 @@ __global__ void split_transpose_kernel(const S* src, int64_t ld, int64_t K, int6
     }
 }
 
+
+// ----------------------------------------------------------------------------
+// 3x3 convolution with zero padding 1 as an implicit GEMM on the tensor cores
+// (the warm-start network's convolutions).  Activations are NHWC BF16 planes
+// [term][image][H][W][Cp] holding a three-term split of the FP32 values
+// (x = x0 + x1 + x2, about 24 significant bits in all); weights are one BF16
+// term (they are BF16 already), laid out [Npad][tap][Cp].  An output tile is
+// 128 pixels (boxh rows of boxw columns) by Npad output channels, accumulated
+// in TMEM over K = 9 taps x Cp channels: for tap (dy, dx) the A operand is the
+// input tile shifted by (dy, dx), loaded by a 4-D TMA whose out-of-range
+// coordinates fill zeros -- the zero padding costs nothing.  Persistent CTAs,
+// two smem stages, two TMEM accumulators so the epilogue (bias, ReLU, NCHW
+// FP32 store) of one tile overlaps the MMAs of the next.
+// ----------------------------------------------------------------------------
+constexpr int CONV_TERMS = 3;
+constexpr int CONV_STAGES = 2;
+constexpr int CONV_A_BYTES = CONV_TERMS * A_TILE;                 // 48 KB
+constexpr int CONV_STAGE_BYTES = CONV_A_BYTES + 128 * BK * 2;       // + B for up to 128 channels
+constexpr int CONV_SMEM_BYTES = CONV_STAGES * CONV_STAGE_BYTES + 1024 + 256;
+
+struct ConvArgs {
+    int nimg, H, W, Cp, Npad, Cout;
+    int boxw, boxh, tiles_x, tiles_y;
+    int tmem_cols;                   // two accumulators, the second at column tmem_cols / 2
+    const float* bias;
+    int relu;
+    float* out;
+    int out_ctot, out_c0;
+    int* err;
+};
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) conv_tc_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                         const __grid_constant__ CUtensorMap tmW, ConvArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    auto sA = [&](int s, int t) { return smem + s * CONV_STAGE_BYTES + t * A_TILE; };
+    auto sB = [&](int s) { return smem + s * CONV_STAGE_BYTES + CONV_A_BYTES; };
+    uint64_t* bars = (uint64_t*)(smem + CONV_STAGES * CONV_STAGE_BYTES);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + CONV_STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * CONV_STAGES), acce0 = smem_u32(bars + 2 * CONV_STAGES + 2);
+    const uint32_t done = smem_u32(bars + 2 * CONV_STAGES + 4);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * CONV_STAGES + 5);
+    __shared__ int s_abort;
+
+    if (*(volatile int*)g.err != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkc = g.Cp / BK;
+    const int nkb = 9 * nkc;
+    const int ntiles = g.nimg * g.tiles_y * g.tiles_x;
+    const uint32_t idesc = idesc_for(g.Npad);
+    const uint32_t stage_tx = (uint32_t)(CONV_A_BYTES + g.Npad * BK * 2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CONV_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(g.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+
+    auto tile_origin = [&](int tile, int& n, int& y0, int& x0) {
+        const int per = g.tiles_y * g.tiles_x;
+        n = tile / per;
+        const int r = tile % per;
+        y0 = (r / g.tiles_x) * g.boxh;
+        x0 = (r % g.tiles_x) * g.boxw;
+    };
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+            int n, y0, x0;
+            tile_origin(tile, n, y0, x0);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int tap = kb / nkc, kc = kb % nkc;
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                const int s = issued % CONV_STAGES;
+                const uint32_t ph = (uint32_t)((issued / CONV_STAGES) & 1);
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                mbar_expect_tx(full0 + 8 * s, stage_tx);
+#pragma unroll
+                for (int t = 0; t < CONV_TERMS; ++t)
+                    tma_load_4d(smem_u32(sA(s, t)), &tmX, kc * BK, x0 + dx, y0 + dy, t * g.nimg + n, full0 + 8 * s);
+                tma_load_2d(smem_u32(sB(s)), &tmW, tap * g.Cp + kc * BK, 0, full0 + 8 * s);
+                ++issued;
+            }
+        }
+        for (int it = (issued > CONV_STAGES ? issued - CONV_STAGES : 0); it < issued; ++it)
+            mbar_wait(full0 + 8 * (it % CONV_STAGES), (uint32_t)((it / CONV_STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        int it = 0, lt = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            if (!mbar_wait(acce0 + 8 * acc, (uint32_t)(((lt >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)(acc * (g.tmem_cols / 2));
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % CONV_STAGES;
+                const uint32_t ph = (uint32_t)((it / CONV_STAGES) & 1);
+                if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t b0 = smem_u32(sB(s));
+                // the smallest terms first, so the FP32 accumulator adds them before the large one
+#pragma unroll
+                for (int t = CONV_TERMS - 1; t >= 0; --t) {
+                    const uint32_t a0 = smem_u32(sA(s, t));
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk)
+                        mma_bf16(dacc, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
+                                 (kb > 0 || t < CONV_TERMS - 1 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            if (!stop) mma_commit(accf0 + 8 * acc);
+        }
+        mma_commit(done);
+    } else if (warp >= 4) {
+        const int e = warp - 4;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const bool ok = mbar_wait(accf0 + 8 * acc, (uint32_t)((lt >> 1) & 1));
+            if (!ok || *(volatile int*)&s_abort) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int n, y0, x0;
+            tile_origin(tile, n, y0, x0);
+            const int r = e * 32 + lane;
+            const int y = y0 + r / g.boxw, x = x0 + r % g.boxw;
+            const bool valid = y < g.H && x < g.W;
+            float* obase = g.out + (((int64_t)n * g.out_ctot + g.out_c0) * g.H + y) * g.W + x;
+            const int64_t cstride = (int64_t)g.H * g.W;
+            for (int cb = 0; cb < g.Npad; cb += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + (uint32_t)(acc * (g.tmem_cols / 2)) + ((uint32_t)(e * 32) << 16) + (uint32_t)cb, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int o = cb + j;
+                    if (o >= g.Cout) break;
+                    float val = __uint_as_float(v[j]) + (g.bias ? g.bias[o] : 0.f);
+                    if (g.relu) val = fmaxf(val, 0.f);
+                    obase[(int64_t)o * cstride] = val;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * acc);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&s_abort) atomicExch(g.err, 1);
+    if (warp == 2) {
+        mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+    }
+}
+
 }  // namespace tc
 
 struct SplitGemm {
@@ -660,6 +857,68 @@ grbk_status splitgemm_check(SplitGemm* g, cudaStream_t st)
 }
 
 int splitgemm_launches(const SplitGemm*) { return 3; }
+
+// pixel tile of the tensor-core convolution: 128 pixels, boxw a power of two up
+// to 128 and no wider than the image, boxh = 128 / boxw rows
+static int conv_boxw(int W)
+{
+    int boxw = 128;
+    while (boxw > W && boxw > 1) boxw >>= 1;
+    return boxw;
+}
+
+bool tc_conv_fits(int H, int W) { return W >= 1 && 128 / conv_boxw(W) <= H; }
+
+grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const void* wtc, int Npad, int Cout,
+                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st)
+{
+    if (Cp % tc::BK != 0 || Npad % 16 != 0 || Npad < 16 || Npad > 128 || Cout > Npad) return GRBK_EINVAL;
+    if (!tc_conv_fits(H, W)) return GRBK_EINVAL;
+    auto enc = tensor_map_encoder();
+    if (!enc) return GRBK_ECUDA;
+    const int boxw = conv_boxw(W);
+    const int boxh = 128 / boxw;
+    CUtensorMap tmX, tmW;
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)Cp, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(tc::CONV_TERMS * nimg)};
+        cuuint64_t strides[3] = {(cuuint64_t)Cp * 2, (cuuint64_t)W * Cp * 2, (cuuint64_t)H * W * Cp * 2};
+        cuuint32_t box[4] = {(cuuint32_t)tc::BK, (cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)xs, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return GRBK_ECUDA;
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)(9 * Cp), (cuuint64_t)Npad};
+        cuuint64_t strides[1] = {(cuuint64_t)9 * Cp * 2};
+        cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)Npad};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)wtc, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return GRBK_ECUDA;
+    }
+    tc::ConvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.nimg = nimg; a.H = H; a.W = W; a.Cp = Cp; a.Npad = Npad; a.Cout = Cout;
+    a.boxw = boxw; a.boxh = boxh;
+    a.tiles_x = (W + boxw - 1) / boxw;
+    a.tiles_y = (H + boxh - 1) / boxh;
+    int cols = 64;
+    while (cols < 2 * ((Npad + 31) / 32 * 32)) cols <<= 1;   // two accumulators, each a power-of-two slot
+    a.tmem_cols = cols;
+    a.bias = bias; a.relu = relu; a.out = out; a.out_ctot = out_ctot; a.out_c0 = out_c0; a.err = err;
+    GRBK_CK(cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::CONV_SMEM_BYTES));
+    int dev = 0, nsm = 0;
+    GRBK_CK(cudaGetDevice(&dev));
+    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t ntiles = (int64_t)nimg * a.tiles_y * a.tiles_x;
+    dim3 grid((unsigned)std::min<int64_t>(ntiles, nsm));
+    tc::conv_tc_kernel<<<grid, 256, tc::CONV_SMEM_BYTES, st>>>(tmX, tmW, a);
+    GRBK_CK(cudaGetLastError());
+    return GRBK_OK;
+}
 
 void splitgemm_destroy(SplitGemm* g)
 {

@@ -233,6 +233,18 @@ grbk_status splitgemm_check(SplitGemm* g, cudaStream_t st);
 // kernel launches made by one splitgemm_residual call
 int splitgemm_launches(const SplitGemm* g);
 
+// 3x3 convolution, zero padding 1, on the tensor cores (grbk_gemm.cu): input planes
+// xs = [3 terms][nimg][H][W][Cp] BF16 (NHWC, Cp a multiple of 64, a three-term split of
+// the FP32 activations), weights wtc = [Npad][9 taps][Cp] BF16 (Npad a multiple of 16,
+// at most 128); out[n][out_c0 + o][y][x] (NCHW FP32, out_ctot channels) = bias[o] +
+// sum over taps and channels, then ReLU when relu != 0, for o < Cout.  err: device
+// flag set when a bounded wait expires.
+grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const void* wtc, int Npad, int Cout,
+                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st);
+// whether an H x W image fits the tensor-core convolution's 128-pixel tile (its rows
+// of a power-of-two width up to 128 stack no higher than H)
+bool tc_conv_fits(int H, int W);
+
 // Row-space form set-up (grbk_rowspace.cu): from B (q x n, ldb) and C (m x n,
 // ldc) in the working precision, the rank r of B, Lt (q x r, compact, with
 // Lt Lt^T = B B^T), Chat = C Bt^T (m x r, compact), K = Lt^T Lt (r x r) and

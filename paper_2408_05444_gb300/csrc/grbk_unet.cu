@@ -306,6 +306,51 @@ __global__ void to_bf16_kernel(const float* w, __nv_bfloat16* wb, int64_t len)
     if (j < len) wb[j] = __float2bfloat16_rn(w[j]);
 }
 
+// Input of a tensor-core convolution: channels [0, Cin) of an NCHW FP32 view as
+// three BF16 planes [term][n][y][x][Cp] (NHWC, channels padded with zeros to Cp)
+// with x = x0 + x1 + x2, x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).
+// One thread per (8-channel group, pixel), pixels fastest so the reads coalesce.
+__global__ void pack_nhwc3_kernel(View in, int Cin, int N, int H, int W, int Cp, __nv_bfloat16* dst)
+{
+    const int64_t npix = (int64_t)N * H * W;
+    const int groups = Cp / 8;
+    const int64_t plane = npix * Cp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < npix * groups;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pix = e % npix;
+        const int cg = (int)(e / npix);
+        const int n = (int)(pix / ((int64_t)H * W));
+        const int64_t yx = pix % ((int64_t)H * W);
+        __align__(16) __nv_bfloat16 t0[8], t1[8], t2[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int c = cg * 8 + k;
+            const float x = c < Cin ? at(in, n, c, H, W)[yx] : 0.f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            const float r1 = x - __bfloat162float(h);
+            const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+            t0[k] = h;
+            t1[k] = l;
+            t2[k] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+        }
+        const int64_t off = pix * Cp + cg * 8;
+        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(t0);
+        *reinterpret_cast<uint4*>(dst + plane + off) = *reinterpret_cast<const uint4*>(t1);
+        *reinterpret_cast<uint4*>(dst + 2 * plane + off) = *reinterpret_cast<const uint4*>(t2);
+    }
+}
+
+// Weights of a tensor-core convolution: wt[o][tap][c] = W[o][c][tap] (BF16 copy),
+// zero for o >= Cout or c >= Cin
+__global__ void pack_wtc_kernel(const __nv_bfloat16* wb, int Cin, int Cout, int Cp, int Npad, __nv_bfloat16* wt)
+{
+    const int64_t total = (int64_t)Npad * 9 * Cp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % Cp), tap = (int)((e / Cp) % 9), o = (int)(e / (9 * (int64_t)Cp));
+        wt[e] = (o < Cout && c < Cin) ? wb[((int64_t)o * Cin + c) * 9 + tap] : __float2bfloat16_rn(0.f);
+    }
+}
+
 }  // namespace unet
 }  // namespace grbk
 
@@ -348,6 +393,12 @@ struct grbk_unet {
     double* lpart_host;
     cudaStream_t stream;
     int cap_n, cap_h, cap_w;  // arena capacity
+    int use_tc;               // tensor-core convolutions where the layer allows (default on)
+    __nv_bfloat16* xs;        // tensor-core input planes (largest layer)
+    size_t xs_elems;
+    __nv_bfloat16* wtc;       // tensor-core weight layouts, per layer at wtc_off
+    int64_t wtc_off[16];
+    int* tc_err;              // device flag: a bounded wait of the tensor-core kernel expired
 };
 
 static void unet_layers(grbk_unet* u)
@@ -401,9 +452,67 @@ static const View kNone = {nullptr, 0, 0};
 
 static unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 65535); }
 
+// The tensor-core path takes layers with at least 16 input and 16 to 128 output
+// channels (the first and last layers, with one channel, stay on the SIMT kernel).
+static bool tc_layer(const grbk_unet* u, int l)
+{
+    return u->use_tc && u->L[l].cin >= 16 && u->L[l].cout >= 16 && u->L[l].cout <= 128;
+}
+static int tc_cp(int cin) { return (cin + 63) / 64 * 64; }
+static int tc_npad(int cout) { return (cout + 15) / 16 * 16; }
+
+// resolution level (1, 2, 3) of each layer's input
+static int layer_level(int l)
+{
+    switch (l) {
+    case ENC2A: case ENC2B: case DEC2A: case DEC2B: return 2;
+    case BOTA: case BOTB: return 3;
+    default: return 1;
+    }
+}
+
+static grbk_status tc_prepare(grbk_unet* u, int N, int H, int W)
+{
+    size_t need = 0;
+    for (int l = 0; l < NLAYERS; ++l) {
+        if (!tc_layer(u, l)) continue;
+        const int sh = layer_level(l) - 1;
+        need = std::max(need, (size_t)3 * N * (H >> sh) * (W >> sh) * tc_cp(u->L[l].cin));
+    }
+    if (need > u->xs_elems) {
+        if (u->xs) cudaFree(u->xs);
+        u->xs = nullptr;
+        u->xs_elems = 0;
+        if (cudaMalloc(&u->xs, need * 2) != cudaSuccess) return GRBK_ENOMEM;
+        u->xs_elems = need;
+    }
+    if (!u->wtc) {
+        int64_t off = 0;
+        for (int l = 0; l < NLAYERS; ++l) {
+            u->wtc_off[l] = off;
+            if (tc_layer(u, l)) off += (int64_t)tc_npad(u->L[l].cout) * 9 * tc_cp(u->L[l].cin);
+        }
+        if (cudaMalloc(&u->wtc, std::max<int64_t>(off, 1) * 2) != cudaSuccess) return GRBK_ENOMEM;
+        if (cudaMalloc(&u->tc_err, sizeof(int)) != cudaSuccess) return GRBK_ENOMEM;
+        if (cudaMemsetAsync(u->tc_err, 0, sizeof(int), u->stream) != cudaSuccess) return GRBK_ECUDA;
+    }
+    return GRBK_OK;
+}
+
 static cudaError_t conv(grbk_unet* u, int l, View in, View out, int N, int H, int W)
 {
     const LayerDef& d = u->L[l];
+    if (tc_layer(u, l) && tc_conv_fits(H, W)) {
+        const int Cp = tc_cp(d.cin), Np = tc_npad(d.cout);
+        const int64_t npix = (int64_t)N * H * W;
+        pack_nhwc3_kernel<<<blocks_for(npix * (Cp / 8)), 256, 0, u->stream>>>(in, d.cin, N, H, W, Cp, u->xs);
+        pack_wtc_kernel<<<blocks_for((int64_t)Np * 9 * Cp), 256, 0, u->stream>>>(u->wb + d.woff, d.cin, d.cout, Cp, Np,
+                                                                                u->wtc + u->wtc_off[l]);
+        const grbk_status s = tc_conv3x3(u->xs, N, H, W, Cp, u->wtc + u->wtc_off[l], Np, d.cout, u->params + d.boff,
+                                         d.relu, out.p, out.ctot, out.c0, u->tc_err, u->stream);
+        if (s != GRBK_OK) return cudaErrorUnknown;
+        return cudaGetLastError();
+    }
     const int tiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
     if (d.cout == 1) {  // the output layer: one channel per CTA instead of CO_T mostly empty ones
         dim3 grid((unsigned)tiles, 1u, (unsigned)N);
@@ -465,10 +574,23 @@ static grbk_status ensure_arena(grbk_unet* u, int N, int H, int W, bool train)
     return GRBK_OK;
 }
 
+// GRBK_ETIMEOUT when a bounded wait of the tensor-core convolution expired (the
+// flag stays set: later convolutions leave at once, so the network's outputs
+// are not trusted until the handle is destroyed)
+static grbk_status tc_check(grbk_unet* u)
+{
+    if (!u->tc_err) return GRBK_OK;
+    int h = 0;
+    GRBK_CK(cudaMemcpyAsync(&h, u->tc_err, sizeof(int), cudaMemcpyDeviceToHost, u->stream));
+    GRBK_CK(cudaStreamSynchronize(u->stream));
+    return h ? GRBK_ETIMEOUT : GRBK_OK;
+}
+
 static cudaError_t forward(grbk_unet* u, const Acts& a, const float* C, int N, int H, int W)
 {
     const int w = u->w, H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4;
     cudaError_t e;
+    if (u->use_tc && tc_prepare(u, N, H, W) != GRBK_OK) return cudaErrorMemoryAllocation;
     if ((e = conv(u, ENC1A, V((float*)C, 1), V(a.a1, w), N, H, W)) != cudaSuccess) return e;
     if ((e = conv(u, ENC1B, V(a.a1, w), V(a.D1, 3 * w, 2 * w), N, H, W)) != cudaSuccess) return e;
     pool_fwd_kernel<<<blocks_for((int64_t)N * w * H2 * W2), 256, 0, u->stream>>>(V(a.D1, 3 * w, 2 * w), V(a.p1, w), w, N, H, W);
@@ -535,6 +657,7 @@ extern "C" grbk_status grbk_unet_create(grbk_unet** out, int32_t width, void* st
     memset(u, 0, sizeof(*u));
     u->w = width;
     u->stream = (cudaStream_t)stream;
+    u->use_tc = 1;
     unet_layers(u);
     const size_t np = (size_t)u->nparams;
     if (cudaMalloc(&u->params, np * 4) != cudaSuccess || cudaMalloc(&u->wb, np * 2) != cudaSuccess ||
@@ -599,11 +722,13 @@ extern "C" grbk_status grbk_unet_forward(grbk_unet* u, const float* C, int32_t n
         GRBK_CK(cudaGetLastError());
     }
     GRBK_CK(cudaStreamSynchronize(u->stream));
-    return GRBK_OK;
+    return tc_check(u);
 }
 
 static grbk_status loss_and_grad(grbk_unet* u, const float* C, const float* T, int n, int h, int w, double* loss)
 {
+    const grbk_status tcs = tc_check(u);
+    if (tcs != GRBK_OK) return tcs;
     grbk_status s = ensure_arena(u, n, h, w, true);
     if (s != GRBK_OK) return s;
     float* p = u->arena;
@@ -655,10 +780,17 @@ extern "C" grbk_status grbk_unet_train_step(grbk_unet* u, const float* C, const 
     return GRBK_OK;
 }
 
+extern "C" grbk_status grbk_unet_use_tensor_cores(grbk_unet* u, int32_t on)
+{
+    if (!u) return GRBK_EINVAL;
+    u->use_tc = on ? 1 : 0;
+    return GRBK_OK;
+}
+
 extern "C" void grbk_unet_destroy(grbk_unet* u)
 {
     if (!u) return;
-    void* bufs[] = {u->params, u->wb, u->grad, u->m1, u->m2, u->arena, u->wpart, u->lpart};
+    void* bufs[] = {u->params, u->wb, u->grad, u->m1, u->m2, u->arena, u->wpart, u->lpart, u->xs, u->wtc, u->tc_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (u->lpart_host) cudaFreeHost(u->lpart_host);
