@@ -749,25 +749,26 @@ def unet_bench(args):
     out = {"mode": "unet", "channels": 16, "side": 512, "width": 20}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     X = {}
-    for tc in (True, False):
-        g.grbk_unet_use_tensor_cores(net, tc)
-        X[tc] = torch.empty_like(C)
+    names = {1: "forward_ms_tensor_cores", 2: "forward_ms_tensor_cores_one_load_per_tap", 0: "forward_ms_simt"}
+    for mode in (1, 2, 0):
+        g.grbk_unet_use_tensor_cores(net, mode)
+        X[mode] = torch.empty_like(C)
         for _ in range(3):
-            g.grbk_unet_forward(net, C, X[tc])
+            g.grbk_unet_forward(net, C, X[mode])
         torch.cuda.synchronize()
         ev0.record()
-        g.grbk_unet_forward(net, C, X[tc])
+        g.grbk_unet_forward(net, C, X[mode])
         ev1.record()
         torch.cuda.synchronize()
-        out["forward_ms_tensor_cores" if tc else "forward_ms_simt"] = ev0.elapsed_time(ev1)
+        out[names[mode]] = ev0.elapsed_time(ev1)
     out["speedup"] = out["forward_ms_simt"] / out["forward_ms_tensor_cores"]
-    out["max_rel_diff"] = float((X[True] - X[False]).abs().max() / (X[False] - C).abs().max())
+    out["max_rel_diff"] = float((X[1] - X[0]).abs().max() / (X[0] - C).abs().max())
     # 192 channels of 512^2 (64 RGB images, the warm start's evaluation) in batches of 16
-    g.grbk_unet_use_tensor_cores(net, True)
+    g.grbk_unet_use_tensor_cores(net, 1)
     torch.cuda.synchronize()
     ev0.record()
     for _ in range(12):
-        g.grbk_unet_forward(net, C, X[True])
+        g.grbk_unet_forward(net, C, X[1])
     ev1.record()
     torch.cuda.synchronize()
     out["forward_ms_192_channels_tensor_cores"] = ev0.elapsed_time(ev1)

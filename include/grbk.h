@@ -413,14 +413,16 @@ grbk_status grbk_unet_loss_grad(grbk_unet* net, const float* C, const float* T, 
 grbk_status grbk_unet_train_step(grbk_unet* net, const float* C, const float* T, int32_t n, int32_t h, int32_t w,
                                  float lr, double* loss);
 /* Convolution path (not part of the paper): on = 1 (the default) runs every
- * convolution with 16 to 128 output channels and at least 16 input channels
- * of the forward pass on the tensor cores -- an implicit GEMM (tcgen05.mma,
- * TMEM accumulators, TMA loads whose out-of-range coordinates give the zero
- * padding) over a three-term BF16 split of the FP32 activations and the BF16
- * weights, accumulated in FP32; on = 0 keeps every convolution on the SIMT
- * kernel.  The backward passes always use the SIMT kernels.  A bounded wait
- * of the tensor-core kernel that expires makes the next forward, loss or
- * training call return GRBK_ETIMEOUT. */
+ * convolution of the forward pass with 16 to 128 input and output channels on
+ * the tensor cores -- an implicit GEMM (tcgen05.mma, TMEM accumulators, TMA
+ * loads whose out-of-range coordinates give the zero padding) over a
+ * three-term BF16 split of the FP32 activations and the BF16 weights,
+ * accumulated in FP32; images at least 128 pixels wide load each kernel row's
+ * input pixels once for its three taps.  on = 2: tensor cores with one load
+ * per tap (the general tiling, for comparison); on = 0: every convolution on
+ * the SIMT kernel.  The backward passes always use the SIMT kernels.  A
+ * bounded wait of the tensor-core kernel that expires makes the next forward,
+ * loss or training call return GRBK_ETIMEOUT.  EINVAL for other values. */
 grbk_status grbk_unet_use_tensor_cores(grbk_unet* net, int32_t on);
 void grbk_unet_destroy(grbk_unet* net);
 

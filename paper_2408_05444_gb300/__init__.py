@@ -608,8 +608,10 @@ def grbk_unet_train_step(net: UNetHandle, C, T, lr) -> float:
     return loss.value
 
 
-def grbk_unet_use_tensor_cores(net: UNetHandle, on: bool = True):
-    st = lib().grbk_unet_use_tensor_cores(net.handle, int(bool(on)))
+def grbk_unet_use_tensor_cores(net: UNetHandle, on=True):
+    """on: True/1 tensor cores (row-halo tiles where the image allows), 2 tensor cores with
+    one load per tap, False/0 SIMT."""
+    st = lib().grbk_unet_use_tensor_cores(net.handle, int(on))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_unet_use_tensor_cores")
 

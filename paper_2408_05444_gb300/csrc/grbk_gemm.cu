@@ -698,6 +698,175 @@ __global__ void __launch_bounds__(256, 1) conv_tc_kernel(const __grid_constant__
     }
 }
 
+// Variant for images at least 128 pixels wide: a tile is 128 pixels of one
+// image row, and for each kernel row dy one TMA brings the 130 input pixels
+// the three taps (dy, -1..1) need (one halo pixel on each side, zeros past the
+// image).  The three A operands are that smem tile read from rows 0, 1 and 2:
+// a start address one 128-byte row apart, with the descriptor's matrix base
+// offset carrying the row's phase in the 8-row swizzle pattern.  Each input
+// pixel crosses L2 three times per term instead of nine.
+constexpr int HALO_ROWS = 130;
+constexpr int HALO_TERM_BYTES = 17 * 1024;                          // 130 rows of 128 B, 1024-aligned
+constexpr int HALO_A_BYTES = CONV_TERMS * HALO_TERM_BYTES;          // 51 KB
+constexpr int HALO_STAGE_BYTES = HALO_A_BYTES + 3 * 128 * BK * 2;   // + three taps of B, up to 128 channels
+constexpr int HALO_SMEM_BYTES = CONV_STAGES * HALO_STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ uint64_t sdesc_rows(uint32_t saddr)
+{
+    return sdesc(saddr) | ((uint64_t)((saddr >> 7) & 7u) << 49);   // matrix base offset
+}
+
+__global__ void __launch_bounds__(256, 1) conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                              const __grid_constant__ CUtensorMap tmW, ConvArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    auto sA = [&](int s, int t) { return smem + s * HALO_STAGE_BYTES + t * HALO_TERM_BYTES; };
+    auto sB = [&](int s, int j) { return smem + s * HALO_STAGE_BYTES + HALO_A_BYTES + j * (g.Npad * BK * 2); };
+    uint64_t* bars = (uint64_t*)(smem + CONV_STAGES * HALO_STAGE_BYTES);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + CONV_STAGES);
+    const uint32_t accf0 = smem_u32(bars + 2 * CONV_STAGES), acce0 = smem_u32(bars + 2 * CONV_STAGES + 2);
+    const uint32_t done = smem_u32(bars + 2 * CONV_STAGES + 4);
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * CONV_STAGES + 5);
+    __shared__ int s_abort;
+
+    if (*(volatile int*)g.err != 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkc = g.Cp / BK;
+    const int nkb = 3 * nkc;                      // (dy, channel chunk)
+    const int ntiles = g.nimg * g.H * g.tiles_x;  // one tile = 128 pixels of one row
+    const uint32_t idesc = idesc_for(g.Npad);
+    const uint32_t stage_tx = (uint32_t)(CONV_TERMS * HALO_ROWS * 128 + 3 * g.Npad * BK * 2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CONV_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(accf0 + 8 * a, 1);
+            mbar_init(acce0 + 8 * a, 4);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(g.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *(volatile uint32_t*)tmem_slot;
+
+    auto tile_origin = [&](int tile, int& n, int& y0, int& x0) {
+        const int per = g.H * g.tiles_x;
+        n = tile / per;
+        const int r = tile % per;
+        y0 = r / g.tiles_x;
+        x0 = (r % g.tiles_x) * 128;
+    };
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+            int n, y0, x0;
+            tile_origin(tile, n, y0, x0);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int dyi = kb / nkc, kc = kb % nkc;    // dy = dyi - 1
+                const int s = issued % CONV_STAGES;
+                const uint32_t ph = (uint32_t)((issued / CONV_STAGES) & 1);
+                if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                mbar_expect_tx(full0 + 8 * s, stage_tx);
+#pragma unroll
+                for (int t = 0; t < CONV_TERMS; ++t)
+                    tma_load_4d(smem_u32(sA(s, t)), &tmX, kc * BK, x0 - 1, y0 + dyi - 1, t * g.nimg + n, full0 + 8 * s);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    tma_load_2d(smem_u32(sB(s, j)), &tmW, (dyi * 3 + j) * g.Cp + kc * BK, 0, full0 + 8 * s);
+                ++issued;
+            }
+        }
+        for (int it = (issued > CONV_STAGES ? issued - CONV_STAGES : 0); it < issued; ++it)
+            mbar_wait(full0 + 8 * (it % CONV_STAGES), (uint32_t)((it / CONV_STAGES) & 1));
+    } else if (warp == 1 && lane == 0) {
+        int it = 0, lt = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            if (!mbar_wait(acce0 + 8 * acc, (uint32_t)(((lt >> 1) & 1) ^ 1))) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)(acc * (g.tmem_cols / 2));
+            for (int kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = it % CONV_STAGES;
+                const uint32_t ph = (uint32_t)((it / CONV_STAGES) & 1);
+                if (!mbar_wait(full0 + 8 * s, ph)) { s_abort = 1; stop = true; break; }
+                if (*(volatile int*)&s_abort) { stop = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {           // dx = j - 1: A rows j .. j + 127
+                    const uint32_t b0 = smem_u32(sB(s, j));
+#pragma unroll
+                    for (int t = CONV_TERMS - 1; t >= 0; --t) {
+                        const uint32_t a0 = smem_u32(sA(s, t)) + (uint32_t)(j * 128);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk)
+                            mma_bf16(dacc, sdesc_rows(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
+                                     (kb > 0 || j > 0 || t < CONV_TERMS - 1 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                mma_commit(empty0 + 8 * s);
+            }
+            if (!stop) mma_commit(accf0 + 8 * acc);
+        }
+        mma_commit(done);
+    } else if (warp >= 4) {
+        const int e = warp - 4;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int acc = lt & 1;
+            const bool ok = mbar_wait(accf0 + 8 * acc, (uint32_t)((lt >> 1) & 1));
+            if (!ok || *(volatile int*)&s_abort) { s_abort = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            int n, y0, x0;
+            tile_origin(tile, n, y0, x0);
+            const int x = x0 + e * 32 + lane;
+            const bool valid = x < g.W;
+            float* obase = g.out + (((int64_t)n * g.out_ctot + g.out_c0) * g.H + y0) * g.W + x;
+            const int64_t cstride = (int64_t)g.H * g.W;
+            for (int cb = 0; cb < g.Npad; cb += 32) {
+                uint32_t v[32];
+                tmem_ld32(tmem + (uint32_t)(acc * (g.tmem_cols / 2)) + ((uint32_t)(e * 32) << 16) + (uint32_t)cb, v);
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int o = cb + j;
+                    if (o >= g.Cout) break;
+                    float val = __uint_as_float(v[j]) + (g.bias ? g.bias[o] : 0.f);
+                    if (g.relu) val = fmaxf(val, 0.f);
+                    obase[(int64_t)o * cstride] = val;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * acc);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int*)&s_abort) atomicExch(g.err, 1);
+    if (warp == 2) {
+        mbar_wait(done, 0);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols) : "memory");
+    }
+}
+
 }  // namespace tc
 
 struct SplitGemm {
@@ -870,7 +1039,8 @@ static int conv_boxw(int W)
 bool tc_conv_fits(int H, int W) { return W >= 1 && 128 / conv_boxw(W) <= H; }
 
 grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const void* wtc, int Npad, int Cout,
-                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st)
+                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st,
+                       bool halo)
 {
     if (Cp % tc::BK != 0 || Npad % 16 != 0 || Npad < 16 || Npad > 128 || Cout > Npad) return GRBK_EINVAL;
     if (!tc_conv_fits(H, W)) return GRBK_EINVAL;
@@ -878,11 +1048,13 @@ grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const voi
     if (!enc) return GRBK_ECUDA;
     const int boxw = conv_boxw(W);
     const int boxh = 128 / boxw;
+    halo = halo && boxw == 128;   // the row variant needs images at least 128 pixels wide
     CUtensorMap tmX, tmW;
     {
         cuuint64_t dims[4] = {(cuuint64_t)Cp, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(tc::CONV_TERMS * nimg)};
         cuuint64_t strides[3] = {(cuuint64_t)Cp * 2, (cuuint64_t)W * Cp * 2, (cuuint64_t)H * W * Cp * 2};
-        cuuint32_t box[4] = {(cuuint32_t)tc::BK, (cuuint32_t)boxw, (cuuint32_t)boxh, 1};
+        cuuint32_t box[4] = {(cuuint32_t)tc::BK, halo ? (cuuint32_t)tc::HALO_ROWS : (cuuint32_t)boxw,
+                             halo ? 1u : (cuuint32_t)boxh, 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
         if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)xs, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -909,13 +1081,22 @@ grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const voi
     while (cols < 2 * ((Npad + 31) / 32 * 32)) cols <<= 1;   // two accumulators, each a power-of-two slot
     a.tmem_cols = cols;
     a.bias = bias; a.relu = relu; a.out = out; a.out_ctot = out_ctot; a.out_c0 = out_c0; a.err = err;
-    GRBK_CK(cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::CONV_SMEM_BYTES));
     int dev = 0, nsm = 0;
     GRBK_CK(cudaGetDevice(&dev));
     GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t ntiles = (int64_t)nimg * a.tiles_y * a.tiles_x;
-    dim3 grid((unsigned)std::min<int64_t>(ntiles, nsm));
-    tc::conv_tc_kernel<<<grid, 256, tc::CONV_SMEM_BYTES, st>>>(tmX, tmW, a);
+    if (halo) {
+        GRBK_CK(cudaFuncSetAttribute(tc::conv_tc_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::HALO_SMEM_BYTES));
+        const int64_t ntiles = (int64_t)nimg * H * a.tiles_x;
+        dim3 grid((unsigned)std::min<int64_t>(ntiles, nsm));
+        tc::conv_tc_halo_kernel<<<grid, 256, tc::HALO_SMEM_BYTES, st>>>(tmX, tmW, a);
+    } else {
+        GRBK_CK(cudaFuncSetAttribute(tc::conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::CONV_SMEM_BYTES));
+        const int64_t ntiles = (int64_t)nimg * a.tiles_y * a.tiles_x;
+        dim3 grid((unsigned)std::min<int64_t>(ntiles, nsm));
+        tc::conv_tc_kernel<<<grid, 256, tc::CONV_SMEM_BYTES, st>>>(tmX, tmW, a);
+    }
     GRBK_CK(cudaGetLastError());
     return GRBK_OK;
 }

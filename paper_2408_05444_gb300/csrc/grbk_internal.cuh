@@ -238,9 +238,12 @@ int splitgemm_launches(const SplitGemm* g);
 // the FP32 activations), weights wtc = [Npad][9 taps][Cp] BF16 (Npad a multiple of 16,
 // at most 128); out[n][out_c0 + o][y][x] (NCHW FP32, out_ctot channels) = bias[o] +
 // sum over taps and channels, then ReLU when relu != 0, for o < Cout.  err: device
-// flag set when a bounded wait expires.
+// flag set when a bounded wait expires.  halo: images at least 128 pixels wide
+// take the variant that loads each kernel row's 130 input pixels once for its
+// three taps.
 grbk_status tc_conv3x3(const void* xs, int nimg, int H, int W, int Cp, const void* wtc, int Npad, int Cout,
-                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st);
+                       const float* bias, int relu, float* out, int out_ctot, int out_c0, int* err, cudaStream_t st,
+                       bool halo);
 // whether an H x W image fits the tensor-core convolution's 128-pixel tile (its rows
 // of a power-of-two width up to 128 stack no higher than H)
 bool tc_conv_fits(int H, int W);

@@ -309,34 +309,46 @@ __global__ void to_bf16_kernel(const float* w, __nv_bfloat16* wb, int64_t len)
 // Input of a tensor-core convolution: channels [0, Cin) of an NCHW FP32 view as
 // three BF16 planes [term][n][y][x][Cp] (NHWC, channels padded with zeros to Cp)
 // with x = x0 + x1 + x2, x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).
-// One thread per (8-channel group, pixel), pixels fastest so the reads coalesce.
-__global__ void pack_nhwc3_kernel(View in, int Cin, int N, int H, int W, int Cp, __nv_bfloat16* dst)
+// A CTA transposes 64 consecutive pixels of one image through shared memory:
+// reads of a channel run along the pixels, writes of a pixel run along its
+// channels, both coalesced.
+constexpr int PACK_PIX = 64;
+__global__ void __launch_bounds__(256) pack_nhwc3_kernel(View in, int Cin, int N, int H, int W, int Cp,
+                                                         __nv_bfloat16* dst)
 {
-    const int64_t npix = (int64_t)N * H * W;
-    const int groups = Cp / 8;
-    const int64_t plane = npix * Cp;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < npix * groups;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pix = e % npix;
-        const int cg = (int)(e / npix);
-        const int n = (int)(pix / ((int64_t)H * W));
-        const int64_t yx = pix % ((int64_t)H * W);
-        __align__(16) __nv_bfloat16 t0[8], t1[8], t2[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int c = cg * 8 + k;
-            const float x = c < Cin ? at(in, n, c, H, W)[yx] : 0.f;
-            const __nv_bfloat16 h = __float2bfloat16_rn(x);
-            const float r1 = x - __bfloat162float(h);
-            const __nv_bfloat16 l = __float2bfloat16_rn(r1);
-            t0[k] = h;
-            t1[k] = l;
-            t2[k] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+    __shared__ float tile[128][PACK_PIX + 1];          // Cp <= 128
+    const int64_t hw = (int64_t)H * W;
+    const int64_t blocks_per_img = (hw + PACK_PIX - 1) / PACK_PIX;
+    const int64_t plane = (int64_t)N * hw * Cp;
+    for (int64_t blk = blockIdx.x; blk < (int64_t)N * blocks_per_img; blk += gridDim.x) {
+        const int n = (int)(blk / blocks_per_img);
+        const int64_t p0 = (blk % blocks_per_img) * PACK_PIX;
+        __syncthreads();
+        for (int e = threadIdx.x; e < Cp * PACK_PIX; e += blockDim.x) {
+            const int c = e / PACK_PIX, j = e % PACK_PIX;
+            tile[c][j] = (c < Cin && p0 + j < hw) ? at(in, n, c, H, W)[p0 + j] : 0.f;
         }
-        const int64_t off = pix * Cp + cg * 8;
-        *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(t0);
-        *reinterpret_cast<uint4*>(dst + plane + off) = *reinterpret_cast<const uint4*>(t1);
-        *reinterpret_cast<uint4*>(dst + 2 * plane + off) = *reinterpret_cast<const uint4*>(t2);
+        __syncthreads();
+        const int groups = Cp / 8;
+        for (int e = threadIdx.x; e < PACK_PIX * groups; e += blockDim.x) {
+            const int j = e / groups, cg = e % groups;
+            if (p0 + j >= hw) continue;
+            __align__(16) __nv_bfloat16 t0[8], t1[8], t2[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float x = tile[cg * 8 + k][j];
+                const __nv_bfloat16 h = __float2bfloat16_rn(x);
+                const float r1 = x - __bfloat162float(h);
+                const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+                t0[k] = h;
+                t1[k] = l;
+                t2[k] = __float2bfloat16_rn(r1 - __bfloat162float(l));
+            }
+            const int64_t off = ((int64_t)n * hw + p0 + j) * Cp + cg * 8;
+            *reinterpret_cast<uint4*>(dst + off) = *reinterpret_cast<const uint4*>(t0);
+            *reinterpret_cast<uint4*>(dst + plane + off) = *reinterpret_cast<const uint4*>(t1);
+            *reinterpret_cast<uint4*>(dst + 2 * plane + off) = *reinterpret_cast<const uint4*>(t2);
+        }
     }
 }
 
@@ -452,11 +464,11 @@ static const View kNone = {nullptr, 0, 0};
 
 static unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 65535); }
 
-// The tensor-core path takes layers with at least 16 input and 16 to 128 output
-// channels (the first and last layers, with one channel, stay on the SIMT kernel).
+// The tensor-core path takes layers with 16 to 128 input and output channels (the
+// first and last layers, with one channel, stay on the SIMT kernel).
 static bool tc_layer(const grbk_unet* u, int l)
 {
-    return u->use_tc && u->L[l].cin >= 16 && u->L[l].cout >= 16 && u->L[l].cout <= 128;
+    return u->use_tc && u->L[l].cin >= 16 && u->L[l].cin <= 128 && u->L[l].cout >= 16 && u->L[l].cout <= 128;
 }
 static int tc_cp(int cin) { return (cin + 63) / 64 * 64; }
 static int tc_npad(int cout) { return (cout + 15) / 16 * 16; }
@@ -505,11 +517,13 @@ static cudaError_t conv(grbk_unet* u, int l, View in, View out, int N, int H, in
     if (tc_layer(u, l) && tc_conv_fits(H, W)) {
         const int Cp = tc_cp(d.cin), Np = tc_npad(d.cout);
         const int64_t npix = (int64_t)N * H * W;
-        pack_nhwc3_kernel<<<blocks_for(npix * (Cp / 8)), 256, 0, u->stream>>>(in, d.cin, N, H, W, Cp, u->xs);
+        const int64_t pblocks = (int64_t)N * (((int64_t)H * W + PACK_PIX - 1) / PACK_PIX);
+        pack_nhwc3_kernel<<<(unsigned)std::min<int64_t>(pblocks, 65535), 256, 0, u->stream>>>(in, d.cin, N, H, W, Cp,
+                                                                                              u->xs);
         pack_wtc_kernel<<<blocks_for((int64_t)Np * 9 * Cp), 256, 0, u->stream>>>(u->wb + d.woff, d.cin, d.cout, Cp, Np,
                                                                                 u->wtc + u->wtc_off[l]);
         const grbk_status s = tc_conv3x3(u->xs, N, H, W, Cp, u->wtc + u->wtc_off[l], Np, d.cout, u->params + d.boff,
-                                         d.relu, out.p, out.ctot, out.c0, u->tc_err, u->stream);
+                                         d.relu, out.p, out.ctot, out.c0, u->tc_err, u->stream, u->use_tc == 1);
         if (s != GRBK_OK) return cudaErrorUnknown;
         return cudaGetLastError();
     }
@@ -783,7 +797,8 @@ extern "C" grbk_status grbk_unet_train_step(grbk_unet* u, const float* C, const 
 extern "C" grbk_status grbk_unet_use_tensor_cores(grbk_unet* u, int32_t on)
 {
     if (!u) return GRBK_EINVAL;
-    u->use_tc = on ? 1 : 0;
+    if (on < 0 || on > 2) return GRBK_EINVAL;
+    u->use_tc = on;
     return GRBK_OK;
 }
 
