@@ -702,19 +702,16 @@ __global__ void __launch_bounds__(256, 1) conv_tc_kernel(const __grid_constant__
 // image row, and for each kernel row dy one TMA brings the 130 input pixels
 // the three taps (dy, -1..1) need (one halo pixel on each side, zeros past the
 // image).  The three A operands are that smem tile read from rows 0, 1 and 2:
-// a start address one 128-byte row apart, with the descriptor's matrix base
-// offset carrying the row's phase in the 8-row swizzle pattern.  Each input
-// pixel crosses L2 three times per term instead of nine.
+// start addresses one 128-byte row apart.  The TMA writes the 128-byte swizzle
+// as a function of the shared-memory address (the tile starts on a 1024-byte
+// boundary), and the MMA unswizzles by address in the same way, so a shifted
+// start needs no other change.  Each input pixel crosses L2 three times per
+// term instead of nine.
 constexpr int HALO_ROWS = 130;
 constexpr int HALO_TERM_BYTES = 17 * 1024;                          // 130 rows of 128 B, 1024-aligned
 constexpr int HALO_A_BYTES = CONV_TERMS * HALO_TERM_BYTES;          // 51 KB
 constexpr int HALO_STAGE_BYTES = HALO_A_BYTES + 3 * 128 * BK * 2;   // + three taps of B, up to 128 channels
 constexpr int HALO_SMEM_BYTES = CONV_STAGES * HALO_STAGE_BYTES + 1024 + 256;
-
-__device__ __forceinline__ uint64_t sdesc_rows(uint32_t saddr)
-{
-    return sdesc(saddr) | ((uint64_t)((saddr >> 7) & 7u) << 49);   // matrix base offset
-}
 
 __global__ void __launch_bounds__(256, 1) conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmX,
                                                               const __grid_constant__ CUtensorMap tmW, ConvArgs g)
@@ -816,7 +813,7 @@ __global__ void __launch_bounds__(256, 1) conv_tc_halo_kernel(const __grid_const
                         const uint32_t a0 = smem_u32(sA(s, t)) + (uint32_t)(j * 128);
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
-                            mma_bf16(dacc, sdesc_rows(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
+                            mma_bf16(dacc, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc,
                                      (kb > 0 || j > 0 || t < CONV_TERMS - 1 || kk > 0) ? 1u : 0u);
                     }
                 }
