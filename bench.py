@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--epochs", type=int, default=2)
     ap.add_argument("--batch-maxit", type=int, default=5_000_000)
     ap.add_argument("--batch-images", type=int, default=64)
+    ap.add_argument("--unet-channels", type=int, default=16, help="--mode unet: channels of 512^2 per forward")
+    ap.add_argument("--colour-iters", type=int, default=150_000, help="--mode colour: iterations per variant")
     return ap.parse_args()
 
 
@@ -713,7 +715,7 @@ def colour_bench(args):
           for i, (h, w) in enumerate(workloads.COLOUR_SIZES.values())]
     As = [sps.csr_matrix((d["A"][2], d["A"][1], d["A"][0]), shape=(d["h"] * d["w"],) * 2) for d in ds]
     sp = g.grbk_sparse_create(As, [d["B"] for d in ds], [d["C"] for d in ds])
-    K = 150_000
+    K = args.colour_iters
     out = {"mode": "colour", "images": names, "iterations": K, "dtype": "f64", "blurred": {}, "variants": {}}
     for nm, d in zip(names, ds):
         bl = workloads.unvec_image(d["C"], d["h"], d["w"])
@@ -745,8 +747,9 @@ def unet_bench(args):
     import paper_2408_05444_gb300 as g
     from paper_2408_05444_gb300 import warmstart as ws
     net = ws.make_net(width=20, seed=0)
-    C = torch.rand(16, 512, 512, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-    out = {"mode": "unet", "channels": 16, "side": 512, "width": 20}
+    nch = args.unet_channels
+    C = torch.rand(nch, 512, 512, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    out = {"mode": "unet", "channels": nch, "side": 512, "width": 20}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     X = {}
     names = {1: "forward_ms_tensor_cores", 2: "forward_ms_tensor_cores_one_load_per_tap", 0: "forward_ms_simt"}
@@ -767,7 +770,7 @@ def unet_bench(args):
     g.grbk_unet_use_tensor_cores(net, 1)
     torch.cuda.synchronize()
     ev0.record()
-    for _ in range(12):
+    for _ in range(192 // nch):
         g.grbk_unet_forward(net, C, X[1])
     ev1.record()
     torch.cuda.synchronize()

@@ -43,7 +43,7 @@ constexpr int kSpBlk = 256;               // rows per summary block
 constexpr int kSpRowsPerLane = kSpBlk / 32;
 constexpr int kSpMaxBlocks = 1024;        // m <= 262144
 constexpr int kSpMaxSide = 1024;          // q, n <= 1024 (R_{i_k}, w, v in shared memory)
-constexpr int kSpMaxRowNnz = 1024;        // nonzeros of one row of A staged in shared memory
+constexpr int kSpMaxRowNnz = 256;         // nonzeros of one row of A staged in shared memory (more: read from L2)
 
 struct SpDesc {
     int m, p, q, n;
@@ -80,9 +80,6 @@ struct SpParams {
     const double* pref;        // running sums of a_i (ME-RBK)
     double* s;                 // ||R_i||^2
     double* r;                 // s_i / a_i (-inf for a zero row of A)
-    double* blk_sum;           // per block: sum of s
-    long long* blk_key;        // per block: largest r as an IEEE bit pattern (r >= 0 or -inf)
-    int* blk_arg;              // per block: its smallest row attaining it
     long long* iters;
     double* S_out;
     int* flag_out;
@@ -359,8 +356,10 @@ __global__ void __launch_bounds__(kSpT) sp_setup_kernel(SpParams P, double* a_ou
 // ---------------------------------------------------------------------------
 
 // summary of block b: sum of s over its rows (lane partials in row order, then
-// a fixed tree), largest r key and the smallest row attaining it; one warp
-__device__ __forceinline__ void sp_block_summary(const SpParams& P, const SpDesc& d, int b)
+// a fixed tree), largest r key and the smallest row attaining it; one warp.
+// The summaries live in the shared memory of the CTA that runs the system.
+__device__ __forceinline__ void sp_block_summary(const SpParams& P, const SpDesc& d, int b, double* bsum,
+                                                 long long* bkey, int* barg)
 {
     const int lane = threadIdx.x & 31;
     const double* s = P.s + d.offRow;
@@ -386,9 +385,9 @@ __device__ __forceinline__ void sp_block_summary(const SpParams& P, const SpDesc
         if (ok > key || (ok == key && oa < arg)) { key = ok; arg = oa; }
     }
     if (lane == 0) {
-        P.blk_sum[d.offBlk + b] = sum;
-        P.blk_key[d.offBlk + b] = key;
-        P.blk_arg[d.offBlk + b] = arg;
+        bsum[b] = sum;
+        bkey[b] = key;
+        barg[b] = arg;
     }
 }
 
@@ -420,22 +419,23 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
         P.s[d.offRow + i] = acc;
         P.r[d.offRow + i] = a[i] > 0.0 ? __ddiv_rn(acc, a[i]) : -INFINITY;
     }
-    __syncthreads();
-    for (int b = threadIdx.x >> 5; b < d.nb; b += kSpW) sp_block_summary(P, d, b);
 }
 
-__global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
+__global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 {
     __shared__ double s_row[kSpMaxSide];      // R_{i_k}, then v
     __shared__ double s_w[kSpMaxSide];        // w; the extended method's z / ||A_{:,j}||^2
-    __shared__ double s_sj[kSpMaxBlocks];     // admitted sum per block
+    __shared__ double s_bsum[kSpMaxBlocks];   // per block of 256 rows: sum of s,
+    __shared__ long long s_bkey[kSpMaxBlocks];//   its largest r (IEEE bits)
+    __shared__ int s_barg[kSpMaxBlocks];      //   and the smallest row attaining it
     __shared__ int s_anz_c[kSpMaxRowNnz];     // nonzeros of A_{i_k}
     __shared__ double s_anz_v[kSpMaxRowNnz];
     __shared__ unsigned s_dirty[kSpMaxBlocks / 32];
     __shared__ double red[kSpW + 1];
     __shared__ long long redk[kSpW];
     __shared__ int reda[kSpW];
-    __shared__ int s_sys, s_stop, s_pick, s_first_blk, s_last_blk, s_col;
+    __shared__ double s_wbase[kSpW];          // exclusive bases of the warps' admitted sums
+    __shared__ int s_sys, s_stop, s_pick, s_last_adm, s_col;
     __shared__ double s_S, s_rmax, s_target;
     __shared__ int s_imax;
 
@@ -467,10 +467,9 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
         const long long* grp = P.g_rowptr + d.gRow;
         const int* gcol = P.g_col + d.gNz;
         const double* gval = P.g_val + d.gNz;
-        const double* blk_sum = P.blk_sum + d.offBlk;
-        const long long* blk_key = P.blk_key + d.offBlk;
-        const int* blk_arg = P.blk_arg + d.offBlk;
         for (int b = threadIdx.x; b < kSpMaxBlocks / 32; b += kSpT) s_dirty[b] = 0u;
+        for (int b = warp; b < d.nb; b += kSpW) sp_block_summary(P, d, b, s_bsum, s_bkey, s_barg);
+        __syncthreads();
 
         long long k = 0;
         int flag = FLAG_RUNNING;
@@ -533,7 +532,7 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                         while (bits) {
                             const int bit = __ffs(bits) - 1;
                             bits &= bits - 1;
-                            if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit);
+                            if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
                             ++idx;
                         }
                     }
@@ -547,9 +546,9 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                 long long key = LLONG_MIN;
                 int arg = INT_MAX;
                 for (int b = threadIdx.x; b < d.nb; b += kSpT) {
-                    Sv += blk_sum[b];
-                    const long long kk = blk_key[b];
-                    const int aa = blk_arg[b];
+                    Sv += s_bsum[b];
+                    const long long kk = s_bkey[b];
+                    const int aa = s_barg[b];
                     if (kk > key || (kk == key && aa < arg)) { key = kk; arg = aa; }
                 }
                 Sv = warp_sum(Sv);
@@ -596,93 +595,57 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                 double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, d.F)));
                 if (t > s_rmax) t = s_rmax;
                 const long long tkey = __double_as_longlong(t);
-                // admitted sum of every block whose largest r reaches t (one warp per block)
-                for (int b = warp; b < d.nb; b += kSpW) {
-                    double sj = 0.0;
-                    if (blk_key[b] >= tkey) {
-                        const int r0 = b * kSpBlk + lane * kSpRowsPerLane;
-                        double loc = 0.0;
+                // thread T owns the contiguous rows [T K, T K + K); 8-row groups inside blocks whose
+                // largest r is below t are skipped, the others load their r and s at once
+                const int K = (d.m + kSpT - 1) / kSpT;
+                const int q0 = threadIdx.x * K, q1 = min(d.m, q0 + K);
+                double loc = 0.0;
+                int lastadm = -1;
+                for (int i0 = q0; i0 < q1; i0 += 8) {
+                    const int ie = min(q1, i0 + 8);
+                    if (s_bkey[i0 / kSpBlk] < tkey && s_bkey[(ie - 1) / kSpBlk] < tkey) continue;
+                    double rv[8], sv[8];
 #pragma unroll
-                        for (int q2 = 0; q2 < kSpRowsPerLane; ++q2) {
-                            const int i = r0 + q2;
-                            if (i < d.m && __double_as_longlong(r[i]) >= tkey) loc += s[i];
-                        }
-                        sj = warp_inclusive_scan(loc);
-                        sj = __shfl_sync(0xffffffffu, sj, 31);
+                    for (int q2 = 0; q2 < 8; ++q2) {
+                        rv[q2] = (i0 + q2 < ie) ? r[i0 + q2] : -INFINITY;
+                        sv[q2] = (i0 + q2 < ie) ? s[i0 + q2] : 0.0;
                     }
-                    if (lane == 0) s_sj[b] = sj;
+#pragma unroll
+                    for (int q2 = 0; q2 < 8; ++q2)
+                        if (__double_as_longlong(rv[q2]) >= tkey) { loc += sv[q2]; lastadm = i0 + q2; }
+                }
+                // block-wide inclusive scan of the threads' admitted sums (fixed order)
+                const double incw = warp_inclusive_scan(loc);
+                if (lane == 31) red[warp] = incw;
+                if (threadIdx.x == 0) { s_pick = INT_MAX; s_last_adm = -1; }
+                __syncthreads();
+                if (warp == 0) {
+                    const double wt = lane < kSpW ? red[lane] : 0.0;
+                    const double inc = warp_inclusive_scan(wt);
+                    if (lane < kSpW) s_wbase[lane] = inc - wt;
+                    if (lane == kSpW - 1) s_target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), inc);
+                }
+                if (lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // the last admitted row overall
+                __syncthreads();
+                const double target = s_target;
+                const double base = s_wbase[warp];
+                const double incl = base + incw;
+                double excl = __shfl_up_sync(0xffffffffu, incw, 1);
+                excl = base + (lane == 0 ? 0.0 : excl);
+                if (lastadm >= 0 && excl <= target && incl > target) {
+                    // the running sum crosses u S_J inside this thread's rows
+                    double run = excl;
+                    int pick = lastadm;
+                    for (int i = q0; i < q1; ++i)
+                        if (__double_as_longlong(r[i]) >= tkey) {
+                            if (run + s[i] > target) { pick = i; break; }
+                            run += s[i];
+                        }
+                    atomicMin(&s_pick, pick);
                 }
                 __syncthreads();
-                // S_J (blocks in order) and the block the target u S_J falls in
-                if (threadIdx.x == 0) {
-                    double SJ = 0.0;
-                    int last = -1;
-                    for (int b = 0; b < d.nb; ++b)
-                        if (blk_key[b] >= tkey) { SJ += s_sj[b]; last = b; }
-                    const double u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
-                    const double target = __dmul_rn(u, SJ);
-                    double run = 0.0;
-                    int fb = -1;
-                    for (int b = 0; b < d.nb; ++b) {
-                        if (blk_key[b] < tkey) continue;
-                        if (run + s_sj[b] > target) { fb = b; break; }
-                        run += s_sj[b];
-                    }
-                    s_target = fb >= 0 ? target - run : -1.0;   // the target within block fb
-                    s_first_blk = fb;
-                    s_last_blk = last;
-                }
-                __syncthreads();
-                if (warp == 0 && s_first_blk < 0 && s_last_blk < 0) {
-                    if (lane == 0) s_pick = s_imax;   // nothing admitted (cannot happen: t <= r_max)
-                } else if (warp == 0) {
-                    const int fb = s_first_blk;
-                    const int b = fb >= 0 ? fb : s_last_blk;
-                    const int r0 = b * kSpBlk + lane * kSpRowsPerLane;
-                    double loc = 0.0;
-                    int lastadm = -1;
-#pragma unroll
-                    for (int q2 = 0; q2 < kSpRowsPerLane; ++q2) {
-                        const int i = r0 + q2;
-                        if (i < d.m && __double_as_longlong(r[i]) >= tkey) { loc += s[i]; lastadm = i; }
-                    }
-                    if (fb >= 0) {
-                        const double inc = warp_inclusive_scan(loc);
-                        double excl = __shfl_up_sync(0xffffffffu, inc, 1);
-                        if (lane == 0) excl = 0.0;
-                        const double target = s_target;
-                        const bool cross = inc > target && lastadm >= 0;
-                        const unsigned m2 = __ballot_sync(0xffffffffu, cross);
-                        const int src = m2 ? __ffs(m2) - 1 : 31;
-                        int pick = -1;
-                        if (lane == src) {
-                            if (m2) {
-                                double run = excl;
-                                pick = lastadm;
-                                for (int q2 = 0; q2 < kSpRowsPerLane; ++q2) {
-                                    const int i = r0 + q2;
-                                    if (i < d.m && __double_as_longlong(r[i]) >= tkey) {
-                                        if (run + s[i] > target) { pick = i; break; }
-                                        run += s[i];
-                                    }
-                                }
-                            }
-                        }
-                        pick = __shfl_sync(0xffffffffu, pick, src);
-                        if (pick < 0) {   // rounding: take the block's last admitted row
-                            int la = lastadm;
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) la = max(la, __shfl_xor_sync(0xffffffffu, la, o));
-                            pick = la;
-                        }
-                        if (lane == 0) s_pick = pick;
-                    } else {
-                        int la = lastadm;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) la = max(la, __shfl_xor_sync(0xffffffffu, la, o));
-                        if (lane == 0) s_pick = la;
-                    }
-                }
+                if (threadIdx.x == 0 && s_pick == INT_MAX)   // rounding left u S_J uncovered
+                    s_pick = s_last_adm >= 0 ? s_last_adm : s_imax;
             } else if (var == GRBK_MWRBK) {
                 if (threadIdx.x == 0) s_pick = s_imax;
             } else if (var == GRBK_RBK) {
@@ -773,7 +736,7 @@ __global__ void __launch_bounds__(kSpT) sp_solve_kernel(SpParams P)
                     while (bits) {
                         const int bit = __ffs(bits) - 1;
                         bits &= bits - 1;
-                        if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit);
+                        if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
                         ++idx;
                     }
                 }
@@ -814,9 +777,6 @@ struct grbk_sparse {
     int* ac_row = nullptr;
     double *ac_val = nullptr, *cn = nullptr, *cpref = nullptr, *Y = nullptr;
     double *C = nullptr, *R = nullptr, *X = nullptr, *a = nullptr, *pref = nullptr, *s = nullptr, *r = nullptr;
-    double* blk_sum = nullptr;
-    long long* blk_key = nullptr;
-    int* blk_arg = nullptr;
     long long* iters = nullptr;
     double* S = nullptr;
     int* flags = nullptr;
@@ -830,7 +790,7 @@ extern "C" void grbk_sparse_destroy(grbk_sparse* b)
     if (!b) return;
     void* bufs[] = {b->dsys, b->dorder, b->dqueue, b->a_rowptr, b->b_rowptr, b->bc_colptr, b->g_rowptr,
                     b->a_col, b->b_col, b->bc_row, b->g_col, b->a_val, b->b_val, b->bc_val, b->g_val, b->C,
-                    b->R, b->X, b->a, b->pref, b->s, b->r, b->blk_sum, b->blk_key, b->blk_arg, b->iters, b->S,
+                    b->R, b->X, b->a, b->pref, b->s, b->r, b->iters, b->S,
                     b->flags, b->trace, b->traceS, b->ac_colptr, b->ac_row, b->ac_val, b->cn, b->cpref, b->Y};
     for (void* p : bufs)
         if (p) cudaFree(p);
@@ -900,7 +860,6 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
               sp_alloc(&b->bc_colptr, oBC) && sp_alloc(&b->bc_row, oBN) && sp_alloc(&b->bc_val, oBN) &&
               sp_alloc(&b->g_rowptr, oGR) && sp_alloc(&b->C, oR) && sp_alloc(&b->R, oR) && sp_alloc(&b->X, oX) &&
               sp_alloc(&b->a, oRow) && sp_alloc(&b->pref, oRow) && sp_alloc(&b->s, oRow) && sp_alloc(&b->r, oRow) &&
-              sp_alloc(&b->blk_sum, oBlk) && sp_alloc(&b->blk_key, oBlk) && sp_alloc(&b->blk_arg, oBlk) &&
               sp_alloc(&b->ac_colptr, oAC) && sp_alloc(&b->ac_row, oAN) && sp_alloc(&b->ac_val, oAN) &&
               sp_alloc(&b->cn, oCol) && sp_alloc(&b->cpref, oCol) && (!o.extended || sp_alloc(&b->Y, oR)) &&
               sp_alloc(&b->dsys, nsys) && sp_alloc(&b->dorder, nsys) && sp_alloc(&b->dqueue, 1) &&
@@ -1098,7 +1057,6 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
     P.ac_colptr = b->ac_colptr; P.ac_row = b->ac_row; P.ac_val = b->ac_val;
     P.cn = b->cn; P.cpref = b->cpref; P.Y = b->Y; P.extended = b->opts.extended ? 1 : 0;
     P.C = b->C; P.R = b->R; P.X = b->X; P.a = b->a; P.pref = b->pref; P.s = b->s; P.r = b->r;
-    P.blk_sum = b->blk_sum; P.blk_key = b->blk_key; P.blk_arg = b->blk_arg;
     P.iters = b->iters; P.S_out = b->S; P.flag_out = b->flags;
     P.variant = variant; P.theta = theta; P.seed = seed; P.maxit = maxit;
     const long long tlen = (b->opts.row_trace || b->opts.s_trace) ? b->opts.trace_len : 0;
