@@ -92,8 +92,10 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
             s_w[o][ci][k] = wv;
         }
         __syncthreads();
+        // channels past Cin were staged as zeros: skip them (they would add exact zeros)
+        const int cmax = min(CI_T, Cin - i0);
 #pragma unroll 2
-        for (int ci = 0; ci < CI_T; ++ci) {
+        for (int ci = 0; ci < cmax; ++ci) {
             float nb[PIX + 2][3];
 #pragma unroll
             for (int r = 0; r < PIX + 2; ++r)
@@ -209,28 +211,30 @@ __global__ void reduce_slices_kernel(const float* part, int S, int64_t len, floa
     g[j] = acc;
 }
 
-// 2x2 average pooling and its adjoint
+// 2x2 average pooling and its adjoint.  Grid: (tiles of the plane, channel, image); 32-bit
+// offsets within a plane (H W < 2^31) keep the index arithmetic off 64-bit division.
 __global__ void pool_fwd_kernel(View in, View out, int C, int N, int H, int W)
 {
     const int Ho = H / 2, Wo = W / 2;
-    const int64_t total = (int64_t)N * C * Ho * Wo;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int x = e % Wo, y = (e / Wo) % Ho, c = (e / ((int64_t)Wo * Ho)) % C, n = e / ((int64_t)Wo * Ho * C);
-        const float* s = at(in, n, c, H, W);
-        const float v = 0.25f * (s[(2 * y) * W + 2 * x] + s[(2 * y) * W + 2 * x + 1] + s[(2 * y + 1) * W + 2 * x] +
-                                 s[(2 * y + 1) * W + 2 * x + 1]);
-        at(out, n, c, Ho, Wo)[y * Wo + x] = v;
+    const int c = blockIdx.y, n = blockIdx.z;
+    const float* s = at(in, n, c, H, W);
+    float* d = at(out, n, c, Ho, Wo);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ho * Wo; e += gridDim.x * blockDim.x) {
+        const int y = e / Wo, x = e - y * Wo;
+        d[e] = 0.25f * (s[(2 * y) * W + 2 * x] + s[(2 * y) * W + 2 * x + 1] + s[(2 * y + 1) * W + 2 * x] +
+                        s[(2 * y + 1) * W + 2 * x + 1]);
     }
 }
 
 __global__ void pool_bwd_kernel(View gout, View gin, int C, int N, int H, int W, int accumulate)
 {
-    const int64_t total = (int64_t)N * C * H * W;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int x = e % W, y = (e / W) % H, c = (e / ((int64_t)W * H)) % C, n = e / ((int64_t)W * H * C);
-        const float v = 0.25f * at(gout, n, c, H / 2, W / 2)[(y / 2) * (W / 2) + x / 2];
-        float* d = at(gin, n, c, H, W) + y * W + x;
-        if (accumulate) *d += v; else *d = v;
+    const int c = blockIdx.y, n = blockIdx.z;
+    const float* g = at(gout, n, c, H / 2, W / 2);
+    float* d = at(gin, n, c, H, W);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * W; e += gridDim.x * blockDim.x) {
+        const int y = e / W, x = e - y * W;
+        const float v = 0.25f * g[(y / 2) * (W / 2) + x / 2];
+        if (accumulate) d[e] += v; else d[e] = v;
     }
 }
 
@@ -238,22 +242,25 @@ __global__ void pool_bwd_kernel(View gout, View gin, int C, int N, int H, int W,
 __global__ void up_fwd_kernel(View in, View out, int C, int N, int H, int W)
 {
     const int Ho = 2 * H, Wo = 2 * W;
-    const int64_t total = (int64_t)N * C * Ho * Wo;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int x = e % Wo, y = (e / Wo) % Ho, c = (e / ((int64_t)Wo * Ho)) % C, n = e / ((int64_t)Wo * Ho * C);
-        at(out, n, c, Ho, Wo)[y * Wo + x] = at(in, n, c, H, W)[(y / 2) * W + x / 2];
+    const int c = blockIdx.y, n = blockIdx.z;
+    const float* s = at(in, n, c, H, W);
+    float* d = at(out, n, c, Ho, Wo);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Ho * Wo; e += gridDim.x * blockDim.x) {
+        const int y = e / Wo, x = e - y * Wo;
+        d[e] = s[(y / 2) * W + x / 2];
     }
 }
 
 __global__ void up_bwd_kernel(View gout, View gin, int C, int N, int H, int W)
 {
-    const int64_t total = (int64_t)N * C * H * W;
-    const int Wo = 2 * W, Ho = 2 * H;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int x = e % W, y = (e / W) % H, c = (e / ((int64_t)W * H)) % C, n = e / ((int64_t)W * H * C);
-        const float* g = at(gout, n, c, Ho, Wo);
-        at(gin, n, c, H, W)[y * W + x] =
-            g[(2 * y) * Wo + 2 * x] + g[(2 * y) * Wo + 2 * x + 1] + g[(2 * y + 1) * Wo + 2 * x] + g[(2 * y + 1) * Wo + 2 * x + 1];
+    const int Wo = 2 * W;
+    const int c = blockIdx.y, n = blockIdx.z;
+    const float* g = at(gout, n, c, 2 * H, Wo);
+    float* d = at(gin, n, c, H, W);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < H * W; e += gridDim.x * blockDim.x) {
+        const int y = e / W, x = e - y * W;
+        d[e] = g[(2 * y) * Wo + 2 * x] + g[(2 * y) * Wo + 2 * x + 1] + g[(2 * y + 1) * Wo + 2 * x] +
+               g[(2 * y + 1) * Wo + 2 * x + 1];
     }
 }
 
@@ -464,6 +471,12 @@ static const View kNone = {nullptr, 0, 0};
 
 static unsigned blocks_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 65535); }
 
+// grid of the per-plane kernels (pooling, upsampling): tiles of a plane of `plane` pixels x C x N
+static dim3 plane_grid(int64_t plane, int C, int N)
+{
+    return dim3((unsigned)std::min<int64_t>((plane + 255) / 256, 4096), (unsigned)C, (unsigned)N);
+}
+
 // The tensor-core path takes layers with 16 to 128 input and output channels (the
 // first and last layers, with one channel, stay on the SIMT kernel).
 static bool tc_layer(const grbk_unet* u, int l)
@@ -607,18 +620,18 @@ static cudaError_t forward(grbk_unet* u, const Acts& a, const float* C, int N, i
     if (u->use_tc && tc_prepare(u, N, H, W) != GRBK_OK) return cudaErrorMemoryAllocation;
     if ((e = conv(u, ENC1A, V((float*)C, 1), V(a.a1, w), N, H, W)) != cudaSuccess) return e;
     if ((e = conv(u, ENC1B, V(a.a1, w), V(a.D1, 3 * w, 2 * w), N, H, W)) != cudaSuccess) return e;
-    pool_fwd_kernel<<<blocks_for((int64_t)N * w * H2 * W2), 256, 0, u->stream>>>(V(a.D1, 3 * w, 2 * w), V(a.p1, w), w, N, H, W);
+    pool_fwd_kernel<<<plane_grid((int64_t)H2 * W2, w, N), 256, 0, u->stream>>>(V(a.D1, 3 * w, 2 * w), V(a.p1, w), w, N, H, W);
     if ((e = conv(u, ENC2A, V(a.p1, w), V(a.a2, 2 * w), N, H2, W2)) != cudaSuccess) return e;
     if ((e = conv(u, ENC2B, V(a.a2, 2 * w), V(a.D2, 6 * w, 4 * w), N, H2, W2)) != cudaSuccess) return e;
-    pool_fwd_kernel<<<blocks_for((int64_t)N * 2 * w * H4 * W4), 256, 0, u->stream>>>(V(a.D2, 6 * w, 4 * w), V(a.p2, 2 * w),
+    pool_fwd_kernel<<<plane_grid((int64_t)H4 * W4, 2 * w, N), 256, 0, u->stream>>>(V(a.D2, 6 * w, 4 * w), V(a.p2, 2 * w),
                                                                                     2 * w, N, H2, W2);
     if ((e = conv(u, BOTA, V(a.p2, 2 * w), V(a.a3, 4 * w), N, H4, W4)) != cudaSuccess) return e;
     if ((e = conv(u, BOTB, V(a.a3, 4 * w), V(a.a3b, 4 * w), N, H4, W4)) != cudaSuccess) return e;
-    up_fwd_kernel<<<blocks_for((int64_t)N * 4 * w * H2 * W2), 256, 0, u->stream>>>(V(a.a3b, 4 * w), V(a.D2, 6 * w, 0),
+    up_fwd_kernel<<<plane_grid((int64_t)H2 * W2, 4 * w, N), 256, 0, u->stream>>>(V(a.a3b, 4 * w), V(a.D2, 6 * w, 0),
                                                                                   4 * w, N, H4, W4);
     if ((e = conv(u, DEC2A, V(a.D2, 6 * w), V(a.d2a, 2 * w), N, H2, W2)) != cudaSuccess) return e;
     if ((e = conv(u, DEC2B, V(a.d2a, 2 * w), V(a.d2b, 2 * w), N, H2, W2)) != cudaSuccess) return e;
-    up_fwd_kernel<<<blocks_for((int64_t)N * 2 * w * H * W), 256, 0, u->stream>>>(V(a.d2b, 2 * w), V(a.D1, 3 * w, 0), 2 * w,
+    up_fwd_kernel<<<plane_grid((int64_t)H * W, 2 * w, N), 256, 0, u->stream>>>(V(a.d2b, 2 * w), V(a.D1, 3 * w, 0), 2 * w,
                                                                                 N, H2, W2);
     if ((e = conv(u, DEC1A, V(a.D1, 3 * w), V(a.d1a, w), N, H, W)) != cudaSuccess) return e;
     if ((e = conv(u, DEC1B, V(a.d1a, w), V(a.d1b, w), N, H, W)) != cudaSuccess) return e;
@@ -634,25 +647,25 @@ static cudaError_t backward(grbk_unet* u, const Acts& a, const Acts& g, const fl
     if ((e = conv_bwd(u, OUTL, V(a.d1b, w), V(a.y, 1), V(g.y, 1), V(g.d1b, w), 0, N, H, W)) != cudaSuccess) return e;
     if ((e = conv_bwd(u, DEC1B, V(a.d1a, w), V(a.d1b, w), V(g.d1b, w), V(g.d1a, w), 0, N, H, W)) != cudaSuccess) return e;
     if ((e = conv_bwd(u, DEC1A, V(a.D1, 3 * w), V(a.d1a, w), V(g.d1a, w), V(g.D1, 3 * w), 0, N, H, W)) != cudaSuccess) return e;
-    up_bwd_kernel<<<blocks_for((int64_t)N * 2 * w * H2 * W2), 256, 0, u->stream>>>(V(g.D1, 3 * w, 0), V(g.d2b, 2 * w), 2 * w,
+    up_bwd_kernel<<<plane_grid((int64_t)H2 * W2, 2 * w, N), 256, 0, u->stream>>>(V(g.D1, 3 * w, 0), V(g.d2b, 2 * w), 2 * w,
                                                                                   N, H2, W2);
     if ((e = conv_bwd(u, DEC2B, V(a.d2a, 2 * w), V(a.d2b, 2 * w), V(g.d2b, 2 * w), V(g.d2a, 2 * w), 0, N, H2, W2)) != cudaSuccess)
         return e;
     if ((e = conv_bwd(u, DEC2A, V(a.D2, 6 * w), V(a.d2a, 2 * w), V(g.d2a, 2 * w), V(g.D2, 6 * w), 0, N, H2, W2)) != cudaSuccess)
         return e;
-    up_bwd_kernel<<<blocks_for((int64_t)N * 4 * w * H4 * W4), 256, 0, u->stream>>>(V(g.D2, 6 * w, 0), V(g.a3b, 4 * w), 4 * w,
+    up_bwd_kernel<<<plane_grid((int64_t)H4 * W4, 4 * w, N), 256, 0, u->stream>>>(V(g.D2, 6 * w, 0), V(g.a3b, 4 * w), 4 * w,
                                                                                   N, H4, W4);
     if ((e = conv_bwd(u, BOTB, V(a.a3, 4 * w), V(a.a3b, 4 * w), V(g.a3b, 4 * w), V(g.a3, 4 * w), 0, N, H4, W4)) != cudaSuccess)
         return e;
     if ((e = conv_bwd(u, BOTA, V(a.p2, 2 * w), V(a.a3, 4 * w), V(g.a3, 4 * w), V(g.p2, 2 * w), 0, N, H4, W4)) != cudaSuccess)
         return e;
-    pool_bwd_kernel<<<blocks_for((int64_t)N * 2 * w * H2 * W2), 256, 0, u->stream>>>(V(g.p2, 2 * w), V(g.D2, 6 * w, 4 * w),
+    pool_bwd_kernel<<<plane_grid((int64_t)H2 * W2, 2 * w, N), 256, 0, u->stream>>>(V(g.p2, 2 * w), V(g.D2, 6 * w, 4 * w),
                                                                                     2 * w, N, H2, W2, 1);
     if ((e = conv_bwd(u, ENC2B, V(a.a2, 2 * w), V(a.D2, 6 * w, 4 * w), V(g.D2, 6 * w, 4 * w), V(g.a2, 2 * w), 0, N, H2, W2)) !=
         cudaSuccess)
         return e;
     if ((e = conv_bwd(u, ENC2A, V(a.p1, w), V(a.a2, 2 * w), V(g.a2, 2 * w), V(g.p1, w), 0, N, H2, W2)) != cudaSuccess) return e;
-    pool_bwd_kernel<<<blocks_for((int64_t)N * w * H * W), 256, 0, u->stream>>>(V(g.p1, w), V(g.D1, 3 * w, 2 * w), w, N, H, W,
+    pool_bwd_kernel<<<plane_grid((int64_t)H * W, w, N), 256, 0, u->stream>>>(V(g.p1, w), V(g.D1, 3 * w, 2 * w), w, N, H, W,
                                                                               1);
     if ((e = conv_bwd(u, ENC1B, V(a.a1, w), V(a.D1, 3 * w, 2 * w), V(g.D1, 3 * w, 2 * w), V(g.a1, w), 0, N, H, W)) !=
         cudaSuccess)
