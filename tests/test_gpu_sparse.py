@@ -195,3 +195,27 @@ def test_extended_reaches_least_squares_solution():
         out[ext] = np.linalg.norm(X - Xls) / np.linalg.norm(Xls)
     assert out[True] < 1e-8, out
     assert out[False] > 1e-4, out
+
+
+@pytest.mark.parametrize("variant,theta", VARIANTS)
+def test_sparse_degenerate_rows_and_columns(variant, theta):
+    """A with an empty row and an empty column, B with an empty column, a one-row
+    system: the empty row is never selected (ME-BK's step on it changes nothing),
+    and rows, S, X, R and s still follow the oracle."""
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((9, 6)) * (rng.random((9, 6)) < 0.6)
+    A[2, :] = 0.0
+    A[:, 4] = 0.0
+    A[0, 0] = A[0, 0] or 1.0
+    B = rng.standard_normal((5, 7)) * (rng.random((5, 7)) < 0.7)
+    B[:, 1] = 0.0
+    B[0, 0] = B[0, 0] or 1.0
+    X = rng.standard_normal((6, 5))
+    C = A @ X @ B + 0.01 * rng.standard_normal((9, 7))
+    rows, orc = _check_parity(A, A, B, B, C, variant, theta, K=300)
+    if variant != "bk":
+        assert 2 not in set(rows.tolist())
+    A1 = rng.standard_normal((1, 4))
+    B1 = rng.standard_normal((3, 5))
+    C1 = A1 @ rng.standard_normal((4, 3)) @ B1
+    _check_parity(A1, A1, B1, B1, C1, variant, theta, K=50)
