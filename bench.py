@@ -360,7 +360,6 @@ def native_arm(args):
         torch.cuda.synchronize(dev)
         setup_s = time.perf_counter() - t0
         r_cols = g.grbk_form_info(ctxz)[1]
-        l2_rows = g.grbk_l2_rows(ctxz)
         Xz = torch.zeros(p, q, dtype=torch.float64, device=dev)
         g.grbk_solve(ctxz, "grbk", X0=Xz, maxit=args.warmup * T, seed=1, X_out=Xz)
         barrier()
@@ -379,16 +378,13 @@ def native_arm(args):
         rowspace = {"precision": "f32", "value": world * kz * T / (msz / 1e3), "unit": UNIT,
                     "ms_per_step": msz / kz, "steps": kz, "kept_columns": r_cols, "setup_s": setup_s,
                     "kernel_ms_per_launch": kmz, "kernel_GBs": bz / (kmz / 1e3) / 1e9,
-                    "l2_resident_rows": l2_rows,
                     "kernel_frac_of_hbm": bz / (kmz / 1e3) / 1e9 / hbm_peak,
                     "algorithmic_bytes_per_launch": bz,
                     "traffic": (recorded_traffic("iterate_kernel<float>/rowspace")
                                 if (wl == "precision" and T == 64) else None),
                     "note": "residual kept as Z = R Bt^T (m x rank B) plus fixed row offsets; same iterates as "
                             "the chosen form; set-up (pivoted Cholesky of B B^T, Z^0, offsets) outside the timed "
-                            "region; the leading l2_resident_rows rows of Z are loaded and stored with an "
-                            "evict-last L2 policy and stay in L2 between iterations, so part of the algorithmic "
-                            "bytes is served by L2"}
+                            "region"}
         g.grbk_destroy(ctxz)
         del Xz
 

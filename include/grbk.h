@@ -115,10 +115,6 @@ typedef struct {
     int32_t tune;         /* batched solver: 1 = choose each system's kernel variant by timing the compiled
                              variants on it (grbk_tune_*; choices kept per system shape for the process);
                              0 = the default variant (512 threads, two rows per warp) for every system */
-    int32_t l2_keep;      /* ROWSPACE form: 0 = the leading rows of the kept residual Z that fit in 60 % of L2
-                             (less the r x r matrix K every iteration reads) are loaded and stored with an
-                             evict-last L2 policy, so they stay in L2 from one iteration to the next and the
-                             rest streams with evict-first; -1 = every row streams.  Ignored by FULL. */
 } grbk_opts;
 
 typedef struct {
@@ -190,11 +186,9 @@ void grbk_trim_cache(void);
 /* Problem sizes (m, p, q, n of the caller's system) and the step in use. */
 grbk_status grbk_info(const grbk_ctx* ctx, int64_t dims[4], double* alpha);
 
-/* The residual form in use (grbk_form), the columns of the kept residual (n
- * for FULL, r = rank B for ROWSPACE) and how many of its leading rows the
- * iteration keeps in L2 between iterations (opts.l2_keep).  Not part of the
- * paper.  Any output pointer may be NULL. */
-grbk_status grbk_form_info(const grbk_ctx* ctx, int32_t* form, int64_t* cols, int64_t* l2_rows);
+/* The residual form in use (grbk_form) and the columns of the kept residual:
+ * n for FULL, r = rank B for ROWSPACE.  Not part of the paper. */
+grbk_status grbk_form_info(const grbk_ctx* ctx, int32_t* form, int64_t* cols);
 
 void grbk_destroy(grbk_ctx* ctx);
 

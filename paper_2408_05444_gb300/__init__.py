@@ -41,7 +41,7 @@ class grbk_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
                 ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double)),
-                ("extended", ctypes.c_int32), ("tune", ctypes.c_int32), ("l2_keep", ctypes.c_int32)]
+                ("extended", ctypes.c_int32), ("tune", ctypes.c_int32)]
 
 
 class grbk_csr(ctypes.Structure):
@@ -104,7 +104,7 @@ def lib():
         L.grbk_info.restype = i32
         L.grbk_trim_cache.argtypes = []
         L.grbk_trim_cache.restype = None
-        L.grbk_form_info.argtypes = [vp, P(i32), P(i64), P(i64)]
+        L.grbk_form_info.argtypes = [vp, P(i32), P(i64)]
         L.grbk_form_info.restype = i32
         L.grbk_destroy.argtypes = [vp]
         L.grbk_destroy.restype = None
@@ -252,7 +252,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None, tune=None, l2_keep=None):
+               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None, tune=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -281,8 +281,6 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.extended = int(bool(extended))
     if tune is not None:
         o.tune = int(bool(tune))
-    if l2_keep is not None:
-        o.l2_keep = 0 if l2_keep else -1
     if alphas is not None:
         keep.alphas = np.ascontiguousarray(alphas, dtype=np.float64)
         o.alphas = keep.alphas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -401,19 +399,10 @@ def grbk_form_info(ctx: Context):
     """-> ('full' | 'rowspace', columns of the kept residual: n or rank B)."""
     f = ctypes.c_int32()
     cols = ctypes.c_int64()
-    st = lib().grbk_form_info(ctx.handle, ctypes.byref(f), ctypes.byref(cols), None)
+    st = lib().grbk_form_info(ctx.handle, ctypes.byref(f), ctypes.byref(cols))
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_form_info")
     return ("full", "rowspace")[f.value], cols.value
-
-
-def grbk_l2_rows(ctx: Context) -> int:
-    """Leading rows of the kept residual held in L2 between iterations (grbk_form_info's third output)."""
-    r = ctypes.c_int64()
-    st = lib().grbk_form_info(ctx.handle, None, None, ctypes.byref(r))
-    if st != GRBK_OK:
-        raise GrbkError(st, "grbk_form_info")
-    return r.value
 
 
 def grbk_trim_cache():

@@ -53,39 +53,6 @@ __device__ __forceinline__ double2 ldcs_v(const double2* p) { return __ldcs(p); 
 __device__ __forceinline__ void stcs_v(float4* p, float4 v) { __stcs(p, v); }
 __device__ __forceinline__ void stcs_v(double2* p, double2 v) { __stcs(p, v); }
 
-// Rows kept in L2 from one iteration to the next (the row-space form's Z is a
-// few hundred MB at most): loads and stores with an evict-last L2 policy.
-__device__ __forceinline__ uint64_t l2_keep_policy()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ float4 ldkeep_v(const float4* p, uint64_t pol)
-{
-    float4 v;
-    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ double2 ldkeep_v(const double2* p, uint64_t pol)
-{
-    double2 v;
-    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ void stkeep_v(float4* p, float4 v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w), "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void stkeep_v(double2* p, double2 v, uint64_t pol)
-{
-    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
-}
-
 // ----------------------------------------------------------------------------
 // kernel parameters
 // ----------------------------------------------------------------------------
@@ -125,7 +92,6 @@ struct IterParams {
     const T* K;                 // row-space form: Lt^T Lt (n x ldk); then v = R_{i_k} K and w is formed per chunk
     int64_t ldk;
     T* hist_z;                  // with K: per chunk the selected rows R_{i_k} (ldr per iteration)
-    int64_t l2_rows;            // rows [0, l2_rows) of R are loaded and stored with an evict-last L2 policy
 };
 
 // balanced contiguous row range of CTA c among G
@@ -174,14 +140,12 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             if (UPDATE) coef = __ldcg(P.u + row);  // c_k u_row, formed once per row
             double acc_d = 0.0;
             float acc_f = 0.f, comp_f = 0.f;
-            const bool keep = row < P.l2_rows;
-            const uint64_t pol = keep ? l2_keep_policy() : 0ull;
             for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
                 V rv[kUnroll];
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
                     const int64_t e = base + uu * 32 + lane;
-                    if (e < e1) rv[uu] = keep ? ldkeep_v(Rrow + e, pol) : ldcs_v(Rrow + e);
+                    if (e < e1) rv[uu] = ldcs_v(Rrow + e);
                 }
 #pragma unroll
                 for (int uu = 0; uu < kUnroll; ++uu) {
@@ -203,10 +167,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
                                 acc_f = tk;
                             }
                         }
-                        if (UPDATE) {
-                            if (keep) stkeep_v(Rrow + e, rv[uu], pol);
-                            else stcs_v(Rrow + e, rv[uu]);
-                        }
+                        if (UPDATE) stcs_v(Rrow + e, rv[uu]);
                     }
                 }
             }
@@ -1035,7 +996,6 @@ struct grbk_ctx {
     double* soff;           // row-space form: ||Rperp_i||^2
     void* K;                // row-space form: Lt^T Lt (n x ldr), when the row fits in shared memory
     void* hist_z;           // with K: the selected rows of a chunk (chunk_cap x ldr)
-    int64_t l2_rows;        // leading rows of the kept residual held in L2 between iterations
     cudaStream_t side;      // set-up only: the copy of a host C overlapped with the rest
     cudaEvent_t side_done;
     struct {                // set-up only: the Lanczos run for ||B||_2^2 (begun, then read back)
@@ -1131,7 +1091,6 @@ static IterParams<T> make_params(grbk_ctx* c)
     P.G = (const T*)c->gram; P.ldg = c->ldg;
     P.soff = c->soff;
     P.K = (const T*)c->K; P.ldk = c->ldr; P.hist_z = (T*)c->hist_z;
-    P.l2_rows = c->l2_rows;
     P.stop_S = -1.0;
     return P;
 }
@@ -1607,16 +1566,6 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
             c->K = nullptr;
         }
     }
-    // row-space form: the leading rows of Z stay in L2 from one iteration to the next
-    // (evict-last policy), within 60 % of L2 less K, which every iteration reads in full
-    c->l2_rows = 0;
-    if (c->K && o.l2_keep >= 0) {
-        int dev = 0, l2 = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess) {
-            const double budget = 0.6 * (double)l2 - (double)c->n * (double)c->ldr * es;
-            if (budget > 0.0) c->l2_rows = std::min<int64_t>(m, (int64_t)(budget / ((double)c->ldr * es)));
-        }
-    }
 
     if (c->prec == GRBK_F32)
         TRY(splitgemm_create(&c->sg, m, p, q, c->n, (const float*)c->A, c->lda, (const float*)c->B, c->ldb,
@@ -1918,12 +1867,11 @@ extern "C" grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream)
     return (grbk_status)h.status;
 }
 
-extern "C" grbk_status grbk_form_info(const grbk_ctx* c, int32_t* form, int64_t* cols, int64_t* l2_rows)
+extern "C" grbk_status grbk_form_info(const grbk_ctx* c, int32_t* form, int64_t* cols)
 {
     if (!c) return GRBK_EINVAL;
     if (form) *form = c->form;
     if (cols) *cols = c->n;
-    if (l2_rows) *l2_rows = c->l2_rows;
     return GRBK_OK;
 }
 
