@@ -92,10 +92,8 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(View in, int Cin, View mas
             s_w[o][ci][k] = wv;
         }
         __syncthreads();
-        // channels past Cin were staged as zeros: skip them (they would add exact zeros)
-        const int cmax = min(CI_T, Cin - i0);
 #pragma unroll 2
-        for (int ci = 0; ci < cmax; ++ci) {
+        for (int ci = 0; ci < CI_T; ++ci) {
             float nb[PIX + 2][3];
 #pragma unroll
             for (int r = 0; r < PIX + 2; ++r)
