@@ -160,9 +160,11 @@ def workload_label(wl, T):
             f"chosen form FP32 + split-BF16 refresh every {T}")
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None when the
-    kernel's sources changed since the counters were taken."""
+def recorded_traffic(kernel, algorithmic_bytes):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, scaled to a
+    launch of `algorithmic_bytes` by the ratio of algorithmic bytes when the
+    counters were taken on a smaller case, or None when the kernel's sources
+    changed since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
@@ -171,7 +173,8 @@ def recorded_traffic(kernel):
             h.update(open(os.path.join(ROOT, f), "rb").read())
         if h.hexdigest() != rec["sources_sha256"]:
             return None
-        return int(rec["dram_bytes_read"] + rec["dram_bytes_write"])
+        measured = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        return int(round(measured * algorithmic_bytes / rec["algorithmic_bytes"]))
     except Exception:
         return None
 
@@ -380,8 +383,8 @@ def native_arm(args):
                     "kernel_ms_per_launch": kmz, "kernel_GBs": bz / (kmz / 1e3) / 1e9,
                     "kernel_frac_of_hbm": bz / (kmz / 1e3) / 1e9 / hbm_peak,
                     "algorithmic_bytes_per_launch": bz,
-                    "traffic": (recorded_traffic("iterate_kernel<float>/rowspace")
-                                if (wl == "precision" and T == 64) else None),
+                    "traffic": (recorded_traffic("iterate_kernel<float>/rowspace", bz)
+                                if T == 64 else None),
                     "note": "residual kept as Z = R Bt^T (m x rank B) plus fixed row offsets; same iterates as "
                             "the chosen form; set-up (pivoted Cholesky of B B^T, Z^0, offsets) outside the timed "
                             "region"}
@@ -438,8 +441,8 @@ def native_arm(args):
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
-                         "traffic": (recorded_traffic("iterate_kernel<float>")
-                                     if (wl == "precision" and T == 64) else None),
+                         "traffic": (recorded_traffic("iterate_kernel<float>", bytes_per_launch)
+                                     if T == 64 else None),
                          "algorithmic_bytes_per_launch": bytes_per_launch,
                          "kernel": "iterate_kernel<float> (persistent, %d iterations per launch)" % T,
                          "kernel_ms_per_launch": kern_ms, "peak_source": peak_src},

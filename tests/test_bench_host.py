@@ -41,17 +41,20 @@ def test_clock_record_summary():
 
 
 def test_recorded_traffic_follows_the_sources(tmp_path, monkeypatch):
+    """DRAM bytes of a capture on a smaller case are scaled to the timed launch by
+    the ratio of algorithmic bytes; any change of the kernel's sources voids them."""
     (tmp_path / "profiles").mkdir()
     (tmp_path / "k.cu").write_bytes(b"kernel v1")
     sha = hashlib.sha256(b"kernel v1").hexdigest()
     rec = {"iterate_kernel<float>": {"sources": ["k.cu"], "sources_sha256": sha,
-                                     "dram_bytes_read": 100, "dram_bytes_write": 23}}
+                                     "dram_bytes_read": 100, "dram_bytes_write": 23, "algorithmic_bytes": 200}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic("iterate_kernel<float>") == 123
-    assert bench.recorded_traffic("other_kernel") is None
+    assert bench.recorded_traffic("iterate_kernel<float>", 200) == 123
+    assert bench.recorded_traffic("iterate_kernel<float>", 1000) == 615
+    assert bench.recorded_traffic("other_kernel", 200) is None
     (tmp_path / "k.cu").write_bytes(b"kernel v2")
-    assert bench.recorded_traffic("iterate_kernel<float>") is None
+    assert bench.recorded_traffic("iterate_kernel<float>", 200) is None
 
 
 def test_reference_arm_prints_the_contract_line():
@@ -62,12 +65,13 @@ def test_reference_arm_prints_the_contract_line():
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
-                          "--warmup", "1"], capture_output=True, text=True, timeout=300, check=True).stdout
+                          "--warmup", "1", "--workload", "precision_slice"], capture_output=True, text=True,
+                         timeout=300, check=True).stdout
     lines = [ln for ln in out.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
-    assert d["config"]["workload"] == bench.workload_label("precision", 64)
+    assert d["config"]["workload"] == bench.workload_label("precision_slice", 64)
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
