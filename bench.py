@@ -396,6 +396,12 @@ def native_arm(args):
     if not args.no_e2e:
         Xh = torch.zeros(p, q, dtype=torch.float64).pin_memory()
         k_e2e = min(args.steps, 3)
+        # one untimed step first: the library's block cache then holds blocks of this context's sizes
+        c2 = g.grbk_create(Ah, Bh, Ch, precision="f32", refresh_T=T, check_every=T, stream=stream,
+                           split_terms=args.split_terms)
+        g.grbk_solve(c2, "grbk", X0=Xh, maxit=T, seed=99, X_out=Xh)
+        g.grbk_destroy(c2)
+        Xh.zero_()
         barrier()
         t0 = time.perf_counter()
         step_s = []
@@ -416,7 +422,8 @@ def native_arm(args):
                "h2d_bytes_per_step": int(Ah.numel() * 4 + Bh.numel() * 4 + Ch.numel() * 4),
                "d2h_bytes_per_step": int(p * q * 8), "step_seconds": step_s,
                "note": "per step: grbk_create from pinned host A, B, C (FP32), X0 from pinned host memory, "
-                       "one refresh and 64 iterations, X copied back to pinned host memory, grbk_destroy"}
+                       "one refresh and 64 iterations, X copied back to pinned host memory, grbk_destroy; one "
+                       "untimed step before the timed ones"}
 
     clocks = clk.summary()
     ttt = None
