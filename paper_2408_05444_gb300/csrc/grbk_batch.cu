@@ -68,6 +68,8 @@ struct BatchParams {
     long long maxit;
     int chunk;
     int init_from_x;                // R = C - A X B before iterating (X holds X0)
+    int band_smem;                  // dynamic shared memory of the launch, bytes (a banded system whose
+                                    // bands fit iterates from a shared-memory copy of them)
 };
 
 // block-wide sum in a fixed order; one thread adds the warp partials (FP64 is
@@ -304,12 +306,13 @@ __global__ void __launch_bounds__(kBB) batch_setup_kernel(const SysDesc* sys, co
     }
 }
 
-// R_i -= coef[i - rb] v for rows [rb, re), fused with the new s_i = ||R_i||^2
-// (Kahan FP32 per lane, double-float across lanes) and r_i = s_i / a_i; RPW rows
-// per warp at a time, float4 columns.  v has ldr entries (padding zero).
+// R_i -= coef[i - rb] v for rows [rb, re), fused with the new ||R_i||^2 (Kahan
+// FP32 per lane, double-float across lanes); RPW rows per warp at a time, float4
+// columns.  v has ldr entries (padding zero).  The norm is left in s_s[i] as a
+// (hi, lo) float pair for batch_finalize, which does the FP64 work with full warps.
 template <int NW, int RPW>
 __device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int re, const float* coef,
-                                                  const float* v, const double* a, double* s_s, double* s_r)
+                                                  const float* v, double* s_s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float4* v4 = reinterpret_cast<const float4*>(v);
@@ -346,30 +349,151 @@ __device__ __forceinline__ void batch_update_rows(float* R, int ldr, int rb, int
         for (int k2 = 0; k2 < RPW; ++k2) {
             float hi = acc[k2], lo = -comp[k2];
             warp_sum_df(hi, lo);
-            if (lane == 0 && i0 + k2 < re) {
-                const double tot = (double)hi + (double)lo;
-                s_s[i0 + k2] = tot;
-                s_r[i0 + k2] = a[i0 + k2] > 0.0 ? __ddiv_rn(tot, a[i0 + k2]) : -INFINITY;
+            if (lane == 0 && i0 + k2 < re) reinterpret_cast<float2*>(s_s)[i0 + k2] = make_float2(hi, lo);
+        }
+    }
+}
+
+// Rows [rb, re) hold their new norms as (hi, lo) float pairs in s_s.  Each warp
+// takes a block of 32 rows (lane = row): s_i = hi + lo and r_i = s_i / a_i in
+// FP64, then the block's summary: the sum of its s (fixed butterfly order), its
+// largest r as an IEEE bit pattern (r >= 0 or -inf, so the integer order is the
+// numeric one; ties: smallest row) and that row.  Blocks outside [rb, re) keep
+// their summaries.  A warp instruction on the FP64 pipe costs about as much with
+// one active lane as with 32, so the FP64 work is spread one row per lane.
+template <int NW>
+__device__ __forceinline__ void batch_finalize(int m, int rb, int re, const double* a, double* s_s, double* s_r,
+                                               double* bsum, long long* bkey, int* barg)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (re <= rb) return;
+    const int b0 = rb >> 5, b1 = (re - 1) >> 5;
+    for (int b = b0 + warp; b <= b1; b += NW) {
+        const int i = (b << 5) + lane;
+        double s = 0.0;
+        long long key = LLONG_MIN;
+        if (i < m) {
+            if (i >= rb && i < re) {
+                const float2 hl = reinterpret_cast<const float2*>(s_s)[i];
+                s = (double)hl.x + (double)hl.y;
+                const double ai = __ldg(a + i);
+                const double r = ai > 0.0 ? __ddiv_rn(s, ai) : -INFINITY;
+                s_s[i] = s;
+                s_r[i] = r;
+                key = __double_as_longlong(r);
+            } else {
+                s = s_s[i];
+                key = __double_as_longlong(s_r[i]);
+            }
+        }
+        s = warp_sum(s);
+        int arg = i;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (ok > key || (ok == key && oa < arg)) { key = ok; arg = oa; }
+        }
+        if (lane == 0) { bsum[b] = s; bkey[b] = key; barg[b] = arg; }
+    }
+}
+
+// The banded forms of w_j = R_ik . B_j, (A A_ik^T)_i and v_l = w . B_{:,l} read
+// their bands through A(i, c) = A_ic and B(j, l) = B_jl.
+struct BandShared {   // the bands of A and B copied to shared memory, diagonal by diagonal
+    const float* Ab;  // Ab[(c - i + bA) * m + i] = A_ic
+    const float* Bb;  // Bb[(l - j + bB) * q + j] = B_jl
+    int m, q, bA, bB;
+    __device__ float A(int i, int c) const { return Ab[(c - i + bA) * m + i]; }
+    __device__ float B(int j, int l) const { return Bb[(l - j + bB) * q + j]; }
+};
+struct BandGlobal {   // the bands read from the padded rows in global memory
+    const float* Ag;
+    const float* Bg;
+    int lda, ldb;
+    __device__ float A(int i, int c) const { return __ldg(Ag + (long long)i * lda + c); }
+    __device__ float B(int j, int l) const { return __ldg(Bg + (long long)j * ldb + l); }
+};
+
+// One banded iteration after the pick (R_ik staged in s_vec): w, c_k u on the rows
+// within 2 bA of i_k, v, this term's X update (the rows of A_ik's band), then R
+// and the norms of the touched rows; each band is summed in ascending index
+// order, one thread per output.  Returns with s_s holding (hi, lo) pairs for rows
+// [u0, u1] (batch_finalize completes them).
+template <int NT, int RPW, class Band>
+__device__ __forceinline__ void batch_banded_step(const Band& bd, const SysDesc& d, float* R, float* X, int ik,
+                                                  double ck, float* s_vec, float* s_w, float* s_u, double* s_s,
+                                                  int& u0, int& u1)
+{
+    constexpr int NW = NT / 32;
+    const int bA = d.bandA, bB = d.bandB;
+    // w_j = sum over |l - j| <= bB of R_ik,l B_jl
+    for (int j = threadIdx.x; j < d.q; j += NT) {
+        const int l0 = max(0, j - bB), l1 = min(d.n - 1, j + bB);
+        float acc = 0.f;
+        for (int l = l0; l <= l1; ++l) acc = fmaf(s_vec[l], bd.B(j, l), acc);
+        s_w[j] = acc;
+    }
+    // c_k u_i for |i - ik| <= 2 bA: u_i = (A A_ik^T)_i vanishes elsewhere
+    u0 = max(0, ik - 2 * bA);
+    u1 = min(d.m - 1, ik + 2 * bA);
+    for (int i = u0 + threadIdx.x; i <= u1; i += NT) {
+        const int c0 = max(0, max(i, ik) - bA), c1 = min(d.p - 1, min(i, ik) + bA);
+        float acc = 0.f;
+        for (int c = c0; c <= c1; ++c) acc = fmaf(bd.A(i, c), bd.A(ik, c), acc);
+        s_u[i - u0] = (float)(ck * (double)acc);
+    }
+    __syncthreads();
+    // v_l = sum over |j - l| <= bB of w_j B_jl (padding columns 0)
+    for (int l = threadIdx.x; l < d.ldr; l += NT) {
+        float acc = 0.f;
+        if (l < d.n) {
+            const int j0 = max(0, l - bB), j1 = min(d.q - 1, l + bB);
+            for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], bd.B(j, l), acc);
+        }
+        s_vec[l] = acc;
+    }
+    // X_c += c_k A_ik,c w for the rows c of A_ik's band (this term of the X update,
+    // applied at once: A_ik^T w has no other nonzero rows)
+    {
+        const int xc0 = max(0, ik - bA), xc1 = min(d.p - 1, ik + bA);
+        const float ckf = (float)ck;
+        for (int j = threadIdx.x; j < d.q; j += NT) {
+            const float wj = s_w[j];
+            for (int c0 = xc0; c0 <= xc1; c0 += 8) {
+                float xv[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (c0 + e <= xc1) xv[e] = X[(long long)(c0 + e) * d.q + j];
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (c0 + e <= xc1) X[(long long)(c0 + e) * d.q + j] = fmaf(ckf * bd.A(ik, c0 + e), wj, xv[e]);
             }
         }
     }
+    __syncthreads();
+    batch_update_rows<NW, RPW>(R, d.ldr, u0, u1 + 1, s_u, s_vec, s_s);
 }
 
 template <int NT, int RPW>
 __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
 {
     constexpr int NW = NT / 32;
-    __shared__ double s_s[kMaxSide];                      // ||R_i||^2
+    constexpr int NB = kMaxSide / 32;                     // row blocks of 32
+    __shared__ double s_s[kMaxSide];                      // ||R_i||^2 (or its (hi, lo) pair while updated)
     __shared__ double s_r[kMaxSide];                      // s_i / a_i
+    __shared__ double s_ck[kMaxSide];                     // c_i = alpha / a_i
     __shared__ __align__(16) float s_vec[kMaxSide];       // R_{i_k} row, then v
-    __shared__ __align__(16) float s_arow[kMaxSide];      // A_{i_k}
+    __shared__ __align__(16) float s_arow[kMaxSide];      // A_{i_k} (dense path)
     __shared__ __align__(16) float s_w[kMaxSide];         // w
-    __shared__ __align__(16) float s_u[kMaxSide];         // u
-    extern __shared__ __align__(16) float fold_smem[];    // kFoldSmemBytes
+    __shared__ __align__(16) float s_u[kMaxSide];         // c_k u
+    extern __shared__ __align__(16) float dyn_smem[];     // dense path: fold tiles; banded path: the bands
+    __shared__ double s_bsum[NB], s_bJ[NB];               // per block: sum of s, admitted sum
+    __shared__ long long s_bkey[NB];                      // per block: largest r (bit pattern)
+    __shared__ int s_barg[NB];                            // per block: its row
     __shared__ double red[2 * 32];
-    __shared__ long long redi[2 * 32];
-    __shared__ int s_sys, s_first, s_last, s_stop;
-    __shared__ double s_S, s_rmax, s_base_next;
+    __shared__ int s_sys, s_first, s_stop, s_ik;
+    __shared__ double s_S, s_t, s_uk;
     __shared__ long long s_imax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -387,19 +511,38 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
         const float* B = P.B + d.offB;
         const float* C = P.C + d.offR;
         float* R = P.R + d.offR;
+        float* X = P.X + d.offX;
         const double* a = P.a + d.offRow;
         const double* pref = P.rbk_prefix + d.offRow;
         int* hrow = P.hist_rows + d.offHist;
         float* hcf = P.hist_c + d.offHist;
         float* hw = P.hist_w + d.offHistW;
+        const bool banded = d.bandA >= 0;
+        const bool band_sm =
+            banded && 4LL * ((2LL * d.bandA + 1) * d.m + (2LL * d.bandB + 1) * d.q) <= (long long)P.band_smem;
+
+        for (int i = threadIdx.x; i < d.m; i += NT) {
+            const double ai = a[i];
+            s_ck[i] = ai > 0.0 ? __ddiv_rn(d.alpha, ai) : 0.0;
+        }
+        if (band_sm) {  // the bands of A and B, diagonal by diagonal (zero outside the matrix)
+            float* Ab = dyn_smem;
+            float* Bb = dyn_smem + (2 * d.bandA + 1) * d.m;
+            for (int e = threadIdx.x; e < (2 * d.bandA + 1) * d.m; e += NT) {
+                const int i = e % d.m, c = i + e / d.m - d.bandA;
+                Ab[e] = (c >= 0 && c < d.p) ? A[(long long)i * d.lda + c] : 0.f;
+            }
+            for (int e = threadIdx.x; e < (2 * d.bandB + 1) * d.q; e += NT) {
+                const int j = e % d.q, l = j + e / d.q - d.bandB;
+                Bb[e] = (l >= 0 && l < d.n) ? B[(long long)j * d.ldb + l] : 0.f;
+            }
+        }
 
         // R^0 = C - A X^0 B (row by row) or R^0 = C
         if (P.init_from_x) {
             // on the banded path only the bands of A_i and of B's columns contribute
-            const float* X = P.X + d.offX;
-            const bool bnd = d.bandA >= 0;
             for (int i = 0; i < d.m; ++i) {
-                const int c0 = bnd ? max(0, i - d.bandA) : 0, c1 = bnd ? min(d.p - 1, i + d.bandA) : d.p - 1;
+                const int c0 = banded ? max(0, i - d.bandA) : 0, c1 = banded ? min(d.p - 1, i + d.bandA) : d.p - 1;
                 for (int j = threadIdx.x; j < d.q; j += NT) {  // t = A_i X
                     float acc = 0.f;
                     for (int c2 = c0; c2 <= c1; ++c2)
@@ -408,7 +551,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                 }
                 __syncthreads();
                 for (int l = threadIdx.x; l < d.n; l += NT) {  // R_i = C_i - t B
-                    const int j0 = bnd ? max(0, l - d.bandB) : 0, j1 = bnd ? min(d.q - 1, l + d.bandB) : d.q - 1;
+                    const int j0 = banded ? max(0, l - d.bandB) : 0, j1 = banded ? min(d.q - 1, l + d.bandB) : d.q - 1;
                     float acc = 0.f;
                     for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], B[(long long)j * d.ldb + l], acc);
                     R[(long long)i * d.ldr + l] = C[(long long)i * d.ldr + l] - acc;
@@ -422,7 +565,8 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
         }
         __syncthreads();
 
-        // row norms of R^0: warp per row (Kahan FP32 lanes, FP64 across lanes)
+        // row norms of R^0: warp per row (Kahan FP32 lanes, double-float across lanes),
+        // then the FP64 values and the block summaries
         for (int pass = 0; pass < 2; ++pass) {
             for (int i = warp; i < d.m; i += NW) {
                 float acc = 0.f, comp = 0.f;
@@ -435,12 +579,10 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                 }
                 float hi = acc, lo = -comp;
                 warp_sum_df(hi, lo);
-                if (lane == 0) {
-                    const double tot = (double)hi + (double)lo;
-                    s_s[i] = tot;
-                    s_r[i] = a[i] > 0.0 ? __ddiv_rn(tot, a[i]) : -INFINITY;
-                }
+                if (lane == 0) reinterpret_cast<float2*>(s_s)[i] = make_float2(hi, lo);
             }
+            __syncthreads();
+            batch_finalize<NW>(d.m, 0, d.m, a, s_s, s_r, s_bsum, s_bkey, s_barg);
             __syncthreads();
             if (!P.init_from_x || pass == 1) break;
             // test the caller's X0 against X0 = 0: keep it only if ||C - A X0 B|| < ||C||
@@ -450,55 +592,48 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
             const bool reject = !(S0 < d.normC2);
             if (threadIdx.x == 0 && P.x0_rejected) P.x0_rejected[sid] = reject ? 1 : 0;
             if (!reject) break;
-            float* X = P.X + d.offX;
             for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += NT) X[e] = 0.f;
             for (long long e = threadIdx.x; e < (long long)d.m * d.ldr; e += NT) R[e] = C[e];
             __syncthreads();
         }
 
+        const int nb = (d.m + 31) >> 5;
+        const int var = P.variant;
         long long k = 0;
         int nh = 0, flag = FLAG_RUNNING;
         for (;;) {
-            // ---- totals and stop test
-            {
-                // r_i is >= 0 or -inf, so its largest value is the largest IEEE bit pattern read as
-                // a signed integer: the argmax runs on the integer pipe (ties: smallest row)
-                double Sv = 0.0;
-                long long bkey = LLONG_MIN, bi = 0x7fffffffffffffffLL;
-                for (int i = threadIdx.x; i < d.m; i += NT) {
-                    Sv += s_s[i];
-                    const long long key = __double_as_longlong(s_r[i]);
-                    if (key > bkey) { bkey = key; bi = i; }
-                }
-                Sv = warp_sum(Sv);
+            // ---- totals from the block summaries (one warp), threshold, draw and stop test
+            if (warp == 0) {
+                double S = lane < nb ? s_bsum[lane] : 0.0;
+                long long key = lane < nb ? s_bkey[lane] : LLONG_MIN;
+                int arg = lane < nb ? s_barg[lane] : INT_MAX;
+                S = warp_sum(S);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const long long ok = __shfl_xor_sync(0xffffffffu, bkey, o);
-                    const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                    if (ok > bkey || (ok == bkey && oi < bi)) { bkey = ok; bi = oi; }
+                    const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+                    const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+                    if (ok > key || (ok == key && oa < arg)) { key = ok; arg = oa; }
                 }
-                if (lane == 0) { red[warp] = Sv; redi[warp] = bi; redi[NW + warp] = bkey; }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double S = 0.0;
-                    long long bbk = LLONG_MIN, bbi = 0x7fffffffffffffffLL;
-                    for (int w2 = 0; w2 < NW; ++w2) {
-                        S += red[w2];
-                        if (redi[NW + w2] > bbk || (redi[NW + w2] == bbk && redi[w2] < bbi)) {
-                            bbk = redi[NW + w2];
-                            bbi = redi[w2];
-                        }
-                    }
-                    const double bb = __longlong_as_double(bbk);
-                    s_S = S; s_rmax = bb; s_imax = bbi;
+                if (lane == 0) {
+                    const double rmax = __longlong_as_double(key);
+                    s_S = S;
+                    s_imax = arg;
                     int stop = 0;
                     if (!(S > 0.0)) stop = 2;
                     else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
                     else if (k >= P.maxit) stop = 4;
                     s_stop = stop;
+                    if (!stop && (var == GRBK_GRBK || var == GRBK_RGRBK)) {
+                        const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
+                        double t = __dadd_rn(__dmul_rn(theta, rmax), __dmul_rn(1.0 - theta, __ddiv_rn(S, d.F)));
+                        if (t > rmax) t = rmax;
+                        s_t = t;
+                    }
+                    if (!stop && var != GRBK_MWRBK && var != GRBK_BK)
+                        s_uk = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
                 }
-                __syncthreads();
             }
+            __syncthreads();
             if (s_stop) {
                 if (s_stop == 1) flag = FLAG_TOL_MET;
                 if (s_stop == 2) flag = FLAG_EXACT;
@@ -506,56 +641,57 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
             }
             // ---- select i_k
             int ik;
-            const int var = P.variant;
             if (var == GRBK_GRBK || var == GRBK_RGRBK) {
-                const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
-                double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, d.F)));
-                if (t > s_rmax) t = s_rmax;
-                // one block scan gives every prefix of the admitted s_i and S_J: thread T owns the
-                // contiguous rows [T K, T K + K); admission r_i >= t compares the IEEE bit patterns
-                // (r_i and t are >= 0 or -inf)
-                const double u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
-                const long long tkey = __double_as_longlong(t);
-                const int K = (d.m + NT - 1) / NT;
-                const int r0 = threadIdx.x * K, r1 = min(d.m, r0 + K);
-                double loc = 0.0;
-                int lastadm = -1;
-                for (int i = r0; i < r1; ++i)
-                    if (__double_as_longlong(s_r[i]) >= tkey) { loc += s_s[i]; lastadm = i; }
-                // warps without admitted rows (most of them when theta is large) skip the FP64 scan
-                const double incw = __any_sync(0xffffffffu, lastadm >= 0) ? warp_inclusive_scan(loc) : 0.0;
-                if (threadIdx.x == 0) { s_first = 0x7fffffff; s_last = -1; }
-                if (lane == 31) red[warp] = incw;
-                __syncthreads();
-                if (warp == 0) {  // exclusive bases of the warps and the total S_J
-                    const double wt = lane < NW ? red[lane] : 0.0;
-                    const double inc = warp_inclusive_scan(wt);
-                    if (lane < NW) red[NW + lane] = inc - wt;
-                    if (lane == NW - 1) s_base_next = inc;
-                }
-                __syncthreads();
-                const double target = __dmul_rn(u, s_base_next);
-                const double incl = red[NW + warp] + incw;
-                if (lastadm >= 0) {
-                    atomicMax(&s_last, lastadm);
-                    if (incl > target) {  // the prefix crosses u S_J within or before these rows
-                        double run = incl - loc;
-                        int pick = lastadm;
-                        for (int i = r0; i < r1; ++i)
-                            if (__double_as_longlong(s_r[i]) >= tkey) {
-                                if (run + s_s[i] > target) { pick = i; break; }
-                                run += s_s[i];
-                            }
-                        atomicMin(&s_first, pick);
+                // the admitted (r_i >= t, compared as bit patterns) sum of every block that
+                // has an admitted row; then one warp finds the block and the row where the
+                // prefix of the admitted s_i first exceeds u S_J
+                const long long tkey = __double_as_longlong(s_t);
+                for (int b = warp; b < nb; b += NW) {
+                    double v = 0.0;
+                    if (s_bkey[b] >= tkey) {
+                        const int i = (b << 5) + lane;
+                        if (i < d.m && __double_as_longlong(s_r[i]) >= tkey) v = s_s[i];
+                        v = warp_sum(v);
                     }
+                    if (lane == 0) s_bJ[b] = v;
                 }
                 __syncthreads();
-                ik = (s_first != 0x7fffffff) ? s_first : s_last;
+                if (warp == 0) {
+                    const double bv = lane < nb ? s_bJ[lane] : 0.0;
+                    const double inc = warp_inclusive_scan(bv);
+                    const double SJ = __shfl_sync(0xffffffffu, inc, 31);
+                    const double target = __dmul_rn(s_uk, SJ);
+                    const unsigned hit = __ballot_sync(0xffffffffu, bv > 0.0 && inc > target);
+                    int cb;
+                    double base;
+                    if (hit) {
+                        cb = __ffs(hit) - 1;
+                        base = __shfl_sync(0xffffffffu, inc - bv, cb);
+                    } else {  // rounding left u S_J uncovered: the last admitted row
+                        const unsigned nz = __ballot_sync(0xffffffffu, bv > 0.0);
+                        cb = nz ? 31 - __clz(nz) : -1;
+                        base = -INFINITY;
+                    }
+                    int pick = -1;
+                    if (cb >= 0) {
+                        const int i = (cb << 5) + lane;
+                        const bool adm = i < d.m && __double_as_longlong(s_r[i]) >= tkey;
+                        const double inc2 = base + warp_inclusive_scan(adm ? s_s[i] : 0.0);
+                        const unsigned h2 = __ballot_sync(0xffffffffu, adm && inc2 > target);
+                        const unsigned am = __ballot_sync(0xffffffffu, adm);
+                        if (h2) pick = (cb << 5) + __ffs(h2) - 1;
+                        else if (am) pick = (cb << 5) + 31 - __clz(am);
+                    }
+                    if (pick < 0) pick = (int)s_imax;
+                    if (lane == 0) s_ik = pick;
+                }
+                __syncthreads();
+                ik = s_ik;
             } else if (var == GRBK_MWRBK) {
                 ik = (int)s_imax;
             } else if (var == GRBK_RBK) {
                 if (threadIdx.x == 0) {
-                    const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), d.F);
+                    const double target = __dmul_rn(s_uk, d.F);
                     int lo = 0, hi = d.m;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -572,55 +708,28 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
             } else {
                 ik = (int)(k % d.m);
             }
-            __syncthreads();
-            const double aik = a[ik];
-            const double ck = aik > 0.0 ? __ddiv_rn(d.alpha, aik) : 0.0;
+            const double ck = s_ck[ik];
             if (threadIdx.x == 0 && k < P.trace_len) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
 
-            if (d.bandA >= 0) {
+            int rb = 0, re = d.m;
+            if (banded) {
                 // ---- banded A and B: u_i = (A A_ik^T)_i vanishes for |i - ik| > 2 bandA, so the
                 // update touches those rows only; w and v use the band of B
-                const int bA = d.bandA, bB = d.bandB;
                 {
                     const float4* Rr = reinterpret_cast<const float4*>(R + (long long)ik * d.ldr);
-                    const float4* Ar = reinterpret_cast<const float4*>(A + (long long)ik * d.lda);
                     for (int e = threadIdx.x; e < d.ldr / 4; e += NT) reinterpret_cast<float4*>(s_vec)[e] = Rr[e];
-                    for (int e = threadIdx.x; e < d.lda / 4; e += NT)
-                        reinterpret_cast<float4*>(s_arow)[e] = __ldg(Ar + e);
                 }
                 __syncthreads();
-                // w_j = sum over |l - j| <= bB of R_ik,l B_jl (one thread per row of B: the band is
-                // short, and the rows of B stay in L1 from one iteration to the next)
-                for (int j = threadIdx.x; j < d.q; j += NT) {
-                    const int l0 = max(0, j - bB), l1 = min(d.n - 1, j + bB);
-                    const float* Bj = B + (long long)j * d.ldb;
-                    float acc = 0.f;
-                    for (int l = l0; l <= l1; ++l) acc = fmaf(s_vec[l], __ldg(Bj + l), acc);
-                    s_w[j] = acc;
+                int u0, u1;
+                if (band_sm) {
+                    const BandShared bd{dyn_smem, dyn_smem + (2 * d.bandA + 1) * d.m, d.m, d.q, d.bandA, d.bandB};
+                    batch_banded_step<NT, RPW>(bd, d, R, X, ik, ck, s_vec, s_w, s_u, s_s, u0, u1);
+                } else {
+                    const BandGlobal bd{A, B, d.lda, d.ldb};
+                    batch_banded_step<NT, RPW>(bd, d, R, X, ik, ck, s_vec, s_w, s_u, s_s, u0, u1);
                 }
-                // c_k u_i for |i - ik| <= 2 bA (one thread per row of A)
-                const int u0 = max(0, ik - 2 * bA), u1 = min(d.m - 1, ik + 2 * bA);
-                for (int i = u0 + threadIdx.x; i <= u1; i += NT) {
-                    const int c0 = max(0, max(i, ik) - bA), c1 = min(d.p - 1, min(i, ik) + bA);
-                    const float* Ai = A + (long long)i * d.lda;
-                    float acc = 0.f;
-                    for (int c = c0; c <= c1; ++c) acc = fmaf(__ldg(Ai + c), s_arow[c], acc);
-                    s_u[i - u0] = (float)(ck * (double)acc);
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) { hrow[nh] = ik; hcf[nh] = (float)ck; }
-                for (int j = threadIdx.x; j < d.q; j += NT) hw[(long long)nh * d.q + j] = s_w[j];
-                // v_l = sum over |j - l| <= bB of w_j B_jl (padding columns 0)
-                for (int l = threadIdx.x; l < d.ldr; l += NT) {
-                    float acc = 0.f;
-                    if (l < d.n) {
-                        const int j0 = max(0, l - bB), j1 = min(d.q - 1, l + bB);
-                        for (int j = j0; j <= j1; ++j) acc = fmaf(s_w[j], __ldg(B + (long long)j * d.ldb + l), acc);
-                    }
-                    s_vec[l] = acc;
-                }
-                __syncthreads();
-                batch_update_rows<NW, RPW>(R, d.ldr, u0, u1 + 1, s_u, s_vec, a, s_s, s_r);
+                rb = u0;
+                re = u1 + 1;
             } else {
                 // ---- w = R_ik B^T, u = A A_ik^T (rows of B and A streamed as float4, 4 rows per warp)
                 {
@@ -639,7 +748,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                 for (int j = threadIdx.x; j < d.q; j += NT) hw[(long long)nh * d.q + j] = s_w[j];
                 {
                     const int nv4 = d.ldb / 4;
-                    float4* red4 = reinterpret_cast<float4*>(fold_smem);  // [RG][cols] float4
+                    float4* red4 = reinterpret_cast<float4*>(dyn_smem);  // [RG][cols] float4
                     for (int cb = 0; cb < nv4; cb += NT) {
                         const int ncols = min(NT, nv4 - cb);
                         const int RG = NT / ncols;
@@ -672,17 +781,19 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                     }
                 }
                 // ---- R -= c u v fused with the new row norms
-                batch_update_rows<NW, RPW>(R, d.ldr, 0, d.m, s_u, s_vec, a, s_s, s_r);
+                batch_update_rows<NW, RPW>(R, d.ldr, 0, d.m, s_u, s_vec, s_s);
+                ++nh;
             }
+            __syncthreads();
+            batch_finalize<NW>(d.m, rb, re, a, s_s, s_r, s_bsum, s_bkey, s_barg);
             ++k;
-            ++nh;
             if (nh == P.chunk) {
-                batch_fold<NT>(P, d, nh, fold_smem);
+                batch_fold<NT>(P, d, nh, dyn_smem);
                 nh = 0;
             }
             __syncthreads();
         }
-        batch_fold<NT>(P, d, nh, fold_smem);
+        batch_fold<NT>(P, d, nh, dyn_smem);
         if (threadIdx.x == 0) {
             P.iters[sid] = k;
             P.S_out[sid] = s_S;
@@ -912,18 +1023,34 @@ static BatchParams batch_params(grbk_batch* b, const int* order, int n, int* que
     return P;
 }
 
-static grbk_status launch_variant(int v, const BatchParams& P, int nsys_launch, int grid_cap, cudaStream_t st)
+// Shared-memory bytes of a banded system's band copies (0 on the dense path, and
+// when they exceed kBandSmemCap: such a system reads its bands from global memory).
+constexpr int kBandSmemCap = 150 * 1024;
+static int band_smem_bytes(const SysDesc& d)
+{
+    if (d.bandA < 0) return 0;
+    const long long bytes = 4LL * ((2LL * d.bandA + 1) * d.m + (2LL * d.bandB + 1) * d.q);
+    return bytes <= kBandSmemCap ? (int)bytes : 0;
+}
+
+// One launch of variant v over nsys_launch systems; band_bytes: the largest band
+// copy among them (the dynamic shared memory is the larger of it and the dense
+// path's fold tiles).
+static grbk_status launch_variant(int v, BatchParams P, int nsys_launch, int grid_cap, int band_bytes,
+                                  cudaStream_t st)
 {
     const BatchVariant& V = kVariants[v];
     int dev = 0, nsm = 0, per_sm = 0;
+    const int smem = std::max(V.smem, band_bytes);
+    P.band_smem = smem;
     GRBK_CK(cudaGetDevice(&dev));
     GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    GRBK_CK(cudaFuncSetAttribute(V.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, V.smem));
-    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.kern, V.threads, V.smem));
+    GRBK_CK(cudaFuncSetAttribute(V.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, V.kern, V.threads, smem));
     int grid = nsm * (per_sm > 0 ? per_sm : 1);
     if (grid_cap > 0) grid = std::min(grid, grid_cap);
     grid = std::min(grid, nsys_launch);
-    V.kern<<<grid, V.threads, V.smem, st>>>(P);
+    V.kern<<<grid, V.threads, smem, st>>>(P);
     GRBK_CK(cudaGetLastError());
     return GRBK_OK;
 }
@@ -959,7 +1086,7 @@ static grbk_status batch_autotune(grbk_batch* b)
             for (int rep = 0; rep < 2 && res == GRBK_OK; ++rep) {
                 if (cudaMemsetAsync(b->dqueue, 0, 4, st) != cudaSuccess) { res = GRBK_ECUDA; break; }
                 if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) { res = GRBK_ECUDA; break; }
-                res = launch_variant(vv, P, 1, 1, st);
+                res = launch_variant(vv, P, 1, 1, band_smem_bytes(d), st);
                 if (res == GRBK_OK && rep == 1 && cudaEventRecord(e1, st) != cudaSuccess) res = GRBK_ECUDA;
             }
             if (res == GRBK_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
@@ -1208,7 +1335,10 @@ extern "C" grbk_status grbk_batch_solve(grbk_batch* b, int32_t variant, double t
             sv = b->side[v];
             GRBK_CK(cudaStreamWaitEvent(sv, b->ev_fork, 0));
         }
-        const grbk_status e = launch_variant(v, Pv, b->gcnt[v], b->opts.grid_ctas, sv);
+        int bbytes = 0;
+        for (int g2 = 0; g2 < b->gcnt[v]; ++g2)
+            bbytes = std::max(bbytes, band_smem_bytes(b->hsys[b->order[b->goff[v] + g2]]));
+        const grbk_status e = launch_variant(v, Pv, b->gcnt[v], b->opts.grid_ctas, bbytes, sv);
         if (e != GRBK_OK) return e;
         if (ngroups > 1) {
             GRBK_CK(cudaEventRecord(b->ev_join[v], sv));
