@@ -70,11 +70,24 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v)
 
 __device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
 
-// Grid-wide barrier for a co-resident (cooperative) grid.  Every wait is
-// bounded: on expiry the CTA records GRBK_ETIMEOUT and the barrier returns
-// false, as it also does when any CTA has recorded an error; callers then
-// leave the kernel.  s_ok must be a __shared__ int.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int site, int& s_ok,
+// Grid-wide barrier for a co-resident (cooperative) grid.  bar->count counts
+// arrivals and bar->gen completed barriers since both were zeroed, so after g
+// barriers count = g x grid.  Each CTA keeps its own copy of gen in s_gen (read
+// once at kernel start by grid_gen_init, when no barrier of the launch can have
+// completed: that needs this CTA's arrival), so an arrival is one atomic add;
+// the CTA whose add brings count to (g + 1) x grid completes the barrier by
+// releasing gen = g + 1, and the others wait for that (unsigned arithmetic wraps
+// consistently).  Every wait is bounded: on expiry the CTA records
+// GRBK_ETIMEOUT and the barrier returns false, as it does when it sees, while
+// waiting, that any CTA has recorded an error; callers then leave the kernel.
+// s_ok and s_gen must be __shared__.
+__device__ __forceinline__ void grid_gen_init(const GridBarrier* bar, unsigned int& s_gen)
+{
+    if (threadIdx.x == 0) s_gen = ld_acquire_u32(&bar->gen);
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int site, int& s_ok, unsigned int& s_gen,
                                           long long budget = kBarrierBudget)
 {
     __syncthreads();
@@ -85,18 +98,22 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
     }
     if (threadIdx.x == 0) {
         // The block barrier orders the CTA's writes before thread 0's release
-        // fence; the arrival is a relaxed atomic after it, the waiters acquire.
+        // fence; the arrival is a relaxed atomic after it.  The completing CTA
+        // fences again (acquire) before its release store; the waiters acquire.
         const unsigned int nb = gridDim.x;
-        const unsigned int g = ld_acquire_u32(&bar->gen);
+        const unsigned int g = s_gen;
         asm volatile("fence.acq_rel.gpu;" ::: "memory");
         const unsigned int arrived = atomicAdd(&bar->count, 1u);
         int ok = 1;
-        if (arrived == nb - 1) {
-            atomicExch(&bar->count, 0u);
+        if (arrived == g * nb + (nb - 1u)) {
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             st_release_u32(&bar->gen, g + 1u);
         } else {
             const long long t0 = clock64();
-            while (ld_acquire_u32(&bar->gen) == g) {
+            for (;;) {
+                const int sv = ld_volatile_int(&st->status);  // issued before the acquire load
+                if (ld_acquire_u32(&bar->gen) != g) break;
+                if (sv != 0) { ok = 0; break; }
                 if (clock64() - t0 > budget) {
                     if (atomicCAS(&st->status, 0, (int)GRBK_ETIMEOUT) == 0) st->timeout_site = site;
                     ok = 0;
@@ -105,8 +122,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, DevState* st, int si
                 __nanosleep(32);  // polling without a pause slows the CTAs still working
             }
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
-        s_ok = ok && (ld_volatile_int(&st->status) == 0);
+        s_gen = g + 1u;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -186,6 +203,26 @@ __device__ __forceinline__ void warp_argmax(double& v, long long& i)
         }
     }
 }
+
+// argmax of signed integer keys across the warp (ties: smallest index); every lane
+// ends with the result
+__device__ __forceinline__ void warp_argmax_key(long long& key, long long& i)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, i, o);
+        if (ok > key || (ok == key && oi < i)) {
+            key = ok;
+            i = oi;
+        }
+    }
+}
+
+// The bit pattern of a double read as a signed integer: for values >= +0 and -inf
+// the integer order is the numeric order, so comparisons of row norms, ratios and
+// their sums can run on the integer pipe instead of the (slow) FP64 pipe.
+__device__ __forceinline__ long long dkey(double v) { return __double_as_longlong(v); }
 
 // inclusive scan across the warp (fixed order)
 __device__ __forceinline__ double warp_inclusive_scan(double v)

@@ -36,6 +36,7 @@ void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int 
 constexpr int kBlock = 512;        // threads per CTA of the persistent kernel
 constexpr int kWarps = kBlock / 32;
 constexpr int kUnroll = 8;         // independent vector loads in flight per lane
+constexpr int kMaxGrid = 320;      // largest grid of the persistent kernel (pick_row: 32 x 10 partials)
 constexpr int kPartsCap = 2048;    // per-CTA (row, chunk) partial slots in shared memory
 
 template <typename T> struct VecOf;
@@ -123,8 +124,8 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
     if (rows_per_batch < 1) rows_per_batch = 1;
     if (rows_per_batch > kBlock) rows_per_batch = kBlock;
 
-    double cta_S = 0.0, cta_best = -INFINITY;
-    long long cta_bi = 0x7fffffffffffffffLL;
+    double cta_S = 0.0;
+    long long cta_key = __double_as_longlong(-INFINITY), cta_bi = LLONG_MAX;
 
     for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
         const int64_t b1 = min(r1, b0 + rows_per_batch);
@@ -182,8 +183,8 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
         }
         __syncthreads();
         // finalise the rows of this batch: one thread per row
-        double my_S = 0.0, my_best = -INFINITY;
-        long long my_bi = 0x7fffffffffffffffLL;
+        double my_S = 0.0;
+        long long my_key = LLONG_MIN, my_bi = LLONG_MAX;
         for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
             double sv = 0.0;
             for (int c = 0; c < nch; ++c) sv += sm_parts[rr * nch + c];
@@ -194,29 +195,38 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             __stcg(P.sr + row, make_double2(sv, ri));
             if (sm_sr) sm_sr[row - r0] = make_double2(sv, ri);
             my_S += sv;
-            if (ri > my_best) { my_best = ri; my_bi = row; }
+            const long long rk = __double_as_longlong(ri);  // r >= 0 or -inf: integer order
+            if (rk > my_key) { my_key = rk; my_bi = row; }
         }
-        // block reduction, fixed order
-        my_S = warp_sum(my_S);
-        warp_argmax(my_best, my_bi);
-        if (lane == 0) { sm_red[warp] = my_S; sm_red[kWarps + warp] = my_best; sm_redi[warp] = my_bi; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double bs = 0.0, bb = -INFINITY;
-            long long bi = 0x7fffffffffffffffLL;
-            for (int w2 = 0; w2 < kWarps; ++w2) {
-                bs += sm_red[w2];
-                const double cand = sm_red[kWarps + w2];
-                if (cand > bb || (cand == bb && sm_redi[w2] < bi)) { bb = cand; bi = sm_redi[w2]; }
+        // block reduction in a fixed order, only on the warps that hold rows of the batch
+        // (an FP64 warp instruction costs the same with idle lanes), argmax on the integer pipe
+        const int nact = (int)min((int64_t)kWarps, (b1 - b0 + 31) / 32);
+        if (warp < nact) {
+            my_S = warp_sum(my_S);
+            warp_argmax_key(my_key, my_bi);
+            if (lane == 0) {
+                sm_red[warp] = my_S;
+                sm_red[kWarps + warp] = __longlong_as_double(my_key);
+                sm_redi[warp] = my_bi;
             }
-            cta_S += bs;
-            if (bb > cta_best || (bb == cta_best && bi < cta_bi)) { cta_best = bb; cta_bi = bi; }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double bs = lane < nact ? sm_red[lane] : 0.0;
+            long long bk = lane < nact ? __double_as_longlong(sm_red[kWarps + lane]) : LLONG_MIN;
+            long long bi = lane < nact ? sm_redi[lane] : LLONG_MAX;
+            bs = warp_sum(bs);
+            warp_argmax_key(bk, bi);
+            if (lane == 0) {
+                cta_S += bs;
+                if (bk > cta_key || (bk == cta_key && bi < cta_bi)) { cta_key = bk; cta_bi = bi; }
+            }
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         double2* pp = reinterpret_cast<double2*>(P.part + blockIdx.x);
-        __stcg(pp, make_double2(cta_S, cta_best));
+        __stcg(pp, make_double2(cta_S, __longlong_as_double(cta_key)));
         __stcg(pp + 1, make_double2(__longlong_as_double(cta_bi), 0.0));
     }
 }
@@ -365,6 +375,116 @@ __device__ __noinline__ void cols_gemv(const T* B, int64_t ldb, int64_t q, const
     }
 }
 
+// ME-GRBK / ME-RGRBK pick by warp 0 of every CTA (all CTAs take the same row):
+// the CTA partials S_J^c (admitted sums, rows in CTA order) are in P.part_SJ.
+template <typename T>
+__device__ __noinline__ long long pick_row(const IterParams<T>& P, int G, long long tkey, double u, long long imax)
+{
+    const int lane = threadIdx.x & 31;
+    // The CTA partials S_J^c: lane l owns the run of CTAs [l P, l P + P), P = ceil(G / 32)
+    // (G <= 32 kPartRegs).  One scan of the run sums gives S_J and the run where the
+    // prefix first exceeds u S_J; a second scan, of that run's partials spread over
+    // the lanes, gives the owning CTA c*; a third, of c*'s rows in per-lane runs, the
+    // row.  Where rounding leaves u S_J uncovered at a level, its last admitted entry
+    // is taken (with base -inf below it).
+    constexpr int kPartRegs = 10;
+    const unsigned FULL = 0xffffffffu;
+    const int PPL = (G + 31) / 32;
+    double pv[kPartRegs];
+    double lsum = 0.0;
+#pragma unroll
+    for (int j = 0; j < kPartRegs; ++j) {
+        const int cc = lane * PPL + j;
+        pv[j] = (j < PPL && cc < G) ? __ldcg(P.part_SJ + cc) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kPartRegs; ++j)
+        if (j < PPL) lsum += pv[j];
+    const double inc = warp_inclusive_scan(lsum);
+    const double SJ = __shfl_sync(FULL, inc, 31);
+    const double target = __dmul_rn(u, SJ);
+    const long long gkey = __double_as_longlong(target);
+    const unsigned hit = __ballot_sync(FULL, dkey(lsum) > 0 && dkey(inc) > gkey);
+    int Lc;
+    double excl;
+    if (hit) {
+        Lc = __ffs(hit) - 1;
+        excl = __shfl_sync(FULL, inc - lsum, Lc);
+    } else {
+        const unsigned nz = __ballot_sync(FULL, dkey(lsum) > 0);
+        Lc = nz ? 31 - __clz(nz) : -1;
+        excl = -INFINITY;
+    }
+    int cstar = -1;
+    double cexcl = -INFINITY;
+    if (Lc >= 0) {
+        double mine = 0.0;
+#pragma unroll
+        for (int j = 0; j < kPartRegs; ++j) {
+            const double x = __shfl_sync(FULL, pv[j], Lc);
+            if (j == lane) mine = x;
+        }
+        if (!(lane < PPL && Lc * PPL + lane < G)) mine = 0.0;
+        const double inc2 = excl + warp_inclusive_scan(mine);
+        const unsigned h2 = __ballot_sync(FULL, dkey(mine) > 0 && dkey(inc2) > gkey);
+        if (h2) {
+            const int l2 = __ffs(h2) - 1;
+            cstar = Lc * PPL + l2;
+            cexcl = __shfl_sync(FULL, inc2 - mine, l2);
+        } else {
+            const unsigned nz2 = __ballot_sync(FULL, dkey(mine) > 0);
+            if (nz2) cstar = Lc * PPL + 31 - __clz(nz2);
+        }
+    }
+    long long pick = -1, last = -1;
+    if (cstar >= 0) {
+        int64_t q0 = 0, q1 = 0;
+        cta_rows(P.m, cstar, G, q0, q1);
+        double run = cexcl;
+        // rounds of up to 32 kRowRegs rows; lane l owns a contiguous run of RPL rows
+        constexpr int kRowRegs = 8;
+        for (int64_t rb = q0; rb < q1 && pick < 0; rb += 32 * kRowRegs) {
+            const int64_t rn = min((int64_t)(32 * kRowRegs), q1 - rb);
+            const int RPL = (int)((rn + 31) / 32);
+            const int64_t lb = rb + (int64_t)lane * RPL;
+            double2 rv[kRowRegs];
+#pragma unroll
+            for (int j = 0; j < kRowRegs; ++j)
+                rv[j] = (j < RPL && lb + j < rb + rn) ? __ldcg(P.sr + lb + j) : make_double2(0.0, -INFINITY);
+            double ls = 0.0;
+            long long lastl = -1;
+#pragma unroll
+            for (int j = 0; j < kRowRegs; ++j)
+                if (j < RPL && dkey(rv[j].y) >= tkey) { ls += rv[j].x; lastl = lb + j; }
+            const double incr = run + warp_inclusive_scan(ls);
+            const unsigned am = __ballot_sync(FULL, lastl >= 0);
+            if (am) last = __shfl_sync(FULL, lastl, 31 - __clz(am));
+            const unsigned hr = __ballot_sync(FULL, dkey(ls) > 0 && dkey(incr) > gkey);
+            if (hr) {
+                const int Lr = __ffs(hr) - 1;
+                const double ex = __shfl_sync(FULL, incr - ls, Lr);
+                double ms = 0.0;
+                long long mk = LLONG_MIN;
+#pragma unroll
+                for (int j = 0; j < kRowRegs; ++j) {
+                    const double xs = __shfl_sync(FULL, rv[j].x, Lr);
+                    const long long xk = __shfl_sync(FULL, dkey(rv[j].y), Lr);
+                    if (j == lane) { ms = xs; mk = xk; }
+                }
+                const bool adm = lane < RPL && mk >= tkey;
+                const double inc3 = ex + warp_inclusive_scan(adm ? ms : 0.0);
+                const unsigned h3 = __ballot_sync(FULL, adm && dkey(inc3) > gkey);
+                const unsigned a3 = __ballot_sync(FULL, adm);
+                pick = rb + (int64_t)Lr * RPL + (h3 ? __ffs(h3) - 1 : 31 - __clz(a3));
+            }
+            run = __shfl_sync(FULL, incr, 31);
+        }
+    }
+    if (pick < 0) pick = last;
+    if (pick < 0) pick = imax;  // admitted sum vanished (cannot happen with S > 0)
+    return pick;
+}
+
 // ----------------------------------------------------------------------------
 // the persistent iteration kernel
 // ----------------------------------------------------------------------------
@@ -376,7 +496,8 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     __shared__ double sm_red[2 * kWarps];
     __shared__ long long sm_redi[kWarps];
     __shared__ int s_ok;
-    __shared__ double s_S, s_rmax, s_t, s_u;
+    __shared__ unsigned int s_gen;
+    __shared__ double s_S, s_t, s_u, s_ck;
     __shared__ long long s_imax, s_ik;
     __shared__ int s_stop;
     __shared__ double2 sm_sr[kSrCap];          // this CTA's (s_i, r_i) when it owns <= kSrCap rows
@@ -394,14 +515,16 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     const bool own_sm = (r1 - r0) <= kSrCap;
     if (own_sm)
         for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) sm_sr[i - r0] = __ldcg(P.sr + i);
-    __syncthreads();
+    grid_gen_init(P.bar, s_gen);
 
     for (int it = 0; it <= P.nit; ++it) {
         const long long k = P.k0 + it;
         // ---------------- select: totals from the per-CTA partials ----------
         if (warp == 0) {
-            double S = 0.0, br = -INFINITY;
-            long long bi = 0x7fffffffffffffffLL;
+            // r >= 0 or -inf, so the largest r is the largest bit pattern read as a signed
+            // integer: the argmax stays off the FP64 pipe (ties: smallest row)
+            double S = 0.0;
+            long long bkey = LLONG_MIN, bi = LLONG_MAX;
             // all of this lane's partials (CTAs lane, lane + 32, ...) are requested
             // before any is used: one L2 round trip per 32 * kSelRegs CTAs
             constexpr int kSelRegs = 5;
@@ -421,23 +544,31 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
                     const int cc = cb + j * 32 + lane;
                     if (cc < G) {
                         S += p0[j].x;
-                        const double rr = p0[j].y;
+                        const long long rk = __double_as_longlong(p0[j].y);
                         const long long ii = __double_as_longlong(p1[j].x);
-                        if (rr > br || (rr == br && ii < bi)) { br = rr; bi = ii; }
+                        if (rk > bkey || (rk == bkey && ii < bi)) { bkey = rk; bi = ii; }
                     }
                 }
             }
             // the draw of this iteration, while the partials are in flight
             if (lane == 0) s_u = philox_uniform(P.seed, (uint64_t)k, P.sys);
             S = warp_sum(S);
-            warp_argmax(br, bi);
+            warp_argmax_key(bkey, bi);
             if (lane == 0) {
-                s_S = S; s_rmax = br; s_imax = bi;
+                const double br = __longlong_as_double(bkey);
+                s_S = S; s_imax = bi;
                 int stop = 0;
                 if (!(S > 0.0)) stop = (S == 0.0) ? 2 : 3;      // 3: NaN
                 else if (P.stop_S >= 0.0 && S <= P.stop_S) stop = 1;
                 else if (it == P.nit) stop = 4;
                 s_stop = stop;
+                // the threshold, once per CTA (Eq. of Algorithm 4; theta = 1/2: Algorithm 3)
+                if (stop == 0 && (P.variant == GRBK_GRBK || P.variant == GRBK_RGRBK)) {
+                    const double theta = (P.variant == GRBK_GRBK) ? 0.5 : P.theta;
+                    double t = __dadd_rn(__dmul_rn(theta, br), __dmul_rn(1.0 - theta, __ddiv_rn(S, P.F)));
+                    if (t > br) t = br;
+                    s_t = t;
+                }
                 if (c == 0) {
                     if (stop == 0 && k < P.trace_len) P.trace_S[k] = S;
                     if (stop != 0) {
@@ -457,98 +588,23 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         long long ik = -1;
         const int var = P.variant;
         if (var == GRBK_GRBK || var == GRBK_RGRBK) {
-            const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
-            double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, P.F)));
-            if (t > s_rmax) t = s_rmax;
+            // admission r_i >= t and the prefix tests below compare bit patterns: t, r_i
+            // and the sums are >= 0 (r_i may be -inf), so the integer order is the numeric one
+            const long long tkey = __double_as_longlong(s_t);
             // admitted sum of this CTA's rows
             if (warp == 0) {
                 double sj = 0.0;
                 for (int64_t i = r0 + lane; i < r1; i += 32) {
                     const double2 v = own_sm ? sm_sr[i - r0] : __ldcg(P.sr + i);
-                    if (v.y >= t) sj += v.x;
+                    if (__double_as_longlong(v.y) >= tkey) sj += v.x;
                 }
                 sj = warp_sum(sj);
                 if (lane == 0) __stcg(P.part_SJ + c, sj);
             }
-            if (!grid_sync(P.bar, P.st, 1, s_ok)) return;
+            if (!grid_sync(P.bar, P.st, 1, s_ok, s_gen)) return;
             if (warp == 0) {
-                // every partial this lane will scan, loaded at once (G <= 32 * kPartRegs)
-                constexpr int kPartRegs = 10;
-                double pv[kPartRegs];
-#pragma unroll
-                for (int j = 0; j < kPartRegs; ++j) {
-                    const int cc = j * 32 + lane;
-                    pv[j] = (cc < G) ? __ldcg(P.part_SJ + cc) : 0.0;
-                }
-                double SJ = 0.0;
-#pragma unroll
-                for (int j = 0; j < kPartRegs; ++j) SJ += pv[j];
-                SJ = warp_sum(SJ);
-                const double u = s_u;
-                const double target = __dmul_rn(u, SJ);
-                // owning CTA: first with inclusive prefix > target
-                double base = 0.0;
-                int cstar = -1;
-                double excl = 0.0;
-                for (int cb = 0; cb < G && cstar < 0; cb += 32) {
-                    const int cc = cb + lane;
-                    double val = 0.0;
-#pragma unroll
-                    for (int j = 0; j < kPartRegs; ++j)
-                        if (j == cb / 32) val = pv[j];
-                    const double inc = base + warp_inclusive_scan(val);
-                    const unsigned hit = __ballot_sync(0xffffffffu, (cc < G) && (inc > target) && val > 0.0);
-                    if (hit) {
-                        const int l = __ffs(hit) - 1;
-                        cstar = cb + l;
-                        excl = __shfl_sync(0xffffffffu, inc - val, l);
-                    }
-                    base = __shfl_sync(0xffffffffu, inc, 31);
-                }
-                if (cstar < 0) {  // rounding left the target uncovered: last CTA with admitted rows
-                    for (int cc = G - 1; cc >= 0; --cc)
-                        if (__ldcg(P.part_SJ + cc) > 0.0) { cstar = cc; break; }
-                    excl = -INFINITY;  // forces the last admitted row of cstar
-                }
-                int64_t q0 = 0, q1 = 0;
-                if (cstar >= 0) cta_rows(P.m, cstar, G, q0, q1);
-                long long pick = -1, last = -1;
-                double run = excl;
-                // the owning CTA's rows, loaded at once (up to 32 * kRowRegs rows, then in further rounds)
-                constexpr int kRowRegs = 8;
-                double2 rv[kRowRegs];
-#pragma unroll
-                for (int j = 0; j < kRowRegs; ++j) {
-                    const int64_t i = q0 + j * 32 + lane;
-                    rv[j] = (i < q1) ? __ldcg(P.sr + i) : make_double2(0.0, -INFINITY);
-                }
-                for (int64_t ib = q0; ib < q1 && pick < 0; ib += 32) {
-                    const int64_t i = ib + lane;
-                    double val = 0.0;
-                    bool adm = false;
-                    if (i < q1) {
-                        const int64_t jr = (ib - q0) / 32;
-                        double2 v = make_double2(0.0, -INFINITY);
-                        if (jr < kRowRegs) {
-#pragma unroll
-                            for (int j = 0; j < kRowRegs; ++j)
-                                if (j == jr) v = rv[j];
-                        } else {
-                            v = __ldcg(P.sr + i);
-                        }
-                        adm = (v.y >= t);
-                        if (adm) val = v.x;
-                    }
-                    const double inc = run + warp_inclusive_scan(val);
-                    const unsigned am = __ballot_sync(0xffffffffu, adm);
-                    if (am) last = ib + (31 - __clz(am));
-                    const unsigned hit = __ballot_sync(0xffffffffu, adm && (inc > target));
-                    if (hit) pick = ib + (__ffs(hit) - 1);
-                    run = __shfl_sync(0xffffffffu, inc, 31);
-                }
-                if (pick < 0) pick = last;
-                if (pick < 0) pick = s_imax;  // admitted sum vanished (cannot happen with S > 0)
-                if (lane == 0) { s_ik = pick; s_t = t; }
+                const long long pick = pick_row(P, G, tkey, s_u, s_imax);
+                if (lane == 0) s_ik = pick;
             }
             __syncthreads();
             ik = s_ik;
@@ -575,13 +631,6 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         } else {  // GRBK_BK
             ik = k % P.m;
         }
-        const double aik = __ldg(P.a + ik);
-        const double ck = (aik > 0.0) ? __ddiv_rn(P.alpha, aik) : 0.0;
-        if (c == 0 && threadIdx.x == 0) {
-            P.hist_rows[it] = (int)ik;
-            P.hist_c[it] = ck;
-            if (k < P.trace_len) P.trace_rows[k] = (int)ik;
-        }
 
         // ---------------- W/U: w = R_ik B^T, u = A A_ik^T ---------------------
         const T* Rik = P.R + ik * P.ldr;
@@ -594,12 +643,29 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             for (int64_t e = threadIdx.x; e < P.lda / VN; e += kBlock)
                 reinterpret_cast<V*>(sa)[e] = __ldg(reinterpret_cast<const V*>(Aik) + e);
         }
+        // this thread's first entry of row i_k of A A^T, loaded with the staging
+        const int64_t ig = r0 + threadIdx.x;
+        T g0 = (T)0;
+        if (P.G && ig < r1) g0 = __ldg(P.G + ik * P.ldg + ig);
+        // c_k = alpha / a_ik by one thread, after its share of the staging loads is issued
+        if (threadIdx.x == 0) {
+            const double aik = __ldg(P.a + ik);
+            const double ckv = (aik > 0.0) ? __ddiv_rn(P.alpha, aik) : 0.0;
+            s_ck = ckv;
+            if (c == 0) {
+                P.hist_rows[it] = (int)ik;
+                P.hist_c[it] = ckv;
+                if (k < P.trace_len) P.trace_rows[k] = (int)ik;
+            }
+        }
         __syncthreads();
+        const double ck = s_ck;
         // u holds the row coefficients c_k (A A_ik^T)_i of this CTA's rows, read from
         // row i_k of the precomputed A A^T when there is one
         if (P.G) {
             const T* Gi = P.G + ik * P.ldg;
-            for (int64_t i = r0 + threadIdx.x; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
+            if (ig < r1) __stcg(P.u + ig, (T)(ck * (double)g0));
+            for (int64_t i = ig + kBlock; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
         } else {
             rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
         }
@@ -617,14 +683,14 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             cta_rows(P.q, c, G, j0, j1);
             rows_dot<T>(P.B, P.ldb, j0, j1, P.smem_v ? sv : Rik, P.smem_v ? 0 : 1, P.w, P.hist_w + (int64_t)it * P.q,
                         sm_parts);
-            if (!grid_sync(P.bar, P.st, 2, s_ok)) return;
+            if (!grid_sync(P.bar, P.st, 2, s_ok, s_gen)) return;
 
             // ---------------- V: v = w B (column slab of this CTA) -----------
             for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
             __syncthreads();
             cols_gemv<T>(P.B, P.ldb, P.q, sw, P.v, c, G, sm_parts);
         }
-        if (!grid_sync(P.bar, P.st, 3, s_ok)) return;
+        if (!grid_sync(P.bar, P.st, 3, s_ok, s_gen)) return;
 
         // ---------------- F: fused rank-1 update + row norms -----------------
         if (P.smem_v) {
@@ -633,7 +699,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             __syncthreads();
         }
         fused_pass<T, true>(P, ck, P.smem_v ? sv : P.v, r0, r1, sm_parts, sm_red, sm_redi, own_sm ? sm_sr : nullptr);
-        if (!grid_sync(P.bar, P.st, 4, s_ok)) return;
+        if (!grid_sync(P.bar, P.st, 4, s_ok, s_gen)) return;
     }
 }
 
@@ -1275,6 +1341,7 @@ static grbk_status setup_launch_shape(grbk_ctx* c)
     if (want < G) G = (int)want;
     if (c->opts.grid_ctas > 0) G = min(c->opts.grid_ctas, prop.multiProcessorCount * per_sm);
     if (G > c->m) G = (int)std::max<int64_t>(1, c->m);
+    G = min(G, kMaxGrid);  // the pick holds up to 32 kPartRegs CTA partials in registers
     c->G = G;
     return GRBK_OK;
 }
@@ -1833,8 +1900,10 @@ extern "C" grbk_status grbk_get_rownorms(grbk_ctx* c, double* s_out, int32_t on_
 __global__ void barrier_selftest_kernel(GridBarrier* bar, DevState* st, int absent, long long budget)
 {
     __shared__ int s_ok;
+    __shared__ unsigned int s_gen;
     if ((int)blockIdx.x == absent) return;
-    grid_sync(bar, st, 9, s_ok, budget);
+    grid_gen_init(bar, s_gen);
+    grid_sync(bar, st, 9, s_ok, s_gen, budget);
 }
 
 extern "C" grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream)
