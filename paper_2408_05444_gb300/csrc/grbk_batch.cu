@@ -615,23 +615,27 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                     if (ok > key || (ok == key && oa < arg)) { key = ok; arg = oa; }
                 }
                 if (lane == 0) {
+                    // S >= 0 (or NaN), stop_S >= 0 or -1: the tests compare bit patterns, off the
+                    // FP64 pipe (a NaN S has a pattern above +inf's and is caught by !(S > 0))
                     const double rmax = __longlong_as_double(key);
+                    const long long Sk = __double_as_longlong(S);
                     s_S = S;
                     s_imax = arg;
                     int stop = 0;
-                    if (!(S > 0.0)) stop = 2;
-                    else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
+                    if (!(Sk > 0 && Sk < 0x7ff0000000000001LL)) stop = 2;
+                    else if (__double_as_longlong(d.stop_S) >= 0 && Sk <= __double_as_longlong(d.stop_S)) stop = 1;
                     else if (k >= P.maxit) stop = 4;
                     s_stop = stop;
                     if (!stop && (var == GRBK_GRBK || var == GRBK_RGRBK)) {
                         const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
                         double t = __dadd_rn(__dmul_rn(theta, rmax), __dmul_rn(1.0 - theta, __ddiv_rn(S, d.F)));
-                        if (t > rmax) t = rmax;
+                        if (__double_as_longlong(t) > key) t = rmax;
                         s_t = t;
                     }
-                    if (!stop && var != GRBK_MWRBK && var != GRBK_BK)
-                        s_uk = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
                 }
+            } else if (warp == 1 && lane == 0 && var != GRBK_MWRBK && var != GRBK_BK) {
+                // the draw of this iteration, beside the totals
+                s_uk = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
             }
             __syncthreads();
             if (s_stop) {
@@ -661,14 +665,16 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                     const double inc = warp_inclusive_scan(bv);
                     const double SJ = __shfl_sync(0xffffffffu, inc, 31);
                     const double target = __dmul_rn(s_uk, SJ);
-                    const unsigned hit = __ballot_sync(0xffffffffu, bv > 0.0 && inc > target);
+                    const long long gk = __double_as_longlong(target);
+                    const unsigned hit =
+                        __ballot_sync(0xffffffffu, __double_as_longlong(bv) > 0 && __double_as_longlong(inc) > gk);
                     int cb;
                     double base;
                     if (hit) {
                         cb = __ffs(hit) - 1;
                         base = __shfl_sync(0xffffffffu, inc - bv, cb);
                     } else {  // rounding left u S_J uncovered: the last admitted row
-                        const unsigned nz = __ballot_sync(0xffffffffu, bv > 0.0);
+                        const unsigned nz = __ballot_sync(0xffffffffu, __double_as_longlong(bv) > 0);
                         cb = nz ? 31 - __clz(nz) : -1;
                         base = -INFINITY;
                     }
@@ -677,7 +683,7 @@ __global__ void __launch_bounds__(NT, 1) batch_kernel_t(BatchParams P)
                         const int i = (cb << 5) + lane;
                         const bool adm = i < d.m && __double_as_longlong(s_r[i]) >= tkey;
                         const double inc2 = base + warp_inclusive_scan(adm ? s_s[i] : 0.0);
-                        const unsigned h2 = __ballot_sync(0xffffffffu, adm && inc2 > target);
+                        const unsigned h2 = __ballot_sync(0xffffffffu, adm && __double_as_longlong(inc2) > gk);
                         const unsigned am = __ballot_sync(0xffffffffu, adm);
                         if (h2) pick = (cb << 5) + __ffs(h2) - 1;
                         else if (am) pick = (cb << 5) + 31 - __clz(am);

@@ -432,11 +432,9 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
     __shared__ double s_anz_v[kSpMaxRowNnz];
     __shared__ unsigned s_dirty[kSpMaxBlocks / 32];
     __shared__ double red[kSpW + 1];
-    __shared__ long long redk[kSpW];
-    __shared__ int reda[kSpW];
     __shared__ double s_wbase[kSpW];          // exclusive bases of the warps' admitted sums
     __shared__ int s_sys, s_stop, s_pick, s_last_adm, s_col;
-    __shared__ double s_S, s_rmax, s_target;
+    __shared__ double s_S, s_t, s_u, s_target, s_ck;
     __shared__ int s_imax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -540,12 +538,14 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 __syncthreads();
                 for (int b = threadIdx.x; b < (d.nb + 31) / 32; b += kSpT) s_dirty[b] = 0u;
             }
-            // ---- totals from the block summaries (fixed order) and the stop test
-            {
+            // ---- totals from the block summaries (one warp, fixed order), threshold and stop test;
+            // the draw on a second warp beside it
+            const int var = P.variant;
+            if (warp == 0) {
                 double Sv = 0.0;
                 long long key = LLONG_MIN;
                 int arg = INT_MAX;
-                for (int b = threadIdx.x; b < d.nb; b += kSpT) {
+                for (int b = lane; b < d.nb; b += 32) {
                     Sv += s_bsum[b];
                     const long long kk = s_bkey[b];
                     const int aa = s_barg[b];
@@ -558,19 +558,11 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
                     if (ok > key || (ok == key && oa < arg)) { key = ok; arg = oa; }
                 }
-                if (lane == 0) { red[warp] = Sv; redk[warp] = key; reda[warp] = arg; }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double S = 0.0;
-                    long long bk = LLONG_MIN;
-                    int ba = INT_MAX;
-                    for (int w = 0; w < kSpW; ++w) {
-                        S += red[w];
-                        if (redk[w] > bk || (redk[w] == bk && reda[w] < ba)) { bk = redk[w]; ba = reda[w]; }
-                    }
+                if (lane == 0) {
+                    const double S = Sv;
+                    const double rmax = __longlong_as_double(key);
                     s_S = S;
-                    s_rmax = __longlong_as_double(bk);
-                    s_imax = ba;
+                    s_imax = arg;
                     int stop = 0;
                     if (!(S > 0.0) && !P.extended) stop = 2;   // the extension's R^0 = 0 while Y moves
                     else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
@@ -579,9 +571,17 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     if (!stop && k < P.trace_len) {
                         if (P.trace_S) P.trace_S[(long long)sid * P.trace_len + k] = S;
                     }
+                    if (!stop && (var == GRBK_GRBK || var == GRBK_RGRBK)) {
+                        const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
+                        double t = __dadd_rn(__dmul_rn(theta, rmax), __dmul_rn(1.0 - theta, __ddiv_rn(S, d.F)));
+                        if (t > rmax) t = rmax;
+                        s_t = t;
+                    }
                 }
-                __syncthreads();
+            } else if (warp == 1 && lane == 0 && (var == GRBK_GRBK || var == GRBK_RGRBK || var == GRBK_RBK)) {
+                s_u = philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid);
             }
+            __syncthreads();
             if (s_stop) {
                 if (s_stop == 1) flag = FLAG_TOL_MET;
                 if (s_stop == 2) flag = FLAG_EXACT;
@@ -589,12 +589,9 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             }
 
             // ---- select i_k
-            const int var = P.variant;
             if (var == GRBK_GRBK || var == GRBK_RGRBK) {
-                const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
-                double t = __dadd_rn(__dmul_rn(theta, s_rmax), __dmul_rn(1.0 - theta, __ddiv_rn(s_S, d.F)));
-                if (t > s_rmax) t = s_rmax;
-                const long long tkey = __double_as_longlong(t);
+                // admission and the prefix tests compare bit patterns (all values >= 0 or -inf)
+                const long long tkey = __double_as_longlong(s_t);
                 // thread T owns the contiguous rows [T K, T K + K); 8-row groups inside blocks whose
                 // largest r is below t are skipped, the others load their r and s at once
                 const int K = (d.m + kSpT - 1) / kSpT;
@@ -614,8 +611,10 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     for (int q2 = 0; q2 < 8; ++q2)
                         if (__double_as_longlong(rv[q2]) >= tkey) { loc += sv[q2]; lastadm = i0 + q2; }
                 }
-                // block-wide inclusive scan of the threads' admitted sums (fixed order)
-                const double incw = warp_inclusive_scan(loc);
+                // block-wide inclusive scan of the threads' admitted sums (fixed order); warps
+                // without an admitted row skip the FP64 scan
+                const bool wany = __any_sync(0xffffffffu, lastadm >= 0);
+                const double incw = wany ? warp_inclusive_scan(loc) : 0.0;
                 if (lane == 31) red[warp] = incw;
                 if (threadIdx.x == 0) { s_pick = INT_MAX; s_last_adm = -1; }
                 __syncthreads();
@@ -623,25 +622,31 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     const double wt = lane < kSpW ? red[lane] : 0.0;
                     const double inc = warp_inclusive_scan(wt);
                     if (lane < kSpW) s_wbase[lane] = inc - wt;
-                    if (lane == kSpW - 1) s_target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), inc);
+                    if (lane == kSpW - 1) s_target = __dmul_rn(s_u, inc);
                 }
                 if (lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // the last admitted row overall
                 __syncthreads();
-                const double target = s_target;
-                const double base = s_wbase[warp];
-                const double incl = base + incw;
-                double excl = __shfl_up_sync(0xffffffffu, incw, 1);
-                excl = base + (lane == 0 ? 0.0 : excl);
-                if (lastadm >= 0 && excl <= target && incl > target) {
-                    // the running sum crosses u S_J inside this thread's rows
-                    double run = excl;
-                    int pick = lastadm;
-                    for (int i = q0; i < q1; ++i)
-                        if (__double_as_longlong(r[i]) >= tkey) {
-                            if (run + s[i] > target) { pick = i; break; }
-                            run += s[i];
+                if (wany) {
+                    const double target = s_target;
+                    const long long gk = __double_as_longlong(target);
+                    const double base = s_wbase[warp];
+                    const double excl0 = __shfl_up_sync(0xffffffffu, incw, 1);
+                    if (lastadm >= 0) {
+                        const double incl = base + incw;
+                        const double excl = base + (lane == 0 ? 0.0 : excl0);
+                        if (__double_as_longlong(excl) <= gk && __double_as_longlong(incl) > gk) {
+                            // the running sum crosses u S_J inside this thread's rows
+                            double run = excl;
+                            int pick = lastadm;
+                            for (int i = q0; i < q1; ++i)
+                                if (__double_as_longlong(r[i]) >= tkey) {
+                                    const double nx = run + s[i];
+                                    if (__double_as_longlong(nx) > gk) { pick = i; break; }
+                                    run = nx;
+                                }
+                            atomicMin(&s_pick, pick);
                         }
-                    atomicMin(&s_pick, pick);
+                    }
                 }
                 __syncthreads();
                 if (threadIdx.x == 0 && s_pick == INT_MAX)   // rounding left u S_J uncovered
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             } else if (var == GRBK_RBK) {
                 if (threadIdx.x == 0) {
                     const double* pref = P.pref + d.offRow;
-                    const double target = __dmul_rn(philox_uniform(P.seed, (uint64_t)k, (uint64_t)sid), d.F);
+                    const double target = __dmul_rn(s_u, d.F);
                     int lo = 0, hi = d.m;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
@@ -670,17 +675,23 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             const int ik = s_pick;
             if (threadIdx.x == 0 && k < P.trace_len && P.trace_rows) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
             const double aik = a[ik];
-            if (!(aik > 0.0)) {   // zero row of A (ME-BK only): the step changes nothing
+            if (!(__double_as_longlong(aik) > 0)) {   // zero row of A (ME-BK only): the step changes nothing
                 ++k;
                 continue;
             }
-            const double ck = __ddiv_rn(d.alpha, aik);
 
             // ---- R_{i_k} and A_{i_k} to shared memory
             const long long ab = arp[ik], ae = arp[ik + 1];
             const int anz = (int)min(ae - ab, (long long)kSpMaxRowNnz);
             for (int l = threadIdx.x; l < d.n; l += kSpT) s_row[l] = R[(long long)ik * d.n + l];
-            for (int e = threadIdx.x; e < anz; e += kSpT) { s_anz_c[e] = acol[ab + e]; s_anz_v[e] = aval[ab + e]; }
+            if (threadIdx.x == 0) s_ck = __ddiv_rn(d.alpha, aik);   // c_k, once
+            __syncthreads();
+            const double ck = s_ck;
+            // A_{i_k}'s nonzeros, scaled by c_k once (c_k a_c: the X update's coefficients)
+            for (int e = threadIdx.x; e < anz; e += kSpT) {
+                s_anz_c[e] = acol[ab + e];
+                s_anz_v[e] = __dmul_rn(ck, aval[ab + e]);
+            }
             __syncthreads();
             // ---- w = R_{i_k} B^T over the rows of B, in ascending column order
             for (int j = threadIdx.x; j < d.q; j += kSpT) {
@@ -696,9 +707,9 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 for (long long t2 = threadIdx.x; t2 < nx; t2 += kSpT) {
                     const int e = (int)(t2 / d.q), j = (int)(t2 % d.q);
                     const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
-                    const double av = e < kSpMaxRowNnz ? s_anz_v[e] : aval[ab + e];
+                    const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
                     double* xp = X + (long long)c * d.q + j;
-                    *xp = __dadd_rn(*xp, __dmul_rn(__dmul_rn(ck, av), s_w[j]));
+                    *xp = __fma_rn(cav, s_w[j], *xp);
                 }
             }
             for (int l = threadIdx.x; l < d.n; l += kSpT) {
@@ -707,7 +718,11 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 s_row[l] = acc;   // v_l (R_{i_k} is no longer needed)
             }
             __syncthreads();
-            // ---- R_k -= (c g_k) v for the rows k sharing a column with A_{i_k}; new s_k, r_k
+            // ---- R_k -= (c g_k) v for the rows k sharing a column with A_{i_k}; new s_k, r_k.
+            // w, v, R and the row norms are formed with the oracle's rounded operations in its
+            // order (one thread per row, ascending columns): rows whose r are equal in exact
+            // arithmetic (a row of A with one nonzero makes several) then tie exactly as in the
+            // oracle, which keeps ME-MWRBK's argmax and the threshold tests identical.
             {
                 const long long gb = grp[ik], ge = grp[ik + 1];
                 for (long long e = gb + threadIdx.x; e < ge; e += kSpT) {

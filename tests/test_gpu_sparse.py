@@ -4,9 +4,9 @@
   variant for 1000 iterations; the selected rows identical to the oracle's
   (FACTORED mode: the rank-1 update with A A_{i_k}^T and (R_{i_k} B^T) B), the
   traced ||R^k||_F^2 within 1e-12, and X, the kept R and its row norms within
-  1e-12 relative.  The library forms every product of the update in the
-  oracle's order with rounded operations, so these agree to the last bits
-  (only S and S_J are summed in another order).
+  1e-12 relative.  The library forms w, v, R and the row norms with the
+  oracle's rounded operations in its order, so these agree to the last bits
+  (S and S_J are summed in another order; X's update uses an FMA).
 * Section 6's colour model on a small synthetic image (24 x 20 pixels: A is the
   480 x 480 blur of the 5 x 5 Gaussian with sigma 6 under zero boundary
   conditions, B = A_c^T): the same parity for ME-RGRBK with theta = 0.8, the
