@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target legs of the default run")
     ap.add_argument("--cpu-iters", type=int, default=20,
                     help="oracle iterations of the full system timed for cpu_baseline")
-    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet", "sparse", "colour"],
+    ap.add_argument("--mode", default="rate", choices=["rate", "ttt", "warmstart", "batch", "unet", "sparse", "colour", "fp64pipe"],
                     help="rate: iterations per second (the bench line); ttt: time to a solution error target")
     ap.add_argument("--split-terms", type=int, default=2)
     ap.add_argument("--train-images", type=int, default=20000)
@@ -788,8 +788,23 @@ def unet_bench(args):
     print(json.dumps(out), flush=True)
 
 
+def fp64pipe_bench(args):
+    """FP64 issue costs on one SM (grbk_fp64_issue_probe): SM cycles per operation
+    per warp for dependent chains, 1 / 4 / 16 warps, 32 or 1 active lanes."""
+    import paper_2408_05444_gb300 as g
+    table = {}
+    for op in ("add", "fma", "mul", "div", "cvt"):
+        for warps in (1, 4, 16):
+            for act in (32, 1):
+                table[f"{op} warps={warps} lanes={act}"] = round(g.grbk_fp64_issue_probe(op, warps, act, 2048), 1)
+    print(json.dumps({"mode": "fp64pipe", "unit": "SM cycles per operation per warp", "table": table}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "fp64pipe":
+        fp64pipe_bench(args)
+        return
     if args.mode == "unet":
         unet_bench(args)
         return

@@ -450,6 +450,23 @@ grbk_status grbk_barrier_selftest(int32_t absent_cta, void* stream);
  */
 grbk_status grbk_fp64_probe(int64_t iters, int32_t blocks_per_sm, double* dfma_per_s, double* ms, void* stream);
 
+/*
+ * grbk_fp64_issue_probe -- no counterpart in the paper: the SM clock cycles one
+ * warp spends per FP64 operation when `warps` warps of one CTA run dependent
+ * chains of `iters` operations on their first `active_lanes` lanes (op: 0 add,
+ * 1 fused multiply-add, 2 multiply, 3 division, 4 double -> float -> double
+ * round trip plus an add).  On one SM, cycles per operation with one warp give
+ * the issue interval, with many warps the share of the SM's FP64 unit; equal
+ * figures for 1 and 32 active lanes mean a warp instruction costs the same
+ * whatever its active lanes.  This is why the kernels keep FP64 arithmetic on
+ * one lane or on full warps of rows and compare non-negative FP64 values on
+ * their bit patterns.  Output: *cycles_per_op (host pointer; the largest of the
+ * warps' spans / iters).  Errors: EINVAL (op outside [0, 4], warps outside
+ * [1, 32], active_lanes outside [1, 32], iters <= 0, null output), ENOMEM, ECUDA.
+ */
+grbk_status grbk_fp64_issue_probe(int32_t op, int32_t warps, int32_t active_lanes, int64_t iters,
+                                  double* cycles_per_op, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* grbk_strerror(int32_t status);
 

@@ -70,7 +70,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_sparse_create",
+           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_fp64_issue_probe", "grbk_sparse_create",
            "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy",
            "grbk_tune_num_variants", "grbk_tune_variant_info", "grbk_tune_choose", "grbk_tune_lookup",
            "grbk_tune_store", "grbk_tune_clear", "grbk_batch_variant", "grbk_unet_use_tensor_cores"]
@@ -166,6 +166,8 @@ def lib():
         L.grbk_batch_variant.restype = i32
         L.grbk_fp64_probe.argtypes = [i64, i32, P(dbl), P(dbl), vp]
         L.grbk_fp64_probe.restype = i32
+        L.grbk_fp64_issue_probe.argtypes = [i32, i32, i32, i64, P(dbl), vp]
+        L.grbk_fp64_issue_probe.restype = i32
         L.grbk_strerror.argtypes = [i32]
         L.grbk_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -634,6 +636,19 @@ def grbk_fp64_probe(iters=1 << 16, blocks_per_sm=8, stream=None):
     if st != GRBK_OK:
         raise GrbkError(st, "grbk_fp64_probe")
     return r.value, ms.value
+
+
+FP64_OPS = {"add": 0, "fma": 1, "mul": 2, "div": 3, "cvt": 4}
+
+
+def grbk_fp64_issue_probe(op="add", warps=1, active_lanes=32, iters=2048, stream=None) -> float:
+    """grbk_fp64_issue_probe -> SM clock cycles per FP64 operation per warp."""
+    c = ctypes.c_double(0.0)
+    st = lib().grbk_fp64_issue_probe(int(FP64_OPS[op]), int(warps), int(active_lanes), int(iters), ctypes.byref(c),
+                                     _stream_ptr(stream))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_fp64_issue_probe")
+    return c.value
 
 
 # ---------------------------------------------------------------------------

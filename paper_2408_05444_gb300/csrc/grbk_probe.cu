@@ -1,4 +1,4 @@
-// grbk_probe.cu -- throughput probe of the FP64 pipe.
+// grbk_probe.cu -- throughput and issue-cost probes of the FP64 pipe.
 //
 // The FP64 form of the residual pass does two fused multiply-adds per element
 // of R (the rank-1 update and the square of the new value).  Whether it is
@@ -33,9 +33,65 @@ __global__ void __launch_bounds__(kProbeThreads) dfma_probe_kernel(long long ite
     out[(long long)blockIdx.x * kProbeThreads + threadIdx.x] = s;
 }
 
+// Issue cost of one FP64 operation on one SM: one CTA of `warps` warps; in each
+// warp the first `active` lanes run a dependent chain of `iters` operations
+// (op 0 add, 1 fused multiply-add, 2 multiply, 3 division, 4 a double -> float
+// -> double round trip plus an add); the others wait at the end.  Each warp
+// records its clock64 span; the chains keep their values finite.
+__global__ void fp64_issue_kernel(int op, int active, long long iters, double* out, long long* cyc)
+{
+    const int lane = threadIdx.x & 31;
+    double x = 1.0 + 1e-3 * threadIdx.x;
+    const double y = 1e-300 * (threadIdx.x + 1);
+    float f = 1.0f;
+    __syncthreads();
+    const long long t0 = clock64();
+    if (lane < active) {
+        for (long long i = 0; i < iters; ++i) {
+            if (op == 0) x = __dadd_rn(x, y);
+            else if (op == 1) x = __fma_rn(x, 0.5, y);
+            else if (op == 2) x = __dmul_rn(x, 1.0000001);
+            else if (op == 3) x = __ddiv_rn(1.0, x);
+            else { f = (float)x; x = (double)f + y; }
+        }
+    }
+    const long long t1 = clock64();
+    out[threadIdx.x] = x + (double)f;
+    if (lane == 0) cyc[threadIdx.x >> 5] = t1 - t0;
+}
+
 }  // namespace grbk
 
 using namespace grbk;
+
+extern "C" grbk_status grbk_fp64_issue_probe(int32_t op, int32_t warps, int32_t active_lanes, int64_t iters,
+                                             double* cycles_per_op, void* stream)
+{
+    if (op < 0 || op > 4 || warps < 1 || warps > 32 || active_lanes < 1 || active_lanes > 32 || iters <= 0 ||
+        !cycles_per_op)
+        return GRBK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* out = nullptr;
+    long long* cyc = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * 32 * (size_t)warps) != cudaSuccess) return GRBK_ENOMEM;
+    if (cudaMalloc(&cyc, sizeof(long long) * (size_t)warps) != cudaSuccess) { cudaFree(out); return GRBK_ENOMEM; }
+    grbk_status r = GRBK_OK;
+    long long h[32] = {0};
+    // one untimed launch, then the measured one
+    fp64_issue_kernel<<<1, 32 * warps, 0, st>>>(op, active_lanes, iters, out, cyc);
+    fp64_issue_kernel<<<1, 32 * warps, 0, st>>>(op, active_lanes, iters, out, cyc);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h, cyc, sizeof(long long) * (size_t)warps, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        r = GRBK_ECUDA;
+    cudaFree(out);
+    cudaFree(cyc);
+    if (r != GRBK_OK) return r;
+    long long mx = 0;
+    for (int w = 0; w < warps; ++w) mx = h[w] > mx ? h[w] : mx;
+    *cycles_per_op = (double)mx / (double)iters;
+    return GRBK_OK;
+}
 
 extern "C" grbk_status grbk_fp64_probe(int64_t iters, int32_t blocks_per_sm, double* dfma_per_s, double* ms_out,
                                        void* stream)
