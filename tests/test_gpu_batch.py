@@ -198,3 +198,48 @@ def test_autotuned_batch_matches_oracle(band_limit):
     b2 = g.grbk_batch_create(As, Bs, Cs, band_limit=band_limit, tune=True)
     assert [g.grbk_batch_variant(b2, sid)[0] for sid in range(len(sy))] == chosen
     g.grbk_tune_clear()
+
+
+def _banded(n, b, rng, diag=2.0):
+    """n x n with half-bandwidth b: a symmetric Toeplitz Gaussian band plus a
+    small random banded perturbation, diagonally weighted (well conditioned)."""
+    i, j = np.indices((n, n))
+    d = np.abs(i - j)
+    M = np.where(d <= b, np.exp(-(d / (0.5 * b + 1.0)) ** 2), 0.0)
+    M += np.where(d <= b, 0.05 * rng.standard_normal((n, n)), 0.0)
+    M[d == 0] += diag
+    return M
+
+
+@pytest.mark.parametrize("variant", ["grbk", "mwrbk"])
+def test_wide_band_reads_bands_from_global_memory(variant):
+    """Two banded systems in one launch: half-bandwidths 40 at side 600, whose
+    band copies ((2 * 40 + 1) * 600 * 2 floats = 389 KB) exceed the 150 KB the
+    kernel keeps in shared memory, so its w, u, v and X update read the bands
+    from global memory; and half-bandwidth 5 at side 200, read from shared
+    memory.  Both against the FP64 oracle as in the per-system test."""
+    rng = np.random.default_rng(31)
+    sy = []
+    for n, bw in ((600, 40), (200, 5)):
+        A = _banded(n, bw, rng)
+        B = _banded(n, bw, rng)
+        Xs = rng.standard_normal((n, n))
+        sy.append(dict(A=A, B=B, C=A @ Xs @ B, X=Xs, bw=bw))
+    As, Bs, Cs = [s["A"] for s in sy], [s["B"] for s in sy], [s["C"] for s in sy]
+    alphas = _alphas(Bs)
+    K = 120
+    b = g.grbk_batch_create(As, Bs, Cs, trace_len=K, alphas=alphas)
+    for sid, s in enumerate(sy):
+        assert g.grbk_batch_info(b, sid) == (_band(s["A"]), _band(s["B"])) == (s["bw"], s["bw"])
+    Xo = [np.zeros_like(s["X"]) for s in sy]
+    st, res = g.grbk_batch_solve(b, variant, maxit=K, seed=5, X_outs=Xo)
+    assert st == g.GRBK_OK
+    for sid, (s, X, r) in enumerate(zip(sy, Xo, res)):
+        assert r["iters"] == K
+        orc = oracle.solve(s["A"], s["B"], s["C"], variant, alpha=alphas[sid], seed=5, sys=sid, maxit=K,
+                           mode=oracle.MODE_FACTORED)
+        kk = compare_rows(b.row_trace[sid], orc, K)
+        assert kk >= 0.9 * K, (sid, kk)
+        if kk == K:
+            assert _rel(X, orc["X"]) < 1e-4
+    g.grbk_batch_destroy(b)
