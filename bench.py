@@ -785,6 +785,20 @@ def unet_bench(args):
     ev1.record()
     torch.cuda.synchronize()
     out["forward_ms_192_channels_tensor_cores"] = ev0.elapsed_time(ev1)
+    # one training step (forward, loss, backward, Adam) on a batch of 64 channels of 128^2,
+    # the warm start's training shape: input gradients on the tensor cores vs all SIMT
+    Ct = torch.rand(64, 128, 128, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    Tt = torch.rand_like(Ct)
+    for mode, name in ((1, "train_step_ms_tensor_cores"), (0, "train_step_ms_simt")):
+        g.grbk_unet_use_tensor_cores(net, mode)
+        for _ in range(3):
+            g.grbk_unet_train_step(net, Ct, Tt, 1e-6)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            g.grbk_unet_train_step(net, Ct, Tt, 1e-6)
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t0) * 100.0
     print(json.dumps(out), flush=True)
 
 

@@ -318,7 +318,9 @@ __global__ void to_bf16_kernel(const float* w, __nv_bfloat16* wb, int64_t len)
 // reads of a channel run along the pixels, writes of a pixel run along its
 // channels, both coalesced.
 constexpr int PACK_PIX = 64;
-__global__ void __launch_bounds__(256) pack_nhwc3_kernel(View in, int Cin, int N, int H, int W, int Cp,
+// mask (optional): the input is multiplied by (mask > 0) (the ReLU derivative, for the
+// gradient with respect to a layer's input).
+__global__ void __launch_bounds__(256) pack_nhwc3_kernel(View in, int Cin, View mask, int N, int H, int W, int Cp,
                                                          __nv_bfloat16* dst)
 {
     __shared__ float tile[128][PACK_PIX + 1];          // Cp <= 128
@@ -331,7 +333,12 @@ __global__ void __launch_bounds__(256) pack_nhwc3_kernel(View in, int Cin, int N
         __syncthreads();
         for (int e = threadIdx.x; e < Cp * PACK_PIX; e += blockDim.x) {
             const int c = e / PACK_PIX, j = e % PACK_PIX;
-            tile[c][j] = (c < Cin && p0 + j < hw) ? at(in, n, c, H, W)[p0 + j] : 0.f;
+            float x = 0.f;
+            if (c < Cin && p0 + j < hw) {
+                x = at(in, n, c, H, W)[p0 + j];
+                if (mask.p && !(at(mask, n, c, H, W)[p0 + j] > 0.f)) x = 0.f;
+            }
+            tile[c][j] = x;
         }
         __syncthreads();
         const int groups = Cp / 8;
@@ -357,14 +364,21 @@ __global__ void __launch_bounds__(256) pack_nhwc3_kernel(View in, int Cin, int N
     }
 }
 
-// Weights of a tensor-core convolution: wt[o][tap][c] = W[o][c][tap] (BF16 copy),
-// zero for o >= Cout or c >= Cin
-__global__ void pack_wtc_kernel(const __nv_bfloat16* wb, int Cin, int Cout, int Cp, int Npad, __nv_bfloat16* wt)
+// Weights of a tensor-core convolution with Cin input and Cout output channels:
+// wt[o][tap][c] = W[o][c][tap] (BF16 copy; flip = 0), or, for the gradient with
+// respect to the input of a layer whose weights are W[c][o][tap] (Cout of this
+// convolution = the layer's inputs), wt[o][tap][c] = W[c][o][8 - tap] (flip = 1).
+// Zero for o >= Cout or c >= Cin.
+__global__ void pack_wtc_kernel(const __nv_bfloat16* wb, int Cin, int Cout, int Cp, int Npad, int flip,
+                                __nv_bfloat16* wt)
 {
     const int64_t total = (int64_t)Npad * 9 * Cp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(e % Cp), tap = (int)((e / Cp) % 9), o = (int)(e / (9 * (int64_t)Cp));
-        wt[e] = (o < Cout && c < Cin) ? wb[((int64_t)o * Cin + c) * 9 + tap] : __float2bfloat16_rn(0.f);
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (o < Cout && c < Cin)
+            v = flip ? wb[((int64_t)c * Cout + o) * 9 + (8 - tap)] : wb[((int64_t)o * Cin + c) * 9 + tap];
+        wt[e] = v;
     }
 }
 
@@ -413,8 +427,9 @@ struct grbk_unet {
     int use_tc;               // tensor-core convolutions where the layer allows (default on)
     __nv_bfloat16* xs;        // tensor-core input planes (largest layer)
     size_t xs_elems;
-    __nv_bfloat16* wtc;       // tensor-core weight layouts, per layer at wtc_off
-    int64_t wtc_off[16];
+    __nv_bfloat16* wtc;       // tensor-core weight layouts, per layer at wtc_off (forward) and
+    int64_t wtc_off[16];      // wtcb_off (gradient with respect to the layer's input)
+    int64_t wtcb_off[16];
     int* tc_err;              // device flag: a bounded wait of the tensor-core kernel expired
 };
 
@@ -481,6 +496,9 @@ static bool tc_layer(const grbk_unet* u, int l)
 {
     return u->use_tc && u->L[l].cin >= 16 && u->L[l].cin <= 128 && u->L[l].cout >= 16 && u->L[l].cout <= 128;
 }
+// the gradient with respect to a layer's input is a 3x3 convolution of the output
+// gradient (cout channels in, cin out), so the same channel limits apply
+static bool tc_bwd_layer(const grbk_unet* u, int l) { return l != ENC1A && tc_layer(u, l); }
 static int tc_cp(int cin) { return (cin + 63) / 64 * 64; }
 static int tc_npad(int cout) { return (cout + 15) / 16 * 16; }
 
@@ -501,6 +519,7 @@ static grbk_status tc_prepare(grbk_unet* u, int N, int H, int W)
         if (!tc_layer(u, l)) continue;
         const int sh = layer_level(l) - 1;
         need = std::max(need, (size_t)3 * N * (H >> sh) * (W >> sh) * tc_cp(u->L[l].cin));
+        if (tc_bwd_layer(u, l)) need = std::max(need, (size_t)3 * N * (H >> sh) * (W >> sh) * tc_cp(u->L[l].cout));
     }
     if (need > u->xs_elems) {
         if (u->xs) cudaFree(u->xs);
@@ -514,6 +533,8 @@ static grbk_status tc_prepare(grbk_unet* u, int N, int H, int W)
         for (int l = 0; l < NLAYERS; ++l) {
             u->wtc_off[l] = off;
             if (tc_layer(u, l)) off += (int64_t)tc_npad(u->L[l].cout) * 9 * tc_cp(u->L[l].cin);
+            u->wtcb_off[l] = off;
+            if (tc_bwd_layer(u, l)) off += (int64_t)tc_npad(u->L[l].cin) * 9 * tc_cp(u->L[l].cout);
         }
         if (cudaMalloc(&u->wtc, std::max<int64_t>(off, 1) * 2) != cudaSuccess) return GRBK_ENOMEM;
         if (cudaMalloc(&u->tc_err, sizeof(int)) != cudaSuccess) return GRBK_ENOMEM;
@@ -529,9 +550,9 @@ static cudaError_t conv(grbk_unet* u, int l, View in, View out, int N, int H, in
         const int Cp = tc_cp(d.cin), Np = tc_npad(d.cout);
         const int64_t npix = (int64_t)N * H * W;
         const int64_t pblocks = (int64_t)N * (((int64_t)H * W + PACK_PIX - 1) / PACK_PIX);
-        pack_nhwc3_kernel<<<(unsigned)std::min<int64_t>(pblocks, 65535), 256, 0, u->stream>>>(in, d.cin, N, H, W, Cp,
-                                                                                              u->xs);
-        pack_wtc_kernel<<<blocks_for((int64_t)Np * 9 * Cp), 256, 0, u->stream>>>(u->wb + d.woff, d.cin, d.cout, Cp, Np,
+        pack_nhwc3_kernel<<<(unsigned)std::min<int64_t>(pblocks, 65535), 256, 0, u->stream>>>(in, d.cin, kNone, N, H, W,
+                                                                                              Cp, u->xs);
+        pack_wtc_kernel<<<blocks_for((int64_t)Np * 9 * Cp), 256, 0, u->stream>>>(u->wb + d.woff, d.cin, d.cout, Cp, Np, 0,
                                                                                 u->wtc + u->wtc_off[l]);
         const grbk_status s = tc_conv3x3(u->xs, N, H, W, Cp, u->wtc + u->wtc_off[l], Np, d.cout, u->params + d.boff,
                                          d.relu, out.p, out.ctot, out.c0, u->tc_err, u->stream, u->use_tc == 1);
@@ -566,7 +587,19 @@ static cudaError_t conv_bwd(grbk_unet* u, int l, View in, View outv, View gout, 
     const int64_t wl = (int64_t)d.cout * d.cin * 9;
     reduce_slices_kernel<<<blocks_for(wl), 256, 0, u->stream>>>(u->wpart, S, wl, u->grad + d.woff);
     reduce_slices_kernel<<<blocks_for(d.cout), 256, 0, u->stream>>>(bpart, S, d.cout, u->grad + d.boff);
-    if (gin.p) {
+    if (gin.p && !accumulate && tc_bwd_layer(u, l) && tc_conv_fits(H, W) && u->xs) {
+        // dL/d(input) on the tensor cores: the output gradient (masked by the ReLU
+        // derivative) convolved with the flipped, channel-transposed weights
+        const int Cp = tc_cp(d.cout), Np = tc_npad(d.cin);
+        const int64_t pblocks = (int64_t)N * (((int64_t)H * W + PACK_PIX - 1) / PACK_PIX);
+        pack_nhwc3_kernel<<<(unsigned)std::min<int64_t>(pblocks, 65535), 256, 0, u->stream>>>(gout, d.cout, mask, N, H, W,
+                                                                                              Cp, u->xs);
+        pack_wtc_kernel<<<blocks_for((int64_t)Np * 9 * Cp), 256, 0, u->stream>>>(u->wb + d.woff, d.cout, d.cin, Cp, Np, 1,
+                                                                                u->wtc + u->wtcb_off[l]);
+        const grbk_status s = tc_conv3x3(u->xs, N, H, W, Cp, u->wtc + u->wtcb_off[l], Np, d.cin, nullptr, 0, gin.p,
+                                         gin.ctot, gin.c0, u->tc_err, u->stream, u->use_tc == 1);
+        if (s != GRBK_OK) return cudaErrorUnknown;
+    } else if (gin.p) {
         const int ctiles = ((W + TILE - 1) / TILE) * ((H + TILE_H - 1) / TILE_H);
         dim3 grid((unsigned)ctiles, (unsigned)((d.cin + CO_T - 1) / CO_T), (unsigned)N);
         conv3x3_kernel<true, CO_T><<<grid, 256, 0, u->stream>>>(gout, d.cout, mask, gin, d.cin, u->wb + d.woff, nullptr, H, W,
@@ -770,7 +803,7 @@ static grbk_status loss_and_grad(grbk_unet* u, const float* C, const float* T, i
     double t = 0.0;
     for (unsigned i = 0; i < nbk; ++i) t += u->lpart_host[i];
     *loss = t / (double)tot;
-    return GRBK_OK;
+    return tc_check(u);
 }
 
 extern "C" grbk_status grbk_unet_loss_grad(grbk_unet* u, const float* C, const float* T, int32_t n, int32_t h, int32_t w,

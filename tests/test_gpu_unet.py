@@ -152,3 +152,28 @@ def test_tensor_core_forward_matches_simt_and_oracle(n, h, w):
     assert np.max(np.abs(out[1] - out[2])) <= 1e-5 * scale
     ref = U.forward(params, width, C.astype(np.float64))
     assert np.max(np.abs(out[1] - ref)) / np.max(np.abs(ref)) < 3e-5
+
+
+@pytest.mark.parametrize("n,h,w", [(2, 64, 96), (1, 144, 256)])
+def test_tensor_core_input_gradients_match_simt(n, h, w):
+    """The gradient with respect to each layer's input runs on the tensor cores
+    (the output gradient, masked by the ReLU derivative, convolved with the
+    flipped, channel-transposed weights): the parameter gradients of a whole
+    backward pass agree with the all-SIMT pass per layer to 2e-4 of the layer's
+    largest entry, and the losses (from the two forward passes, which agree to
+    3e-5 of the output's scale) to 1e-4; 144 x 256 takes the row-halo variant
+    on its two upper levels."""
+    width = 20
+    net, params, C, T, Ct, Tt = _setup(width, n, h, w, seed=90 + h)
+    res = {}
+    for mode in (1, 0):
+        g.grbk_unet_use_tensor_cores(net, mode)
+        res[mode] = g.grbk_unet_loss_grad(net, Ct, Tt)
+    (l1, g1), (l0, g0) = res[1], res[0]
+    assert abs(l1 - l0) <= 1e-4 * l0
+    off = 0
+    for ci, co in U.layer_io(width):
+        for size in (ci * co * 9, co):
+            a, b = g1[off:off + size], g0[off:off + size]
+            assert np.max(np.abs(a - b)) <= 2e-4 * max(np.max(np.abs(b)), 1e-12), (off, size)
+            off += size
