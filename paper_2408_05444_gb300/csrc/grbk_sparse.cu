@@ -44,6 +44,7 @@ constexpr int kSpRowsPerLane = kSpBlk / 32;
 constexpr int kSpMaxBlocks = 1024;        // m <= 262144
 constexpr int kSpMaxSide = 1024;          // q, n <= 1024 (R_{i_k}, w, v in shared memory)
 constexpr int kSpMaxRowNnz = 256;         // nonzeros of one row of A staged in shared memory (more: read from L2)
+constexpr long long kSpSqCap = 23552;     // doubles of dynamic shared memory for the row update's squares (184 KB)
 
 struct SpDesc {
     int m, p, q, n;
@@ -90,6 +91,7 @@ struct SpParams {
     double theta;
     uint64_t seed;
     long long maxit;
+    long long sq_cap;          // doubles of dynamic shared memory for the row update's squares
 };
 
 // ---------------------------------------------------------------------------
@@ -131,6 +133,17 @@ __global__ void __launch_bounds__(kSpT) sp_scan_kernel(const long long* cnt, lon
 }
 
 // per-column entry counts of a CSR matrix (rows x cols)
+// largest entry of cnt[0..len) into *out (atomic maximum; *out zeroed before)
+__global__ void sp_rowmax_kernel(const long long* cnt, long long len, unsigned long long* out)
+{
+    unsigned long long mx = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (long long)gridDim.x * blockDim.x)
+        mx = max(mx, (unsigned long long)cnt[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
 __global__ void sp_colcount_kernel(const int* col, long long nnz, long long* cnt)
 {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x)
@@ -423,6 +436,7 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
 
 __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 {
+    extern __shared__ double sp_sq[];        // P.sq_cap: squares of the updated rows (row update, phase 1)
     __shared__ double s_row[kSpMaxSide];      // R_{i_k}, then v
     __shared__ double s_w[kSpMaxSide];        // w; the extended method's z / ||A_{:,j}||^2
     __shared__ double s_bsum[kSpMaxBlocks];   // per block of 256 rows: sum of s,
@@ -703,13 +717,41 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             __syncthreads();
             // ---- X += (c A_{i_k}^T) w over the nonzeros of A_{i_k}; v = w B over the columns of B
             {
-                const long long nx = (ae - ab) * (long long)d.q;
-                for (long long t2 = threadIdx.x; t2 < nx; t2 += kSpT) {
-                    const int e = (int)(t2 / d.q), j = (int)(t2 % d.q);
-                    const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
-                    const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
-                    double* xp = X + (long long)c * d.q + j;
-                    *xp = __fma_rn(cav, s_w[j], *xp);
+                const int anz_all = (int)(ae - ab);
+                if (d.q >= 32) {
+                    // tasks (group of 8 of A_{i_k}'s nonzeros, column j of X): a task's 8 loads
+                    // are issued before its first update
+                    const long long ntask = (long long)((anz_all + 7) / 8) * d.q;
+                    for (long long t2 = threadIdx.x; t2 < ntask; t2 += kSpT) {
+                        const int j = (int)(t2 % d.q), e0 = (int)(t2 / d.q) * 8;
+                        const double wj = s_w[j];
+                        double xv[8];
+                        int cc[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int e = e0 + u;
+                            cc[u] = (e < anz_all) ? (e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e]) : 0;
+                            if (e < anz_all) xv[u] = X[(long long)cc[u] * d.q + j];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int e = e0 + u;
+                            if (e < anz_all) {
+                                const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
+                                X[(long long)cc[u] * d.q + j] = __fma_rn(cav, wj, xv[u]);
+                            }
+                        }
+                    }
+                } else {
+                    // few columns (the colour model's q = 3): one thread per element
+                    const long long nx = (long long)anz_all * d.q;
+                    for (long long t2 = threadIdx.x; t2 < nx; t2 += kSpT) {
+                        const int e = (int)(t2 / d.q), j = (int)(t2 % d.q);
+                        const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
+                        const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
+                        double* xp = X + (long long)c * d.q + j;
+                        *xp = __fma_rn(cav, s_w[j], *xp);
+                    }
                 }
             }
             for (int l = threadIdx.x; l < d.n; l += kSpT) {
@@ -723,8 +765,36 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             // order (one thread per row, ascending columns): rows whose r are equal in exact
             // arithmetic (a row of A with one nonzero makes several) then tie exactly as in the
             // oracle, which keeps ME-MWRBK's argmax and the threshold tests identical.
-            {
-                const long long gb = grp[ik], ge = grp[ik + 1];
+            const long long gb = grp[ik], ge = grp[ik + 1];
+            const int nrow = (int)(ge - gb);
+            if (d.n >= 8 && (long long)nrow * d.n <= P.sq_cap) {
+                // the same operations in two phases: (1) every element, one warp per row and
+                // lanes over columns: v = R - (c g) v_l and its square, rounded as above; (2) one
+                // thread per row adds its squares in ascending column order.  Phase 1 keeps the
+                // FP64 unit busy with full warps; phase 2 is the oracle's chain of additions.
+                for (int t = warp; t < nrow; t += kSpW) {
+                    const int kr = gcol[gb + t];
+                    const double cg = __dmul_rn(ck, gval[gb + t]);
+                    double* Rk = R + (long long)kr * d.n;
+                    double* q = sp_sq + (long long)t * d.n;
+                    for (int l = lane; l < d.n; l += 32) {
+                        const double v = __dsub_rn(Rk[l], __dmul_rn(cg, s_row[l]));
+                        Rk[l] = v;
+                        q[l] = __dmul_rn(v, v);
+                    }
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < nrow; t += kSpT) {
+                    const int kr = gcol[gb + t];
+                    const double* q = sp_sq + (long long)t * d.n;
+                    double acc = 0.0;
+                    for (int l = 0; l < d.n; ++l) acc = __dadd_rn(acc, q[l]);
+                    s[kr] = acc;
+                    r[kr] = a[kr] > 0.0 ? __ddiv_rn(acc, a[kr]) : -INFINITY;
+                    const int b = kr / kSpBlk;
+                    atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
+                }
+            } else {
                 for (long long e = gb + threadIdx.x; e < ge; e += kSpT) {
                     const int kr = gcol[e];
                     const double cg = __dmul_rn(ck, gval[e]);
@@ -782,6 +852,7 @@ struct grbk_sparse {
     std::vector<SpDesc> hsys;
     std::vector<int> order;
     std::vector<long long> gnnz;
+    std::vector<long long> growmax;    // largest row of A A^T per system
     SpDesc* dsys = nullptr;
     int* dorder = nullptr;
     int* dqueue = nullptr;
@@ -928,6 +999,7 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
     if (err != GRBK_OK) return fail(err);
     // CSC of B (for v = w B) and of A (for the Gram matrix), then A A^T: count, scan, fill
     b->gnnz.assign(nsys, 0);
+    b->growmax.assign(nsys, 0);
     for (int s = 0; s < nsys; ++s) {
         const SpDesc& d = b->hsys[s];
         const int grid = 64;
@@ -955,12 +1027,18 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
         sp_gram_kernel<<<gb, kSpT, 0, st>>>(b->a_rowptr + d.aRow, b->a_col + d.aNz, b->a_val + d.aNz, d.m,
                                             a_colptr, a_crow, cnt, nullptr, nullptr, nullptr, 0);
         sp_scan_kernel<<<1, kSpT, 0, st>>>(cnt, d.m, b->g_rowptr + d.gRow);
+        // the largest row, in the scan's last slot's neighbour (fill is free until the next system)
+        unsigned long long* dmax = reinterpret_cast<unsigned long long*>(fill);
+        cudaMemsetAsync(dmax, 0, 8, st);
+        sp_rowmax_kernel<<<std::max(1, std::min(256, (d.m + 255) / 256)), 256, 0, st>>>(cnt, d.m, dmax);
         if (cudaGetLastError() != cudaSuccess) return fail(GRBK_ECUDA);
         long long gn = 0;
+        unsigned long long gmax = 0;
         if (cudaMemcpyAsync(&gn, b->g_rowptr + d.gRow + d.m, 8, cudaMemcpyDeviceToHost, st) ||
-            cudaStreamSynchronize(st))
+            cudaMemcpyAsync(&gmax, dmax, 8, cudaMemcpyDeviceToHost, st) || cudaStreamSynchronize(st))
             return fail(GRBK_ECUDA);
         b->gnnz[s] = gn;
+        b->growmax[s] = (long long)gmax;
     }
     long long oGN = 0;
     for (int s = 0; s < nsys; ++s) { b->hsys[s].gNz = oGN; oGN += b->gnnz[s]; }
@@ -1095,7 +1173,14 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
     GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     int grid = std::min(b->nsys, nsm * 4);
     if (b->opts.grid_ctas > 0) grid = std::min(grid, (int)b->opts.grid_ctas);
-    sp_solve_kernel<<<grid, kSpT, 0, st>>>(P);
+    // shared memory for the row update's squares: the largest (row of A A^T) x n, at most
+    // kSpSqCap; an iteration whose row does not fit takes the one-thread-per-row update
+    long long sq = 0;
+    for (int s = 0; s < b->nsys; ++s)
+        if (b->hsys[s].n >= 8) sq = std::max(sq, std::min(kSpSqCap, b->growmax[s] * b->hsys[s].n));
+    P.sq_cap = sq;
+    GRBK_CK(cudaFuncSetAttribute(sp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sq * 8)));
+    sp_solve_kernel<<<grid, kSpT, (size_t)sq * 8, st>>>(P);
     GRBK_CK(cudaGetLastError());
     std::vector<long long> it(b->nsys);
     std::vector<double> S(b->nsys);
