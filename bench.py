@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--batch-images", type=int, default=64)
     ap.add_argument("--unet-channels", type=int, default=16, help="--mode unet: channels of 512^2 per forward")
     ap.add_argument("--colour-iters", type=int, default=150_000, help="--mode colour: iterations per variant")
+    ap.add_argument("--sparse-iters", type=int, default=100_000, help="--mode sparse: iterations per system and variant")
     return ap.parse_args()
 
 
@@ -672,15 +673,15 @@ def batch_bench(args):
 
 def sparse_bench(args):
     """Sparse A and B (CSR, FP64): the paper's four sprandn-shaped sets (Tables 3
-    and 5, sets 3 and 6) in one launch, every variant for a fixed 1e5 iterations
-    per system, timed with CUDA events; the FP64 oracle's single-thread rate on
-    the same dense systems for comparison."""
+    and 5, sets 3 and 6) in one launch, every variant for a fixed number of
+    iterations per system (--sparse-iters, default 1e5), timed with CUDA events;
+    the FP64 oracle's single-thread rate on the same dense systems for comparison."""
     import torch
     import oracle
     import paper_2408_05444_gb300 as g
     names = sorted(workloads.SPARSE_SETS)
     sets = [workloads.sparse_set(nm) for nm in names]
-    K = 100_000
+    K = args.sparse_iters
     out = {"mode": "sparse", "systems": names, "iters_per_system": K, "dtype": "f64", "variants": {}}
     sp = g.grbk_sparse_create([s_[0] for s_ in sets], [s_[1] for s_ in sets], [s_[2] for s_ in sets])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -368,6 +368,20 @@ __global__ void __launch_bounds__(kSpT) sp_setup_kernel(SpParams P, double* a_ou
 // the iteration
 // ---------------------------------------------------------------------------
 
+// floor(s 2^(62 - E)) for 0 <= s <= S < 2^E, where ebS is S's biased exponent
+// (E = ebS - 1022): s = mant 2^(e - 1075) scaled by 2^(1084 - ebS), a shift of
+// e - ebS + 9 <= 9 places, so the result and any sum of results stay below 2^62.
+__device__ __forceinline__ unsigned long long sp_fix(double s, int ebS)
+{
+    const long long b = __double_as_longlong(s);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0ull;   // zero (a subnormal is below every admitted row's share)
+    const unsigned long long mant = (unsigned long long)(b & 0xfffffffffffffLL) | (1ull << 52);
+    const int sh = e - ebS + 9;
+    if (sh >= 0) return mant << sh;
+    return sh > -64 ? (mant >> (-sh)) : 0ull;
+}
+
 // summary of block b: sum of s over its rows (lane partials in row order, then
 // a fixed tree), largest r key and the smallest row attaining it; one warp.
 // The summaries live in the shared memory of the CTA that runs the system.
@@ -436,7 +450,7 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
 
 __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 {
-    extern __shared__ double sp_sq[];        // P.sq_cap: squares of the updated rows (row update, phase 1)
+    extern __shared__ double sp_sq[];        // squares of the updated rows (row update) / the select's block sums
     __shared__ double s_row[kSpMaxSide];      // R_{i_k}, then v
     __shared__ double s_w[kSpMaxSide];        // w; the extended method's z / ||A_{:,j}||^2
     __shared__ double s_bsum[kSpMaxBlocks];   // per block of 256 rows: sum of s,
@@ -448,7 +462,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
     __shared__ double red[kSpW + 1];
     __shared__ double s_wbase[kSpW];          // exclusive bases of the warps' admitted sums
     __shared__ int s_sys, s_stop, s_pick, s_last_adm, s_col;
-    __shared__ double s_S, s_t, s_u, s_target, s_ck;
+    __shared__ double s_S, s_t, s_u, s_ck;
     __shared__ int s_imax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -604,66 +618,105 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 
             // ---- select i_k
             if (var == GRBK_GRBK || var == GRBK_RGRBK) {
-                // admission and the prefix tests compare bit patterns (all values >= 0 or -inf)
+                // Admission compares bit patterns (r_i and t are >= 0 or -inf).  The admitted sums
+                // are exact 64-bit fixed-point sums on the integer pipe (sp_fix: s_i truncated to
+                // a multiple of 2^(E-62), S < 2^E), so their order does not matter; they differ
+                // from the oracle's sequential FP64 sums only by that sum's own rounding.
                 const long long tkey = __double_as_longlong(s_t);
-                // thread T owns the contiguous rows [T K, T K + K); 8-row groups inside blocks whose
-                // largest r is below t are skipped, the others load their r and s at once
-                const int K = (d.m + kSpT - 1) / kSpT;
-                const int q0 = threadIdx.x * K, q1 = min(d.m, q0 + K);
-                double loc = 0.0;
+                const int ebS = (int)((__double_as_longlong(s_S) >> 52) & 0x7ff);
+                // Warps take the 256-row summary blocks round robin; a block whose largest r is
+                // below t counts 0 without loads, the others are read in 8 chunks of 32 rows (lane =
+                // row: coalesced loads, all 16 in flight), each lane adds its rows' fixed-point
+                // shares and one warp reduction gives the block's admitted sum (bs[b], shared
+                // memory).  Warp 0 then scans the block sums for the block where the prefix first
+                // exceeds floor(u S_J) and scans that block's rows for the row.
+                unsigned long long* bs = reinterpret_cast<unsigned long long*>(sp_sq);
                 int lastadm = -1;
-                for (int i0 = q0; i0 < q1; i0 += 8) {
-                    const int ie = min(q1, i0 + 8);
-                    if (s_bkey[i0 / kSpBlk] < tkey && s_bkey[(ie - 1) / kSpBlk] < tkey) continue;
-                    double rv[8], sv[8];
+                for (int bb = warp; bb < d.nb; bb += kSpW) {
+                    unsigned long long f = 0;
+                    if (s_bkey[bb] >= tkey) {
+                        double rv[8], sv[8];
 #pragma unroll
-                    for (int q2 = 0; q2 < 8; ++q2) {
-                        rv[q2] = (i0 + q2 < ie) ? r[i0 + q2] : -INFINITY;
-                        sv[q2] = (i0 + q2 < ie) ? s[i0 + q2] : 0.0;
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = bb * kSpBlk + 32 * u + lane;
+                            rv[u] = (i < d.m) ? r[i] : -INFINITY;
+                            sv[u] = (i < d.m) ? s[i] : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (__double_as_longlong(rv[u]) >= tkey) {
+                                f += sp_fix(sv[u], ebS);
+                                lastadm = max(lastadm, bb * kSpBlk + 32 * u + lane);
+                            }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
                     }
-#pragma unroll
-                    for (int q2 = 0; q2 < 8; ++q2)
-                        if (__double_as_longlong(rv[q2]) >= tkey) { loc += sv[q2]; lastadm = i0 + q2; }
+                    if (lane == 0) bs[bb] = f;
                 }
-                // block-wide inclusive scan of the threads' admitted sums (fixed order); warps
-                // without an admitted row skip the FP64 scan
-                const bool wany = __any_sync(0xffffffffu, lastadm >= 0);
-                const double incw = wany ? warp_inclusive_scan(loc) : 0.0;
-                if (lane == 31) red[warp] = incw;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lastadm = max(lastadm, __shfl_xor_sync(0xffffffffu, lastadm, o));
                 if (threadIdx.x == 0) { s_pick = INT_MAX; s_last_adm = -1; }
                 __syncthreads();
+                if (lane == 0 && lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // the last admitted row overall
                 if (warp == 0) {
-                    const double wt = lane < kSpW ? red[lane] : 0.0;
-                    const double inc = warp_inclusive_scan(wt);
-                    if (lane < kSpW) s_wbase[lane] = inc - wt;
-                    if (lane == kSpW - 1) s_target = __dmul_rn(s_u, inc);
-                }
-                if (lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // the last admitted row overall
-                __syncthreads();
-                if (wany) {
-                    const double target = s_target;
-                    const long long gk = __double_as_longlong(target);
-                    const double base = s_wbase[warp];
-                    const double excl0 = __shfl_up_sync(0xffffffffu, incw, 1);
-                    if (lastadm >= 0) {
-                        const double incl = base + incw;
-                        const double excl = base + (lane == 0 ? 0.0 : excl0);
-                        if (__double_as_longlong(excl) <= gk && __double_as_longlong(incl) > gk) {
-                            // the running sum crosses u S_J inside this thread's rows
-                            double run = excl;
-                            int pick = lastadm;
-                            for (int i = q0; i < q1; ++i)
-                                if (__double_as_longlong(r[i]) >= tkey) {
-                                    const double nx = run + s[i];
-                                    if (__double_as_longlong(nx) > gk) { pick = i; break; }
-                                    run = nx;
+                    // lanes take runs of `per` block sums; one scan gives S_J and the crossing run
+                    const int per = (d.nb + 31) / 32;
+                    unsigned long long ls = 0;
+                    for (int j = 0; j < per; ++j) {
+                        const int bb = lane * per + j;
+                        if (bb < d.nb) ls += bs[bb];
+                    }
+                    unsigned long long inc = ls;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned long long t2 = __shfl_up_sync(0xffffffffu, inc, o);
+                        if (lane >= o) inc += t2;
+                    }
+                    const unsigned long long SJ = __shfl_sync(0xffffffffu, inc, 31);
+                    // floor(u S_J) in the same fixed point: u = U 2^-53 exactly (the draw's 53 bits)
+                    const unsigned long long U = (unsigned long long)__dmul_rn(s_u, 9007199254740992.0);
+                    const unsigned long long target = __umul64hi(U << 11, SJ);
+                    const unsigned hl = __ballot_sync(0xffffffffu, ls > 0 && inc > target);
+                    int pick = -1;
+                    if (hl) {
+                        const int L = __ffs(hl) - 1;
+                        unsigned long long run = __shfl_sync(0xffffffffu, inc - ls, L);
+                        int bstar = -1;
+                        for (int j = 0; j < per && bstar < 0; ++j) {   // lane L's blocks, every lane follows
+                            const int bb = L * per + j;
+                            if (bb >= d.nb) break;
+                            const unsigned long long v = bs[bb];
+                            if (v > 0 && run + v > target) bstar = bb;
+                            else run += v;
+                        }
+                        if (bstar >= 0) {
+                            double rv[8], sv[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const int i = bstar * kSpBlk + 32 * u + lane;
+                                rv[u] = (i < d.m) ? r[i] : -INFINITY;
+                                sv[u] = (i < d.m) ? s[i] : 0.0;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                if (pick >= 0) break;
+                                const bool adm = __double_as_longlong(rv[u]) >= tkey;
+                                unsigned long long ic = adm ? sp_fix(sv[u], ebS) : 0ull;
+#pragma unroll
+                                for (int o = 1; o < 32; o <<= 1) {
+                                    const unsigned long long t2 = __shfl_up_sync(0xffffffffu, ic, o);
+                                    if (lane >= o) ic += t2;
                                 }
-                            atomicMin(&s_pick, pick);
+                                const unsigned h2 = __ballot_sync(0xffffffffu, adm && run + ic > target);
+                                if (h2) pick = bstar * kSpBlk + 32 * u + __ffs(h2) - 1;
+                                run += __shfl_sync(0xffffffffu, ic, 31);
+                            }
                         }
                     }
+                    if (lane == 0 && pick >= 0) s_pick = pick;
                 }
                 __syncthreads();
-                if (threadIdx.x == 0 && s_pick == INT_MAX)   // rounding left u S_J uncovered
+                if (threadIdx.x == 0 && s_pick == INT_MAX)   // no admitted mass (every s_i below 2^(E-62))
                     s_pick = s_last_adm >= 0 ? s_last_adm : s_imax;
             } else if (var == GRBK_MWRBK) {
                 if (threadIdx.x == 0) s_pick = s_imax;
@@ -1176,8 +1229,11 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
     // shared memory for the row update's squares: the largest (row of A A^T) x n, at most
     // kSpSqCap; an iteration whose row does not fit takes the one-thread-per-row update
     long long sq = 0;
-    for (int s = 0; s < b->nsys; ++s)
+    for (int s = 0; s < b->nsys; ++s) {
         if (b->hsys[s].n >= 8) sq = std::max(sq, std::min(kSpSqCap, b->growmax[s] * b->hsys[s].n));
+        // the select's block sums (one 8-byte word per 256-row block) share the same memory
+        sq = std::max(sq, (long long)b->hsys[s].nb);
+    }
     P.sq_cap = sq;
     GRBK_CK(cudaFuncSetAttribute(sp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sq * 8)));
     sp_solve_kernel<<<grid, kSpT, (size_t)sq * 8, st>>>(P);
