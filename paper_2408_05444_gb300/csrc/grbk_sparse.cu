@@ -772,26 +772,21 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             {
                 const int anz_all = (int)(ae - ab);
                 if (d.q >= 32) {
-                    // tasks (group of 8 of A_{i_k}'s nonzeros, column j of X): a task's 8 loads
-                    // are issued before its first update
-                    const long long ntask = (long long)((anz_all + 7) / 8) * d.q;
-                    for (long long t2 = threadIdx.x; t2 < ntask; t2 += kSpT) {
-                        const int j = (int)(t2 % d.q), e0 = (int)(t2 / d.q) * 8;
-                        const double wj = s_w[j];
-                        double xv[8];
-                        int cc[8];
+                    // one warp per nonzero c of A_{i_k}: row c of X, lanes over its columns, 8
+                    // columns per lane loaded together before their updates
+                    for (int e = warp; e < anz_all; e += kSpW) {
+                        const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
+                        const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
+                        double* Xc = X + (long long)c * d.q;
+                        for (int j0 = lane; j0 < d.q; j0 += 256) {
+                            double xv[8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int e = e0 + u;
-                            cc[u] = (e < anz_all) ? (e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e]) : 0;
-                            if (e < anz_all) xv[u] = X[(long long)cc[u] * d.q + j];
-                        }
+                            for (int u = 0; u < 8; ++u)
+                                if (j0 + 32 * u < d.q) xv[u] = Xc[j0 + 32 * u];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int e = e0 + u;
-                            if (e < anz_all) {
-                                const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
-                                X[(long long)cc[u] * d.q + j] = __fma_rn(cav, wj, xv[u]);
+                            for (int u = 0; u < 8; ++u) {
+                                const int j = j0 + 32 * u;
+                                if (j < d.q) Xc[j] = __fma_rn(cav, s_w[j], xv[u]);
                             }
                         }
                     }
@@ -830,10 +825,21 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     const double cg = __dmul_rn(ck, gval[gb + t]);
                     double* Rk = R + (long long)kr * d.n;
                     double* q = sp_sq + (long long)t * d.n;
-                    for (int l = lane; l < d.n; l += 32) {
-                        const double v = __dsub_rn(Rk[l], __dmul_rn(cg, s_row[l]));
-                        Rk[l] = v;
-                        q[l] = __dmul_rn(v, v);
+                    // 8 columns per lane at a time: their loads are issued before the first store
+                    for (int l0 = lane; l0 < d.n; l0 += 256) {
+                        double rv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (l0 + 32 * u < d.n) rv[u] = Rk[l0 + 32 * u];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int l = l0 + 32 * u;
+                            if (l < d.n) {
+                                const double v = __dsub_rn(rv[u], __dmul_rn(cg, s_row[l]));
+                                Rk[l] = v;
+                                q[l] = __dmul_rn(v, v);
+                            }
+                        }
                     }
                 }
                 __syncthreads();
