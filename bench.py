@@ -698,6 +698,7 @@ def sparse_bench(args):
             "seconds": sec, "system_iters_per_s": len(sets) * K / sec,
             "us_per_iteration_longest": 1e6 * sec / K,
             "relres": [r["relres"] for r in res]}
+    out["ctas_per_system"] = g.grbk_sparse_cluster(sp)
     for nm, (A, B, C, Xs) in zip(names, sets):
         gn, al = g.grbk_sparse_info(sp, names.index(nm))
         out.setdefault("gram_nnz", {})[nm] = gn

@@ -329,6 +329,12 @@ grbk_status grbk_sparse_solve(grbk_sparse* sp, int32_t variant, double theta, do
 /* Entries of the sparse Gram matrix A_s A_s^T and the step of system `sys`. */
 grbk_status grbk_sparse_info(const grbk_sparse* sp, int32_t sys, int64_t* gram_nnz, double* alpha);
 
+/* CTAs per system of the last grbk_sparse_solve (1 before any solve): a thread-
+ * block cluster of up to 8 CTAs, one per SM, shares each system's row update,
+ * X update and admitted scan when the systems leave SMs idle and n >= 8
+ * (no counterpart in the paper: a layout choice).  Errors: EINVAL (null). */
+grbk_status grbk_sparse_cluster(const grbk_sparse* sp, int32_t* ctas);
+
 /* The kept residual R_s (m x n FP64, row-major) and its row norms ||R_i||^2
  * (m doubles) after a solve, into host buffers (either may be NULL). */
 grbk_status grbk_sparse_get_residual(const grbk_sparse* sp, int32_t sys, double* R_out, double* s_out);

@@ -70,7 +70,7 @@ EXPORTS = ["grbk_default_opts", "grbk_create", "grbk_solve", "grbk_residual", "g
            "grbk_batch_destroy", "grbk_strerror", "grbk_solve_small_noalloc", "grbk_unet_create",
            "grbk_unet_num_params", "grbk_unet_set_params", "grbk_unet_get_params", "grbk_unet_forward",
            "grbk_unet_loss_grad", "grbk_unet_train_step", "grbk_unet_destroy", "grbk_barrier_selftest",
-           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_fp64_issue_probe", "grbk_sparse_create",
+           "grbk_form_info", "grbk_batch_info", "grbk_trim_cache", "grbk_fp64_probe", "grbk_fp64_issue_probe", "grbk_sparse_create", "grbk_sparse_cluster",
            "grbk_sparse_solve", "grbk_sparse_info", "grbk_sparse_get_residual", "grbk_sparse_destroy",
            "grbk_tune_num_variants", "grbk_tune_variant_info", "grbk_tune_choose", "grbk_tune_lookup",
            "grbk_tune_store", "grbk_tune_clear", "grbk_batch_variant", "grbk_unet_use_tensor_cores"]
@@ -146,6 +146,8 @@ def lib():
         L.grbk_sparse_solve.restype = i32
         L.grbk_sparse_info.argtypes = [vp, i32, P(i64), P(dbl)]
         L.grbk_sparse_info.restype = i32
+        L.grbk_sparse_cluster.argtypes = [vp, P(i32)]
+        L.grbk_sparse_cluster.restype = i32
         L.grbk_sparse_get_residual.argtypes = [vp, i32, vp, vp]
         L.grbk_sparse_get_residual.restype = i32
         L.grbk_sparse_destroy.argtypes = [vp]
@@ -743,6 +745,15 @@ def grbk_sparse_solve(sp: Sparse, variant, theta=0.5, tol=0.0, targets=None, max
     if st not in (GRBK_OK, GRBK_ENOTCONV):
         raise GrbkError(st, "grbk_sparse_solve")
     return st, [r.as_dict() for r in res]
+
+
+def grbk_sparse_cluster(sp: Sparse) -> int:
+    """-> CTAs per system (thread-block cluster size) of the last solve."""
+    c = ctypes.c_int32(0)
+    st = lib().grbk_sparse_cluster(sp.handle, ctypes.byref(c))
+    if st != GRBK_OK:
+        raise GrbkError(st, "grbk_sparse_cluster")
+    return c.value
 
 
 def grbk_sparse_info(sp: Sparse, sys: int):

@@ -33,7 +33,11 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "grbk_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace grbk {
 
@@ -385,6 +389,29 @@ __device__ __forceinline__ unsigned long long sp_fix(double s, int ebS)
 // summary of block b: sum of s over its rows (lane partials in row order, then
 // a fixed tree), largest r key and the smallest row attaining it; one warp.
 // The summaries live in the shared memory of the CTA that runs the system.
+// Cluster form (CL) or one CTA per system: loads of rows other CTAs of the cluster
+// write go through L2 (ld.global.cg) and the CTA barriers are cluster barriers; the
+// one-CTA form keeps cached loads and block barriers.
+template <bool CL>
+__device__ __forceinline__ double ldx(const double* p)
+{
+    if constexpr (CL) return __ldcg(p);
+    else return *p;
+}
+template <bool CL>
+__device__ __forceinline__ void csync(cg::cluster_group& cl)
+{
+    if constexpr (CL) cl.sync();
+    else __syncthreads();
+}
+template <bool CL, class T>
+__device__ __forceinline__ T rank_read(cg::cluster_group& cl, T* p, int rank)
+{
+    if constexpr (CL) return *cl.map_shared_rank(p, rank);
+    else return *p;
+}
+
+template <bool CL>
 __device__ __forceinline__ void sp_block_summary(const SpParams& P, const SpDesc& d, int b, double* bsum,
                                                  long long* bkey, int* barg)
 {
@@ -399,8 +426,8 @@ __device__ __forceinline__ void sp_block_summary(const SpParams& P, const SpDesc
     for (int k = 0; k < kSpRowsPerLane; ++k) {
         const int i = r0 + k;
         if (i < d.m) {
-            sum += s[i];
-            const long long kk = __double_as_longlong(r[i]);
+            sum += ldx<CL>(s + i);
+            const long long kk = __double_as_longlong(ldx<CL>(r + i));
             if (kk > key) { key = kk; arg = i; }
         }
     }
@@ -448,6 +475,7 @@ __global__ void __launch_bounds__(kSpT) sp_init_kernel(SpParams P)
     }
 }
 
+template <bool CL>
 __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 {
     extern __shared__ double sp_sq[];        // squares of the updated rows (row update) / the select's block sums
@@ -466,15 +494,25 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
     __shared__ int s_imax;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // A cluster of CS CTAs (one per SM) runs one system: every CTA forms the totals, the
+    // pick, R_{i_k}, w and v itself; CTA `crank` scans the blocks b = crank mod CS, updates
+    // the X rows of A_{i_k}'s nonzeros e = crank mod CS and the rows of Gram row i_k at
+    // positions t = crank mod CS.  Rows written by one CTA and read by another go through
+    // L2 (ld.global.cg) after a cluster barrier.  CS = 1 is the plain one-CTA solver.
+    cg::cluster_group cl = cg::this_cluster();
+    const int crank = (int)cl.block_rank(), CS = (int)cl.num_blocks();
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        csync<CL>(cl);
+        if (crank == 0 && threadIdx.x == 0) {
             const int slot = atomicAdd(P.queue, 1);
             s_sys = slot < P.nsys ? P.order[slot] : -1;
         }
-        __syncthreads();
-        const int sid = s_sys;
-        if (sid < 0) return;
+        csync<CL>(cl);
+        const int sid = rank_read<CL>(cl, &s_sys, 0);
+        if (sid < 0) {
+            csync<CL>(cl);   // no CTA leaves while another may still read its shared memory
+            return;
+        }
         const SpDesc d = P.sys[sid];
         double* R = P.R + d.offR;
         double* X = P.X + d.offX;
@@ -494,7 +532,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
         const int* gcol = P.g_col + d.gNz;
         const double* gval = P.g_val + d.gNz;
         for (int b = threadIdx.x; b < kSpMaxBlocks / 32; b += kSpT) s_dirty[b] = 0u;
-        for (int b = warp; b < d.nb; b += kSpW) sp_block_summary(P, d, b, s_bsum, s_bkey, s_barg);
+        for (int b = warp; b < d.nb; b += kSpW) sp_block_summary<CL>(P, d, b, s_bsum, s_bkey, s_barg);
         __syncthreads();
 
         long long k = 0;
@@ -527,11 +565,11 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 for (int l = threadIdx.x; l < d.n; l += kSpT) {
                     double acc = 0.0;
                     for (long long e = cb; e < ce; ++e)
-                        acc = __dadd_rn(acc, __dmul_rn(cvl[e], Y[(long long)crw[e] * d.n + l]));
+                        acc = __dadd_rn(acc, __dmul_rn(cvl[e], ldx<CL>(Y + (long long)crw[e] * d.n + l)));
                     s_w[l] = __ddiv_rn(acc, cnj);
                 }
-                __syncthreads();
-                for (long long e = cb + threadIdx.x; e < ce; e += kSpT) {
+                csync<CL>(cl);   // every CTA has z before any CTA updates Y
+                for (long long e = cb + (long long)crank * kSpT + threadIdx.x; e < ce; e += (long long)CS * kSpT) {
                     const int i = crw[e];
                     const double av = cvl[e];
                     double* Yi = Y + (long long)i * d.n;
@@ -539,17 +577,19 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     double acc = 0.0;
                     for (int l = 0; l < d.n; ++l) {
                         const double gl = __dmul_rn(av, s_w[l]);
-                        Yi[l] = __dsub_rn(Yi[l], gl);
-                        const double v = __dadd_rn(Ri[l], gl);
+                        Yi[l] = __dsub_rn(ldx<CL>(Yi + l), gl);
+                        const double v = __dadd_rn(ldx<CL>(Ri + l), gl);
                         Ri[l] = v;
                         acc = __dadd_rn(acc, __dmul_rn(v, v));
                     }
                     s[i] = acc;
                     r[i] = a[i] > 0.0 ? __ddiv_rn(acc, a[i]) : -INFINITY;
-                    const int b = i / kSpBlk;
+                }
+                for (long long e = cb + threadIdx.x; e < ce; e += kSpT) {   // every CTA marks every row
+                    const int b = crw[e] / kSpBlk;
                     atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
                 }
-                __syncthreads();
+                csync<CL>(cl);
                 {
                     const int nw = (d.nb + 31) / 32;
                     for (int wi = 0; wi < nw; ++wi) {
@@ -558,7 +598,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                         while (bits) {
                             const int bit = __ffs(bits) - 1;
                             bits &= bits - 1;
-                            if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
+                            if (idx % kSpW == warp) sp_block_summary<CL>(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
                             ++idx;
                         }
                     }
@@ -596,9 +636,11 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     else if (d.stop_S >= 0.0 && S <= d.stop_S) stop = 1;
                     else if (k >= P.maxit) stop = 4;
                     s_stop = stop;
-                    if (!stop && k < P.trace_len) {
+                    if (!stop && k < P.trace_len && crank == 0) {
                         if (P.trace_S) P.trace_S[(long long)sid * P.trace_len + k] = S;
                     }
+                    s_pick = INT_MAX;
+                    s_last_adm = -1;
                     if (!stop && (var == GRBK_GRBK || var == GRBK_RGRBK)) {
                         const double theta = (var == GRBK_GRBK) ? 0.5 : P.theta;
                         double t = __dadd_rn(__dmul_rn(theta, rmax), __dmul_rn(1.0 - theta, __ddiv_rn(S, d.F)));
@@ -632,15 +674,15 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 // exceeds floor(u S_J) and scans that block's rows for the row.
                 unsigned long long* bs = reinterpret_cast<unsigned long long*>(sp_sq);
                 int lastadm = -1;
-                for (int bb = warp; bb < d.nb; bb += kSpW) {
+                for (int bb = crank + CS * warp; bb < d.nb; bb += CS * kSpW) {
                     unsigned long long f = 0;
                     if (s_bkey[bb] >= tkey) {
                         double rv[8], sv[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const int i = bb * kSpBlk + 32 * u + lane;
-                            rv[u] = (i < d.m) ? r[i] : -INFINITY;
-                            sv[u] = (i < d.m) ? s[i] : 0.0;
+                            rv[u] = (i < d.m) ? ldx<CL>(r + i) : -INFINITY;
+                            sv[u] = (i < d.m) ? ldx<CL>(s + i) : 0.0;
                         }
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
@@ -655,16 +697,15 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) lastadm = max(lastadm, __shfl_xor_sync(0xffffffffu, lastadm, o));
-                if (threadIdx.x == 0) { s_pick = INT_MAX; s_last_adm = -1; }
-                __syncthreads();
-                if (lane == 0 && lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // the last admitted row overall
+                if (lane == 0 && lastadm >= 0) atomicMax(&s_last_adm, lastadm);   // this CTA's last admitted row
+                csync<CL>(cl);   // every CTA's block sums are in its shared memory
                 if (warp == 0) {
                     // lanes take runs of `per` block sums; one scan gives S_J and the crossing run
                     const int per = (d.nb + 31) / 32;
                     unsigned long long ls = 0;
                     for (int j = 0; j < per; ++j) {
                         const int bb = lane * per + j;
-                        if (bb < d.nb) ls += bs[bb];
+                        if (bb < d.nb) ls += rank_read<CL>(cl, bs + bb, bb % CS);
                     }
                     unsigned long long inc = ls;
 #pragma unroll
@@ -685,7 +726,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                         for (int j = 0; j < per && bstar < 0; ++j) {   // lane L's blocks, every lane follows
                             const int bb = L * per + j;
                             if (bb >= d.nb) break;
-                            const unsigned long long v = bs[bb];
+                            const unsigned long long v = rank_read<CL>(cl, bs + bb, bb % CS);
                             if (v > 0 && run + v > target) bstar = bb;
                             else run += v;
                         }
@@ -694,8 +735,8 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
                                 const int i = bstar * kSpBlk + 32 * u + lane;
-                                rv[u] = (i < d.m) ? r[i] : -INFINITY;
-                                sv[u] = (i < d.m) ? s[i] : 0.0;
+                                rv[u] = (i < d.m) ? ldx<CL>(r + i) : -INFINITY;
+                                sv[u] = (i < d.m) ? ldx<CL>(s + i) : 0.0;
                             }
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
@@ -713,11 +754,15 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                             }
                         }
                     }
-                    if (lane == 0 && pick >= 0) s_pick = pick;
+                    if (pick < 0) {   // no admitted mass (every s_i below 2^(E-62)): the last admitted row
+                        int gl = lane < CS ? rank_read<CL>(cl, &s_last_adm, lane) : -1;
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) gl = max(gl, __shfl_xor_sync(0xffffffffu, gl, o));
+                        pick = gl >= 0 ? gl : s_imax;
+                    }
+                    if (lane == 0) s_pick = pick;
                 }
                 __syncthreads();
-                if (threadIdx.x == 0 && s_pick == INT_MAX)   // no admitted mass (every s_i below 2^(E-62))
-                    s_pick = s_last_adm >= 0 ? s_last_adm : s_imax;
             } else if (var == GRBK_MWRBK) {
                 if (threadIdx.x == 0) s_pick = s_imax;
             } else if (var == GRBK_RBK) {
@@ -740,7 +785,8 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             }
             __syncthreads();
             const int ik = s_pick;
-            if (threadIdx.x == 0 && k < P.trace_len && P.trace_rows) P.trace_rows[(long long)sid * P.trace_len + k] = ik;
+            if (crank == 0 && threadIdx.x == 0 && k < P.trace_len && P.trace_rows)
+                P.trace_rows[(long long)sid * P.trace_len + k] = ik;
             const double aik = a[ik];
             if (!(__double_as_longlong(aik) > 0)) {   // zero row of A (ME-BK only): the step changes nothing
                 ++k;
@@ -750,7 +796,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             // ---- R_{i_k} and A_{i_k} to shared memory
             const long long ab = arp[ik], ae = arp[ik + 1];
             const int anz = (int)min(ae - ab, (long long)kSpMaxRowNnz);
-            for (int l = threadIdx.x; l < d.n; l += kSpT) s_row[l] = R[(long long)ik * d.n + l];
+            for (int l = threadIdx.x; l < d.n; l += kSpT) s_row[l] = ldx<CL>(R + (long long)ik * d.n + l);
             if (threadIdx.x == 0) s_ck = __ddiv_rn(d.alpha, aik);   // c_k, once
             __syncthreads();
             const double ck = s_ck;
@@ -767,14 +813,14 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     acc = __dadd_rn(acc, __dmul_rn(s_row[bcol[e]], bval[e]));
                 s_w[j] = acc;
             }
-            __syncthreads();
+            csync<CL>(cl);   // every CTA has R_{i_k} (and is done with the block sums) before rows change
             // ---- X += (c A_{i_k}^T) w over the nonzeros of A_{i_k}; v = w B over the columns of B
             {
                 const int anz_all = (int)(ae - ab);
                 if (d.q >= 32) {
                     // one warp per nonzero c of A_{i_k}: row c of X, lanes over its columns, 8
                     // columns per lane loaded together before their updates
-                    for (int e = warp; e < anz_all; e += kSpW) {
+                    for (int e = crank + CS * warp; e < anz_all; e += CS * kSpW) {
                         const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
                         const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
                         double* Xc = X + (long long)c * d.q;
@@ -782,7 +828,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                             double xv[8];
 #pragma unroll
                             for (int u = 0; u < 8; ++u)
-                                if (j0 + 32 * u < d.q) xv[u] = Xc[j0 + 32 * u];
+                                if (j0 + 32 * u < d.q) xv[u] = ldx<CL>(Xc + j0 + 32 * u);
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
                                 const int j = j0 + 32 * u;
@@ -793,12 +839,12 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 } else {
                     // few columns (the colour model's q = 3): one thread per element
                     const long long nx = (long long)anz_all * d.q;
-                    for (long long t2 = threadIdx.x; t2 < nx; t2 += kSpT) {
+                    for (long long t2 = (long long)crank * kSpT + threadIdx.x; t2 < nx; t2 += (long long)CS * kSpT) {
                         const int e = (int)(t2 / d.q), j = (int)(t2 % d.q);
                         const int c = e < kSpMaxRowNnz ? s_anz_c[e] : acol[ab + e];
                         const double cav = e < kSpMaxRowNnz ? s_anz_v[e] : __dmul_rn(ck, aval[ab + e]);
                         double* xp = X + (long long)c * d.q + j;
-                        *xp = __fma_rn(cav, s_w[j], *xp);
+                        *xp = __fma_rn(cav, s_w[j], ldx<CL>(xp));
                     }
                 }
             }
@@ -820,17 +866,17 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                 // lanes over columns: v = R - (c g) v_l and its square, rounded as above; (2) one
                 // thread per row adds its squares in ascending column order.  Phase 1 keeps the
                 // FP64 unit busy with full warps; phase 2 is the oracle's chain of additions.
-                for (int t = warp; t < nrow; t += kSpW) {
+                for (int t = crank + CS * warp; t < nrow; t += CS * kSpW) {
                     const int kr = gcol[gb + t];
                     const double cg = __dmul_rn(ck, gval[gb + t]);
                     double* Rk = R + (long long)kr * d.n;
-                    double* q = sp_sq + (long long)t * d.n;
+                    double* q = sp_sq + (long long)(t / CS) * d.n;
                     // 8 columns per lane at a time: their loads are issued before the first store
                     for (int l0 = lane; l0 < d.n; l0 += 256) {
                         double rv[8];
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
-                            if (l0 + 32 * u < d.n) rv[u] = Rk[l0 + 32 * u];
+                            if (l0 + 32 * u < d.n) rv[u] = ldx<CL>(Rk + l0 + 32 * u);
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
                             const int l = l0 + 32 * u;
@@ -843,34 +889,34 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     }
                 }
                 __syncthreads();
-                for (int t = threadIdx.x; t < nrow; t += kSpT) {
+                for (int t = crank + CS * threadIdx.x; t < nrow; t += CS * kSpT) {
                     const int kr = gcol[gb + t];
-                    const double* q = sp_sq + (long long)t * d.n;
+                    const double* q = sp_sq + (long long)(t / CS) * d.n;
                     double acc = 0.0;
                     for (int l = 0; l < d.n; ++l) acc = __dadd_rn(acc, q[l]);
                     s[kr] = acc;
                     r[kr] = a[kr] > 0.0 ? __ddiv_rn(acc, a[kr]) : -INFINITY;
-                    const int b = kr / kSpBlk;
-                    atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
                 }
             } else {
-                for (long long e = gb + threadIdx.x; e < ge; e += kSpT) {
+                for (long long e = gb + crank + (long long)CS * threadIdx.x; e < ge; e += (long long)CS * kSpT) {
                     const int kr = gcol[e];
                     const double cg = __dmul_rn(ck, gval[e]);
                     double* Rk = R + (long long)kr * d.n;
                     double acc = 0.0;
                     for (int l = 0; l < d.n; ++l) {
-                        const double v = __dsub_rn(Rk[l], __dmul_rn(cg, s_row[l]));
+                        const double v = __dsub_rn(ldx<CL>(Rk + l), __dmul_rn(cg, s_row[l]));
                         Rk[l] = v;
                         acc = __dadd_rn(acc, __dmul_rn(v, v));
                     }
                     s[kr] = acc;
                     r[kr] = a[kr] > 0.0 ? __ddiv_rn(acc, a[kr]) : -INFINITY;
-                    const int b = kr / kSpBlk;
-                    atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
                 }
             }
-            __syncthreads();
+            for (long long e = gb + threadIdx.x; e < ge; e += kSpT) {   // every CTA marks every updated row
+                const int b = gcol[e] / kSpBlk;
+                atomicOr(&s_dirty[b >> 5], 1u << (b & 31));
+            }
+            csync<CL>(cl);   // every CTA's rows, s and r written before the summaries are refreshed
             // ---- refresh the summaries of the blocks that changed
             {
                 const int nw = (d.nb + 31) / 32;
@@ -880,7 +926,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
                     while (bits) {
                         const int bit = __ffs(bits) - 1;
                         bits &= bits - 1;
-                        if (idx % kSpW == warp) sp_block_summary(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
+                        if (idx % kSpW == warp) sp_block_summary<CL>(P, d, wi * 32 + bit, s_bsum, s_bkey, s_barg);
                         ++idx;
                     }
                 }
@@ -889,7 +935,7 @@ __global__ void __launch_bounds__(kSpT, 2) sp_solve_kernel(SpParams P)
             for (int b = threadIdx.x; b < (d.nb + 31) / 32; b += kSpT) s_dirty[b] = 0u;
             ++k;
         }
-        if (threadIdx.x == 0) {
+        if (crank == 0 && threadIdx.x == 0) {
             P.iters[sid] = k;
             P.S_out[sid] = s_S;
             P.flag_out[sid] = flag;
@@ -912,6 +958,7 @@ struct grbk_sparse {
     std::vector<int> order;
     std::vector<long long> gnnz;
     std::vector<long long> growmax;    // largest row of A A^T per system
+    int last_cluster = 1;               // CTAs per system of the last solve
     SpDesc* dsys = nullptr;
     int* dorder = nullptr;
     int* dqueue = nullptr;
@@ -1165,6 +1212,13 @@ extern "C" grbk_status grbk_sparse_create(grbk_sparse** out, int32_t nsys, const
     return GRBK_OK;
 }
 
+extern "C" grbk_status grbk_sparse_cluster(const grbk_sparse* b, int32_t* ctas)
+{
+    if (!b || !ctas) return GRBK_EINVAL;
+    *ctas = b->last_cluster;
+    return GRBK_OK;
+}
+
 extern "C" grbk_status grbk_sparse_info(const grbk_sparse* b, int32_t sys, int64_t* gram_nnz, double* alpha)
 {
     if (!b || sys < 0 || sys >= b->nsys) return GRBK_EINVAL;
@@ -1241,8 +1295,53 @@ extern "C" grbk_status grbk_sparse_solve(grbk_sparse* b, int32_t variant, double
         sq = std::max(sq, (long long)b->hsys[s].nb);
     }
     P.sq_cap = sq;
-    GRBK_CK(cudaFuncSetAttribute(sp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sq * 8)));
-    sp_solve_kernel<<<grid, kSpT, (size_t)sq * 8, st>>>(P);
+    // a cluster of CS CTAs per system when the systems leave SMs idle (CS * systems <= SMs) and
+    // the row update is heavy (n >= 8: its element work splits over the cluster; with few
+    // columns, as in the colour model, three cluster barriers per iteration cost more than the
+    // split saves); with clusters every CTA asks for at least 120 KB of shared memory, so that
+    // no two CTAs of a cluster share an SM (and its FP64 unit)
+    int nmax = 0;
+    for (int s = 0; s < b->nsys; ++s) nmax = std::max(nmax, b->hsys[s].n);
+    int CS = 1;
+    for (int c = 8; c >= 2; c >>= 1)
+        if ((long long)b->nsys * c <= nsm && b->opts.grid_ctas <= 0 && nmax >= 8) { CS = c; break; }
+    size_t smem = (size_t)sq * 8;
+    if (CS > 1) smem = std::max(smem, (size_t)120 * 1024);
+    GRBK_CK(cudaFuncSetAttribute(sp_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GRBK_CK(cudaFuncSetAttribute(sp_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    cfg.blockDim = dim3(kSpT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (;;) {
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(CS == 1 ? grid : std::min(b->nsys, nsm / CS) * CS));
+        int nclus = 0;
+        if (CS == 1 || (cudaOccupancyMaxActiveClusters(&nclus, (const void*)sp_solve_kernel<true>, &cfg) == cudaSuccess &&
+                        nclus >= 1)) {
+            if (CS > 1) cfg.gridDim = dim3((unsigned)(std::min(std::min(b->nsys, nsm / CS), nclus) * CS));
+            break;
+        }
+        cudaGetLastError();
+        CS >>= 1;   // that cluster size does not fit: a smaller one
+        if (CS == 1) {
+            smem = (size_t)sq * 8;
+            cfg.dynamicSmemBytes = smem;
+        }
+    }
+    b->last_cluster = CS;
+    if (CS > 1) {
+        GRBK_CK(cudaLaunchKernelEx(&cfg, sp_solve_kernel<true>, P));
+    } else {
+        sp_solve_kernel<false><<<cfg.gridDim, kSpT, cfg.dynamicSmemBytes, st>>>(P);
+    }
     GRBK_CK(cudaGetLastError());
     std::vector<long long> it(b->nsys);
     std::vector<double> S(b->nsys);

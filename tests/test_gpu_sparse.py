@@ -219,3 +219,39 @@ def test_sparse_degenerate_rows_and_columns(variant, theta):
     B1 = rng.standard_normal((3, 5))
     C1 = A1 @ rng.standard_normal((4, 3)) @ B1
     _check_parity(A1, A1, B1, B1, C1, variant, theta, K=50)
+
+
+@pytest.mark.parametrize("variant,theta", [("grbk", 0.5), ("rgrbk", 0.8), ("mwrbk", 1.0), ("bk", 0.5)])
+def test_cluster_split_matches_one_cta(variant, theta):
+    """The four sprandn sets in one launch: with a thread-block cluster of 8 CTAs per
+    system (the default here: 4 systems leave SMs idle and n >= 8) and with one CTA
+    per system (an explicit grid size turns the clusters off) the solves are the
+    same computation spread differently, so the selected rows, X, R and the row
+    norms agree bit for bit, with the extended method's column steps too."""
+    names = sorted(workloads.SPARSE_SETS)
+    sets = [workloads.sparse_set(nm) for nm in names]
+    import scipy.sparse as sps
+    As = [sps.csr_matrix(s_[0]) for s_ in sets]
+    Bs = [sps.csr_matrix(s_[1]) for s_ in sets]
+    Cs = [s_[2] for s_ in sets]
+    K = 400
+    out = {}
+    for label, kw in (("cluster", {}), ("one", {"grid_ctas": 4})):
+        for ext in (0, 1):
+            sp = g.grbk_sparse_create(As, Bs, Cs, trace_len=K, extended=ext, **kw)
+            X = [np.zeros((s_[0].shape[1], s_[1].shape[0])) for s_ in sets]
+            st, res = g.grbk_sparse_solve(sp, variant, theta=theta, maxit=K, seed=9, X_outs=X)
+            assert st in (g.GRBK_OK, g.GRBK_ENOTCONV)
+            ctas = g.grbk_sparse_cluster(sp)
+            R = [g.grbk_sparse_get_residual(sp, i, s_[0].shape[0], s_[1].shape[1]) for i, s_ in enumerate(sets)]
+            out[(label, ext)] = (ctas, sp.row_trace.copy(), X, R)
+            g.grbk_sparse_destroy(sp)
+    for ext in (0, 1):
+        c8, rows8, X8, R8 = out[("cluster", ext)]
+        c1, rows1, X1, R1 = out[("one", ext)]
+        assert (c8, c1) == (8, 1)
+        assert np.array_equal(rows8, rows1)
+        for a, b in zip(X8, X1):
+            assert np.array_equal(a, b)
+        for (ra, sa), (rb, sb) in zip(R8, R1):
+            assert np.array_equal(ra, rb) and np.array_equal(sa, sb)
