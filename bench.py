@@ -180,15 +180,20 @@ def recorded_traffic(kernel, algorithmic_bytes):
         return None
 
 
-def iter_bytes(m, p, q, n, esz, gram=False, kpath=False):
+def iter_bytes(m, p, q, n, esz, gram=False, kpath=False, deferred=False, T=64):
     """Algorithmic bytes of one iteration: R read + written, B read twice
     (w = R_i B^T and v = w B), A read once for u = A A_i^T (or one row of the
     precomputed A A^T), the vectors u, v, w and the row norms.  kpath: the
     row-space form, whose update vector is R_i K with K = Lt^T Lt (n x n, read
-    once) instead of two passes over B (then n is the kept rank)."""
+    once) instead of two passes over B (then n is the kept rank).  deferred:
+    R is read once and not written (the chunk's updates are applied by the
+    refresh or a write-back after it); an iteration also reads, on average over
+    a chunk of T, (T - 1) / 2 of the kept U' columns (m) and v rows (n)."""
     u_bytes = m * esz if gram else m * p * esz
     b_bytes = n * n * esz if kpath else 2 * q * n * esz
-    return 2 * m * n * esz + b_bytes + u_bytes + (m + n + q) * esz + 3 * m * 8
+    r_bytes = (1 if deferred else 2) * m * n * esz
+    extra = (T - 1) / 2 * (m + n) * esz if deferred else 0
+    return r_bytes + b_bytes + u_bytes + (m + n + q) * esz + 3 * m * 8 + extra
 
 
 def _alpha_estimate(B, iters=30):
@@ -320,7 +325,8 @@ def native_arm(args):
     iters = args.steps * T
     value = world * iters / (el_ms / 1e3)
     kern_ms = res["iter_kernel_ms"] / max(res["iter_kernel_launches"], 1)
-    bytes_per_launch = iter_bytes(m, p, q, n, 4, gram=bool(res["gram"])) * T
+    deferred = bool(res["deferred"])
+    bytes_per_launch = iter_bytes(m, p, q, n, 4, gram=bool(res["gram"]), deferred=deferred, T=T) * T
     hbm_peak, bf16_peak, peak_src = peaks()
     achieved = bytes_per_launch / (kern_ms / 1e3) / 1e9
 
@@ -378,7 +384,8 @@ def native_arm(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             msz = float(t.item())
         kmz = rz["iter_kernel_ms"] / max(rz["iter_kernel_launches"], 1)
-        bz = iter_bytes(m, p, q, r_cols, 4, gram=bool(rz["gram"]), kpath=True) * T
+        bz = iter_bytes(m, p, q, r_cols, 4, gram=bool(rz["gram"]), kpath=True, deferred=bool(rz["deferred"]),
+                        T=T) * T
         rowspace = {"precision": "f32", "value": world * kz * T / (msz / 1e3), "unit": UNIT,
                     "ms_per_step": msz / kz, "steps": kz, "kept_columns": r_cols, "setup_s": setup_s,
                     "kernel_ms_per_launch": kmz, "kernel_GBs": bz / (kmz / 1e3) / 1e9,
@@ -446,6 +453,8 @@ def native_arm(args):
             "config": {"workload": workload_label(wl, T),
                        "iters_per_step": T, "variant": "ME-GRBK", "parallelism": f"replicas{world}",
                        "split_terms": args.split_terms, "gram": bool(res["gram"]),
+                       "update": "deferred (R read once per iteration, applied by the refresh)" if deferred
+                                 else "in place (R read and written every iteration)",
                        "l2": "inputs larger than L2 (R is %.2f GB)" % (m * n * 4 / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,

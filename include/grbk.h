@@ -115,6 +115,16 @@ typedef struct {
     int32_t tune;         /* batched solver: 1 = choose each system's kernel variant by timing the compiled
                              variants on it (grbk_tune_*; choices kept per system shape for the process);
                              0 = the default variant (512 threads, two rows per warp) for every system */
+    int32_t deferred;     /* F32 single-system solver: -1 = off; otherwise on when a chunk (check_every)
+                             is at most 64 iterations and each CTA owns at most 512 rows.  During a chunk
+                             R stays at its value R^0 from the chunk's start and the current residual is
+                             R^0 - sum_j U'_j v_j^T (U'_j = c_j A A_{i_j}^T, v_j = w_j B of iteration j);
+                             an iteration reads R^0 once (R^0_i . v), the row norms follow by
+                             ||R_i - U'_i v||^2 = s_i - 2 U'_i (R_i . v) + U'_i^2 ||v||^2 (not a form of the
+                             paper: its iterates, with the update applied later), the selected row is
+                             assembled from R^0 and the kept terms, and after the chunk R is written back
+                             with the terms in order (the in-place update's arithmetic) unless the periodic
+                             refresh recomputes it */
 } grbk_opts;
 
 typedef struct {
@@ -129,6 +139,7 @@ typedef struct {
     int32_t gram;         /* 1 when u came from the precomputed A A^T */
     int32_t x0_rejected;  /* batched solves: 1 when the given X0 had ||C - A X0 B|| >= ||C|| and 0 was used */
     int32_t status;       /* grbk_status of the call */
+    int32_t deferred;     /* 1 when the solve used the deferred update (grbk_opts.deferred) */
 } grbk_result;
 
 typedef struct grbk_ctx grbk_ctx;

@@ -41,7 +41,7 @@ class grbk_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("grid_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("use_gram", ctypes.c_int32), ("form", ctypes.c_int32), ("rank_tol", ctypes.c_double),
                 ("band_limit", ctypes.c_int32), ("alphas", ctypes.POINTER(ctypes.c_double)),
-                ("extended", ctypes.c_int32), ("tune", ctypes.c_int32)]
+                ("extended", ctypes.c_int32), ("tune", ctypes.c_int32), ("deferred", ctypes.c_int32)]
 
 
 class grbk_csr(ctypes.Structure):
@@ -53,7 +53,8 @@ class grbk_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("relres", ctypes.c_double), ("rse", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("alpha", ctypes.c_double), ("iter_kernel_ms", ctypes.c_double),
                 ("iter_kernel_launches", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("gram", ctypes.c_int32), ("x0_rejected", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("gram", ctypes.c_int32), ("x0_rejected", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("deferred", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -256,7 +257,7 @@ class _Keep:
 
 def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None, split_terms=None,
                x_ref=None, trace_len=0, stream=None, grid_ctas=None, check_every=None, use_gram=None,
-               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None, tune=None):
+               form=None, rank_tol=None, band_limit=None, alphas=None, extended=None, tune=None, deferred=None):
     o = grbk_default_opts() if opts is None else opts
     keep = _Keep()
     if precision is not None:
@@ -285,6 +286,8 @@ def _make_opts(opts, precision=None, refresh_T=None, alpha=None, stop_kind=None,
         o.extended = int(bool(extended))
     if tune is not None:
         o.tune = int(bool(tune))
+    if deferred is not None:
+        o.deferred = {True: 1, False: -1}.get(deferred, deferred)
     if alphas is not None:
         keep.alphas = np.ascontiguousarray(alphas, dtype=np.float64)
         o.alphas = keep.alphas.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -332,7 +335,7 @@ def grbk_create(A, B, C, opts=None, **kw) -> Context:
     """grbk_create(A, B, C, opts) -- set up one system; keyword options fill
     grbk_opts (precision='f64'|'f32', refresh_T, alpha, stop_kind, split_terms,
     x_ref, trace_len, stream, grid_ctas, check_every, use_gram, form='full'|'rowspace',
-    rank_tol)."""
+    rank_tol, deferred)."""
     o, keep = _make_opts(opts, **kw)
     h = ctypes.c_void_p()
     mA, mB, mC = mat(A), mat(B), mat(C)

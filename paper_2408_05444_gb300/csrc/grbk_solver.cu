@@ -93,7 +93,19 @@ struct IterParams {
     const T* K;                 // row-space form: Lt^T Lt (n x ldk); then v = R_{i_k} K and w is formed per chunk
     int64_t ldk;
     T* hist_z;                  // with K: per chunk the selected rows R_{i_k} (ldr per iteration)
+    // deferred update (FP32): during a chunk R stays at its value R^0 from the chunk's start;
+    // the current residual is R^0 - sum_j U'_j v_j^T over the chunk's iterations j so far,
+    // with U'_j = c_j A A_{i_j}^T and v_j kept below; row norms follow by recurrence, and
+    // R is written back (or refreshed) after the chunk
+    int defer;
+    T* uh;                      // cap x m: U'_j
+    T* vh;                      // cap x ldr: v_j
+    float2* gp;                 // (cap + 1) x G: per-CTA double-float partials of v_j . v_it
+    T* rik;                     // ldr: the current row R_{i_k}, assembled across the CTAs
+    int defer_stage;            // the slab's v_j of a whole chunk fit in the dynamic shared memory
 };
+
+constexpr int kDeferCap = 64;   // longest chunk the deferred update keeps
 
 // balanced contiguous row range of CTA c among G
 __device__ __forceinline__ void cta_rows(int64_t m, int c, int G, int64_t& r0, int64_t& r1)
@@ -228,6 +240,290 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
         double2* pp = reinterpret_cast<double2*>(P.part + blockIdx.x);
         __stcg(pp, make_double2(cta_S, __longlong_as_double(cta_key)));
         __stcg(pp + 1, make_double2(__longlong_as_double(cta_bi), 0.0));
+    }
+}
+
+// (hi, lo) += (bh, bl) in FP32 arithmetic (two-sum, then renormalised)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
+{
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    const float l = __fadd_rn(__fadd_rn(err, lo), bl);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// (hi, lo) += a * (bh + bl): the product a bh exactly as p + e (one FMA), a bl rounded
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float bh, float bl)
+{
+    const float p = __fmul_rn(a, bh);
+    const float e = __fmaf_rn(a, bh, -p);
+    df_add(hi, lo, p, __fmaf_rn(a, bl, e));
+}
+
+// The vector slab [e0, e1) of CTA c: the same split as cols_gemv's.
+__device__ __forceinline__ void v_slab(int64_t nvt, int c, int G, int64_t& e0, int64_t& e1)
+{
+    const int64_t slab = (nvt + G - 1) / G;
+    e0 = (int64_t)c * slab;
+    e1 = min(nvt, e0 + slab);
+}
+
+// Deferred update: this CTA's slab of the current row R_ik = R^0_ik - sum_{j<it} U'_{ik,j} v_j
+// into P.rik, the terms in iteration order as the in-place update applies them.
+// With P.defer_stage the slab's v_j are first copied into `stage` (the dynamic shared
+// memory, idle at this point of the iteration) by all threads, one load each.
+template <typename T>
+__device__ __noinline__ void defer_row(const IterParams<T>& P, int it, long long ik, int c, int G, float* s_uik,
+                                       T* stage)
+{
+    if constexpr (sizeof(T) == 4) {
+        using V = typename VecOf<T>::V;
+        constexpr int VN = VecOf<T>::N;
+        int64_t e0, e1;
+        v_slab(P.ldr / VN, c, G, e0, e1);
+        const int64_t ns = e1 - e0;
+        const V* R0 = reinterpret_cast<const V*>(P.R + ik * P.ldr);
+        for (int j = threadIdx.x; j < it; j += kBlock) s_uik[j] = __ldcg(P.uh + (int64_t)j * P.m + ik);
+        if (P.defer_stage) {
+            V* st = reinterpret_cast<V*>(stage);
+            if (ns > 0)
+                for (int64_t t = threadIdx.x; t < (int64_t)it * ns; t += kBlock) {
+                    const int64_t j = t / ns;
+                    st[t] = ldcg_v(reinterpret_cast<const V*>(P.vh + j * P.ldr) + e0 + (t - j * ns));
+                }
+            __syncthreads();
+            for (int64_t e = threadIdx.x; e < ns; e += kBlock) {
+                V x = __ldg(R0 + e0 + e);  // R is not written during a deferred chunk
+                float* xf = reinterpret_cast<float*>(&x);
+#pragma unroll 8
+                for (int j = 0; j < it; ++j) {
+                    const float cj = s_uik[j];
+                    const V y4 = st[(int64_t)j * ns + e];
+                    const float* y = reinterpret_cast<const float*>(&y4);
+#pragma unroll
+                    for (int cc = 0; cc < VN; ++cc) xf[cc] = __fmaf_rn(-cj, y[cc], xf[cc]);
+                }
+                stcg_v(reinterpret_cast<V*>(P.rik) + e0 + e, x);
+            }
+            return;
+        }
+        __syncthreads();
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += kBlock) {
+            V x = __ldg(R0 + e);  // R is not written during a deferred chunk
+            float* xf = reinterpret_cast<float*>(&x);
+            for (int jb = 0; jb < it; jb += 8) {
+                V vv[8];
+#pragma unroll
+                for (int uu = 0; uu < 8; ++uu)
+                    if (jb + uu < it) vv[uu] = ldcg_v(reinterpret_cast<const V*>(P.vh + (int64_t)(jb + uu) * P.ldr) + e);
+#pragma unroll
+                for (int uu = 0; uu < 8; ++uu) {
+                    if (jb + uu < it) {
+                        const float cj = s_uik[jb + uu];
+                        const float* y = reinterpret_cast<const float*>(&vv[uu]);
+#pragma unroll
+                        for (int cc = 0; cc < VN; ++cc) xf[cc] = __fmaf_rn(-cj, y[cc], xf[cc]);
+                    }
+                }
+            }
+            stcg_v(reinterpret_cast<V*>(P.rik) + e, x);
+        }
+    }
+}
+
+// Deferred update: this CTA's partials of v_j . v_it, j <= it, over its slab of v (the
+// slab cols_gemv just wrote), one warp per j, exact products summed in double-float.
+template <typename T>
+__device__ __noinline__ void defer_gram_partial(const IterParams<T>& P, int it, int c, int G)
+{
+    if constexpr (sizeof(T) == 4) {
+        constexpr int VN = VecOf<T>::N;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int64_t e0, e1;
+        v_slab((P.K ? P.ldk : P.ldb) / VN, c, G, e0, e1);
+        const int64_t f0 = e0 * VN, f1 = max(f0, e1 * VN);
+        const float* vi = P.vh + (int64_t)it * P.ldr;
+        for (int j = warp; j <= it; j += kWarps) {
+            const float* vj = P.vh + (int64_t)j * P.ldr;
+            float hi = 0.f, lo = 0.f;
+            for (int64_t f = f0 + lane; f < f1; f += 32) {
+                const float a = __ldcg(vj + f), b = __ldcg(vi + f);
+                const float pr = __fmul_rn(a, b);
+                df_add(hi, lo, pr, __fmaf_rn(a, b, -pr));
+            }
+            warp_sum_df(hi, lo);
+            if (lane == 0) __stcg(P.gp + (int64_t)j * G + c, make_float2(hi, lo));
+        }
+    }
+}
+
+// Deferred update: the Gram column v_j . v_it, j <= it, from the CTA partials in one fixed
+// order (every CTA forms the same values).
+template <typename T>
+__device__ __noinline__ void defer_gram_column(const IterParams<T>& P, int it, int G, float2* s_gf)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j <= it; j += kWarps) {
+        float hi = 0.f, lo = 0.f;
+        for (int cc = lane; cc < G; cc += 32) {
+            const float2 pg = __ldcg(P.gp + (int64_t)j * G + cc);
+            df_add(hi, lo, pg.x, pg.y);
+        }
+        warp_sum_df(hi, lo);
+        if (lane == 0) s_gf[j] = make_float2(hi, lo);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Deferred form of the residual pass over rows [r0, r1) (R itself is not written):
+// d_i = R_i . v_it with R_i the current row, then
+//     ||R_i - U'_i v||^2 = s_i - 2 U'_i d_i + U'_i^2 ||v||^2,
+// with R_i . v_it = R^0_i . v_it - sum_{j<it} U'_{ij} (v_j . v_it): one read of R^0 per
+// iteration instead of a read and a write of R.  R^0_i . v_it is summed from exact FP32
+// products in double-float (hi, lo) arithmetic, the correction from the Gram column
+// s_gf (double-float) and the CTA's U' rows; s_corr holds the correction in four
+// partial sums per row (quarters of the j range), formed before the streaming starts.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ void deferred_pass(const IterParams<T>& P, int it, const T* vsrc, const T* ucur,
+                                           int64_t r0, int64_t r1, const float2* s_gf, double gkk,
+                                           float2* s_corr, double* sm_parts, double* sm_red, long long* sm_redi,
+                                           double2* sm_sr)
+{
+    if constexpr (sizeof(T) == 4) {
+        using V = typename VecOf<T>::V;
+        constexpr int VN = VecOf<T>::N;
+        constexpr int CHV = 32 * kUnroll * 2;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int64_t nvec_row = P.ldr / VN;
+        const int nch = (int)((nvec_row + CHV - 1) / CHV);
+        int64_t rows_per_batch = kPartsCap / nch;
+        if (rows_per_batch < 1) rows_per_batch = 1;
+        if (rows_per_batch > kBlock) rows_per_batch = kBlock;
+        const int nr = (int)(r1 - r0);
+
+        // the correction sum_{j<it} U'_{ij} g_j, four quarters of j per row, coalesced over rows
+        {
+            const int qlen = (it + 3) / 4;
+            for (int t = threadIdx.x; t < 4 * nr; t += kBlock) {
+                const int qq = t / nr, rl = t - qq * nr;
+                const int j0 = qq * qlen, j1 = min(it, j0 + qlen);
+                float hi = 0.f, lo = 0.f;
+                for (int jb = j0; jb < j1; jb += 8) {
+                    float uv[8];
+#pragma unroll
+                    for (int uu = 0; uu < 8; ++uu)
+                        uv[uu] = (jb + uu < j1) ? __ldcg(P.uh + (int64_t)(jb + uu) * P.m + r0 + rl) : 0.f;
+#pragma unroll
+                    for (int uu = 0; uu < 8; ++uu)
+                        if (jb + uu < j1) df_fma(hi, lo, uv[uu], s_gf[jb + uu].x, s_gf[jb + uu].y);
+                }
+                s_corr[qq * kSrCap + rl] = make_float2(hi, lo);
+            }
+        }
+
+        double cta_S = 0.0;
+        long long cta_key = __double_as_longlong(-INFINITY), cta_bi = LLONG_MAX;
+        for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
+            const int64_t b1 = min(r1, b0 + rows_per_batch);
+            const int64_t units = (b1 - b0) * nch;
+            for (int64_t unit = warp; unit < units; unit += kWarps) {
+                const int64_t row = b0 + unit / nch;
+                const int ch = (int)(unit % nch);
+                const int64_t e0 = (int64_t)ch * CHV;
+                const int64_t e1 = min(nvec_row, e0 + CHV);
+                const V* Rrow = reinterpret_cast<const V*>(P.R + row * P.ldr);
+                const V* vrow = reinterpret_cast<const V*>(vsrc);
+                // one Kahan chain per vector component: four independent dependency chains per lane
+                float acc[VN], comp[VN], err[VN];
+#pragma unroll
+                for (int cc = 0; cc < VN; ++cc) acc[cc] = comp[cc] = err[cc] = 0.f;
+                for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
+                    V rv[kUnroll];
+#pragma unroll
+                    for (int uu = 0; uu < kUnroll; ++uu) {
+                        const int64_t e = base + uu * 32 + lane;
+                        if (e < e1) rv[uu] = ldcs_v(Rrow + e);
+                    }
+#pragma unroll
+                    for (int uu = 0; uu < kUnroll; ++uu) {
+                        const int64_t e = base + uu * 32 + lane;
+                        if (e < e1) {
+                            const V vv = P.smem_v ? vrow[e] : ldcg_v(vrow + e);
+                            const float* x = reinterpret_cast<const float*>(&rv[uu]);
+                            const float* y = reinterpret_cast<const float*>(&vv);
+#pragma unroll
+                            for (int cc = 0; cc < VN; ++cc) {
+                                const float pr = __fmul_rn(x[cc], y[cc]);
+                                err[cc] = __fadd_rn(err[cc], __fmaf_rn(x[cc], y[cc], -pr));
+                                const float yk = __fsub_rn(pr, comp[cc]);
+                                const float tk = __fadd_rn(acc[cc], yk);
+                                comp[cc] = __fsub_rn(__fsub_rn(tk, acc[cc]), yk);
+                                acc[cc] = tk;
+                            }
+                        }
+                    }
+                }
+                float hi = acc[0], lo = __fsub_rn(err[0], comp[0]);
+#pragma unroll
+                for (int cc = 1; cc < VN; ++cc) df_add(hi, lo, acc[cc], __fsub_rn(err[cc], comp[cc]));
+                warp_sum_df(hi, lo);
+                if (lane == 0) sm_parts[unit] = (double)hi + (double)lo;
+            }
+            __syncthreads();
+            double my_S = 0.0;
+            long long my_key = LLONG_MIN, my_bi = LLONG_MAX;
+            for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
+                double dot = 0.0;
+                for (int c2 = 0; c2 < nch; ++c2) dot += sm_parts[rr * nch + c2];
+                const int64_t row = b0 + rr;
+                const int rl = (int)(row - r0);
+                float ch = s_corr[rl].x, cl = s_corr[rl].y;
+#pragma unroll
+                for (int qq = 1; qq < 4; ++qq) df_add(ch, cl, s_corr[qq * kSrCap + rl].x, s_corr[qq * kSrCap + rl].y);
+                const double d = dot - ((double)ch + (double)cl);
+                const double coef = (double)__ldcg(ucur + row);
+                double sv = sm_sr[rl].x + coef * (coef * gkk - 2.0 * d);
+                if (sv < 0.0) sv = 0.0;  // rounding below an exactly vanishing row
+                const double ai = __ldg(P.a + row);
+                const double ri = (ai > 0.0) ? __ddiv_rn(sv, ai) : -INFINITY;
+                __stcg(P.sr + row, make_double2(sv, ri));
+                sm_sr[rl] = make_double2(sv, ri);
+                my_S += sv;
+                const long long rk = __double_as_longlong(ri);
+                if (rk > my_key) { my_key = rk; my_bi = row; }
+            }
+            const int nact = (int)min((int64_t)kWarps, (b1 - b0 + 31) / 32);
+            if (warp < nact) {
+                my_S = warp_sum(my_S);
+                warp_argmax_key(my_key, my_bi);
+                if (lane == 0) {
+                    sm_red[warp] = my_S;
+                    sm_red[kWarps + warp] = __longlong_as_double(my_key);
+                    sm_redi[warp] = my_bi;
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double bs = lane < nact ? sm_red[lane] : 0.0;
+                long long bk = lane < nact ? __double_as_longlong(sm_red[kWarps + lane]) : LLONG_MIN;
+                long long bi = lane < nact ? sm_redi[lane] : LLONG_MAX;
+                bs = warp_sum(bs);
+                warp_argmax_key(bk, bi);
+                if (lane == 0) {
+                    cta_S += bs;
+                    if (bk > cta_key || (bk == cta_key && bi < cta_bi)) { cta_key = bk; cta_bi = bi; }
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            double2* pp = reinterpret_cast<double2*>(P.part + blockIdx.x);
+            __stcg(pp, make_double2(cta_S, __longlong_as_double(cta_key)));
+            __stcg(pp + 1, make_double2(__longlong_as_double(cta_bi), 0.0));
+        }
     }
 }
 
@@ -501,6 +797,11 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     __shared__ long long s_imax, s_ik;
     __shared__ int s_stop;
     __shared__ double2 sm_sr[kSrCap];          // this CTA's (s_i, r_i) when it owns <= kSrCap rows
+    // deferred update: U'_{i_k, j} of the chunk so far, the Gram column v_j . v_it (double-float)
+    // and the per-row corrections (four partial sums per row)
+    __shared__ float s_uik[kDeferCap];
+    __shared__ float2 s_gf[kDeferCap + 1];
+    __shared__ float2 s_corr[4 * kSrCap];
 
     T* sv = reinterpret_cast<T*>(dsm);                               // ldr: R_{i_k}, then v
     T* sa = sv + (P.smem_v ? P.ldr : 0);                              // lda: A_{i_k}
@@ -632,8 +933,25 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             ik = k % P.m;
         }
 
-        // ---------------- W/U: w = R_ik B^T, u = A A_ik^T ---------------------
+        // per-iteration slots of the deferred update's history
+        T* ucur = P.u;
+        T* vcur = P.v;
         const T* Rik = P.R + ik * P.ldr;
+        if constexpr (sizeof(T) == 4) {
+            if (P.defer) {
+                ucur = P.uh + (int64_t)it * P.m;
+                vcur = P.vh + (int64_t)it * P.ldr;
+                if (it > 0) {
+                    // the current row R_ik = R^0_ik - sum_{j<it} U'_{ik,j} v_j, each CTA its slab
+                    // of columns, the terms in iteration order as the in-place update applies them
+                    defer_row<T>(P, it, ik, c, G, s_uik, reinterpret_cast<T*>(dsm));
+                    if (!grid_sync(P.bar, P.st, 5, s_ok, s_gen)) return;
+                    Rik = P.rik;
+                }
+            }
+        }
+
+        // ---------------- W/U: w = R_ik B^T, u = A A_ik^T ---------------------
         const T* Aik = P.A + ik * P.lda;
         if (P.smem_v) {
             for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
@@ -664,10 +982,10 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         // row i_k of the precomputed A A^T when there is one
         if (P.G) {
             const T* Gi = P.G + ik * P.ldg;
-            if (ig < r1) __stcg(P.u + ig, (T)(ck * (double)g0));
-            for (int64_t i = ig + kBlock; i < r1; i += kBlock) __stcg(P.u + i, (T)(ck * (double)__ldg(Gi + i)));
+            if (ig < r1) __stcg(ucur + ig, (T)(ck * (double)g0));
+            for (int64_t i = ig + kBlock; i < r1; i += kBlock) __stcg(ucur + i, (T)(ck * (double)__ldg(Gi + i)));
         } else {
-            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, P.u, nullptr, sm_parts, ck);
+            rows_dot<T>(P.A, P.lda, r0, r1, P.smem_arow ? sa : Aik, P.smem_arow ? 0 : 2, ucur, nullptr, sm_parts, ck);
         }
         if (P.K) {
             // row-space form: the update vector is R_ik K (K = Lt^T Lt), one pass over
@@ -675,7 +993,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             if (c == 0)
                 for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
                     reinterpret_cast<V*>(P.hist_z + (int64_t)it * P.ldr)[e] = reinterpret_cast<const V*>(sv)[e];
-            cols_gemv<T>(P.K, P.ldk, P.n, sv, P.v, c, G, sm_parts);
+            cols_gemv<T>(P.K, P.ldk, P.n, sv, vcur, c, G, sm_parts);
         } else {
             // each CTA streams a contiguous block of rows of B for w; B is read last
             // here, so the part of it still in L2 serves the v = w B phase that follows
@@ -688,18 +1006,88 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             // ---------------- V: v = w B (column slab of this CTA) -----------
             for (int64_t j = threadIdx.x; j < P.q; j += kBlock) sw[j] = __ldcg(P.w + j);
             __syncthreads();
-            cols_gemv<T>(P.B, P.ldb, P.q, sw, P.v, c, G, sm_parts);
+            cols_gemv<T>(P.B, P.ldb, P.q, sw, vcur, c, G, sm_parts);
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (P.defer) {
+                defer_gram_partial<T>(P, it, c, G);
+            }
         }
         if (!grid_sync(P.bar, P.st, 3, s_ok, s_gen)) return;
 
         // ---------------- F: fused rank-1 update + row norms -----------------
         if (P.smem_v) {
             for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
-                reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(P.v) + e);
-            __syncthreads();
+                reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(vcur) + e);
         }
-        fused_pass<T, true>(P, ck, P.smem_v ? sv : P.v, r0, r1, sm_parts, sm_red, sm_redi, own_sm ? sm_sr : nullptr);
+        bool deferred = false;
+        if constexpr (sizeof(T) == 4) deferred = P.defer != 0;
+        if (deferred) {
+            defer_gram_column<T>(P, it, G, s_gf);
+            __syncthreads();
+            const double gkk = (double)s_gf[it].x + (double)s_gf[it].y;
+            deferred_pass<T>(P, it, P.smem_v ? sv : vcur, ucur, r0, r1, s_gf, gkk, s_corr, sm_parts, sm_red,
+                             sm_redi, sm_sr);
+        } else {
+            if (P.smem_v) __syncthreads();
+            fused_pass<T, true>(P, ck, P.smem_v ? sv : vcur, r0, r1, sm_parts, sm_red, sm_redi,
+                                own_sm ? sm_sr : nullptr);
+        }
         if (!grid_sync(P.bar, P.st, 4, s_ok, s_gen)) return;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Write-back of a deferred chunk: R <- R - sum_{j<nw} U'_j v_j^T with the terms in
+// iteration order, each element by one fused multiply-add per term: the in-place
+// update's order and rounding.  Tiles of kWbRows rows x kWbVec vectors of 4 columns;
+// the tile's U' and v in shared memory (nw KB); each thread keeps 16 rows of one vector.
+// ----------------------------------------------------------------------------
+constexpr int kWbRows = 128, kWbVec = 32;
+
+__global__ void __launch_bounds__(256) defer_writeback_kernel(float* R, int64_t ldr, int64_t m, const float* uh,
+                                                              const float* vh, int nw)
+{
+    extern __shared__ __align__(16) float wb_sm[];
+    float* su = wb_sm;                                                    // nw x kWbRows
+    float4* sv4 = reinterpret_cast<float4*>(wb_sm + (int64_t)nw * kWbRows);  // nw x kWbVec
+    const int64_t nvr = ldr / 4;
+    const int64_t rt = (int64_t)blockIdx.y * kWbRows, vt = (int64_t)blockIdx.x * kWbVec;
+    for (int t = threadIdx.x; t < nw * kWbRows; t += blockDim.x) {
+        const int j = t / kWbRows, rr = t - j * kWbRows;
+        su[t] = (rt + rr < m) ? __ldg(uh + (int64_t)j * m + rt + rr) : 0.f;
+    }
+    for (int t = threadIdx.x; t < nw * kWbVec; t += blockDim.x) {
+        const int j = t / kWbVec, e = t - j * kWbVec;
+        sv4[t] = (vt + e < nvr) ? __ldg(reinterpret_cast<const float4*>(vh + (int64_t)j * ldr) + vt + e)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const int cv = threadIdx.x % kWbVec, rg = threadIdx.x / kWbVec;
+    if (vt + cv >= nvr) return;
+    float4* R4 = reinterpret_cast<float4*>(R);
+    float4 x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int64_t row = rt + rg * 16 + r;
+        x[r] = (row < m) ? __ldcs(R4 + row * nvr + vt + cv) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int j = 0; j < nw; ++j) {
+        const float4 vv = sv4[j * kWbVec + cv];
+        const float* uj = su + j * kWbRows + rg * 16;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float cj = uj[r];
+            x[r].x = __fmaf_rn(-cj, vv.x, x[r].x);
+            x[r].y = __fmaf_rn(-cj, vv.y, x[r].y);
+            x[r].z = __fmaf_rn(-cj, vv.z, x[r].z);
+            x[r].w = __fmaf_rn(-cj, vv.w, x[r].w);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int64_t row = rt + rg * 16 + r;
+        if (row < m) __stcs(R4 + row * nvr + vt + cv, x[r]);
     }
 }
 
@@ -1072,6 +1460,10 @@ struct grbk_ctx {
     } lz;
     cudaEvent_t ev0, ev1;   // around each persistent-kernel launch
     long long launches;     // kernel launches issued (reset per solve)
+    int defer;              // FP32 deferred update (R read once per iteration, written back per chunk)
+    int defer_stage;        //   a chunk's v_j over one CTA's slab fit in the dynamic shared memory
+    void *uh, *vh, *rik;    //   its U' and v of the chunk, and the assembled row R_{i_k}
+    float2* gp;             //   per-CTA partials of the Gram column
 };
 
 static grbk_status ensure_tmp(grbk_ctx* c, size_t bytes)
@@ -1157,6 +1549,9 @@ static IterParams<T> make_params(grbk_ctx* c)
     P.G = (const T*)c->gram; P.ldg = c->ldg;
     P.soff = c->soff;
     P.K = (const T*)c->K; P.ldk = c->ldr; P.hist_z = (T*)c->hist_z;
+    P.defer = c->defer;
+    P.uh = (T*)c->uh; P.vh = (T*)c->vh; P.gp = c->gp; P.rik = (T*)c->rik;
+    P.defer_stage = c->defer_stage;
     P.stop_S = -1.0;
     return P;
 }
@@ -1249,7 +1644,8 @@ extern "C" void grbk_destroy(grbk_ctx* c)
     end_side(c);
     void* bufs[] = {c->A, c->B, c->C, c->R, c->u, c->v, c->w, c->a, c->rbk_prefix, c->sr, c->X,
                     c->part, c->part_SJ, c->hist_rows, c->hist_c,
-                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff, c->K, c->hist_z};
+                    c->hist_w, c->bar, c->st, c->scratch, c->tmp, c->gram, c->soff, c->K, c->hist_z,
+                    c->uh, c->vh, c->rik, c->gp};
     // the blocks go back to the cache: let queued work on the context's stream finish first
     cudaStreamSynchronize(c->stream);
     for (void* b : bufs)
@@ -1319,8 +1715,9 @@ static grbk_status setup_launch_shape(grbk_ctx* c)
     cudaDeviceProp prop;
     GRBK_CK(cudaGetDeviceProperties(&prop, dev));
     const size_t esz = sizeof(T);
-    const size_t static_est = sizeof(double) * (kPartsCap + 2 * kWarps) + 8 * kWarps + 256;
-    const size_t budget = (size_t)prop.sharedMemPerBlockOptin - static_est - 1024;
+    cudaFuncAttributes fa;
+    GRBK_CK(cudaFuncGetAttributes(&fa, iterate_kernel<T>));
+    const size_t budget = (size_t)prop.sharedMemPerBlockOptin - fa.sharedSizeBytes - 1024;
     size_t need = (size_t)c->q * esz;
     c->smem_arow = 0;
     c->smem_v = 0;
@@ -1625,6 +2022,25 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     ALLOC(c->hist_rows, (size_t)c->chunk_cap * 4);
     ALLOC(c->hist_c, (size_t)c->chunk_cap * 8);
     ALLOC(c->hist_w, (size_t)c->chunk_cap * q * 8);
+    // the deferred update: FP32, chunks of at most kDeferCap iterations, at most kSrCap rows per CTA
+    c->defer = 0;
+    c->defer_stage = 0;
+    if (c->prec == GRBK_F32 && o.deferred >= 0 && c->chunk_cap <= kDeferCap && (m + c->G - 1) / c->G <= kSrCap) {
+        ALLOC(c->uh, (size_t)c->chunk_cap * m * 4);
+        ALLOC(c->vh, (size_t)c->chunk_cap * c->ldr * 4);
+        ALLOC(c->gp, (size_t)(c->chunk_cap + 1) * c->G * sizeof(float2));
+        ALLOC(c->rik, (size_t)c->ldr * 4);
+        if (cudaMemsetAsync(c->vh, 0, (size_t)c->chunk_cap * c->ldr * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(c->rik, 0, (size_t)c->ldr * 4, st) != cudaSuccess ||
+            cudaFuncSetAttribute(defer_writeback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kDeferCap * (kWbRows + 4 * kWbVec) * 4) != cudaSuccess) {
+            grbk_destroy(c);
+            return GRBK_ECUDA;
+        }
+        c->defer = 1;
+        const int64_t nvr = c->ldr / 4, slab = (nvr + c->G - 1) / c->G;
+        c->defer_stage = (size_t)c->chunk_cap * slab * 16 <= c->dyn_smem;
+    }
     if (c->K) {
         if (c->smem_v) {
             ALLOC(c->hist_z, (size_t)c->chunk_cap * c->ldr * es);
@@ -1725,6 +2141,21 @@ static grbk_status fold_x(grbk_ctx* c, int nit)
     return GRBK_OK;
 }
 
+// R <- R - sum_j U'_j v_j^T over the nw iterations of a deferred chunk, then the row norms of
+// the written-back R (they replace the ones the chunk carried by recurrence)
+static grbk_status defer_writeback(grbk_ctx* c, int nw)
+{
+    if (nw <= 0) return GRBK_OK;
+    c->launches += 1;
+    const int64_t nvr = c->ldr / 4;
+    const dim3 grid((unsigned)((nvr + kWbVec - 1) / kWbVec), (unsigned)((c->m + kWbRows - 1) / kWbRows));
+    const size_t smem = (size_t)nw * (kWbRows + 4 * kWbVec) * 4;
+    defer_writeback_kernel<<<grid, 256, smem, c->stream>>>((float*)c->R, c->ldr, c->m, (const float*)c->uh,
+                                                           (const float*)c->vh, nw);
+    GRBK_CK(cudaGetLastError());
+    return run_rownorms(c);
+}
+
 static grbk_status compute_rse(grbk_ctx* c, const double* Xref_d, double* rse)
 {
     c->launches += 1;
@@ -1820,14 +2251,21 @@ extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, co
         k = ds.k;
         S = ds.S;
         flag = ds.flag;
-        if (flag != FLAG_RUNNING) break;
-        if (o.stop_kind == GRBK_STOP_RSE) {
+        bool stop = flag != FLAG_RUNNING;
+        if (!stop && o.stop_kind == GRBK_STOP_RSE) {
             result = compute_rse(c, Xref_d, &rse);
             if (result != GRBK_OK) break;
-            if (rse <= tol) { flag = FLAG_TOL_MET; break; }
+            if (rse <= tol) { flag = FLAG_TOL_MET; stop = true; }
         }
-        if (k >= maxit) break;
-        if (o.refresh_T > 0 && k % o.refresh_T == 0) {
+        if (!stop && k >= maxit) stop = true;
+        const bool refresh = !stop && o.refresh_T > 0 && k % o.refresh_T == 0;
+        // a deferred chunk leaves R at its start: write it back unless a refresh replaces it
+        if (c->defer && !refresh) {
+            result = defer_writeback(c, done);
+            if (result != GRBK_OK) break;
+        }
+        if (stop) break;
+        if (refresh) {
             result = compute_residual(c, c->X, c->R);
             if (result == GRBK_OK) result = run_rownorms(c);
         }
@@ -1851,6 +2289,7 @@ extern "C" grbk_status grbk_solve(grbk_ctx* c, int32_t variant, double theta, co
         res->iter_kernel_ms = iter_ms;
         res->iter_kernel_launches = iter_launches;
         res->gram = c->gram != nullptr;
+        res->deferred = c->defer;
         res->launches = c->launches;
         res->status = result;
         res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

@@ -47,10 +47,11 @@ def test_struct_layout_matches_header(tmp_path):
 #include "grbk.h"
 int main(void) {
   printf("%zu %zu %zu\\n", sizeof(grbk_mat), sizeof(grbk_opts), sizeof(grbk_result));
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(grbk_opts, alpha), offsetof(grbk_opts, x_ref),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", offsetof(grbk_opts, alpha), offsetof(grbk_opts, x_ref),
          offsetof(grbk_opts, trace_len), offsetof(grbk_opts, stream), offsetof(grbk_opts, check_every),
          offsetof(grbk_result, status), offsetof(grbk_result, x0_rejected), offsetof(grbk_opts, use_gram),
-         offsetof(grbk_opts, alphas), offsetof(grbk_opts, extended), offsetof(grbk_opts, tune));
+         offsetof(grbk_opts, alphas), offsetof(grbk_opts, extended), offsetof(grbk_opts, tune),
+         offsetof(grbk_opts, deferred), offsetof(grbk_result, deferred));
   return 0;
 }
 """)
@@ -63,7 +64,8 @@ int main(void) {
     assert offs == [g.grbk_opts.alpha.offset, g.grbk_opts.x_ref.offset, g.grbk_opts.trace_len.offset,
                     g.grbk_opts.stream.offset, g.grbk_opts.check_every.offset, g.grbk_result.status.offset,
                     g.grbk_result.x0_rejected.offset, g.grbk_opts.use_gram.offset, g.grbk_opts.alphas.offset,
-                    g.grbk_opts.extended.offset, g.grbk_opts.tune.offset]
+                    g.grbk_opts.extended.offset, g.grbk_opts.tune.offset, g.grbk_opts.deferred.offset,
+                    g.grbk_result.deferred.offset]
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
