@@ -107,6 +107,25 @@ struct IterParams {
 
 constexpr int kDeferCap = 64;   // longest chunk the deferred update keeps
 
+// (hi, lo) += (bh, bl) in FP32 arithmetic (two-sum, then renormalised)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
+{
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    const float l = __fadd_rn(__fadd_rn(err, lo), bl);
+    hi = __fadd_rn(s, l);
+    lo = __fsub_rn(l, __fsub_rn(hi, s));
+}
+
+// (hi, lo) += a * (bh + bl): the product a bh exactly as p + e (one FMA), a bl rounded
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float bh, float bl)
+{
+    const float p = __fmul_rn(a, bh);
+    const float e = __fmaf_rn(a, bh, -p);
+    df_add(hi, lo, p, __fmaf_rn(a, bl, e));
+}
+
 // balanced contiguous row range of CTA c among G
 __device__ __forceinline__ void cta_rows(int64_t m, int c, int G, int64_t& r0, int64_t& r1)
 {
@@ -139,13 +158,14 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
     double cta_S = 0.0;
     long long cta_key = __double_as_longlong(-INFINITY), cta_bi = LLONG_MAX;
 
+    float2* sm_df = reinterpret_cast<float2*>(sm_parts);   // FP32: (row, chunk) partials as double-float pairs
     for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
         const int64_t b1 = min(r1, b0 + rows_per_batch);
-        const int64_t units = (b1 - b0) * nch;
-        for (int64_t unit = warp; unit < units; unit += kWarps) {
-            const int64_t row = b0 + unit / nch;
-            const int ch = (int)(unit % nch);
-            const int64_t e0 = (int64_t)ch * CHV;
+        const int units = (int)((b1 - b0) * nch);
+        for (int unit = warp; unit < units; unit += kWarps) {
+            const int rq = unit / nch;
+            const int64_t row = b0 + rq;
+            const int64_t e0 = (int64_t)(unit - rq * nch) * CHV;
             const int64_t e1 = min(nvec_row, e0 + CHV);
             V* Rrow = reinterpret_cast<V*>(P.R + row * P.ldr);
             const V* vrow = reinterpret_cast<const V*>(vsrc);
@@ -190,7 +210,7 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
             } else {
                 float hi = acc_f, lo = -comp_f;  // Kahan state as a double-float
                 warp_sum_df(hi, lo);
-                if (lane == 0) sm_parts[unit] = (double)hi + (double)lo;
+                if (lane == 0) sm_df[unit] = make_float2(hi, lo);
             }
         }
         __syncthreads();
@@ -199,7 +219,13 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
         long long my_key = LLONG_MIN, my_bi = LLONG_MAX;
         for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
             double sv = 0.0;
-            for (int c = 0; c < nch; ++c) sv += sm_parts[rr * nch + c];
+            if constexpr (sizeof(T) == 8) {
+                for (int c = 0; c < nch; ++c) sv += sm_parts[rr * nch + c];
+            } else {
+                float sh = 0.f, sl = 0.f;
+                for (int c = 0; c < nch; ++c) df_add(sh, sl, sm_df[rr * nch + c].x, sm_df[rr * nch + c].y);
+                sv = (double)sh + (double)sl;
+            }
             const int64_t row = b0 + rr;
             if (P.soff) sv += __ldg(P.soff + row);
             const double ai = __ldg(P.a + row);
@@ -241,25 +267,6 @@ __device__ __noinline__ void fused_pass(const IterParams<T>& P, double ck, const
         __stcg(pp, make_double2(cta_S, __longlong_as_double(cta_key)));
         __stcg(pp + 1, make_double2(__longlong_as_double(cta_bi), 0.0));
     }
-}
-
-// (hi, lo) += (bh, bl) in FP32 arithmetic (two-sum, then renormalised)
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
-{
-    const float s = __fadd_rn(hi, bh);
-    const float bb = __fsub_rn(s, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-    const float l = __fadd_rn(__fadd_rn(err, lo), bl);
-    hi = __fadd_rn(s, l);
-    lo = __fsub_rn(l, __fsub_rn(hi, s));
-}
-
-// (hi, lo) += a * (bh + bl): the product a bh exactly as p + e (one FMA), a bl rounded
-__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float bh, float bl)
-{
-    const float p = __fmul_rn(a, bh);
-    const float e = __fmaf_rn(a, bh, -p);
-    df_add(hi, lo, p, __fmaf_rn(a, bl, e));
 }
 
 // The vector slab [e0, e1) of CTA c: the same split as cols_gemv's.
@@ -424,22 +431,21 @@ __device__ __noinline__ void deferred_pass(const IterParams<T>& P, int it, const
             }
         }
 
+        // (row, chunk) partials as double-float pairs: no FP64 instruction per unit
+        float2* sm_df = reinterpret_cast<float2*>(sm_parts);
         double cta_S = 0.0;
         long long cta_key = __double_as_longlong(-INFINITY), cta_bi = LLONG_MAX;
         for (int64_t b0 = r0; b0 < r1; b0 += rows_per_batch) {
             const int64_t b1 = min(r1, b0 + rows_per_batch);
-            const int64_t units = (b1 - b0) * nch;
-            for (int64_t unit = warp; unit < units; unit += kWarps) {
-                const int64_t row = b0 + unit / nch;
-                const int ch = (int)(unit % nch);
-                const int64_t e0 = (int64_t)ch * CHV;
+            const int units = (int)((b1 - b0) * nch);
+            for (int unit = warp; unit < units; unit += kWarps) {
+                const int rq = unit / nch;
+                const int64_t row = b0 + rq;
+                const int64_t e0 = (int64_t)(unit - rq * nch) * CHV;
                 const int64_t e1 = min(nvec_row, e0 + CHV);
                 const V* Rrow = reinterpret_cast<const V*>(P.R + row * P.ldr);
                 const V* vrow = reinterpret_cast<const V*>(vsrc);
-                // one Kahan chain per vector component: four independent dependency chains per lane
-                float acc[VN], comp[VN], err[VN];
-#pragma unroll
-                for (int cc = 0; cc < VN; ++cc) acc[cc] = comp[cc] = err[cc] = 0.f;
+                float acc = 0.f, comp = 0.f, err = 0.f;
                 for (int64_t base = e0; base < e1; base += 32 * kUnroll) {
                     V rv[kUnroll];
 #pragma unroll
@@ -457,27 +463,26 @@ __device__ __noinline__ void deferred_pass(const IterParams<T>& P, int it, const
 #pragma unroll
                             for (int cc = 0; cc < VN; ++cc) {
                                 const float pr = __fmul_rn(x[cc], y[cc]);
-                                err[cc] = __fadd_rn(err[cc], __fmaf_rn(x[cc], y[cc], -pr));
-                                const float yk = __fsub_rn(pr, comp[cc]);
-                                const float tk = __fadd_rn(acc[cc], yk);
-                                comp[cc] = __fsub_rn(__fsub_rn(tk, acc[cc]), yk);
-                                acc[cc] = tk;
+                                err = __fadd_rn(err, __fmaf_rn(x[cc], y[cc], -pr));
+                                const float yk = __fsub_rn(pr, comp);
+                                const float tk = __fadd_rn(acc, yk);
+                                comp = __fsub_rn(__fsub_rn(tk, acc), yk);
+                                acc = tk;
                             }
                         }
                     }
                 }
-                float hi = acc[0], lo = __fsub_rn(err[0], comp[0]);
-#pragma unroll
-                for (int cc = 1; cc < VN; ++cc) df_add(hi, lo, acc[cc], __fsub_rn(err[cc], comp[cc]));
+                float hi = acc, lo = __fsub_rn(err, comp);
                 warp_sum_df(hi, lo);
-                if (lane == 0) sm_parts[unit] = (double)hi + (double)lo;
+                if (lane == 0) sm_df[unit] = make_float2(hi, lo);
             }
             __syncthreads();
             double my_S = 0.0;
             long long my_key = LLONG_MIN, my_bi = LLONG_MAX;
             for (int64_t rr = threadIdx.x; rr < b1 - b0; rr += kBlock) {
-                double dot = 0.0;
-                for (int c2 = 0; c2 < nch; ++c2) dot += sm_parts[rr * nch + c2];
+                float dh = 0.f, dl = 0.f;
+                for (int c2 = 0; c2 < nch; ++c2) df_add(dh, dl, sm_df[rr * nch + c2].x, sm_df[rr * nch + c2].y);
+                const double dot = (double)dh + (double)dl;
                 const int64_t row = b0 + rr;
                 const int rl = (int)(row - r0);
                 float ch = s_corr[rl].x, cl = s_corr[rl].y;
