@@ -115,8 +115,9 @@ typedef struct {
     int32_t tune;         /* batched solver: 1 = choose each system's kernel variant by timing the compiled
                              variants on it (grbk_tune_*; choices kept per system shape for the process);
                              0 = the default variant (512 threads, two rows per warp) for every system */
-    int32_t deferred;     /* F32 single-system solver: -1 = off; otherwise on when a chunk (check_every)
-                             is at most 64 iterations and each CTA owns at most 512 rows.  During a chunk
+    int32_t deferred;     /* F32 single-system solver: -1 = off, 1 = on, 0 = on in the FULL form only; on
+                             only when a chunk (check_every) is at most 64 iterations and each CTA owns at
+                             most 512 rows.  During a chunk
                              R stays at its value R^0 from the chunk's start and the current residual is
                              R^0 - sum_j U'_j v_j^T (U'_j = c_j A A_{i_j}^T, v_j = w_j B of iteration j);
                              an iteration reads R^0 once (R^0_i . v), the row norms follow by

@@ -2027,10 +2027,13 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
     ALLOC(c->hist_rows, (size_t)c->chunk_cap * 4);
     ALLOC(c->hist_c, (size_t)c->chunk_cap * 8);
     ALLOC(c->hist_w, (size_t)c->chunk_cap * q * 8);
-    // the deferred update: FP32, chunks of at most kDeferCap iterations, at most kSrCap rows per CTA
+    // the deferred update: FP32, chunks of at most kDeferCap iterations, at most kSrCap rows per CTA; by default
+    // only in the full form (in the row-space form the assembly barrier and the Gram column cost about what the
+    // halved pass over Z saves)
     c->defer = 0;
     c->defer_stage = 0;
-    if (c->prec == GRBK_F32 && o.deferred >= 0 && c->chunk_cap <= kDeferCap && (m + c->G - 1) / c->G <= kSrCap) {
+    const bool want_defer = o.deferred > 0 || (o.deferred == 0 && c->form == GRBK_FORM_FULL);
+    if (c->prec == GRBK_F32 && want_defer && c->chunk_cap <= kDeferCap && (m + c->G - 1) / c->G <= kSrCap) {
         ALLOC(c->uh, (size_t)c->chunk_cap * m * 4);
         ALLOC(c->vh, (size_t)c->chunk_cap * c->ldr * 4);
         ALLOC(c->gp, (size_t)(c->chunk_cap + 1) * c->G * sizeof(float2));
