@@ -789,7 +789,8 @@ __device__ __noinline__ long long pick_row(const IterParams<T>& P, int G, long l
 // ----------------------------------------------------------------------------
 // the persistent iteration kernel
 // ----------------------------------------------------------------------------
-template <typename T>
+// DEFER: the deferred update (FP32 only); the in-place instantiation carries none of its code.
+template <typename T, bool DEFER = false>
 __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -806,11 +807,12 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
     // and the per-row corrections (four partial sums per row)
     __shared__ float s_uik[kDeferCap];
     __shared__ float2 s_gf[kDeferCap + 1];
-    __shared__ float2 s_corr[4 * kSrCap];
 
     T* sv = reinterpret_cast<T*>(dsm);                               // ldr: R_{i_k}, then v
     T* sa = sv + (P.smem_v ? P.ldr : 0);                              // lda: A_{i_k}
     T* sw = sa + (P.smem_arow ? P.lda : 0);                           // q: w
+    // deferred update only: the per-row corrections, four partial sums per row (4 kSrCap pairs)
+    float2* s_corr = reinterpret_cast<float2*>(sw + ((P.q + VecOf<T>::N - 1) / VecOf<T>::N) * VecOf<T>::N);
 
     const int G = gridDim.x, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -942,8 +944,8 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
         T* ucur = P.u;
         T* vcur = P.v;
         const T* Rik = P.R + ik * P.ldr;
-        if constexpr (sizeof(T) == 4) {
-            if (P.defer) {
+        if constexpr (DEFER) {
+            {
                 ucur = P.uh + (int64_t)it * P.m;
                 vcur = P.vh + (int64_t)it * P.ldr;
                 if (it > 0) {
@@ -1013,8 +1015,8 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             __syncthreads();
             cols_gemv<T>(P.B, P.ldb, P.q, sw, vcur, c, G, sm_parts);
         }
-        if constexpr (sizeof(T) == 4) {
-            if (P.defer) {
+        if constexpr (DEFER) {
+            {
                 defer_gram_partial<T>(P, it, c, G);
             }
         }
@@ -1025,9 +1027,7 @@ __global__ void __launch_bounds__(kBlock) iterate_kernel(IterParams<T> P)
             for (int64_t e = threadIdx.x; e < P.ldr / VN; e += kBlock)
                 reinterpret_cast<V*>(sv)[e] = ldcg_v(reinterpret_cast<const V*>(vcur) + e);
         }
-        bool deferred = false;
-        if constexpr (sizeof(T) == 4) deferred = P.defer != 0;
-        if (deferred) {
+        if constexpr (DEFER) {
             defer_gram_column<T>(P, it, G, s_gf);
             __syncthreads();
             const double gkk = (double)s_gf[it].x + (double)s_gf[it].y;
@@ -1715,14 +1715,14 @@ static grbk_status sumsq_nonfinite(grbk_ctx* c, const void* M, int64_t rows, int
 template <typename T>
 static grbk_status setup_launch_shape(grbk_ctx* c)
 {
-    int dev = 0;
+    int dev = 0, optin = 0, nsm = 0;
     GRBK_CK(cudaGetDevice(&dev));
-    cudaDeviceProp prop;
-    GRBK_CK(cudaGetDeviceProperties(&prop, dev));
+    GRBK_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    GRBK_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const size_t esz = sizeof(T);
     cudaFuncAttributes fa;
     GRBK_CK(cudaFuncGetAttributes(&fa, iterate_kernel<T>));
-    const size_t budget = (size_t)prop.sharedMemPerBlockOptin - fa.sharedSizeBytes - 1024;
+    const size_t budget = (size_t)optin - fa.sharedSizeBytes - 1024;
     size_t need = (size_t)c->q * esz;
     c->smem_arow = 0;
     c->smem_v = 0;
@@ -1737,11 +1737,11 @@ static grbk_status setup_launch_shape(grbk_ctx* c)
     int per_sm = 0;
     GRBK_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, iterate_kernel<T>, kBlock, need));
     if (per_sm < 1) return GRBK_EINVAL;
-    int G = prop.multiProcessorCount * min(per_sm, 1);
+    int G = nsm * min(per_sm, 1);
     // small systems: fewer CTAs keep the barriers cheap (about 4K elements of R per CTA)
     const int64_t want = std::max<int64_t>(1, (c->m * c->ldr) / 4096);
     if (want < G) G = (int)want;
-    if (c->opts.grid_ctas > 0) G = min(c->opts.grid_ctas, prop.multiProcessorCount * per_sm);
+    if (c->opts.grid_ctas > 0) G = min(c->opts.grid_ctas, nsm * per_sm);
     if (G > c->m) G = (int)std::max<int64_t>(1, c->m);
     G = min(G, kMaxGrid);  // the pick holds up to 32 kPartRegs CTA partials in registers
     c->G = G;
@@ -2045,9 +2045,28 @@ extern "C" grbk_status grbk_create(grbk_ctx** out, const grbk_mat* A, const grbk
             grbk_destroy(c);
             return GRBK_ECUDA;
         }
-        c->defer = 1;
         const int64_t nvr = c->ldr / 4, slab = (nvr + c->G - 1) / c->G;
         c->defer_stage = (size_t)c->chunk_cap * slab * 16 <= c->dyn_smem;
+        // the per-row corrections after the row, A_ik and w buffers in the dynamic shared memory
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        const size_t need = (size_t)(c->ldr + (c->smem_arow ? c->lda : 0) + (q + 3) / 4 * 4) * 4 +
+                            (size_t)4 * kSrCap * sizeof(float2);
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, iterate_kernel<float, true>) != cudaSuccess) {
+            grbk_destroy(c);
+            return GRBK_ECUDA;
+        }
+        if (c->smem_v && need + fa.sharedSizeBytes + 1024 <= (size_t)optin) {
+            if (cudaFuncSetAttribute(iterate_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)need) != cudaSuccess) {
+                grbk_destroy(c);
+                return GRBK_ECUDA;
+            }
+            c->dyn_smem = std::max(c->dyn_smem, need);
+            c->defer = 1;
+        }
     }
     if (c->K) {
         if (c->smem_v) {
@@ -2112,7 +2131,8 @@ static grbk_status launch_chunk(grbk_ctx* c, int variant, double theta, uint64_t
         P.variant = variant; P.theta = theta; P.seed = seed; P.sys = 0; P.k0 = k0; P.nit = nit;
         P.stop_S = stop_S; P.trace_rows = d_trace_rows; P.trace_S = d_trace_S; P.trace_len = trace_len;
         args[0] = &P;
-        GRBK_CK(cudaLaunchCooperativeKernel((const void*)iterate_kernel<float>, dim3(c->G), dim3(kBlock),
+        GRBK_CK(cudaLaunchCooperativeKernel(c->defer ? (const void*)iterate_kernel<float, true>
+                                                     : (const void*)iterate_kernel<float>, dim3(c->G), dim3(kBlock),
                                             args, c->dyn_smem, c->stream));
     }
     return GRBK_OK;
