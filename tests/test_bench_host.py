@@ -24,6 +24,19 @@ def test_algorithmic_bytes_of_one_iteration():
     assert bench.iter_bytes(m, p, q, n, 8, gram=True) - 3 * m * 8 == 2 * (full - 3 * m * 8)
 
 
+def test_algorithmic_bytes_of_the_deferred_update():
+    """Deferred update, same system, chunks of T = 64: R read once (mn, no store),
+    plus on average (T - 1) / 2 of the chunk's kept U' columns (m) and v rows (n)
+    per iteration -- 1.93 GB per iteration, 123.25 GB per launch, the figure the
+    bench line divides by the launch time."""
+    m, p, q, n = 20000, 2000, 2000, 20000
+    full = bench.iter_bytes(m, p, q, n, 4, gram=True)
+    dfr = bench.iter_bytes(m, p, q, n, 4, gram=True, deferred=True, T=64)
+    assert dfr == full - m * n * 4 + 31.5 * (m + n) * 4
+    assert round(dfr / 1e9, 2) == 1.93
+    assert round(dfr * 64 / 1e9, 2) == 123.25
+
+
 def test_clock_record_summary():
     c = bench.ClockSampler(0)
     c.lines = [
